@@ -1,0 +1,189 @@
+"""CPU oracle of the per-sector TPC tracker (test infrastructure only).
+
+Only tests/, the package smoke check and the CPU-baseline leg of the
+benchmark load this module.  The CUDA path never imports it, and it imports
+nothing from the CUDA path.  See tpc_oracle.c for what each function follows
+and what pins it.
+
+Two builds of the same C source:
+  mode="f64"  FP64 accuracy reference
+  mode="f32"  FP32_EXACT: the same expressions in binary32, no FMA contraction
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "tpc_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIBS = {}
+
+N_TL_F = 16  # x y z s t q cy[6] cz[3] chi2
+
+
+class Params(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("k_win", "d_max2", "n_sigma", "w_min", "w_max",
+                                          "s_max", "y_margin", "sigma_y", "sigma_z", "var_s",
+                                          "var_q", "var_t")] + \
+               [(n, C.c_int) for n in ("g_max", "l_seed", "n_min_tracklet", "n_min_track",
+                                       "own_num", "own_den")]
+
+
+class Geom(C.Structure):
+    _fields_ = [("n_rows", C.c_int), ("n_sectors", C.c_int), ("row_x", C.POINTER(C.c_float)),
+                ("tan_half_open", C.c_float), ("z_max", C.c_float)]
+
+
+def _lib_path(mode):
+    return os.path.join(_BUILD, f"liboracle_{mode}.so")
+
+
+def build(force=False):
+    """Compile both oracle modes with gcc (-ffp-contract=off, no fast math)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    for mode, real in (("f64", "double"), ("f32", "float")):
+        out = _lib_path(mode)
+        if not force and os.path.exists(out) and os.path.getmtime(out) >= os.path.getmtime(_SRC):
+            continue
+        base = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+                "-shared", f"-DORACLE_REAL={real}", _SRC, "-o", out + ".tmp", "-lm"]
+        try:
+            subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True, capture_output=True)
+        except subprocess.CalledProcessError:
+            subprocess.run(base, check=True)
+        os.replace(out + ".tmp", out)
+
+
+def lib(mode="f64"):
+    if mode not in _LIBS:
+        build()
+        L = C.CDLL(_lib_path(mode))
+        P, V = C.POINTER, C.c_void_p
+        L.orc_params_default.argtypes = [P(Params)]
+        L.orc_run.restype = V
+        L.orc_run.argtypes = [P(Params), P(Geom), C.c_double, C.c_int, V, V, C.c_int]
+        L.orc_sizes.argtypes = [V, P(C.c_int64), P(C.c_double)]
+        L.orc_copy_links.argtypes = [V, V, V, V, V]
+        L.orc_copy_tracklets.argtypes = [V, V, V, V, V, V, V, V]
+        L.orc_copy_tracks.argtypes = [V, V, V, V, V]
+        L.orc_free.argtypes = [V]
+        L.orc_propagate.argtypes = [P(Params), C.c_double, V, C.c_double]
+        L.orc_update_state.argtypes = [P(Params), V, C.c_double, C.c_double, P(C.c_double)]
+        L.orc_fit_hits.argtypes = [P(Params), C.c_double, V, C.c_int, V, V, V, P(C.c_double)]
+        L.orc_max_threads.restype = C.c_int
+        L.orc_real_size.restype = C.c_int
+        _LIBS[mode] = L
+    return _LIBS[mode]
+
+
+def default_params(**over) -> Params:
+    p = Params()
+    lib("f64").orc_params_default(C.byref(p))
+    for k, v in over.items():
+        setattr(p, k, v)
+    return p
+
+
+def _ptr(a):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def geometry(row_x, n_sectors=36, tan_half_open=None, z_max=250.0):
+    import math
+    xr = np.ascontiguousarray(row_x, dtype=np.float32)
+    g = Geom()
+    g.n_rows = len(xr)
+    g.n_sectors = n_sectors
+    g.row_x = xr.ctypes.data_as(C.POINTER(C.c_float))
+    g.tan_half_open = math.tan(math.radians(10.0)) if tan_half_open is None else tan_half_open
+    g.z_max = z_max
+    g._keep = xr
+    return g
+
+
+def run(clusters, row_counts, n_events, bz, row_x, params=None, mode="f64", threads=0,
+        n_sectors=36):
+    """Track a batch of events; returns a dict of numpy arrays.
+
+    clusters   float32 [N, 4] (x, y, z, id bits), grouped by (event, sector, row)
+    row_counts int32 [n_events * n_sectors * n_rows]
+    Output indices are global cluster indices (positions in `clusters`);
+    tracklets and tracks are in canonical order (event, sector, row, id)."""
+    L = lib(mode)
+    p = params if params is not None else default_params()
+    g = geometry(row_x, n_sectors=n_sectors)
+    cl = np.ascontiguousarray(clusters, dtype=np.float32)
+    rc = np.ascontiguousarray(row_counts, dtype=np.int32)
+    assert cl.ndim == 2 and cl.shape[1] == 4
+    assert rc.size == n_events * n_sectors * g.n_rows and int(rc.sum()) == len(cl)
+    res = L.orc_run(C.byref(p), C.byref(g), float(bz), int(n_events), _ptr(cl), _ptr(rc), int(threads))
+    try:
+        sz = (C.c_int64 * 5)()
+        secs = C.c_double()
+        L.orc_sizes(res, sz, C.byref(secs))
+        N, T, TH, M, MH = [int(v) for v in sz]
+        out = dict(seconds=secs.value)
+        for k in ("up_raw", "dn_raw", "up", "dn"):
+            out[k] = np.empty(N, np.int32)
+        L.orc_copy_links(res, _ptr(out["up_raw"]), _ptr(out["dn_raw"]), _ptr(out["up"]),
+                         _ptr(out["dn"]))
+        out["start"] = np.empty(T, np.int32)
+        out["tl_unit"] = np.empty(T, np.int32)
+        out["tl_f"] = np.empty((T, N_TL_F), np.float64)
+        out["tl_n"] = np.empty(T, np.int32)
+        out["tl_alive"] = np.empty(T, np.int32)
+        out["tl_hit_off"] = np.empty(T + 1, np.int64)
+        out["tl_hits"] = np.empty(TH, np.int32)
+        L.orc_copy_tracklets(res, _ptr(out["start"]), _ptr(out["tl_unit"]), _ptr(out["tl_f"]),
+                             _ptr(out["tl_n"]), _ptr(out["tl_alive"]), _ptr(out["tl_hit_off"]),
+                             _ptr(out["tl_hits"]))
+        out["trk_t"] = np.empty(M, np.int32)
+        out["trk_n"] = np.empty(M, np.int32)
+        out["trk_hit_off"] = np.empty(M + 1, np.int64)
+        out["trk_hits"] = np.empty(MH, np.int32)
+        L.orc_copy_tracks(res, _ptr(out["trk_t"]), _ptr(out["trk_n"]), _ptr(out["trk_hit_off"]),
+                          _ptr(out["trk_hits"]))
+        return out
+    finally:
+        L.orc_free(res)
+
+
+# single-function access for the pin tests ---------------------------------
+
+def state_vec(x, y, z, s, t, q, cy=(0, 0, 0, 0, 0, 0), cz=(0, 0, 0)):
+    return np.array([x, y, z, s, t, q, *cy, *cz], dtype=np.float64)
+
+
+def propagate(v, x1, bz, params=None, mode="f64"):
+    v = np.array(v, dtype=np.float64)
+    p = params if params is not None else default_params()
+    ok = lib(mode).orc_propagate(C.byref(p), float(bz), _ptr(v), float(x1))
+    return bool(ok), v
+
+
+def update(v, my, mz, params=None, mode="f64", chi2=0.0):
+    v = np.array(v, dtype=np.float64)
+    p = params if params is not None else default_params()
+    c = C.c_double(chi2)
+    lib(mode).orc_update_state(C.byref(p), _ptr(v), float(my), float(mz), C.byref(c))
+    return v, c.value
+
+
+def fit_hits(v, x, y, z, bz, params=None, mode="f64"):
+    v = np.array(v, dtype=np.float64)
+    x = np.ascontiguousarray(x, np.float64)
+    y = np.ascontiguousarray(y, np.float64)
+    z = np.ascontiguousarray(z, np.float64)
+    p = params if params is not None else default_params()
+    c = C.c_double(0.0)
+    n = lib(mode).orc_fit_hits(C.byref(p), float(bz), _ptr(v), len(x), _ptr(x), _ptr(y), _ptr(z),
+                               C.byref(c))
+    return n, v, c.value
+
+
+def max_threads():
+    return int(lib("f64").orc_max_threads())
