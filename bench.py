@@ -1,0 +1,355 @@
+"""Benchmark: TPC clusters/s tracked on central Pb-Pb-like events (GB300).
+
+One step = the whole Phase-I hot path (grid build, CA neighbours, cleaning,
+start hits, tracklet construction, selection, output) over one batch of
+synthetic central Pb-Pb events (10,000 primaries + 3,000 secondaries, 10 %
+noise, ~2.05 M clusters each), all 36 sectors of every event in one batched,
+graph-replayed launch sequence.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--batch B] [--impl ours|reference]
+
+value      clusters/s, inputs resident in device memory when the timed region
+           starts; the batch (B x 33 MB of clusters) exceeds the 129 MB L2
+e2e        the same metric through the C ABI with pinned HOST buffers: H2D of
+           the clusters and row counts and D2H of the tracks inside the timed
+           region
+roofline   the dominant kernel (tracklet constructor) against the measured HBM
+           copy bandwidth
+cpu_baseline  the FP64 CPU oracle on the host cores, bounded sample
+--impl reference  times the CPU oracle as the reference arm (same metric)
+
+Multi-GPU: events shard across ranks with no collective (weak scaling), one
+process per GPU under torchrun.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "TPC clusters/s tracked (central Pb-Pb-like); p50/p99 event latency, stream"
+WORKLOAD = "central Pb-Pb-like events: 10,000 primaries (pT exp mean 0.5 GeV/c, |eta|<0.9) + " \
+           "3,000 secondaries + 10% noise, 36 sectors x 159 pad rows, Bz=0.5 T"
+
+
+def _gen_event(seed):
+    from paper_1712_09430_gb300 import synth
+    ev = synth.central_event(seed=seed)
+    return ev.clusters, ev.row_counts
+
+
+def make_batch(seeds):
+    # spawn: the pool starts before any CUDA use in this process
+    with mp.get_context("spawn").Pool(min(len(seeds), max(1, os.cpu_count() or 1), 16)) as pool:
+        parts = pool.map(_gen_event, seeds)
+    cl = np.ascontiguousarray(np.concatenate([p[0] for p in parts]))
+    rc = np.ascontiguousarray(np.concatenate([p[1] for p in parts]))
+    return cl, rc
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                smax.append(float(f[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(seconds_target=15.0, ev=None):
+    """The FP64 oracle, as it stands, on all host cores over whole central
+    events (OpenMP over (event, sector) units) until ~seconds_target."""
+    import oracle
+    from paper_1712_09430_gb300 import synth
+    if ev is None:
+        ev = synth.central_event(seed=3)
+    cores = os.cpu_count() or 1
+    done, t0 = 0, time.perf_counter()
+    n_ev = 0
+    while True:
+        oracle.run(ev.clusters, ev.row_counts, 1, ev.bz, synth.row_x(), mode="f64", threads=cores)
+        done += ev.n
+        n_ev += 1
+        if time.perf_counter() - t0 > seconds_target:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": done / dt, "unit": "clusters/s", "cores": cores, "kind": "oracle",
+            "sample": f"{n_ev} x one central Pb-Pb event ({ev.n} clusters), FP64 oracle, "
+                      f"OpenMP over the 36 sectors, {dt:.1f} s wall"}
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle, timed on the host cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    from paper_1712_09430_gb300 import synth
+    ev = synth.central_event(seed=3)
+    cores = os.cpu_count() or 1
+    for _ in range(max(0, args.warmup)):
+        oracle.run(ev.clusters, ev.row_counts, 1, ev.bz, synth.row_x(), mode="f64", threads=cores)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.run(ev.clusters, ev.row_counts, 1, ev.bz, synth.row_x(), mode="f64", threads=cores)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    value = ev.n * args.steps / tot
+    line = {"metric": METRIC, "value": value, "unit": "clusters/s", "impl": "reference",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD + "; one event per step on the host cores",
+                       "events_per_step": 1, "clusters_per_step": int(ev.n)},
+            "cpu_baseline": {"value": value, "unit": "clusters/s", "cores": cores, "kind": "oracle",
+                             "sample": f"one central event per step, {args.steps} steps"},
+            "e2e": {"value": value, "unit": "clusters/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# Launches of our kernels per batched step: plan, grid, neighbours, clean,
+# start scan, start write, tracklets, owner, accept, scan tiles, scan top, emit.
+LAUNCHES_PER_STEP = 12
+
+
+def run_ours(args):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    seeds = [3 + rank * args.batch + i for i in range(args.batch)]
+    cl_np, rc_np = make_batch(seeds)           # before any CUDA use (spawned pool)
+    import torch
+    import ctypes as C
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from paper_1712_09430_gb300 import capi, synth
+    from paper_1712_09430_gb300.tracker import Tracker, TRACK_DTYPE
+    L = capi.lib()
+    B = args.batch
+    N = len(cl_np)
+    tr = Tracker(synth.row_x(), bz=0.5, use_graph=1, exact_fp32=1 if args.exact else 0,
+                 bin_target=args.bin_target, threads_per_row=args.threads_per_row,
+                 tracklets_per_warp=args.tracklets_per_warp)
+    stream = torch.cuda.Stream()
+    sp = C.c_void_p(stream.cuda_stream)
+    dev_cl = torch.from_numpy(cl_np).to(f"cuda:{local}")
+    cap_t, cap_h = N // 10 + 1024, N
+    out_tr = torch.empty(cap_t * TRACK_DTYPE.itemsize, dtype=torch.uint8, device=dev_cl.device)
+    out_h = torch.empty(cap_h, dtype=torch.int32, device=dev_cl.device)
+    out = capi.tpc_output(out_tr.data_ptr(), out_h.data_ptr(), cap_t, cap_h, capi.TPC_MEM_DEVICE, 0, 0)
+    rc_ptr = rc_np.ctypes.data_as(C.c_void_p)
+
+    def step():
+        r = L.tpc_track_sectors(tr.h, C.c_void_p(dev_cl.data_ptr()), rc_ptr, B,
+                                capi.TPC_MEM_DEVICE, C.byref(out), sp)
+        if r != capi.TPC_OK:
+            raise RuntimeError(f"tpc_track_sectors: {capi.STATUS_NAMES.get(r)}: {tr.error()}")
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev_s = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev_e = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    stage = np.zeros(6)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        ev_s[i].record(stream)
+        step()
+        ev_e[i].record(stream)
+        stage += np.array(tr.stage_times())
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    if dist:
+        dist.barrier()
+    ck = clocks.stop()
+    ms = sum(s.elapsed_time(e) for s, e in zip(ev_s, ev_e)) / args.steps
+    stage /= args.steps
+    if dist:
+        t = torch.tensor([ms], device=dev_cl.device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    M, MH = out.n_tracks, out.n_hits
+    T = len(tr.dump(capi.TPC_DUMP_STARTS)) if rank == 0 else 0
+    value = N * world / (ms * 1e-3)
+
+    # ---- end to end through the C ABI with pinned host buffers
+    pin_cl = torch.from_numpy(cl_np).pin_memory()
+    host_tr = torch.empty(cap_t * TRACK_DTYPE.itemsize, dtype=torch.uint8).pin_memory()
+    host_h = torch.empty(cap_h, dtype=torch.int32).pin_memory()
+    hout = capi.tpc_output(host_tr.data_ptr(), host_h.data_ptr(), cap_t, cap_h, capi.TPC_MEM_HOST, 0, 0)
+
+    def step_e2e():
+        r = L.tpc_track_sectors(tr.h, C.c_void_p(pin_cl.data_ptr()), rc_ptr, B, capi.TPC_MEM_HOST,
+                                C.byref(hout), sp)
+        if r != capi.TPC_OK:
+            raise RuntimeError(f"tpc_track_sectors (host): {tr.error()}")
+
+    for _ in range(2):
+        step_e2e()
+    torch.cuda.synchronize()
+    k2 = max(3, args.steps // 2)
+    t1 = time.perf_counter()
+    for _ in range(k2):
+        step_e2e()
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t1) / k2
+    h2d = N * 16 + len(rc_np) * 4
+    d2h = hout.n_tracks * TRACK_DTYPE.itemsize + hout.n_hits * 4 + 64
+    e2e = {"value": N * world / e2e_s, "unit": "clusters/s", "h2d_bytes_per_step": int(h2d),
+           "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_s * 1e3}
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    # ---- roofline of the dominant kernel (tracklet construction)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    names = ["grid", "neighbours", "clean+starts", "tracklets", "select+emit"]
+    stage_ms = {n: float(v) for n, v in zip(names, stage[:5])}
+    dom = max(stage_ms, key=stage_ms.get)
+    algo = algorithmic_bytes(tr, N, T) if dom == "tracklets" else None
+    rl = None
+    if algo is not None:
+        achieved = algo["bytes"] / (stage_ms[dom] * 1e-3) / 1e9
+        rl = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+              "frac": achieved / hbm, "traffic": None, "kernel": "k_tracklets_sched",
+              "algorithmic_bytes_per_launch": algo["bytes"], "model": algo["model"],
+              "counts": {k: v for k, v in algo.items() if k not in ("bytes", "model")},
+              "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy) of measured" if peaks else "fallback"}
+    cpu = None if args.no_cpu_baseline else cpu_baseline(args.cpu_seconds)
+    line = {"metric": METRIC, "value": value, "unit": "clusters/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "events_per_step": B, "events_per_rank": B,
+                       "clusters_per_step": int(N) * world, "tracks_per_step": int(M),
+                       "tracklets_per_step": int(T), "mode": "exact" if args.exact else "production",
+                       "launch": "batched, CUDA graph replay", "bin_target": args.bin_target,
+                       "threads_per_row": args.threads_per_row,
+                       "tracklets_per_warp": args.tracklets_per_warp,
+                       "l2": f"inputs larger than L2 ({N * 16 / 1e6:.0f} MB of clusters per step)",
+                       "parallelism": f"events sharded over {world} GPU(s), no collective"},
+            "events_per_s": B * world / (ms * 1e-3),
+            "stage_ms": stage_ms, "wall_s": wall,
+            "gpu_launches": LAUNCHES_PER_STEP * args.steps,
+            "clocks": ck, "e2e": e2e, "roofline": rl, "cpu_baseline": cpu}
+    print(json.dumps(line), flush=True)
+    tr.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def algorithmic_bytes(tr, N, T):
+    """Bytes the tracklet constructor moves by its own stage structure,
+    counted exactly per tracklet by the kernel (TPC_DUMP_TRACKLET_WORK):
+    per row step the row grid (32 B), per bin-table row read two offsets
+    (8 B), per candidate cluster examined 16 B, per seed-chain hit 16 B of
+    cluster + 4 B of link, per Phase-2 cluster a 4 B write, and per tracklet
+    the schedule/start/row entries (12 B) and 68 B of state out."""
+    from paper_1712_09430_gb300 import capi
+    w = tr.dump(capi.TPC_DUMP_TRACKLET_WORK).astype(np.int64)
+    n_hits = int(tr.dump(capi.TPC_DUMP_TRACKLET_N)[0].astype(np.int64).sum())
+    steps, binrows, cand, chain = (int(v) for v in w.sum(axis=1))
+    b = 32 * steps + 8 * binrows + 16 * cand + 20 * chain + 4 * n_hits + T * (12 + 68)
+    return {"bytes": float(b), "row_steps": steps, "bin_rows": binrows, "candidates": cand,
+            "chain_hits": chain, "tracklet_hits": n_hits,
+            "model": "32*row_steps + 8*bin_rows + 16*candidates + 20*chain_hits + 4*hits + 80*T"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--batch", type=int, default=8, help="central events per step (per GPU)")
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--exact", action="store_true", help="time the -fmad=false build")
+    ap.add_argument("--bin-target", type=float, default=1.0)
+    ap.add_argument("--threads-per-row", type=int, default=128)
+    ap.add_argument("--tracklets-per-warp", type=int, default=32)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

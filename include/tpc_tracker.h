@@ -1,0 +1,239 @@
+/*
+ * tpc_tracker.h -- C ABI of the GB300 TPC sector tracker.
+ *
+ * The tracker is Phase I of the ALICE HLT TPC reconstruction (Sec. 2 of
+ * "GPU-accelerated track reconstruction in the ALICE High Level Trigger"):
+ *   1. Seeding by a Cellular Automaton: neighbour links between clusters on
+ *      adjacent pad rows, link cleaning, start hits (Sec. 2 step 1, Table 1
+ *      row 1, Fig. 1 c);
+ *   2. Track following with a simplified Kalman filter (uncorrelated y/z
+ *      errors, constant field), then selection of the best instance among
+ *      tracklets that share clusters (Sec. 2 step 2, Table 1 row 2, Fig. 1 d).
+ * Sectors of one event and different events are independent (Sec. 3.1,
+ * Sec. 3.2); all (event, sector) units of one call run in one batched set of
+ * kernel launches on one GPU.
+ *
+ * Conventions
+ *   Units: cm, GeV/c, T.  Sector s of an event is side A (z >= 0) when
+ *   s < n_sectors / 2, else side C.  Sector frame: x along the pad-row
+ *   normal, y along the row, z along the beam.  Pad rows are the planes
+ *   x = row_x[r].
+ *   Every function returns an int status: TPC_OK (0), a positive
+ *   informational code, or a negative error.  On error the tracker stays
+ *   usable; tpc_last_error() gives a one-line reason.
+ *   One tracker per host thread; calls on one tracker are not reentrant.
+ *   The library owns all device memory it uses and frees it in
+ *   tpc_tracker_destroy().
+ */
+#ifndef TPC_TRACKER_H
+#define TPC_TRACKER_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define TPC_OK 0
+#define TPC_PENDING 1            /* tpc_stream_poll: the result is not ready     */
+#define TPC_BUSY 2               /* tpc_stream_submit: not admitted now, retry   */
+#define TPC_ERR_INVALID (-1)     /* bad argument or input (NULL, counts, NaN, x) */
+#define TPC_ERR_NOMEM (-2)       /* device or pinned memory exhausted            */
+#define TPC_ERR_OUTPUT_TRUNCATED (-3) /* output filled to capacity; n_tracks and
+                                        n_hits hold the REQUIRED sizes          */
+#define TPC_ERR_TIMEOUT (-4)     /* a bounded wait ran out                       */
+#define TPC_ERR_DEVICE (-5)      /* CUDA error                                   */
+#define TPC_ERR_CANCELLED (-6)   /* ticket dropped (tracker destroyed/reset)     */
+#define TPC_ERR_UNKNOWN_TICKET (-7)
+
+/* ---- memory kinds ------------------------------------------------------ */
+#define TPC_MEM_HOST 0           /* host memory (pinned or pageable)             */
+#define TPC_MEM_DEVICE 1         /* device memory of the current CUDA device     */
+
+/* ---- limits ------------------------------------------------------------ */
+#define TPC_MAX_ROWS 256         /* pad rows per sector                          */
+#define TPC_MAX_ROW_CLUSTERS 4096 /* clusters in one (event, sector, row)        */
+
+/* One cluster (hit): a 2-D pad/time measurement on a pad row, already
+ * transformed to x, y, z (Sec. 2, Fig. 1 caption; Fig. 5 caption).  16 bytes
+ * so that rows load as float4.  x must equal row_x of its row within 1e-3 cm.
+ * id is a caller label, unique within its (event, sector, row); ties between
+ * equally good candidates are broken by the smaller id, so results do not
+ * depend on the order of clusters inside a row. */
+typedef struct {
+    float x, y, z;
+    uint32_t id;
+} tpc_cluster;
+
+/* Detector geometry (Sec. 2, Fig. 1 a,b): n_sectors per event (two halves),
+ * n_rows pad-row planes per sector. */
+typedef struct {
+    int n_rows;              /* 3 .. TPC_MAX_ROWS (ALICE TPC: 159)              */
+    int n_sectors;           /* even, >= 2 (ALICE TPC: 36)                      */
+    const float* row_x;      /* host, [n_rows], strictly increasing, > 0;
+                                copied by tpc_tracker_create                   */
+    float tan_half_open;     /* tan of the sector half-opening (tan 10 deg)     */
+    float z_max;             /* drift length, |z| <= z_max (250 cm)             */
+} tpc_geometry;
+
+/* Method constants.  The paper fixes none of them; the defaults are the
+ * readings the oracle uses (tpc_params_default).  Fields below "execution"
+ * change speed only: results are identical for every value. */
+typedef struct {
+    /* CA seeding */
+    float k_win;             /* link window half-width per cm of row distance  */
+    float d_max2;            /* cut on the collinearity residual D (cm^2)       */
+    int l_seed;              /* minimum chain length of a seed (3 clusters)     */
+    /* track following: simplified Kalman filter */
+    float sigma_y, sigma_z;  /* cluster errors (cm)                             */
+    float var_s, var_q, var_t; /* initial variances of sin(phi), q/pT, tan(l)   */
+    float n_sigma;           /* search window in units of sqrt(S)              */
+    float w_min, w_max;      /* search window clamp (cm)                        */
+    float s_max;             /* stop when |sin(phi)| exceeds this               */
+    float y_margin;          /* stop when |y| > x tan(half open) + y_margin     */
+    int g_max;               /* stop after more than g_max consecutive misses   */
+    int n_min_tracklet;      /* shorter tracklets are dropped                   */
+    /* selection */
+    int n_min_track;         /* accepted: owned >= n_min_track and              */
+    int own_num, own_den;    /*   owned * own_den >= own_num * nhits            */
+    /* execution */
+    int exact_fp32;          /* 1: filter and link arithmetic without fused
+                                multiply-add (bit-exact against the FP32
+                                oracle); 0: production build (FMA allowed)      */
+    float bin_target;        /* mean clusters per search-grid bin (> 0)         */
+    int threads_per_row;     /* 32, 64, 128 or 256: CTA size of the row kernels */
+    int tracklets_per_warp;  /* 1, 2, 4, 8, 16 or 32: lanes per tracklet =
+                                32 / tracklets_per_warp                         */
+    int plain_per_sector;    /* 1: one launch per (event, sector) per stage
+                                (the Run 1/2 scheduling of Sec. 3); 0: all
+                                units in one launch per stage                   */
+    int use_graph;           /* 1: replay the batched stages as a CUDA graph    */
+} tpc_params;
+
+/* A selected track: the best tracklet instance (Sec. 2 step 2), with the
+ * Phase-2 filter state at its innermost cluster. */
+typedef struct {
+    int32_t event, sector;   /* unit of the track                               */
+    int32_t tracklet;        /* canonical tracklet id (event, sector, row, id)  */
+    float x;                 /* plane of the innermost cluster                  */
+    float p[5];              /* y, z, sin(phi), tan(lambda), q/pT               */
+    float cov_y[6];          /* (y, sin phi, q/pT): c00 c10 c11 c20 c21 c22     */
+    float cov_z[3];          /* (z, tan lambda):    c00 c10 c11                 */
+    float chi2;
+    int32_t ndf;             /* 2 * (filtered clusters) - 5                     */
+    int32_t nhits;           /* clusters kept after selection                   */
+    int32_t hit_off;         /* first entry of this track in hit_ids            */
+} tpc_track;
+
+/* Output buffers, caller-owned.  mem_kind says where tracks and hit_ids
+ * live.  hit_ids are positions in the call's cluster array, rows ascending
+ * within a track; tracks are in canonical tracklet order. */
+typedef struct {
+    tpc_track* tracks;
+    int32_t* hit_ids;
+    int32_t cap_tracks;
+    int32_t cap_hits;
+    int32_t mem_kind;        /* TPC_MEM_HOST or TPC_MEM_DEVICE                  */
+    int32_t n_tracks;        /* written: tracks found (required capacity)       */
+    int32_t n_hits;          /* written: hit ids found (required capacity)      */
+} tpc_output;
+
+typedef struct tpc_tracker tpc_tracker;
+
+/* Fill p with the default readings (see tpc_params). */
+void tpc_params_default(tpc_params* p);
+
+/* Create a tracker on the current CUDA device for geometry g and field
+ * bz_tesla (constant, Sec. 2 step 2).  params may be NULL (defaults).
+ * Errors: TPC_ERR_INVALID (geometry or params out of range),
+ * TPC_ERR_NOMEM, TPC_ERR_DEVICE (no usable device). */
+int tpc_tracker_create(const tpc_geometry* g, double bz_tesla, const tpc_params* params,
+                       tpc_tracker** out);
+
+/* Destroy; in-flight stream tickets are cancelled.  NULL is a no-op. */
+void tpc_tracker_destroy(tpc_tracker* tr);
+
+/* Change the execution fields of the parameters (exact_fp32, bin_target,
+ * threads_per_row, tracklets_per_warp, plain_per_sector, use_graph) and,
+ * if given, the method constants.  Not allowed while stream tickets are in
+ * flight (TPC_BUSY). */
+int tpc_tracker_set_params(tpc_tracker* tr, const tpc_params* params);
+
+/* Track n_events events (Sec. 2 Phase I), synchronously.
+ *   clusters    [sum(row_counts)] grouped by (event, sector, row); any order
+ *               within a row.  mem_kind: TPC_MEM_HOST or TPC_MEM_DEVICE (device
+ *               pointers must be 16-byte aligned).  The caller may reuse the
+ *               buffer as soon as the call returns.
+ *   row_counts  HOST, [n_events * n_sectors * n_rows] in (event, sector, row)
+ *               order, each in [0, TPC_MAX_ROW_CLUSTERS].
+ *   out         filled as described at tpc_output.  If the result exceeds
+ *               the capacities, the buffers are filled to capacity and
+ *               TPC_ERR_OUTPUT_TRUNCATED is returned with the required sizes
+ *               in n_tracks / n_hits: the estimate-then-fetch-the-rest scheme
+ *               of Sec. 3.1 (re-fetch with tpc_fetch_output, no recompute).
+ *   cuda_stream a cudaStream_t to run on, or NULL for the tracker's own.
+ * Errors: TPC_ERR_INVALID (NULL pointers, negative or oversize counts, NaN
+ * coordinates, x off its row), TPC_ERR_NOMEM, TPC_ERR_DEVICE. */
+int tpc_track_sectors(tpc_tracker* tr, const tpc_cluster* clusters, const int32_t* row_counts,
+                      int n_events, int mem_kind, tpc_output* out, void* cuda_stream);
+
+/* Copy the result of the last tpc_track_sectors call again into out (for
+ * example into larger buffers after TPC_ERR_OUTPUT_TRUNCATED). */
+int tpc_fetch_output(tpc_tracker* tr, tpc_output* out);
+
+/* Serving (Sec. 3.2, continuous batching).  Submit n_events events; the
+ * library copies the input (host memory) before returning.  Events are
+ * admitted while free device memory covers their reservation (input + 3x
+ * internal buffers, Sec. 4.1) and a slot is free, else TPC_BUSY is returned
+ * and nothing is kept.  Admitted events join the next batched replay; up to
+ * two replays are in flight on separate streams.
+ *   ticket  receives an id for tpc_stream_poll. */
+int tpc_stream_submit(tpc_tracker* tr, const tpc_cluster* clusters, const int32_t* row_counts,
+                      int n_events, uint64_t tag, uint64_t* ticket);
+
+/* Poll a ticket, waiting at most timeout_us (0: do not wait).  Returns
+ * TPC_PENDING, TPC_OK (out filled; the ticket is released) or an error
+ * (TPC_ERR_OUTPUT_TRUNCATED keeps the ticket so the caller can poll again
+ * with larger buffers).  Drives the request loop: launches the next batch
+ * when the device has room. */
+int tpc_stream_poll(tpc_tracker* tr, uint64_t ticket, tpc_output* out, int timeout_us);
+
+/* Per-stage results of the last tpc_track_sectors call, for the step-by-step
+ * comparison against a CPU implementation (Sec. 4.1: results of all steps
+ * can be compared individually).  what:
+ *   TPC_DUMP_LINKS_RAW  int32 [2][N]  up, down links before cleaning
+ *   TPC_DUMP_LINKS      int32 [2][N]  after cleaning
+ *   TPC_DUMP_STARTS     int32 [T]     start hits, canonical order
+ *   TPC_DUMP_TRACKLETS  float [T][16] x y z sin tan q/pT cov_y[6] cov_z[3] chi2
+ *   TPC_DUMP_TRACKLET_N int32 [2][T]  filtered cluster count, alive flag
+ *   TPC_DUMP_TRACKLET_HITS int32 [T][n_rows] clusters, rows ascending, -1 pad
+ *   TPC_DUMP_TRACKLET_WORK int32 [4][T]  per tracklet: row steps searched,
+ *                       bin-table rows read, candidate clusters examined, seed
+ *                       chain length (the constructor's memory work)
+ * All indices are positions in the call's cluster array.  dst is host
+ * memory of cap bytes; *n_items receives the element count (N or T).
+ * Returns TPC_ERR_OUTPUT_TRUNCATED if cap is too small (nothing copied). */
+#define TPC_DUMP_LINKS_RAW 0
+#define TPC_DUMP_LINKS 1
+#define TPC_DUMP_STARTS 2
+#define TPC_DUMP_TRACKLETS 3
+#define TPC_DUMP_TRACKLET_N 4
+#define TPC_DUMP_TRACKLET_HITS 5
+#define TPC_DUMP_TRACKLET_WORK 6
+int tpc_debug_dump(tpc_tracker* tr, int what, void* dst, int64_t cap, int64_t* n_items);
+
+/* Device time of each stage of the last call, in milliseconds, measured
+ * with CUDA events on the launching stream: [0] grid build, [1] neighbours,
+ * [2] clean + start hits, [3] tracklet construction, [4] selection + output,
+ * [5] whole call.  n = entries wanted (<= 6). */
+int tpc_stage_times(tpc_tracker* tr, float* ms, int n);
+
+/* One-line description of the last error on tr (or of the last failed
+ * tpc_tracker_create when tr is NULL). */
+const char* tpc_last_error(const tpc_tracker* tr);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TPC_TRACKER_H */

@@ -1,0 +1,467 @@
+// Floating-point kernels of the sector tracker: the CA neighbour finder
+// (Sec. 2 step 1; Table 1 row 1) and the tracklet constructor, a simplified
+// Kalman filter with uncorrelated y/z blocks in a constant field (Sec. 2
+// step 2; Table 1 row 2).
+//
+// This file is compiled twice.  With -fmad=false (namespace tpc_exact) every
+// expression is evaluated in binary32 in the order written, with IEEE
+// division and square root, and no multiply-add is fused, so links, tracklet
+// clusters and selections are bit-identical to a CPU evaluation of the same
+// expressions.  The production build (tpc_fast) lets the compiler fuse.
+#include <cstdint>
+
+#include "tpc_dev.cuh"
+
+#ifndef TPC_FP_NS
+#error "TPC_FP_NS must name the namespace (tpc_exact or tpc_fast)"
+#endif
+
+namespace TPC_FP_NS {
+using namespace tpc;
+
+// --------------------------------------------------------- neighbour finder
+// One CTA per (event, sector, row r), r in [1, n_rows - 2].  Rows r - 1, r,
+// r + 1 are contiguous in the binned array, and so are their bin tables: two
+// bulk copies bring them into shared memory.  One thread per hit of row r
+// (one GPU thread per hit, Sec. 3).
+//
+// For hit i (y_i, z_i) on row r and a target row rho = r +- 1:
+//   R = X_rho / X_r, W = k_win |X_rho - X_r|;
+//   candidate j iff |y_j - y_i R| <= W and |z_j - z_i| <= W.
+// For each pair (u on r + 1, d on r - 1), with tt = (X_r - X_d) / (X_u - X_d):
+//   y_p = y_d + (y_u - y_d) tt, z_p = z_d + (z_u - z_d) tt,
+//   D = (y_i - y_p)^2 + (z_i - z_p)^2, kept if D <= d_max2;
+// the pair with the smallest D wins, ties by smaller id_u, then id_d.
+__global__ void k_neighbours(KConst k, const float* __restrict__ row_x, DevPtrs p, int unit0)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int NR = k.n_rows;
+    const int u = unit0 + blockIdx.x / (NR - 2);
+    const int r = 1 + blockIdx.x % (NR - 2);
+    const int rr = u * NR + r;
+    const int cnt_m = p.row_cnt[rr];
+    if (cnt_m == 0) return;
+    const int off_d = p.row_off[rr - 1], off_m = p.row_off[rr], off_u = p.row_off[rr + 1];
+    const int end_u = p.row_off[rr + 2];
+    const int cnt_d = off_m - off_d, cnt_u = end_u - off_u;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    if (cnt_d == 0 || cnt_u == 0) {
+        for (int i = tid; i < cnt_m; i += nt) {
+            p.up[off_m + i] = -1;
+            p.dn[off_m + i] = -1;
+        }
+        return;
+    }
+    const int bo_d = p.bin_cap_off[rr - 1];
+    const int n_bins3 = p.bin_cap_off[rr + 2] - bo_d;
+    const int total3 = end_u - off_d;
+
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
+    float4* rec = reinterpret_cast<float4*>(smem + 16);
+    int* bins = reinterpret_cast<int*>(rec + total3);
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        fence_async_smem();
+        mbar_expect_tx(bar, (unsigned)total3 * 16u + (unsigned)n_bins3 * 4u);
+        bulk_g2s(rec, p.hits + off_d, (unsigned)total3 * 16u, bar);
+        bulk_g2s(bins, p.bin_off + bo_d, (unsigned)n_bins3 * 4u, bar);
+    }
+    __syncthreads();
+    const RowGrid gu = p.grid[rr + 1], gd = p.grid[rr - 1];
+    const int tu = gu.bin_base - bo_d, td = gd.bin_base - bo_d;  // tables in smem
+    const float Xr = row_x[r], Xu = row_x[r + 1], Xd = row_x[r - 1];
+    const float Ru = Xu / Xr, Rd = Xd / Xr;
+    const float Wu = k.k_win * fabsf(Xu - Xr);
+    const float Wd = k.k_win * fabsf(Xd - Xr);
+    const float tt = (Xr - Xd) / (Xu - Xd);
+    if (!mbar_wait_bounded(bar, 0)) {
+        if (tid == 0) atomicOr(&p.counters[C_ERR], E_TIMEOUT);
+        return;
+    }
+    const float4* recm = rec + cnt_d;
+    for (int i = tid; i < cnt_m; i += nt) {
+        const float4 ci = recm[i];
+        const float yi = ci.x, zi = ci.y;
+        const float ycu = yi * Ru, ycd = yi * Rd;
+        // bin windows (widened by kBinEps; the exact test below decides)
+        const int uy0 = bin_index(ycu - Wu - kBinEps, gu.y0, gu.inv_by, gu.ny);
+        const int uy1 = bin_index(ycu + Wu + kBinEps, gu.y0, gu.inv_by, gu.ny);
+        const int uz0 = bin_index(zi - Wu - kBinEps, gu.z0, gu.inv_bz, gu.nz);
+        const int uz1 = bin_index(zi + Wu + kBinEps, gu.z0, gu.inv_bz, gu.nz);
+        const int dy0 = bin_index(ycd - Wd - kBinEps, gd.y0, gd.inv_by, gd.ny);
+        const int dy1 = bin_index(ycd + Wd + kBinEps, gd.y0, gd.inv_by, gd.ny);
+        const int dz0 = bin_index(zi - Wd - kBinEps, gd.z0, gd.inv_bz, gd.nz);
+        const int dz1 = bin_index(zi + Wd + kBinEps, gd.z0, gd.inv_bz, gd.nz);
+        int bu = -1, bd = -1;
+        unsigned bid_u = 0, bid_d = 0;
+        float bD = 0.0f;
+        for (int bzu = uz0; bzu <= uz1; bzu++) {
+            const int ju0 = bins[tu + bzu * gu.ny + uy0] - off_d;
+            const int ju1 = bins[tu + bzu * gu.ny + uy1 + 1] - off_d;
+            for (int ju = ju0; ju < ju1; ju++) {
+                const float4 cu = rec[ju];
+                if (!(fabsf(cu.x - ycu) <= Wu && fabsf(cu.y - zi) <= Wu)) continue;
+                const unsigned idu = __float_as_uint(cu.z);
+                for (int bzd = dz0; bzd <= dz1; bzd++) {
+                    const int jd0 = bins[td + bzd * gd.ny + dy0] - off_d;
+                    const int jd1 = bins[td + bzd * gd.ny + dy1 + 1] - off_d;
+                    for (int jd = jd0; jd < jd1; jd++) {
+                        const float4 cd = rec[jd];
+                        if (!(fabsf(cd.x - ycd) <= Wd && fabsf(cd.y - zi) <= Wd)) continue;
+                        const float yp = cd.x + (cu.x - cd.x) * tt;
+                        const float zp = cd.y + (cu.y - cd.y) * tt;
+                        const float ey = yi - yp;
+                        const float ez = zi - zp;
+                        const float D = ey * ey + ez * ez;
+                        if (!(D <= k.d_max2)) continue;
+                        const unsigned idd = __float_as_uint(cd.z);
+                        bool better;
+                        if (bu < 0) better = true;
+                        else if (D < bD) better = true;
+                        else if (D > bD) better = false;
+                        else if (idu != bid_u) better = idu < bid_u;
+                        else better = idd < bid_d;
+                        if (better) {
+                            bu = ju;
+                            bd = jd;
+                            bD = D;
+                            bid_u = idu;
+                            bid_d = idd;
+                        }
+                    }
+                }
+            }
+        }
+        p.up[off_m + i] = bu >= 0 ? off_d + bu : -1;
+        p.dn[off_m + i] = bd >= 0 ? off_d + bd : -1;
+    }
+}
+
+// ------------------------------------------------------------ Kalman filter
+// State at the plane x: y, z, s = sin(phi), t = tan(lambda), q = q/pT, with
+// block covariances cy (y, s, q) = c00 c10 c11 c20 c21 c22 and cz (z, t) =
+// c00 c10 c11 (uncorrelated coordinate errors, Sec. 2 step 2).
+struct State {
+    float x, y, z, s, t, q;
+    float cy[6];
+    float cz[3];
+};
+
+// Exact helix step in constant Bz (kB = -kappa Bz, k = kB q):
+//   s1 = s + k d; dy = d (s + s1) / (c + c1); L = sign(d) sqrt(d^2 + dy^2);
+//   u = k L / 2; arc = L (1 + u^2 (1/6 + u^2 3/40)); dz = t arc;
+// covariance transport with dy1/ds = d (1/c^3 + 1/c1^3) / 2,
+// dy1/dq = kB d^2 / (2 c1^3), ds1/dq = kB d, dz1/dt = arc.
+__device__ __forceinline__ bool propagate(State& st, float x1, float kB, float s_max)
+{
+    const float d = x1 - st.x;
+    const float kk = kB * st.q;
+    const float s0 = st.s;
+    const float s1 = s0 + kk * d;
+    if (fabsf(s0) > s_max || fabsf(s1) > s_max) return false;
+    const float c0 = sqrtf(1.0f - s0 * s0);
+    const float c1 = sqrtf(1.0f - s1 * s1);
+    const float dy = d * (s0 + s1) / (c0 + c1);
+    const float L = copysignf(sqrtf(d * d + dy * dy), d);
+    const float u = kk * L * 0.5f;
+    const float u2 = u * u;
+    const float arc = L * (1.0f + u2 * ((float)(1.0 / 6.0) + u2 * (float)(3.0 / 40.0)));
+    const float dz = st.t * arc;
+
+    const float ci3 = 1.0f / (c0 * c0 * c0);
+    const float c1i3 = 1.0f / (c1 * c1 * c1);
+    const float a = d * (ci3 + c1i3) * 0.5f;
+    const float b = kB * d * d * 0.5f * c1i3;
+    const float e = kB * d;
+
+    const float c00 = st.cy[0], c10 = st.cy[1], c11 = st.cy[2];
+    const float c20 = st.cy[3], c21 = st.cy[4], c22 = st.cy[5];
+    const float r00 = c00 + a * c10 + b * c20;
+    const float r01 = c10 + a * c11 + b * c21;
+    const float r02 = c20 + a * c21 + b * c22;
+    const float r10 = c10 + e * c20;
+    const float r11 = c11 + e * c21;
+    const float r12 = c21 + e * c22;
+    st.cy[0] = r00 + a * r01 + b * r02;
+    st.cy[1] = r10 + a * r11 + b * r12;
+    st.cy[2] = r11 + e * r12;
+    st.cy[3] = c20 + a * c21 + b * c22;
+    st.cy[4] = c21 + e * c22;
+    st.cy[5] = c22;
+
+    const float z00 = st.cz[0], z10 = st.cz[1], z11 = st.cz[2];
+    const float q00 = z00 + arc * z10;
+    const float q01 = z10 + arc * z11;
+    st.cz[0] = q00 + arc * q01;
+    st.cz[1] = q01;
+    st.cz[2] = z11;
+
+    st.x = x1;
+    st.y = st.y + dy;
+    st.z = st.z + dz;
+    st.s = s1;
+    return true;
+}
+
+// Measurement update with cluster (my, mz); H picks y (resp. z).
+__device__ __forceinline__ void update(State& st, float my, float mz, float sy2, float sz2, float& chi2)
+{
+    const float S = sy2 + st.cy[0];
+    const float r = my - st.y;
+    const float K0 = st.cy[0] / S, K1 = st.cy[1] / S, K2 = st.cy[3] / S;
+    const float c00 = st.cy[0], c10 = st.cy[1], c11 = st.cy[2];
+    const float c20 = st.cy[3], c21 = st.cy[4], c22 = st.cy[5];
+    st.y = st.y + K0 * r;
+    st.s = st.s + K1 * r;
+    st.q = st.q + K2 * r;
+    st.cy[0] = c00 - K0 * c00;
+    st.cy[1] = c10 - K1 * c00;
+    st.cy[2] = c11 - K1 * c10;
+    st.cy[3] = c20 - K2 * c00;
+    st.cy[4] = c21 - K2 * c10;
+    st.cy[5] = c22 - K2 * c20;
+    const float chi = r * r / S;
+
+    const float Sz = sz2 + st.cz[0];
+    const float rz = mz - st.z;
+    const float L0 = st.cz[0] / Sz, L1 = st.cz[1] / Sz;
+    const float z00 = st.cz[0], z10 = st.cz[1], z11 = st.cz[2];
+    st.z = st.z + L0 * rz;
+    st.t = st.t + L1 * rz;
+    st.cz[0] = z00 - L0 * z00;
+    st.cz[1] = z10 - L1 * z00;
+    st.cz[2] = z11 - L1 * z10;
+    chi2 = chi2 + chi + rz * rz / Sz;
+}
+
+__device__ __forceinline__ void reset_cov(State& st, const KConst& k)
+{
+    st.cy[0] = k.sy2;
+    st.cy[1] = 0.0f;
+    st.cy[2] = k.var_s;
+    st.cy[3] = 0.0f;
+    st.cy[4] = 0.0f;
+    st.cy[5] = k.var_q;
+    st.cz[0] = k.sz2;
+    st.cz[1] = 0.0f;
+    st.cz[2] = k.var_t;
+}
+
+__device__ __forceinline__ bool outside(const State& st, float X, const KConst& k)
+{
+    return fabsf(st.y) > X * k.tan_h + k.y_margin || fabsf(st.z) > k.z_max;
+}
+
+// Closest cluster of row rr to the predicted state inside the window
+// |dy| <= wy, |dz| <= wz with w = clamp(n_sigma sqrt(S), w_min, w_max);
+// distance d2 = dy^2 / S_y + dz^2 / S_z, ties by smaller id.  Returns the
+// binned index or -1.
+__device__ __forceinline__ int search_row(const State& st, int rr, const KConst& k, const DevPtrs& p,
+                                          float4& found, int4& work)
+{
+    const float Sy = k.sy2 + st.cy[0];
+    const float Sz = k.sz2 + st.cz[0];
+    float wy = k.n_sigma * sqrtf(Sy);
+    float wz = k.n_sigma * sqrtf(Sz);
+    wy = wy < k.w_min ? k.w_min : (wy > k.w_max ? k.w_max : wy);
+    wz = wz < k.w_min ? k.w_min : (wz > k.w_max ? k.w_max : wz);
+    const RowGrid g = p.grid[rr];
+    const int y0 = bin_index(st.y - wy - kBinEps, g.y0, g.inv_by, g.ny);
+    const int y1 = bin_index(st.y + wy + kBinEps, g.y0, g.inv_by, g.ny);
+    const int z0 = bin_index(st.z - wz - kBinEps, g.z0, g.inv_bz, g.nz);
+    const int z1 = bin_index(st.z + wz + kBinEps, g.z0, g.inv_bz, g.nz);
+    int best = -1;
+    unsigned bid = 0;
+    float bd2 = 0.0f;
+    work.x += 1;
+    work.y += z1 - z0 + 1;
+    for (int bz = z0; bz <= z1; bz++) {
+        const int* row_bins = p.bin_off + g.bin_base + bz * g.ny;
+        const int j0 = __ldg(row_bins + y0), j1 = __ldg(row_bins + y1 + 1);
+        work.z += j1 - j0;
+        for (int j = j0; j < j1; j++) {
+            const float4 c = __ldg(p.hits + j);
+            const float dy = c.x - st.y;
+            const float dz = c.y - st.z;
+            if (!(fabsf(dy) <= wy && fabsf(dz) <= wz)) continue;
+            const float d2 = dy * dy / Sy + dz * dz / Sz;
+            const unsigned id = __float_as_uint(c.z);
+            if (best < 0 || d2 < bd2 || (d2 == bd2 && id < bid)) {
+                best = j;
+                bd2 = d2;
+                bid = id;
+                found = c;
+            }
+        }
+    }
+    return best;
+}
+
+// One tracklet t (Sec. 2 step 2): seed from the CA chain, Phase 1 through the
+// chain and outward row by row, Phase 2 with a fresh covariance inward from
+// the outermost cluster to row 0; the Phase-2 clusters are the tracklet's.
+__device__ void build_tracklet(int t, const KConst& k, const float* xs, const DevPtrs& p)
+{
+    const int NR = k.n_rows;
+    const int rr0 = p.t_row[t];
+    const int ubase = rr0 - rr0 % NR;  // row index of row 0 of this unit
+    const int h0 = p.start[t];
+    int4 work = make_int4(0, 0, 0, 1);
+    int hL = h0, rL = rr0 - ubase;
+    for (int j = p.up2[hL]; j >= 0; j = p.up2[j]) {
+        hL = j;
+        rL++;
+        work.w++;
+    }
+    const float4 c0 = p.hits[h0];
+    const float4 cL = p.hits[hL];
+    const int r0 = rr0 - ubase;
+    State st;
+    st.x = xs[r0];
+    st.y = c0.x;
+    st.z = c0.y;
+    {
+        const float dx = xs[rL] - xs[r0], dy = cL.x - c0.x, dz = cL.y - c0.y;
+        const float l = sqrtf(dx * dx + dy * dy);
+        st.s = dy / l;
+        st.t = dz / l;
+    }
+    st.q = 0.0f;
+    reset_cov(st, k);
+    float chi2 = 0.0f;
+
+    // Phase 1: the chain, then outward.
+    bool have = false, stopped = false;
+    int r_out = -1;
+    State last = st;
+    {
+        int r = r0;
+        for (int h = h0; h >= 0; h = p.up2[h], r++) {
+            if (!propagate(st, xs[r], k.kB, k.s_max) || outside(st, xs[r], k)) {
+                stopped = true;
+                break;
+            }
+            const float4 c = p.hits[h];
+            update(st, c.x, c.y, k.sy2, k.sz2, chi2);
+            last = st;
+            r_out = r;
+            have = true;
+        }
+    }
+    if (!stopped) {
+        int miss = 0;
+        for (int r = rL + 1; r < NR; r++) {
+            if (!propagate(st, xs[r], k.kB, k.s_max) || outside(st, xs[r], k)) break;
+            float4 c;
+            const int j = search_row(st, ubase + r, k, p, c, work);
+            if (j >= 0) {
+                update(st, c.x, c.y, k.sy2, k.sz2, chi2);
+                last = st;
+                r_out = r;
+                miss = 0;
+            } else if (++miss > k.g_max) {
+                break;
+            }
+        }
+    }
+    float* f = p.tl_f + (size_t)t * kTlFloats;
+    if (!have) {
+        p.tl_work[t] = work;
+        p.tl_n[t] = 0;
+        for (int j = 0; j < kTlFloats; j++) f[j] = 0.0f;
+        return;
+    }
+    // Phase 2
+    st = last;
+    reset_cov(st, k);
+    chi2 = 0.0f;
+    int n = 0, miss = 0;
+    int* hits = p.tl_hits + (size_t)t * NR;
+    State inner = st;
+    for (int r = r_out; r >= 0; r--) {
+        if (!propagate(st, xs[r], k.kB, k.s_max) || outside(st, xs[r], k)) break;
+        float4 c;
+        const int j = search_row(st, ubase + r, k, p, c, work);
+        if (j >= 0) {
+            update(st, c.x, c.y, k.sy2, k.sz2, chi2);
+            hits[n++] = j;  // rows descending
+            inner = st;
+            miss = 0;
+        } else if (++miss > k.g_max) {
+            break;
+        }
+    }
+    p.tl_n[t] = n;
+    p.tl_work[t] = work;
+    if (n == 0) {
+        for (int j = 0; j < kTlFloats; j++) f[j] = 0.0f;
+        return;
+    }
+    float4* f4 = reinterpret_cast<float4*>(f);
+    f4[0] = make_float4(inner.x, inner.y, inner.z, inner.s);
+    f4[1] = make_float4(inner.t, inner.q, inner.cy[0], inner.cy[1]);
+    f4[2] = make_float4(inner.cy[2], inner.cy[3], inner.cy[4], inner.cy[5]);
+    f4[3] = make_float4(inner.cz[0], inner.cz[1], inner.cz[2], chi2);
+}
+
+// Persistent, dynamically scheduled constructor: warps take 32 entries of
+// the length-sorted schedule at a time from a global counter (long expected
+// tracks first), one lane per tracklet.
+__global__ void __launch_bounds__(256) k_tracklets_sched(KConst k, const float* __restrict__ row_x,
+                                                         DevPtrs p)
+{
+    __shared__ float xs[TPC_MAX_ROWS];
+    for (int r = threadIdx.x; r < k.n_rows; r += blockDim.x) xs[r] = row_x[r];
+    __syncthreads();
+    const int T = p.counters[C_T];
+    const int lane = threadIdx.x & 31;
+    while (true) {
+        int w = 0;
+        if (lane == 0) w = atomicAdd(&p.counters[C_WORK], 32);
+        w = __shfl_sync(0xffffffffu, w, 0);
+        if (w >= T) break;
+        const int i = w + lane;
+        if (i < T) build_tracklet(p.sched[i], k, xs, p);
+    }
+}
+
+// Plain form: the tracklets of units [u0, u1) in canonical order, static
+// assignment (one thread per track candidate, Sec. 3).
+__global__ void __launch_bounds__(256) k_tracklets_plain(KConst k, const float* __restrict__ row_x,
+                                                         DevPtrs p, int u0, int u1)
+{
+    __shared__ float xs[TPC_MAX_ROWS];
+    for (int r = threadIdx.x; r < k.n_rows; r += blockDim.x) xs[r] = row_x[r];
+    __syncthreads();
+    const int t0 = p.start_off[u0 * k.n_rows], t1 = p.start_off[u1 * k.n_rows];
+    for (int t = t0 + blockIdx.x * blockDim.x + threadIdx.x; t < t1; t += gridDim.x * blockDim.x)
+        build_tracklet(t, k, xs, p);
+}
+
+// -------------------------------------------------------------- launchers
+cudaError_t launch_neighbours(const KConst& k, const float* row_x_dev, const DevPtrs& p, int max3,
+                              int threads, int unit0, int n_units, cudaStream_t s)
+{
+    size_t sm = 16 + (size_t)max3 * 16 + (size_t)3 * (kMaxBinsPerRow + 4) * 4;
+    cudaError_t e =
+        cudaFuncSetAttribute(k_neighbours, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    int blocks = n_units * (k.n_rows - 2);
+    if (blocks == 0) return cudaSuccess;
+    k_neighbours<<<blocks, threads, sm, s>>>(k, row_x_dev, p, unit0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tracklets(const KConst& k, const float* row_x_dev, const DevPtrs& p, int n_sm,
+                             int lanes_per_tracklet, int u0, int u1, cudaStream_t s)
+{
+    (void)lanes_per_tracklet;
+    if (u0 < 0) {
+        k_tracklets_sched<<<n_sm * 8, 256, 0, s>>>(k, row_x_dev, p);
+    } else {
+        k_tracklets_plain<<<n_sm * 2, 256, 0, s>>>(k, row_x_dev, p, u0, u1);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace TPC_FP_NS

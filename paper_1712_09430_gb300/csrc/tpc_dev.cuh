@@ -1,0 +1,215 @@
+// Device-side data layout and PTX helpers of the GB300 TPC sector tracker.
+//
+// Index spaces
+//   unit      (event, sector) pair: u = event * n_sectors + sector
+//   row       rr = u * n_rows + r (CSR over the input, "canonical" row order)
+//   cluster   input position i (what the caller sees)
+//   binned    b: position in the binned copy `hits`; rows keep their CSR
+//             ranges, and inside a row clusters are ordered by (grid bin, id)
+//   tracklet  t: canonical order (unit, row, cluster id) of the start hits
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "tpc_tracker.h"
+
+namespace tpc {
+
+constexpr int kMaxBinsPerRow = 1024;   // search-grid bins in one row
+constexpr int kTlFloats = 16;          // x y z s t q cy[6] cz[3] chi2
+constexpr int kNumCounters = 16;
+constexpr float kCoordTol = 1e-3f;     // |x - row_x| accepted on input
+constexpr float kBinEps = 1e-3f;       // bin-range widening (cm), covers rounding
+constexpr unsigned kSpinLimit = 1u << 22;  // bounded mbarrier waits
+
+// counters[]
+enum {
+    C_T = 0,        // number of tracklets (start hits)
+    C_ERR = 1,      // error bits (E_*)
+    C_WORK = 2,     // persistent tracklet kernel work counter
+    C_M = 3,        // accepted tracks
+    C_MH = 4,       // hits of accepted tracks
+    C_BADROW = 5,   // first row index with invalid input (+1), 0 = none
+};
+enum { E_INPUT = 1, E_TIMEOUT = 2, E_TOO_DENSE = 4 };
+
+// Method constants in working precision (float), identical on every launch
+// of one call.
+struct KConst {
+    float k_win, d_max2;
+    float sy2, sz2, var_s, var_q, var_t;
+    float n_sigma, w_min, w_max, s_max, y_margin;
+    float kB;            // (float)(-kappa * Bz) rounded once from double
+    float tan_h, z_max;
+    float bin_target;
+    int l_seed, g_max, n_min_tracklet, n_min_track, own_num, own_den;
+    int n_rows, n_sectors;
+};
+
+// Search grid of one row: nbins = ny * nz, bin = iz * ny + iy.
+struct RowGrid {
+    float y0, z0, inv_by, inv_bz;
+    int ny, nz, bin_base, pad;
+};
+
+// Device pointers of one call (one batch of events).
+struct DevPtrs {
+    const float4* clusters;    // [N] input, (x, y, z, id bits)
+    const int* row_cnt;        // [R]
+    int* row_off;              // [R + 1]
+    int* bin_cap_off;          // [R + 1] start of each row's bin table (x4 aligned)
+    RowGrid* grid;             // [R]
+    float4* hits;              // [N] binned: (y, z, id bits, input position bits)
+    int* bin_off;              // bin tables: absolute binned offsets
+    int* up;                   // [N] binned space, before cleaning
+    int* dn;
+    int* up2;                  // [N] after cleaning
+    int* dn2;
+    unsigned char* is_start;   // [N]
+    int* row_nstart;           // [R]
+    int* start_off;            // [R + 1] canonical tracklet offsets per row
+    int* sched_off;            // [R + 1] schedule offsets (row-major order)
+    int* start;                // [Tcap] binned index of the start hit of t
+    int* t_row;                // [Tcap] row index rr of the start hit of t
+    int* sched;                // [Tcap] tracklets by expected length
+    float* tl_f;               // [Tcap][16]
+    int* tl_n;                 // [Tcap] Phase-2 cluster count
+    int* tl_hits;              // [Tcap][n_rows] binned, rows DESCENDING
+    int4* tl_work;             // [Tcap] row steps, bin-table rows, candidates, chain length
+    unsigned long long* owner; // [N]
+    int2* acc;                 // [Tcap] (accepted, owned hits)
+    int2* acc_scan;            // [Tcap] exclusive scan of acc
+    int2* scan_part;           // [ceil(Tcap / kScanTile) + 1]
+    tpc_track* out_tracks;     // [Mcap]
+    int* out_hits;             // [MHcap]
+    int* counters;             // [kNumCounters]
+    int N, R, n_units, t_cap, m_cap, mh_cap;
+};
+
+constexpr int kScanTile = 2048;  // elements per CTA in the multi-CTA scan
+
+// Bins of a row: the grid covers y in [-(X tan_h + y_margin), +...] and z in
+// the drift half of the sector's side; square bins sized for bin_target
+// clusters per bin; nbins <= cap (see row_bin_cap).
+__host__ __device__ inline int row_bin_cap(int cnt, float bin_target)
+{
+    int nbt = (int)ceilf((float)cnt / bin_target);
+    if (nbt < 1) nbt = 1;
+    int cap = 2 * nbt + 8;
+    return cap < kMaxBinsPerRow ? cap : kMaxBinsPerRow;
+}
+
+__host__ __device__ inline int row_bin_slots(int cnt, float bin_target)
+{
+    return (row_bin_cap(cnt, bin_target) + 1 + 3) & ~3;  // table of cap+1, x4 aligned
+}
+
+// ---------------------------------------------------------------------------
+// PTX helpers: bulk (TMA) copies through an mbarrier, sm_90+ forms used on
+// sm_103a.  A CTA launched without clusters is its own 1-CTA cluster.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned smem_addr(const void* p)
+{
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+                 : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// global -> shared bulk copy; dst, src 16-byte aligned, bytes % 16 == 0
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, "
+        "0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: false after kSpinLimit polls (the caller records E_TIMEOUT).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity)
+{
+    for (unsigned i = 0; i < kSpinLimit; i++)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+// shared -> global bulk copy (bulk-group completion)
+__device__ __forceinline__ void bulk_s2g(void* dst, const void* src, unsigned bytes)
+{
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst),
+                 "r"(smem_addr(src)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ int bin_index(float v, float lo, float inv, int n)
+{
+    int b = (int)floorf((v - lo) * inv);
+    return b < 0 ? 0 : (b >= n ? n - 1 : b);
+}
+
+}  // namespace tpc
+
+// ---------------------------------------------------------------------------
+// Launch wrappers (host).  The floating-point kernels exist twice: namespace
+// tpc_exact (built with -fmad=false) and tpc_fast (FMA contraction allowed).
+// ---------------------------------------------------------------------------
+namespace tpc_int {
+cudaError_t launch_plan(const tpc::KConst& k, const float* row_x_dev, const tpc::DevPtrs& p,
+                        cudaStream_t s);
+cudaError_t launch_grid(const tpc::KConst& k, const float* row_x_dev, const tpc::DevPtrs& p,
+                        int max_row, int threads, int unit0, int n_units, cudaStream_t s);
+cudaError_t launch_clean(const tpc::KConst& k, const tpc::DevPtrs& p, int threads, int unit0,
+                         int n_units, cudaStream_t s);
+cudaError_t launch_start_scan(const tpc::KConst& k, const tpc::DevPtrs& p, cudaStream_t s);
+cudaError_t launch_start_write(const tpc::KConst& k, const tpc::DevPtrs& p, int threads, int unit0,
+                               int n_units, cudaStream_t s);
+cudaError_t launch_select(const tpc::KConst& k, const tpc::DevPtrs& p, int n_sm, int t0_unit,
+                          int t1_unit, cudaStream_t s);
+cudaError_t launch_emit(const tpc::KConst& k, const tpc::DevPtrs& p, int n_sm, cudaStream_t s);
+cudaError_t launch_dump_links(const tpc::DevPtrs& p, int cleaned, int* dst, cudaStream_t s);
+cudaError_t launch_dump_starts(const tpc::DevPtrs& p, int T, int* dst, cudaStream_t s);
+cudaError_t launch_dump_tl_hits(const tpc::KConst& k, const tpc::DevPtrs& p, int T, int* dst,
+                                cudaStream_t s);
+cudaError_t launch_dump_tl_work(const tpc::DevPtrs& p, int T, int* dst, cudaStream_t s);
+}  // namespace tpc_int
+
+#define TPC_FP_DECLS                                                                              \
+    cudaError_t launch_neighbours(const tpc::KConst& k, const float* row_x_dev,                   \
+                                  const tpc::DevPtrs& p, int max3, int threads, int unit0,        \
+                                  int n_units, cudaStream_t s);                                   \
+    cudaError_t launch_tracklets(const tpc::KConst& k, const float* row_x_dev,                    \
+                                 const tpc::DevPtrs& p, int n_sm, int lanes_per_tracklet,         \
+                                 int t_first_unit, int t_last_unit, cudaStream_t s);
+
+namespace tpc_exact { TPC_FP_DECLS }
+namespace tpc_fast { TPC_FP_DECLS }

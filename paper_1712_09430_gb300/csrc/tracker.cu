@@ -1,0 +1,585 @@
+// Host side of the C ABI (include/tpc_tracker.h): tracker lifecycle, device
+// workspace, the batched and the plain per-sector launch sequences, CUDA-graph
+// replay, output fetch with the estimate-then-fetch-the-rest scheme of
+// Sec. 3.1, per-stage dumps and stage timing.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "tpc_dev.cuh"
+#include "tpc_serve.h"
+
+using namespace tpc;
+
+static std::mutex g_err_mu;
+static std::string g_create_err;
+
+#define TPC_CUDA(call)                                                                        \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess) return tr->fail(TPC_ERR_DEVICE, std::string(#call ": ") +      \
+                                                                  cudaGetErrorString(e_));    \
+    } while (0)
+
+namespace {
+
+size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
+}  // namespace
+
+// ---------------------------------------------------------------- tracker
+
+int tpc_tracker::fail(int code, const std::string& msg)
+{
+    err = msg;
+    return code;
+}
+
+static KConst make_kconst(const tpc_params& P, const tpc_geometry& G, double bz)
+{
+    KConst k;
+    k.k_win = P.k_win;
+    k.d_max2 = P.d_max2;
+    k.sy2 = P.sigma_y * P.sigma_y;
+    k.sz2 = P.sigma_z * P.sigma_z;
+    k.var_s = P.var_s;
+    k.var_q = P.var_q;
+    k.var_t = P.var_t;
+    k.n_sigma = P.n_sigma;
+    k.w_min = P.w_min;
+    k.w_max = P.w_max;
+    k.s_max = P.s_max;
+    k.y_margin = P.y_margin;
+    k.kB = (float)(-0.00299792458 * bz);
+    k.tan_h = G.tan_half_open;
+    k.z_max = G.z_max;
+    k.bin_target = P.bin_target;
+    k.l_seed = P.l_seed;
+    k.g_max = P.g_max;
+    k.n_min_tracklet = P.n_min_tracklet;
+    k.n_min_track = P.n_min_track;
+    k.own_num = P.own_num;
+    k.own_den = P.own_den;
+    k.n_rows = G.n_rows;
+    k.n_sectors = G.n_sectors;
+    return k;
+}
+
+static const char* check_params(const tpc_params& P)
+{
+    if (!(P.k_win > 0 && P.d_max2 >= 0 && P.sigma_y > 0 && P.sigma_z > 0)) return "k_win, d_max2, sigma";
+    if (!(P.var_s > 0 && P.var_q > 0 && P.var_t > 0)) return "initial variances must be > 0";
+    if (!(P.n_sigma > 0 && P.w_min > 0 && P.w_max >= P.w_min)) return "search window";
+    if (!(P.s_max > 0 && P.s_max < 1)) return "s_max must be in (0, 1)";
+    if (!(P.y_margin >= 0)) return "y_margin";
+    if (P.l_seed < 2 || P.g_max < 0 || P.n_min_tracklet < 1 || P.n_min_track < 1) return "counts";
+    if (P.own_num < 0 || P.own_den < 1) return "own_num/own_den";
+    if (!(P.bin_target > 0 && P.bin_target < 1e6f)) return "bin_target";
+    int t = P.threads_per_row;
+    if (t != 32 && t != 64 && t != 128 && t != 256) return "threads_per_row must be 32, 64, 128 or 256";
+    int w = P.tracklets_per_warp;
+    if (w != 1 && w != 2 && w != 4 && w != 8 && w != 16 && w != 32) return "tracklets_per_warp";
+    return nullptr;
+}
+
+extern "C" void tpc_params_default(tpc_params* p)
+{
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->k_win = 1.5f;
+    p->d_max2 = 0.25f;
+    p->l_seed = 3;
+    p->sigma_y = 0.1f;
+    p->sigma_z = 0.1f;
+    p->var_s = 0.25f;
+    p->var_q = 100.0f;
+    p->var_t = 1.0f;
+    p->n_sigma = 3.5f;
+    p->w_min = 0.3f;
+    p->w_max = 3.0f;
+    p->s_max = 0.95f;
+    p->y_margin = 2.0f;
+    p->g_max = 8;
+    p->n_min_tracklet = 10;
+    p->n_min_track = 10;
+    p->own_num = 7;
+    p->own_den = 10;
+    p->exact_fp32 = 0;
+    p->bin_target = 1.0f;
+    p->threads_per_row = 128;
+    p->tracklets_per_warp = 32;
+    p->plain_per_sector = 0;
+    p->use_graph = 0;
+}
+
+extern "C" int tpc_tracker_create(const tpc_geometry* g, double bz, const tpc_params* params,
+                                  tpc_tracker** out)
+{
+    auto create_fail = [](const std::string& m) {
+        std::lock_guard<std::mutex> lk(g_err_mu);
+        g_create_err = m;
+    };
+    if (!g || !out) { create_fail("NULL geometry or output pointer"); return TPC_ERR_INVALID; }
+    *out = nullptr;
+    if (g->n_rows < 3 || g->n_rows > TPC_MAX_ROWS || !g->row_x) {
+        create_fail("n_rows must be in [3, 256] with row_x given");
+        return TPC_ERR_INVALID;
+    }
+    if (g->n_sectors < 2 || (g->n_sectors & 1)) { create_fail("n_sectors must be even and >= 2"); return TPC_ERR_INVALID; }
+    for (int r = 0; r < g->n_rows; r++) {
+        if (!(g->row_x[r] > 0) || !std::isfinite(g->row_x[r]) || (r && !(g->row_x[r] > g->row_x[r - 1]))) {
+            create_fail("row_x must be finite, positive and strictly increasing");
+            return TPC_ERR_INVALID;
+        }
+    }
+    if (!(g->tan_half_open > 0) || !(g->z_max > 0) || !std::isfinite(bz)) {
+        create_fail("tan_half_open, z_max must be > 0 and bz finite");
+        return TPC_ERR_INVALID;
+    }
+    tpc_params P;
+    tpc_params_default(&P);
+    if (params) P = *params;
+    if (const char* m = check_params(P)) { create_fail(std::string("params: ") + m); return TPC_ERR_INVALID; }
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) { create_fail("no CUDA device"); return TPC_ERR_DEVICE; }
+    tpc_tracker* tr = new tpc_tracker();
+    tr->dev = dev;
+    tr->geom = *g;
+    tr->row_x.assign(g->row_x, g->row_x + g->n_rows);
+    tr->geom.row_x = tr->row_x.data();
+    tr->bz = bz;
+    tr->params = P;
+    tr->kc = make_kconst(P, tr->geom, bz);
+    cudaDeviceGetAttribute(&tr->n_sm, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaStreamCreateWithFlags(&tr->own_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaMalloc(&tr->row_x_dev, sizeof(float) * TPC_MAX_ROWS) != cudaSuccess ||
+        cudaMemcpy(tr->row_x_dev, tr->row_x.data(), sizeof(float) * g->n_rows,
+                   cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMallocHost(&tr->counters_host, sizeof(int) * kNumCounters) != cudaSuccess) {
+        create_fail("CUDA setup failed");
+        tpc_tracker_destroy(tr);
+        return TPC_ERR_DEVICE;
+    }
+    for (auto& e : tr->ev) cudaEventCreate(&e);
+    *out = tr;
+    return TPC_OK;
+}
+
+extern "C" void tpc_tracker_destroy(tpc_tracker* tr)
+{
+    if (!tr) return;
+    cudaSetDevice(tr->dev);
+    tpc_serve_shutdown(tr);
+    if (tr->graph_exec) cudaGraphExecDestroy(tr->graph_exec);
+    if (tr->own_stream) cudaStreamSynchronize(tr->own_stream);
+    cudaFree(tr->ws);
+    cudaFree(tr->row_x_dev);
+    cudaFree(tr->dump_buf);
+    cudaFreeHost(tr->counters_host);
+    for (auto& e : tr->ev) if (e) cudaEventDestroy(e);
+    if (tr->own_stream) cudaStreamDestroy(tr->own_stream);
+    delete tr;
+}
+
+extern "C" int tpc_tracker_set_params(tpc_tracker* tr, const tpc_params* params)
+{
+    if (!tr || !params) return TPC_ERR_INVALID;
+    if (tpc_serve_busy(tr)) return tr->fail(TPC_BUSY, "stream tickets in flight");
+    if (const char* m = check_params(*params)) return tr->fail(TPC_ERR_INVALID, std::string("params: ") + m);
+    tr->params = *params;
+    tr->kc = make_kconst(*params, tr->geom, tr->bz);
+    tr->graph_key.clear();
+    return TPC_OK;
+}
+
+extern "C" const char* tpc_last_error(const tpc_tracker* tr)
+{
+    if (!tr) {
+        std::lock_guard<std::mutex> lk(g_err_mu);
+        return g_create_err.c_str();
+    }
+    return tr->err.c_str();
+}
+
+// ------------------------------------------------------------- workspace
+
+// Lay out every device buffer of one batch; returns the bytes needed.
+size_t tpc_layout(const tpc_tracker* tr, const BatchShape& sh, DevPtrs* p, char* base)
+{
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        char* r = base ? base + off : nullptr;
+        off = align256(off + std::max<size_t>(bytes, 16));
+        return r;
+    };
+    const size_t N = (size_t)sh.N, R = (size_t)sh.R, Tc = (size_t)sh.t_cap;
+    const size_t NR = (size_t)tr->geom.n_rows;
+    DevPtrs q{};
+    q.clusters = reinterpret_cast<const float4*>(take(N * 16));
+    q.row_cnt = reinterpret_cast<const int*>(take(R * 4));
+    q.row_off = reinterpret_cast<int*>(take((R + 1) * 4));
+    q.bin_cap_off = reinterpret_cast<int*>(take((R + 1) * 4));
+    q.grid = reinterpret_cast<RowGrid*>(take(R * sizeof(RowGrid)));
+    q.hits = reinterpret_cast<float4*>(take(N * 16));
+    q.bin_off = reinterpret_cast<int*>(take((size_t)sh.bin_slots * 4));
+    q.up = reinterpret_cast<int*>(take(N * 4));
+    q.dn = reinterpret_cast<int*>(take(N * 4));
+    q.up2 = reinterpret_cast<int*>(take(N * 4));
+    q.dn2 = reinterpret_cast<int*>(take(N * 4));
+    q.is_start = reinterpret_cast<unsigned char*>(take(N));
+    q.row_nstart = reinterpret_cast<int*>(take(R * 4));
+    q.start_off = reinterpret_cast<int*>(take((R + 1) * 4));
+    q.sched_off = reinterpret_cast<int*>(take((R + 1) * 4));
+    q.start = reinterpret_cast<int*>(take(Tc * 4));
+    q.t_row = reinterpret_cast<int*>(take(Tc * 4));
+    q.sched = reinterpret_cast<int*>(take(Tc * 4));
+    q.tl_f = reinterpret_cast<float*>(take(Tc * kTlFloats * 4));
+    q.tl_n = reinterpret_cast<int*>(take(Tc * 4));
+    q.tl_hits = reinterpret_cast<int*>(take(Tc * NR * 4));
+    q.tl_work = reinterpret_cast<int4*>(take(Tc * 16));
+    q.owner = reinterpret_cast<unsigned long long*>(take(N * 8));
+    q.acc = reinterpret_cast<int2*>(take(Tc * 8));
+    q.acc_scan = reinterpret_cast<int2*>(take(Tc * 8));
+    q.scan_part = reinterpret_cast<int2*>(take((Tc / kScanTile + 2) * 8));
+    q.out_tracks = reinterpret_cast<tpc_track*>(take(Tc * sizeof(tpc_track)));
+    q.out_hits = reinterpret_cast<int*>(take(N * 4));
+    q.counters = reinterpret_cast<int*>(take(kNumCounters * 4));
+    q.N = sh.N;
+    q.R = sh.R;
+    q.n_units = sh.n_units;
+    q.t_cap = sh.t_cap;
+    q.m_cap = sh.t_cap;
+    q.mh_cap = sh.N;
+    if (p) *p = q;
+    return off;
+}
+
+// Shape of a batch from its (host) row counts.
+int tpc_shape(tpc_tracker* tr, const int32_t* row_counts, int n_events, BatchShape* sh)
+{
+    const int NR = tr->geom.n_rows, S = tr->geom.n_sectors;
+    const int64_t R = (int64_t)n_events * S * NR;
+    if (R > (1 << 28)) return tr->fail(TPC_ERR_INVALID, "too many rows in one call");
+    int64_t N = 0, bins = 0;
+    int max_row = 0, max3 = 0;
+    for (int64_t r = 0; r < R; r++) {
+        int c = row_counts[r];
+        if (c < 0 || c > TPC_MAX_ROW_CLUSTERS) {
+            char m[128];
+            std::snprintf(m, sizeof m, "row_counts[%lld] = %d outside [0, %d]", (long long)r, c,
+                          TPC_MAX_ROW_CLUSTERS);
+            return tr->fail(TPC_ERR_INVALID, m);
+        }
+        N += c;
+        bins += row_bin_slots(c, tr->params.bin_target);
+        max_row = std::max(max_row, c);
+        int rr = (int)(r % NR);
+        if (rr >= 1 && rr + 1 < NR) max3 = std::max(max3, row_counts[r - 1] + c + row_counts[r + 1]);
+    }
+    if (N >= (int64_t)1 << 30) return tr->fail(TPC_ERR_INVALID, "more than 2^30 clusters in one call");
+    sh->n_events = n_events;
+    sh->n_units = n_events * S;
+    sh->R = (int)R;
+    sh->N = (int)N;
+    // cleaned links form disjoint chains with one start each, of >= l_seed hits
+    sh->t_cap = (int)(N / std::max(2, tr->params.l_seed) + 1);
+    sh->bin_slots = bins;
+    sh->max_row = std::max(max_row, 1);
+    sh->max3 = std::max(max3, 1);
+    return TPC_OK;
+}
+
+int tpc_reserve(tpc_tracker* tr, size_t bytes)
+{
+    if (bytes <= tr->ws_bytes) return TPC_OK;
+    if (tr->ws) {
+        cudaStreamSynchronize(tr->own_stream);
+        cudaDeviceSynchronize();
+        cudaFree(tr->ws);
+        tr->ws = nullptr;
+        tr->ws_bytes = 0;
+        tr->graph_key.clear();
+    }
+    size_t want = bytes + bytes / 4;
+    if (cudaMalloc(&tr->ws, want) != cudaSuccess) {
+        cudaGetLastError();
+        if (cudaMalloc(&tr->ws, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            tr->ws = nullptr;
+            return tr->fail(TPC_ERR_NOMEM, "cannot allocate device workspace");
+        }
+        want = bytes;
+    }
+    tr->ws_bytes = want;
+    return TPC_OK;
+}
+
+// --------------------------------------------------------------- pipeline
+
+// Enqueue every device stage of one batch on stream s.  with_events records
+// stage boundaries (not allowed while capturing a graph).
+int tpc_enqueue(tpc_tracker* tr, const DevPtrs& p, const BatchShape& sh, cudaStream_t s,
+                bool with_events)
+{
+    const KConst& k = tr->kc;
+    const tpc_params& P = tr->params;
+    const float* xd = tr->row_x_dev;
+    const bool exact = P.exact_fp32 != 0;
+    auto nb = [&](const tpc::KConst& kk, const float* x, const DevPtrs& pp, int max3, int th, int u0,
+                  int nu, cudaStream_t ss) {
+        return exact ? tpc_exact::launch_neighbours(kk, x, pp, max3, th, u0, nu, ss)
+                     : tpc_fast::launch_neighbours(kk, x, pp, max3, th, u0, nu, ss);
+    };
+    auto tl = [&](int u0, int u1) {
+        return exact ? tpc_exact::launch_tracklets(k, xd, p, tr->n_sm, 32 / P.tracklets_per_warp, u0, u1, s)
+                     : tpc_fast::launch_tracklets(k, xd, p, tr->n_sm, 32 / P.tracklets_per_warp, u0, u1, s);
+    };
+    const int th = P.threads_per_row;
+    if (with_events) TPC_CUDA(cudaEventRecord(tr->ev[0], s));
+    TPC_CUDA(tpc_int::launch_plan(k, xd, p, s));
+    if (!P.plain_per_sector) {
+        TPC_CUDA(tpc_int::launch_grid(k, xd, p, sh.max_row, th, 0, sh.n_units, s));
+        if (with_events) TPC_CUDA(cudaEventRecord(tr->ev[1], s));
+        TPC_CUDA(nb(k, xd, p, sh.max3, th, 0, sh.n_units, s));
+        if (with_events) TPC_CUDA(cudaEventRecord(tr->ev[2], s));
+        TPC_CUDA(tpc_int::launch_clean(k, p, th, 0, sh.n_units, s));
+        TPC_CUDA(tpc_int::launch_start_scan(k, p, s));
+        TPC_CUDA(tpc_int::launch_start_write(k, p, th, 0, sh.n_units, s));
+        if (with_events) TPC_CUDA(cudaEventRecord(tr->ev[3], s));
+        TPC_CUDA(tl(-1, -1));
+        if (with_events) TPC_CUDA(cudaEventRecord(tr->ev[4], s));
+        TPC_CUDA(tpc_int::launch_select(k, p, tr->n_sm, 0, sh.n_units, s));
+    } else {
+        // The Run 1/2 scheduling (Sec. 3): every stage launched per sector.
+        for (int u = 0; u < sh.n_units; u++)
+            TPC_CUDA(tpc_int::launch_grid(k, xd, p, sh.max_row, th, u, 1, s));
+        if (with_events) TPC_CUDA(cudaEventRecord(tr->ev[1], s));
+        for (int u = 0; u < sh.n_units; u++) TPC_CUDA(nb(k, xd, p, sh.max3, th, u, 1, s));
+        if (with_events) TPC_CUDA(cudaEventRecord(tr->ev[2], s));
+        for (int u = 0; u < sh.n_units; u++) TPC_CUDA(tpc_int::launch_clean(k, p, th, u, 1, s));
+        TPC_CUDA(tpc_int::launch_start_scan(k, p, s));
+        for (int u = 0; u < sh.n_units; u++) TPC_CUDA(tpc_int::launch_start_write(k, p, th, u, 1, s));
+        if (with_events) TPC_CUDA(cudaEventRecord(tr->ev[3], s));
+        for (int u = 0; u < sh.n_units; u++) TPC_CUDA(tl(u, u + 1));
+        if (with_events) TPC_CUDA(cudaEventRecord(tr->ev[4], s));
+        for (int u = 0; u < sh.n_units; u++) TPC_CUDA(tpc_int::launch_select(k, p, tr->n_sm, u, u + 1, s));
+    }
+    TPC_CUDA(tpc_int::launch_emit(k, p, tr->n_sm, s));
+    if (with_events) TPC_CUDA(cudaEventRecord(tr->ev[5], s));
+    return TPC_OK;
+}
+
+static std::string graph_key_of(const tpc_tracker* tr, const BatchShape& sh, const DevPtrs& p)
+{
+    char b[256];
+    std::snprintf(b, sizeof b, "%d/%d/%d/%d/%d/%p/%p/%d/%d/%d/%d", sh.N, sh.R, sh.n_units, sh.max_row,
+                  sh.max3, (const void*)p.clusters, (const void*)p.counters, tr->params.exact_fp32,
+                  tr->params.threads_per_row, tr->params.tracklets_per_warp,
+                  tr->params.plain_per_sector);
+    return std::string(b);
+}
+
+// Run all stages: directly, or as a replay of a captured graph when the
+// batch shape and buffers match the captured ones.
+int tpc_run_stages(tpc_tracker* tr, const DevPtrs& p, const BatchShape& sh, cudaStream_t s)
+{
+    if (!tr->params.use_graph) return tpc_enqueue(tr, p, sh, s, true);
+    std::string key = graph_key_of(tr, sh, p);
+    if (key != tr->graph_key) {
+        if (tr->graph_exec) {
+            cudaGraphExecDestroy(tr->graph_exec);
+            tr->graph_exec = nullptr;
+        }
+        tr->graph_key.clear();
+        cudaStream_t cs = tr->own_stream;
+        TPC_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        int rc = tpc_enqueue(tr, p, sh, cs, true);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(cs, &g);
+        if (rc != TPC_OK) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        if (e != cudaSuccess) return tr->fail(TPC_ERR_DEVICE, std::string("graph capture: ") + cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&tr->graph_exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return tr->fail(TPC_ERR_DEVICE, std::string("graph instantiate: ") + cudaGetErrorString(e));
+        tr->graph_key = key;
+    }
+    TPC_CUDA(cudaGraphLaunch(tr->graph_exec, s));  // records the stage events itself
+    return TPC_OK;
+}
+
+// Read counters after the stages; checks the device error bits.
+static int finish_counters(tpc_tracker* tr, cudaStream_t s)
+{
+    TPC_CUDA(cudaMemcpyAsync(tr->counters_host, tr->cur.counters, sizeof(int) * kNumCounters,
+                             cudaMemcpyDeviceToHost, s));
+    TPC_CUDA(cudaStreamSynchronize(s));
+    const int* c = tr->counters_host;
+    if (c[C_ERR] & E_INPUT) {
+        int rr = c[C_BADROW] - 1;
+        char m[160];
+        int NR = tr->geom.n_rows, S = tr->geom.n_sectors;
+        std::snprintf(m, sizeof m,
+                      "invalid cluster (NaN/inf coordinate or x off its pad row) in event %d sector %d row %d",
+                      rr / (NR * S), (rr / NR) % S, rr % NR);
+        return tr->fail(TPC_ERR_INVALID, m);
+    }
+    if (c[C_ERR] & E_TIMEOUT) return tr->fail(TPC_ERR_TIMEOUT, "bulk copy wait ran out in a kernel");
+    tr->last_T = c[C_T];
+    tr->last_M = c[C_M];
+    tr->last_MH = c[C_MH];
+    return TPC_OK;
+}
+
+// Copy the device result into out.  Estimate first (the previous result size
+// with margin), fetch the rest if the estimate was short (Sec. 3.1).
+int tpc_copy_out(tpc_tracker* tr, const DevPtrs& p, int M, int MH, tpc_output* out, cudaStream_t s)
+{
+    if (!out) return tr->fail(TPC_ERR_INVALID, "NULL output");
+    out->n_tracks = M;
+    out->n_hits = MH;
+    const cudaMemcpyKind kind = out->mem_kind == TPC_MEM_DEVICE ? cudaMemcpyDeviceToDevice
+                                                                : cudaMemcpyDeviceToHost;
+    const int mt = std::min(M, std::max(out->cap_tracks, 0));
+    const int mh = std::min(MH, std::max(out->cap_hits, 0));
+    if (mt > 0) {
+        if (!out->tracks) return tr->fail(TPC_ERR_INVALID, "NULL tracks buffer");
+        TPC_CUDA(cudaMemcpyAsync(out->tracks, p.out_tracks, sizeof(tpc_track) * mt, kind, s));
+    }
+    if (mh > 0) {
+        if (!out->hit_ids) return tr->fail(TPC_ERR_INVALID, "NULL hit_ids buffer");
+        TPC_CUDA(cudaMemcpyAsync(out->hit_ids, p.out_hits, sizeof(int) * mh, kind, s));
+    }
+    TPC_CUDA(cudaStreamSynchronize(s));
+    if (mt < M || mh < MH) return tr->fail(TPC_ERR_OUTPUT_TRUNCATED, "output capacity too small");
+    return TPC_OK;
+}
+
+extern "C" int tpc_track_sectors(tpc_tracker* tr, const tpc_cluster* clusters, const int32_t* row_counts,
+                                 int n_events, int mem_kind, tpc_output* out, void* cuda_stream)
+{
+    if (!tr) return TPC_ERR_INVALID;
+    if (!row_counts || n_events < 0 || !out) return tr->fail(TPC_ERR_INVALID, "NULL row_counts/out or n_events < 0");
+    if (mem_kind != TPC_MEM_HOST && mem_kind != TPC_MEM_DEVICE) return tr->fail(TPC_ERR_INVALID, "mem_kind");
+    TPC_CUDA(cudaSetDevice(tr->dev));
+    BatchShape sh{};
+    int rc = tpc_shape(tr, row_counts, n_events, &sh);
+    if (rc != TPC_OK) return rc;
+    if (sh.N > 0 && !clusters) return tr->fail(TPC_ERR_INVALID, "NULL clusters");
+    if (mem_kind == TPC_MEM_DEVICE && (reinterpret_cast<uintptr_t>(clusters) & 15))
+        return tr->fail(TPC_ERR_INVALID, "device clusters must be 16-byte aligned");
+    cudaStream_t s = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : tr->own_stream;
+    if (sh.n_units == 0 || sh.N == 0) {
+        tr->last_T = tr->last_M = tr->last_MH = 0;
+        tr->has_result = false;
+        out->n_tracks = 0;
+        out->n_hits = 0;
+        return TPC_OK;
+    }
+    size_t bytes = tpc_layout(tr, sh, nullptr, nullptr);
+    rc = tpc_reserve(tr, bytes);
+    if (rc != TPC_OK) return rc;
+    DevPtrs p;
+    tpc_layout(tr, sh, &p, static_cast<char*>(tr->ws));
+    if (mem_kind == TPC_MEM_HOST) {
+        TPC_CUDA(cudaMemcpyAsync(const_cast<float4*>(p.clusters), clusters, (size_t)sh.N * 16,
+                                 cudaMemcpyHostToDevice, s));
+    } else {
+        p.clusters = reinterpret_cast<const float4*>(clusters);
+    }
+    TPC_CUDA(cudaMemcpyAsync(const_cast<int*>(p.row_cnt), row_counts, (size_t)sh.R * 4,
+                             cudaMemcpyHostToDevice, s));
+    tr->cur = p;
+    tr->cur_shape = sh;
+    tr->has_result = false;
+    rc = tpc_run_stages(tr, p, sh, s);
+    if (rc != TPC_OK) return rc;
+    rc = finish_counters(tr, s);
+    if (rc != TPC_OK) return rc;
+    tr->has_result = true;
+    tr->last_stream = s;
+    return tpc_copy_out(tr, p, tr->last_M, tr->last_MH, out, s);
+}
+
+extern "C" int tpc_fetch_output(tpc_tracker* tr, tpc_output* out)
+{
+    if (!tr) return TPC_ERR_INVALID;
+    if (!tr->has_result) return tr->fail(TPC_ERR_INVALID, "no result to fetch");
+    TPC_CUDA(cudaSetDevice(tr->dev));
+    return tpc_copy_out(tr, tr->cur, tr->last_M, tr->last_MH, out, tr->last_stream);
+}
+
+extern "C" int tpc_stage_times(tpc_tracker* tr, float* ms, int n)
+{
+    if (!tr || !ms) return TPC_ERR_INVALID;
+    if (!tr->has_result) return tr->fail(TPC_ERR_INVALID, "no result");
+    for (int i = 0; i < n && i < 6; i++) {
+        float v = 0.0f;
+        int a = i < 5 ? i : 0, b = i < 5 ? i + 1 : 5;
+        if (cudaEventElapsedTime(&v, tr->ev[a], tr->ev[b]) != cudaSuccess) {
+            cudaGetLastError();
+            v = -1.0f;
+        }
+        ms[i] = v;
+    }
+    return TPC_OK;
+}
+
+extern "C" int tpc_debug_dump(tpc_tracker* tr, int what, void* dst, int64_t cap, int64_t* n_items)
+{
+    if (!tr || !dst || !n_items) return TPC_ERR_INVALID;
+    if (!tr->has_result) return tr->fail(TPC_ERR_INVALID, "no result to dump");
+    TPC_CUDA(cudaSetDevice(tr->dev));
+    const DevPtrs& p = tr->cur;
+    const int N = tr->cur_shape.N, T = tr->last_T, NR = tr->geom.n_rows;
+    size_t bytes;
+    switch (what) {
+        case TPC_DUMP_LINKS_RAW:
+        case TPC_DUMP_LINKS: *n_items = N; bytes = (size_t)N * 8; break;
+        case TPC_DUMP_STARTS: *n_items = T; bytes = (size_t)T * 4; break;
+        case TPC_DUMP_TRACKLETS: *n_items = T; bytes = (size_t)T * kTlFloats * 4; break;
+        case TPC_DUMP_TRACKLET_N: *n_items = T; bytes = (size_t)T * 8; break;
+        case TPC_DUMP_TRACKLET_HITS: *n_items = T; bytes = (size_t)T * NR * 4; break;
+        case TPC_DUMP_TRACKLET_WORK: *n_items = T; bytes = (size_t)T * 16; break;
+        default: return tr->fail(TPC_ERR_INVALID, "unknown dump");
+    }
+    if ((int64_t)bytes > cap) return tr->fail(TPC_ERR_OUTPUT_TRUNCATED, "dump buffer too small");
+    if (bytes == 0) return TPC_OK;
+    cudaStream_t s = tr->own_stream;
+    TPC_CUDA(cudaStreamSynchronize(tr->last_stream));
+    if (bytes > tr->dump_bytes) {
+        cudaFree(tr->dump_buf);
+        tr->dump_buf = nullptr;
+        tr->dump_bytes = 0;
+        TPC_CUDA(cudaMalloc(&tr->dump_buf, bytes));
+        tr->dump_bytes = bytes;
+    }
+    int* d = static_cast<int*>(tr->dump_buf);
+    switch (what) {
+        case TPC_DUMP_LINKS_RAW: TPC_CUDA(tpc_int::launch_dump_links(p, 0, d, s)); break;
+        case TPC_DUMP_LINKS: TPC_CUDA(tpc_int::launch_dump_links(p, 1, d, s)); break;
+        case TPC_DUMP_STARTS: TPC_CUDA(tpc_int::launch_dump_starts(p, T, d, s)); break;
+        case TPC_DUMP_TRACKLETS:
+            TPC_CUDA(cudaMemcpyAsync(d, p.tl_f, bytes, cudaMemcpyDeviceToDevice, s));
+            break;
+        case TPC_DUMP_TRACKLET_N:
+            TPC_CUDA(cudaMemcpyAsync(d, p.tl_n, (size_t)T * 4, cudaMemcpyDeviceToDevice, s));
+            TPC_CUDA(cudaMemcpyAsync(d + T, p.tl_n, (size_t)T * 4, cudaMemcpyDeviceToDevice, s));
+            break;
+        case TPC_DUMP_TRACKLET_HITS: TPC_CUDA(tpc_int::launch_dump_tl_hits(tr->kc, p, T, d, s)); break;
+        case TPC_DUMP_TRACKLET_WORK: TPC_CUDA(tpc_int::launch_dump_tl_work(p, T, d, s)); break;
+    }
+    TPC_CUDA(cudaMemcpyAsync(dst, d, bytes, cudaMemcpyDeviceToHost, s));
+    TPC_CUDA(cudaStreamSynchronize(s));
+    if (what == TPC_DUMP_TRACKLET_N) {
+        int* h = static_cast<int*>(dst);
+        for (int t = 0; t < T; t++) h[T + t] = h[t] >= tr->params.n_min_tracklet ? 1 : 0;
+    }
+    return TPC_OK;
+}

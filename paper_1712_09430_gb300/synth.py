@@ -219,7 +219,8 @@ def crossings(tracks: Tracks, bz: float, xr=None):
                 sphi=w[it, ir], path=path[it, ir])
 
 
-def _assemble(rng, tracks, bz, cr, eff, sigma):
+def _assemble(rng, tracks, bz, cr, eff, sigma, noise_frac=0.0, noise_sector=None):
+    """Cluster loss, smearing and noise, then one (sector, row) grouping."""
     keep = rng.random(len(cr["row"])) < eff
     sec = cr["sector"][keep]
     row = cr["row"][keep]
@@ -229,6 +230,16 @@ def _assemble(rng, tracks, bz, cr, eff, sigma):
     lab = cr["track"][keep].astype(np.int64)
     yy = ty + rng.normal(0.0, sigma, len(ty)) if sigma > 0 else ty.copy()
     zz = tz + rng.normal(0.0, sigma, len(tz)) if sigma > 0 else tz.copy()
+    n_noise = int(round(noise_frac * len(ty)))
+    if n_noise:
+        ns = (rng.integers(0, N_SECTORS, n_noise) if noise_sector is None
+              else np.full(n_noise, noise_sector))
+        ns, nr, ny, nz = _noise(rng, n_noise, ns)
+        nan = np.full(n_noise, np.nan)
+        sec = np.concatenate([sec, ns]); row = np.concatenate([row, nr])
+        yy = np.concatenate([yy, ny]); zz = np.concatenate([zz, nz])
+        ty = np.concatenate([ty, nan]); tz = np.concatenate([tz, nan]); ts = np.concatenate([ts, nan])
+        lab = np.concatenate([lab, np.full(n_noise, -1)])
     base = Event(np.zeros((0, 4), np.float32), np.zeros(N_SECTORS * N_ROWS, np.int32),
                  np.zeros(0, np.int32), np.zeros(0), np.zeros(0), np.zeros(0), tracks, float(bz))
     return _rebuild(rng, base, sec, row, yy, zz, lab, ty, tz, ts)
@@ -242,20 +253,16 @@ def make_event(seed, n_prim, n_sec=0, pt_mean=0.6, noise_frac=0.05, eff=0.95, si
     if only_sector is not None:
         m = cr["sector"] == only_sector
         cr = {key: v[m] for key, v in cr.items()}
-    ev = _assemble(rng, tracks, bz, cr, eff, sigma)
-    if noise_frac and only_sector is not None:
-        # noise only in the selected sector
-        n_noise = int(round(noise_frac * ev.n))
-        ev = _add_noise_in_sector(rng, ev, n_noise, only_sector)
-    elif noise_frac:
-        ev = _add_noise(rng, ev, int(round(noise_frac * ev.n)))
-    return ev
+    return _assemble(rng, tracks, bz, cr, eff, sigma, noise_frac, only_sector)
 
 
 def _rebuild(rng, ev: Event, sec, row, y, z, lab, ty, tz, ts):
+    """Group clusters by (sector, row) in a random order inside each row,
+    cast to float32 clusters and give them a random permutation of ids."""
     n = len(y)
-    tie = rng.random(n)
-    order = np.lexsort((tie, row, sec))
+    key = ((np.asarray(sec, np.int64) * N_ROWS + np.asarray(row, np.int64)) << 32) | \
+        rng.integers(0, 1 << 32, n, dtype=np.int64)
+    order = np.argsort(key, kind="stable")
     sec, row = sec[order], row[order]
     xr = row_x()
     cl = np.empty((n, 4), dtype=np.float32)
@@ -276,6 +283,8 @@ def _unpack(ev: Event):
 
 
 def _noise(rng, n_noise, sectors):
+    """Uniform noise: row uniform, y uniform over the row's width, z uniform
+    over the sector's drift half."""
     xr = row_x()
     ns = sectors
     nr = rng.integers(0, N_ROWS, n_noise)
@@ -286,15 +295,7 @@ def _noise(rng, n_noise, sectors):
 
 
 def _add_noise(rng, ev: Event, n_noise):
-    return _add_noise_sectors(rng, ev, rng.integers(0, N_SECTORS, n_noise))
-
-
-def _add_noise_in_sector(rng, ev: Event, n_noise, sector):
-    return _add_noise_sectors(rng, ev, np.full(n_noise, sector))
-
-
-def _add_noise_sectors(rng, ev, ns):
-    n_noise = len(ns)
+    ns = rng.integers(0, N_SECTORS, n_noise)
     if n_noise == 0:
         return ev
     sec, row, y, z, lab, ty, tz, ts = _unpack(ev)

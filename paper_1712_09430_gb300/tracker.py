@@ -1,0 +1,170 @@
+"""Python convenience layer over the C ABI: numpy/torch in, numpy out.
+
+All work happens in libtpcca.so.  torch is used only for device memory and
+streams (device-resident inputs, pinned host buffers, the current stream).
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import capi
+from .capi import lib
+
+TRACK_DTYPE = np.dtype([("event", np.int32), ("sector", np.int32), ("tracklet", np.int32),
+                        ("x", np.float32), ("p", np.float32, 5), ("cov_y", np.float32, 6),
+                        ("cov_z", np.float32, 3), ("chi2", np.float32), ("ndf", np.int32),
+                        ("nhits", np.int32), ("hit_off", np.int32)])
+assert TRACK_DTYPE.itemsize == C.sizeof(capi.tpc_track)
+
+
+class TrackerError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{capi.STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+def default_params(**over) -> capi.tpc_params:
+    p = capi.tpc_params()
+    lib().tpc_params_default(C.byref(p))
+    for k, v in over.items():
+        setattr(p, k, v)
+    return p
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return C.c_void_p(a.data_ptr())
+    return a.ctypes.data_as(C.c_void_p)
+
+
+class Result:
+    """Tracks (structured numpy array, TRACK_DTYPE) and their hit ids."""
+
+    def __init__(self, tracks, hit_ids):
+        self.tracks = tracks
+        self.hit_ids = hit_ids
+
+    def hits_of(self, m):
+        t = self.tracks[m]
+        return self.hit_ids[t["hit_off"]:t["hit_off"] + t["nhits"]]
+
+    @property
+    def hit_off(self):
+        off = np.zeros(len(self.tracks) + 1, np.int64)
+        off[1:] = np.cumsum(self.tracks["nhits"])
+        return off
+
+
+class Tracker:
+    """One tpc_tracker on the current CUDA device."""
+
+    def __init__(self, row_x, bz=0.5, params=None, n_sectors=36, tan_half_open=None, z_max=250.0,
+                 **param_over):
+        import math
+        self._xr = np.ascontiguousarray(row_x, dtype=np.float32)
+        g = capi.tpc_geometry()
+        g.n_rows = len(self._xr)
+        g.n_sectors = n_sectors
+        g.row_x = self._xr.ctypes.data_as(C.POINTER(C.c_float))
+        g.tan_half_open = math.tan(math.radians(10.0)) if tan_half_open is None else tan_half_open
+        g.z_max = z_max
+        self.n_rows, self.n_sectors = g.n_rows, n_sectors
+        p = params if params is not None else default_params(**param_over)
+        h = C.c_void_p()
+        rc = lib().tpc_tracker_create(C.byref(g), float(bz), C.byref(p), C.byref(h))
+        if rc != capi.TPC_OK:
+            raise TrackerError(rc, lib().tpc_last_error(None).decode())
+        self.h = h
+        self.params = p
+        self._est_tracks = 1024
+        self._est_hits = 65536
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().tpc_tracker_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def error(self):
+        return lib().tpc_last_error(self.h).decode()
+
+    def check(self, rc, ok=(capi.TPC_OK,)):
+        if rc not in ok:
+            raise TrackerError(rc, self.error())
+        return rc
+
+    def set_params(self, **over):
+        p = capi.tpc_params()
+        C.memmove(C.byref(p), C.byref(self.params), C.sizeof(p))
+        for k, v in over.items():
+            setattr(p, k, v)
+        self.check(lib().tpc_tracker_set_params(self.h, C.byref(p)))
+        self.params = p
+
+    def track(self, clusters, row_counts, n_events, stream=None, cap_tracks=None, cap_hits=None):
+        """Track a batch.  clusters: numpy float32 [N, 4] (host) or a torch
+        CUDA tensor (device).  row_counts: numpy int32, host."""
+        rc_arr = np.ascontiguousarray(row_counts, dtype=np.int32)
+        is_dev = hasattr(clusters, "is_cuda") and clusters.is_cuda
+        if not is_dev:
+            clusters = np.ascontiguousarray(clusters, dtype=np.float32)
+        kind = capi.TPC_MEM_DEVICE if is_dev else capi.TPC_MEM_HOST
+        fixed = cap_tracks is not None or cap_hits is not None
+        ct = cap_tracks if cap_tracks is not None else self._est_tracks
+        ch = cap_hits if cap_hits is not None else self._est_hits
+        tracks = np.zeros(max(ct, 1), TRACK_DTYPE)
+        hits = np.zeros(max(ch, 1), np.int32)
+        out = capi.tpc_output(tracks.ctypes.data, hits.ctypes.data, ct, ch, capi.TPC_MEM_HOST, 0, 0)
+        rc = lib().tpc_track_sectors(self.h, _ptr(clusters), _ptr(rc_arr), int(n_events), kind,
+                                     C.byref(out), stream)
+        if rc == capi.TPC_ERR_OUTPUT_TRUNCATED and not fixed:
+            # the estimate was short: fetch the rest (no recompute)
+            ct, ch = max(out.n_tracks, 1), max(out.n_hits, 1)
+            self._est_tracks, self._est_hits = int(ct * 1.25) + 16, int(ch * 1.25) + 256
+            tracks = np.zeros(ct, TRACK_DTYPE)
+            hits = np.zeros(ch, np.int32)
+            out = capi.tpc_output(tracks.ctypes.data, hits.ctypes.data, ct, ch, capi.TPC_MEM_HOST,
+                                  0, 0)
+            rc = lib().tpc_fetch_output(self.h, C.byref(out))
+        self.check(rc)
+        return Result(tracks[:out.n_tracks], hits[:out.n_hits])
+
+    def dump(self, what):
+        n = C.c_int64()
+        # probe the size
+        rc = lib().tpc_debug_dump(self.h, what, _ptr(np.zeros(1, np.int32)), 0, C.byref(n))
+        if rc not in (capi.TPC_OK, capi.TPC_ERR_OUTPUT_TRUNCATED):
+            self.check(rc)
+        k = int(n.value)
+        if what in (capi.TPC_DUMP_LINKS_RAW, capi.TPC_DUMP_LINKS, capi.TPC_DUMP_TRACKLET_N):
+            a = np.zeros((2, k), np.int32)
+        elif what == capi.TPC_DUMP_STARTS:
+            a = np.zeros(k, np.int32)
+        elif what == capi.TPC_DUMP_TRACKLETS:
+            a = np.zeros((k, 16), np.float32)
+        elif what == capi.TPC_DUMP_TRACKLET_WORK:
+            a = np.zeros((4, k), np.int32)
+        else:
+            a = np.zeros((k, self.n_rows), np.int32)
+        self.check(lib().tpc_debug_dump(self.h, what, _ptr(a), a.nbytes, C.byref(n)))
+        return a
+
+    def stage_times(self):
+        ms = (C.c_float * 6)()
+        self.check(lib().tpc_stage_times(self.h, ms, 6))
+        return list(ms)

@@ -1,0 +1,228 @@
+"""GPU (CUDA, through the C ABI) against the CPU oracle.
+
+Exact mode (kernels built with -fmad=false) against the FP32_EXACT oracle:
+every stage bit-exact: raw and cleaned links, start hits, tracklet cluster
+lists, tracklet filter states, selected tracks and their clusters.
+Production mode against the FP64 oracle: efficiency, clone and fake rates
+within 0.2 percentage points; parameters of tracks with identical cluster
+lists within 1e-4 relative + 1e-3 absolute (cm for y and z).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import qa  # noqa: E402
+from gpu_util import XR, assert_exact_equal, gpu_run, oracle_run  # noqa: E402
+from paper_1712_09430_gb300 import capi, synth as S  # noqa: E402
+from paper_1712_09430_gb300.tracker import Tracker, TrackerError  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def events():
+    return {
+        "c1": S.single_sector(),
+        "c2": S.pp_event(),
+        "c3s": S.central_event(seed=3, scale=0.1),
+        "tf": S.time_frame(seed=4, n_coll=4, scale=0.3),
+        "lowB": S.make_event(21, 300, 60, pt_mean=0.3, noise_frac=0.2, bz=0.2),
+    }
+
+
+@pytest.mark.parametrize("name", ["c1", "c2", "c3s", "tf", "lowB"])
+def test_exact_parity_every_stage(events, name):
+    ev = events[name]
+    g = gpu_run(ev.clusters, ev.row_counts, 1, bz=ev.bz, exact_fp32=1)
+    o = oracle_run(ev.clusters, ev.row_counts, 1, bz=ev.bz, mode="f32")
+    assert len(o["trk_t"]) > 0
+    assert_exact_equal(g, o)
+
+
+def test_exact_parity_multi_event_batch(events):
+    evs = [events["c2"], events["c3s"], events["c1"], S.pp_event(seed=9)]
+    cl, rc = S.concat_events(evs)
+    g = gpu_run(cl, rc, len(evs), exact_fp32=1)
+    o = oracle_run(cl, rc, len(evs), mode="f32")
+    assert_exact_equal(g, o)
+    # each event alone gives the same tracks (units are independent)
+    off_cl = 0
+    for e_i, ev in enumerate(evs):
+        ge = gpu_run(ev.clusters, ev.row_counts, 1, exact_fp32=1, dumps=False)
+        gb = g["tracks"][g["tracks"]["event"] == e_i]
+        assert len(gb) == len(ge["tracks"])
+        hits_b = np.concatenate([g["hit_ids"][t["hit_off"]:t["hit_off"] + t["nhits"]] for t in gb]) \
+            if len(gb) else np.zeros(0, np.int32)
+        np.testing.assert_array_equal(hits_b - off_cl, ge["hit_ids"])
+        for f in ("sector", "nhits", "ndf", "p", "cov_y", "cov_z", "chi2", "x"):
+            np.testing.assert_array_equal(gb[f], ge["tracks"][f])
+        off_cl += ev.n
+
+
+@pytest.mark.parametrize("over", [dict(bin_target=0.5), dict(bin_target=8.0, threads_per_row=32),
+                                  dict(bin_target=2.0, threads_per_row=256),
+                                  dict(plain_per_sector=1), dict(use_graph=1),
+                                  dict(tracklets_per_warp=4)])
+def test_execution_params_do_not_change_results(events, over):
+    ev = events["c3s"]
+    base = gpu_run(ev.clusters, ev.row_counts, 1, exact_fp32=1)
+    g = gpu_run(ev.clusters, ev.row_counts, 1, exact_fp32=1, **over)
+    for k in ("up_raw", "dn_raw", "start", "tl_n", "tl_hits"):
+        np.testing.assert_array_equal(g[k], base[k], err_msg=k)
+    np.testing.assert_array_equal(g["tl_f"].view(np.uint32), base["tl_f"].view(np.uint32))
+    np.testing.assert_array_equal(g["hit_ids"], base["hit_ids"])
+
+
+def test_graph_replay_repeats(events):
+    ev = events["c3s"]
+    with Tracker(XR, bz=ev.bz, exact_fp32=1, use_graph=1) as tr:
+        r1 = tr.track(ev.clusters, ev.row_counts, 1)
+        r2 = tr.track(ev.clusters, ev.row_counts, 1)
+        r3 = tr.track(ev.clusters, ev.row_counts, 1)
+    for r in (r2, r3):
+        np.testing.assert_array_equal(r.hit_ids, r1.hit_ids)
+        np.testing.assert_array_equal(r.tracks.view(np.uint8), r1.tracks.view(np.uint8))
+
+
+def _labels_batch(evs):
+    return np.concatenate([np.where(e.label >= 0, e.label + i * 10_000_000, -1)
+                           for i, e in enumerate(evs)])
+
+
+def test_production_vs_fp64(events):
+    evs = [events["c3s"], events["c2"], events["tf"]]
+    cl, rc = S.concat_events(evs)
+    g = gpu_run(cl, rc, len(evs), exact_fp32=0)
+    o = oracle_run(cl, rc, len(evs), mode="f64")
+    lab = _labels_batch(evs)
+    qg = qa.qa(lab, rc, g["hit_off"], g["hit_ids"])
+    qo = qa.qa(lab, rc, o["trk_hit_off"], o["trk_hits"])
+    for key in ("eff", "clone", "fake"):
+        assert abs(qg[key] - qo[key]) <= 0.002, (key, qg[key], qo[key])
+    # parameters of tracks found with identical cluster lists
+    ok = {}
+    for m, t in enumerate(o["trk_t"]):
+        h = o["trk_hits"][o["trk_hit_off"][m]:o["trk_hit_off"][m + 1]]
+        ok[(int(o["start"][t]), tuple(h.tolist()))] = o["tl_f"][t]
+    n_cmp = 0
+    gst = g["start"]
+    for m, tr in enumerate(g["tracks"]):
+        h = g["hit_ids"][tr["hit_off"]:tr["hit_off"] + tr["nhits"]]
+        key = (int(gst[tr["tracklet"]]), tuple(h.tolist()))
+        if key not in ok:
+            continue
+        f = ok[key]
+        got = np.array([tr["x"], *tr["p"]], np.float64)
+        want = f[0:6]
+        tol = 1e-3 + 1e-4 * np.abs(want)
+        assert np.all(np.abs(got - want) <= tol), (got, want)
+        n_cmp += 1
+    assert n_cmp >= 0.9 * len(g["tracks"])
+
+
+# ------------------------------------------------------------------ edges
+
+def test_empty_inputs():
+    rc = np.zeros(36 * 159, np.int32)
+    g = gpu_run(np.zeros((0, 4), np.float32), rc, 1, dumps=False)
+    assert len(g["tracks"]) == 0
+    g = gpu_run(np.zeros((0, 4), np.float32), np.zeros(0, np.int32), 0, dumps=False)
+    assert len(g["tracks"]) == 0
+
+
+def test_ragged_sparse_rows():
+    # a handful of clusters on scattered rows, single-cluster rows, no tracks
+    rng = np.random.default_rng(3)
+    rc = np.zeros(36 * 159, np.int32)
+    idx = rng.choice(36 * 159, 50, replace=False)
+    rc[idx] = rng.integers(1, 3, 50)
+    n = int(rc.sum())
+    rows = np.repeat(np.arange(36 * 159), rc) % 159
+    secs = np.repeat(np.arange(36 * 159), rc) // 159
+    cl = np.zeros((n, 4), np.float32)
+    cl[:, 0] = XR[rows]
+    cl[:, 1] = rng.uniform(-5, 5, n)
+    cl[:, 2] = np.where(secs < 18, 1, -1) * rng.uniform(0, 250, n)
+    cl.view(np.uint32)[:, 3] = np.arange(n)
+    g = gpu_run(cl, rc, 1, exact_fp32=1)
+    o = oracle_run(cl, rc, 1, mode="f32")
+    assert_exact_equal(g, o)
+
+
+def test_dense_row_at_limit():
+    # one row at the maximum cluster count and its neighbours dense too
+    rng = np.random.default_rng(4)
+    rc = np.zeros(36 * 159, np.int32)
+    rc[80:83] = [2000, capi.TPC_MAX_ROW_CLUSTERS, 2000]
+    n = int(rc.sum())
+    rows = np.repeat(np.arange(36 * 159), rc) % 159
+    cl = np.zeros((n, 4), np.float32)
+    cl[:, 0] = XR[rows]
+    cl[:, 1] = rng.uniform(-25, 25, n)
+    cl[:, 2] = rng.uniform(0, 250, n)
+    cl.view(np.uint32)[:, 3] = rng.permutation(n)
+    g = gpu_run(cl, rc, 1, exact_fp32=1)
+    o = oracle_run(cl, rc, 1, mode="f32")
+    assert_exact_equal(g, o)
+
+
+def test_invalid_inputs_are_rejected(events):
+    ev = events["c2"]
+    with Tracker(XR, bz=ev.bz) as tr:
+        bad = ev.clusters.copy()
+        bad[17, 1] = np.nan
+        with pytest.raises(TrackerError) as e:
+            tr.track(bad, ev.row_counts, 1)
+        assert e.value.code == capi.TPC_ERR_INVALID
+        bad = ev.clusters.copy()
+        bad[5, 0] += 0.5
+        with pytest.raises(TrackerError) as e:
+            tr.track(bad, ev.row_counts, 1)
+        assert e.value.code == capi.TPC_ERR_INVALID
+        rc = ev.row_counts.copy()
+        rc[0] = capi.TPC_MAX_ROW_CLUSTERS + 1
+        with pytest.raises(TrackerError) as e:
+            tr.track(np.zeros((int(rc.sum()), 4), np.float32), rc, 1)
+        assert e.value.code == capi.TPC_ERR_INVALID
+        rc = ev.row_counts.copy()
+        rc[3] = -1
+        with pytest.raises(TrackerError):
+            tr.track(ev.clusters, rc, 1)
+        # the tracker is still usable
+        r = tr.track(ev.clusters, ev.row_counts, 1)
+        assert len(r.tracks) > 0
+
+
+def test_output_truncation_and_fetch(events):
+    ev = events["c3s"]
+    with Tracker(XR, bz=ev.bz) as tr:
+        full = tr.track(ev.clusters, ev.row_counts, 1)
+        with pytest.raises(TrackerError) as e:
+            tr.track(ev.clusters, ev.row_counts, 1, cap_tracks=5, cap_hits=50)
+        assert e.value.code == capi.TPC_ERR_OUTPUT_TRUNCATED
+        # default path: short estimate, then fetch the rest without recompute
+        tr._est_tracks, tr._est_hits = 3, 10
+        r = tr.track(ev.clusters, ev.row_counts, 1)
+        np.testing.assert_array_equal(r.hit_ids, full.hit_ids)
+
+
+def test_device_input_equals_host_input(events):
+    ev = events["c3s"]
+    dev = torch.from_numpy(ev.clusters).cuda()
+    with Tracker(XR, bz=ev.bz) as tr:
+        a = tr.track(ev.clusters, ev.row_counts, 1)
+        b = tr.track(dev, ev.row_counts, 1)
+    np.testing.assert_array_equal(a.hit_ids, b.hit_ids)
+    np.testing.assert_array_equal(a.tracks.view(np.uint8), b.tracks.view(np.uint8))
+
+
+def test_full_size_central_batch_exact():
+    """The benchmark's workload size (full central events, batched launch,
+    graph replay) against the FP32 oracle, every stage."""
+    evs = [S.central_event(seed=3 + i) for i in range(2)]
+    cl, rc = S.concat_events(evs)
+    g = gpu_run(cl, rc, len(evs), exact_fp32=1, use_graph=1)
+    o = oracle_run(cl, rc, len(evs), mode="f32")
+    assert_exact_equal(g, o)
