@@ -241,36 +241,13 @@ def run_ours(args):
     value = N * world / (ms * 1e-3)
 
     # ---- end to end through the C ABI with pinned host buffers
-    pin_cl = torch.from_numpy(cl_np).pin_memory()
-    host_tr = torch.empty(cap_t * TRACK_DTYPE.itemsize, dtype=torch.uint8).pin_memory()
-    host_h = torch.empty(cap_h, dtype=torch.int32).pin_memory()
-    hout = capi.tpc_output(host_tr.data_ptr(), host_h.data_ptr(), cap_t, cap_h, capi.TPC_MEM_HOST, 0, 0)
-
-    def step_e2e():
-        r = L.tpc_track_sectors(tr.h, C.c_void_p(pin_cl.data_ptr()), rc_ptr, B, capi.TPC_MEM_HOST,
-                                C.byref(hout), sp)
-        if r != capi.TPC_OK:
-            raise RuntimeError(f"tpc_track_sectors (host): {tr.error()}")
-
-    for _ in range(2):
-        step_e2e()
-    torch.cuda.synchronize()
-    k2 = max(3, args.steps // 2)
-    t1 = time.perf_counter()
-    for _ in range(k2):
-        step_e2e()
-    torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t1) / k2
-    h2d = N * 16 + len(rc_np) * 4
-    d2h = hout.n_tracks * TRACK_DTYPE.itemsize + hout.n_hits * 4 + 64
-    e2e = {"value": N * world / e2e_s, "unit": "clusters/s", "h2d_bytes_per_step": int(h2d),
-           "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_s * 1e3}
-
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(L, tr, cl_np, rc_ptr, rc_np, B, N, world, sp, cap_t, cap_h, args)
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return
-
     # ---- roofline of the dominant kernel (tracklet construction)
     peaks = {}
     try:
@@ -312,6 +289,41 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_e2e(L, tr, cl_np, rc_ptr, rc_np, B, N, world, sp, cap_t, cap_h, args):
+    """Same metric through the C ABI with pinned HOST input and output: the
+    H2D of the clusters and row counts and the D2H of the tracks are inside
+    every timed step."""
+    import ctypes as C
+    import torch
+    from paper_1712_09430_gb300 import capi
+    from paper_1712_09430_gb300.tracker import TRACK_DTYPE
+    pin_cl = torch.from_numpy(cl_np).pin_memory()
+    host_tr = torch.empty(cap_t * TRACK_DTYPE.itemsize, dtype=torch.uint8).pin_memory()
+    host_h = torch.empty(cap_h, dtype=torch.int32).pin_memory()
+    hout = capi.tpc_output(host_tr.data_ptr(), host_h.data_ptr(), cap_t, cap_h, capi.TPC_MEM_HOST,
+                           0, 0)
+
+    def step_e2e():
+        r = L.tpc_track_sectors(tr.h, C.c_void_p(pin_cl.data_ptr()), rc_ptr, B, capi.TPC_MEM_HOST,
+                                C.byref(hout), sp)
+        if r != capi.TPC_OK:
+            raise RuntimeError(f"tpc_track_sectors (host): {tr.error()}")
+
+    for _ in range(3):
+        step_e2e()
+    torch.cuda.synchronize()
+    k2 = max(3, args.steps // 2)
+    t1 = time.perf_counter()
+    for _ in range(k2):
+        step_e2e()
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t1) / k2
+    h2d = N * 16 + len(rc_np) * 4
+    d2h = hout.n_tracks * TRACK_DTYPE.itemsize + hout.n_hits * 4 + 64
+    return {"value": N * world / e2e_s, "unit": "clusters/s", "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_s * 1e3, "steps": k2}
+
+
 def algorithmic_bytes(tr, N, T):
     """Bytes the tracklet constructor moves by its own stage structure,
     counted exactly per tracklet by the kernel (TPC_DUMP_TRACKLET_WORK):
@@ -332,7 +344,7 @@ def algorithmic_bytes(tr, N, T):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--batch", type=int, default=8, help="central events per step (per GPU)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
@@ -342,6 +354,7 @@ def main():
     ap.add_argument("--tracklets-per-warp", type=int, default=32)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

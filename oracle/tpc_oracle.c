@@ -443,28 +443,33 @@ static void orc_tracklet(const orc_ctx* c, const orc_unit* u, const int* up2, in
     orc_reset_cov(&st, c->sy2, c->sz2, c->var_s, c->var_q, c->var_t);
     real chi2 = RC(0);
 
-    /* Phase 1: the chain, then outward row by row. */
+    /* Phase 1: the chain, then outward row by row.  Every row step predicts
+     * on a copy of the state (T5); the state itself moves only when a cluster
+     * is filtered, so after a miss the next prediction starts again from the
+     * last filtered cluster. */
     int have = 0, stopped = 0, r_out = -1;
-    orc_state last;
+    orc_state pr;
     for (int h = h0; h >= 0; h = up2[h]) {
         int r = u->row[h];
-        if (!orc_prop(&st, RC(c->row_x[r]), c->kB, c->s_max) || orc_outside(c, &st, r)) {
+        pr = st;
+        if (!orc_prop(&pr, RC(c->row_x[r]), c->kB, c->s_max) || orc_outside(c, &pr, r)) {
             stopped = 1;
             break;
         }
-        orc_update(&st, u->y[h], u->z[h], c->sy2, c->sz2, &chi2);
-        last = st;
+        orc_update(&pr, u->y[h], u->z[h], c->sy2, c->sz2, &chi2);
+        st = pr;
         r_out = r;
         have = 1;
     }
     if (!stopped) {
         int miss = 0;
         for (int r = u->row[hL] + 1; r < c->n_rows; r++) {
-            if (!orc_prop(&st, RC(c->row_x[r]), c->kB, c->s_max) || orc_outside(c, &st, r)) break;
-            int j = orc_search(c, u, &st, r);
+            pr = st;
+            if (!orc_prop(&pr, RC(c->row_x[r]), c->kB, c->s_max) || orc_outside(c, &pr, r)) break;
+            int j = orc_search(c, u, &pr, r);
             if (j >= 0) {
-                orc_update(&st, u->y[j], u->z[j], c->sy2, c->sz2, &chi2);
-                last = st;
+                orc_update(&pr, u->y[j], u->z[j], c->sy2, c->sz2, &chi2);
+                st = pr;
                 r_out = r;
                 miss = 0;
             } else if (++miss > c->g_max) {
@@ -477,19 +482,19 @@ static void orc_tracklet(const orc_ctx* c, const orc_unit* u, const int* up2, in
     for (int k = 0; k < ORC_NTF; k++) f[k] = 0.0;
     if (!have) return;
 
-    /* Phase 2: fresh covariance, inward from P1's outermost hit to row 0. */
-    st = last;
+    /* Phase 2: fresh covariance, inward from P1's outermost cluster (where
+     * the state now is) to row 0. */
     orc_reset_cov(&st, c->sy2, c->sz2, c->var_s, c->var_q, c->var_t);
     chi2 = RC(0);
     int n = 0, miss = 0;
-    orc_state inner = st;
     for (int r = r_out; r >= 0; r--) {
-        if (!orc_prop(&st, RC(c->row_x[r]), c->kB, c->s_max) || orc_outside(c, &st, r)) break;
-        int j = orc_search(c, u, &st, r);
+        pr = st;
+        if (!orc_prop(&pr, RC(c->row_x[r]), c->kB, c->s_max) || orc_outside(c, &pr, r)) break;
+        int j = orc_search(c, u, &pr, r);
         if (j >= 0) {
-            orc_update(&st, u->y[j], u->z[j], c->sy2, c->sz2, &chi2);
+            orc_update(&pr, u->y[j], u->z[j], c->sy2, c->sz2, &chi2);
+            st = pr;
             hits[n++] = j; /* rows descending for now */
-            inner = st;
             miss = 0;
         } else if (++miss > c->g_max) {
             break;
@@ -497,7 +502,7 @@ static void orc_tracklet(const orc_ctx* c, const orc_unit* u, const int* up2, in
     }
     *n_out = n;
     for (int a = 0, b = n - 1; a < b; a++, b--) { int x = hits[a]; hits[a] = hits[b]; hits[b] = x; }
-    if (n > 0) orc_store(&inner, chi2, f);
+    if (n > 0) orc_store(&st, chi2, f); /* the state at the innermost cluster */
     *alive = n >= c->n_min_tracklet;
 }
 

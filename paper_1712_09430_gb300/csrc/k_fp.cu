@@ -254,10 +254,13 @@ __device__ __forceinline__ bool outside(const State& st, float X, const KConst& 
 
 // Closest cluster of row rr to the predicted state inside the window
 // |dy| <= wy, |dz| <= wz with w = clamp(n_sigma sqrt(S), w_min, w_max);
-// distance d2 = dy^2 / S_y + dz^2 / S_z, ties by smaller id.  Returns the
-// binned index or -1.
-__device__ __forceinline__ int search_row(const State& st, int rr, const KConst& k, const DevPtrs& p,
-                                          float4& found, int4& work)
+// distance d2 = dy^2 / S_y + dz^2 / S_z, ties by smaller id.  The G lanes of
+// a group share the candidate scan (lane gl takes every G-th candidate) and
+// reduce the best (d2, id) with warp shuffles; every lane of the group
+// returns the same binned index (or -1).
+template <int G>
+__device__ __forceinline__ int search_row(const State& st, int rr, const KConst& k,
+                                          const DevPtrs& p, int gl, unsigned gmask, int4& work)
 {
     const float Sy = k.sy2 + st.cy[0];
     const float Sz = k.sz2 + st.cz[0];
@@ -279,7 +282,7 @@ __device__ __forceinline__ int search_row(const State& st, int rr, const KConst&
         const int* row_bins = p.bin_off + g.bin_base + bz * g.ny;
         const int j0 = __ldg(row_bins + y0), j1 = __ldg(row_bins + y1 + 1);
         work.z += j1 - j0;
-        for (int j = j0; j < j1; j++) {
+        for (int j = j0 + gl; j < j1; j += G) {
             const float4 c = __ldg(p.hits + j);
             const float dy = c.x - st.y;
             const float dz = c.y - st.z;
@@ -290,152 +293,207 @@ __device__ __forceinline__ int search_row(const State& st, int rr, const KConst&
                 best = j;
                 bd2 = d2;
                 bid = id;
-                found = c;
+            }
+        }
+    }
+    if (G > 1) {
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) {
+            const int ob = __shfl_xor_sync(gmask, best, o);
+            const float od = __shfl_xor_sync(gmask, bd2, o);
+            const unsigned oi = __shfl_xor_sync(gmask, bid, o);
+            if (ob >= 0 && (best < 0 || od < bd2 || (od == bd2 && oi < bid))) {
+                best = ob;
+                bd2 = od;
+                bid = oi;
             }
         }
     }
     return best;
 }
 
-// One tracklet t (Sec. 2 step 2): seed from the CA chain, Phase 1 through the
-// chain and outward row by row, Phase 2 with a fresh covariance inward from
-// the outermost cluster to row 0; the Phase-2 clusters are the tracklet's.
-__device__ void build_tracklet(int t, const KConst& k, const float* xs, const DevPtrs& p)
+// Tracklet construction (Sec. 2 step 2) as a per-lane state machine, so that
+// every iteration of the warp is one uniform row step: predict a copy of the
+// state to the row, take the chain cluster (phase 0) or search the window
+// (phases 1, 2), filter on a hit.  Phase 0/1: Phase 1 through the seed chain,
+// then outward; phase 2: fresh covariance, inward from the outermost cluster
+// to row 0, collecting the tracklet's clusters.
+struct Lane {
+    int t;        // tracklet, -1 idle
+    int phase;    // 0 chain, 1 outward search, 2 inward search
+    int r;        // row of the next step
+    int h;        // next chain hit (phase 0)
+    int ubase;    // row index of row 0 of the unit
+    int r_out;    // row of the outermost filtered cluster
+    int miss, n;
+    bool have;
+    float chi2;
+    State st;
+    int4 work;
+};
+
+__device__ __forceinline__ void lane_init(Lane& L, int t, const KConst& k, const float* xs,
+                                          const DevPtrs& p)
 {
     const int NR = k.n_rows;
     const int rr0 = p.t_row[t];
-    const int ubase = rr0 - rr0 % NR;  // row index of row 0 of this unit
+    const int2 e = p.t_end[t];
+    L.t = t;
+    L.ubase = rr0 - rr0 % NR;
+    const int r0 = rr0 - L.ubase;
     const int h0 = p.start[t];
-    int4 work = make_int4(0, 0, 0, 1);
-    int hL = h0, rL = rr0 - ubase;
-    for (int j = p.up2[hL]; j >= 0; j = p.up2[j]) {
-        hL = j;
-        rL++;
-        work.w++;
-    }
+    const int rL = r0 + e.y - 1;
     const float4 c0 = p.hits[h0];
-    const float4 cL = p.hits[hL];
-    const int r0 = rr0 - ubase;
-    State st;
-    st.x = xs[r0];
-    st.y = c0.x;
-    st.z = c0.y;
-    {
-        const float dx = xs[rL] - xs[r0], dy = cL.x - c0.x, dz = cL.y - c0.y;
-        const float l = sqrtf(dx * dx + dy * dy);
-        st.s = dy / l;
-        st.t = dz / l;
-    }
-    st.q = 0.0f;
-    reset_cov(st, k);
-    float chi2 = 0.0f;
-
-    // Phase 1: the chain, then outward.
-    bool have = false, stopped = false;
-    int r_out = -1;
-    State last = st;
-    {
-        int r = r0;
-        for (int h = h0; h >= 0; h = p.up2[h], r++) {
-            if (!propagate(st, xs[r], k.kB, k.s_max) || outside(st, xs[r], k)) {
-                stopped = true;
-                break;
-            }
-            const float4 c = p.hits[h];
-            update(st, c.x, c.y, k.sy2, k.sz2, chi2);
-            last = st;
-            r_out = r;
-            have = true;
-        }
-    }
-    if (!stopped) {
-        int miss = 0;
-        for (int r = rL + 1; r < NR; r++) {
-            if (!propagate(st, xs[r], k.kB, k.s_max) || outside(st, xs[r], k)) break;
-            float4 c;
-            const int j = search_row(st, ubase + r, k, p, c, work);
-            if (j >= 0) {
-                update(st, c.x, c.y, k.sy2, k.sz2, chi2);
-                last = st;
-                r_out = r;
-                miss = 0;
-            } else if (++miss > k.g_max) {
-                break;
-            }
-        }
-    }
-    float* f = p.tl_f + (size_t)t * kTlFloats;
-    if (!have) {
-        p.tl_work[t] = work;
-        p.tl_n[t] = 0;
-        for (int j = 0; j < kTlFloats; j++) f[j] = 0.0f;
-        return;
-    }
-    // Phase 2
-    st = last;
-    reset_cov(st, k);
-    chi2 = 0.0f;
-    int n = 0, miss = 0;
-    int* hits = p.tl_hits + (size_t)t * NR;
-    State inner = st;
-    for (int r = r_out; r >= 0; r--) {
-        if (!propagate(st, xs[r], k.kB, k.s_max) || outside(st, xs[r], k)) break;
-        float4 c;
-        const int j = search_row(st, ubase + r, k, p, c, work);
-        if (j >= 0) {
-            update(st, c.x, c.y, k.sy2, k.sz2, chi2);
-            hits[n++] = j;  // rows descending
-            inner = st;
-            miss = 0;
-        } else if (++miss > k.g_max) {
-            break;
-        }
-    }
-    p.tl_n[t] = n;
-    p.tl_work[t] = work;
-    if (n == 0) {
-        for (int j = 0; j < kTlFloats; j++) f[j] = 0.0f;
-        return;
-    }
-    float4* f4 = reinterpret_cast<float4*>(f);
-    f4[0] = make_float4(inner.x, inner.y, inner.z, inner.s);
-    f4[1] = make_float4(inner.t, inner.q, inner.cy[0], inner.cy[1]);
-    f4[2] = make_float4(inner.cy[2], inner.cy[3], inner.cy[4], inner.cy[5]);
-    f4[3] = make_float4(inner.cz[0], inner.cz[1], inner.cz[2], chi2);
+    const float4 cL = p.hits[e.x];
+    L.st.x = xs[r0];
+    L.st.y = c0.x;
+    L.st.z = c0.y;
+    const float dx = xs[rL] - xs[r0], dy = cL.x - c0.x, dz = cL.y - c0.y;
+    const float l = sqrtf(dx * dx + dy * dy);
+    L.st.s = dy / l;
+    L.st.t = dz / l;
+    L.st.q = 0.0f;
+    reset_cov(L.st, k);
+    L.chi2 = 0.0f;
+    L.phase = 0;
+    L.r = r0;
+    L.h = h0;
+    L.have = false;
+    L.r_out = -1;
+    L.miss = 0;
+    L.n = 0;
+    L.work = make_int4(0, 0, 0, e.y);
 }
 
-// Persistent, dynamically scheduled constructor: warps take 32 entries of
-// the length-sorted schedule at a time from a global counter (long expected
-// tracks first), one lane per tracklet.
-__global__ void __launch_bounds__(256) k_tracklets_sched(KConst k, const float* __restrict__ row_x,
-                                                         DevPtrs p)
+__device__ __forceinline__ void lane_finish(Lane& L, const KConst& k, const DevPtrs& p, bool writer)
+{
+    if (writer) {
+        const int t = L.t;
+        p.tl_n[t] = L.n;
+        p.tl_work[t] = L.work;
+        float4* f4 = reinterpret_cast<float4*>(p.tl_f + (size_t)t * kTlFloats);
+        if (L.n > 0) {
+            const State& s = L.st;
+            f4[0] = make_float4(s.x, s.y, s.z, s.s);
+            f4[1] = make_float4(s.t, s.q, s.cy[0], s.cy[1]);
+            f4[2] = make_float4(s.cy[2], s.cy[3], s.cy[4], s.cy[5]);
+            f4[3] = make_float4(s.cz[0], s.cz[1], s.cz[2], L.chi2);
+        } else {
+            const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+            f4[0] = z; f4[1] = z; f4[2] = z; f4[3] = z;
+        }
+    }
+    L.t = -1;
+}
+
+template <int G>
+__device__ __forceinline__ void lane_step(Lane& L, const KConst& k, const float* xs,
+                                          const DevPtrs& p, int gl, unsigned gmask)
+{
+    const int NR = k.n_rows;
+    State pr = L.st;
+    const float X = xs[L.r];
+    const bool ok = propagate(pr, X, k.kB, k.s_max) && !outside(pr, X, k);
+    int j = -1;
+    if (ok) j = L.phase == 0 ? L.h : search_row<G>(pr, L.ubase + L.r, k, p, gl, gmask, L.work);
+    bool end_phase = !ok;
+    if (j >= 0) {
+        const float4 c = __ldg(p.hits + j);
+        update(pr, c.x, c.y, k.sy2, k.sz2, L.chi2);
+        L.st = pr;
+        if (L.phase == 2) {
+            if (gl == 0) p.tl_hits[(size_t)L.t * NR + L.n] = j;  // rows descending
+            L.n++;
+        } else {
+            L.r_out = L.r;
+            L.have = true;
+        }
+        L.miss = 0;
+    } else if (ok) {
+        end_phase = ++L.miss > k.g_max;
+    }
+    if (!end_phase) {
+        if (L.phase == 0) {
+            L.h = p.up2[L.h];
+            L.r++;
+            if (L.h < 0) {
+                L.phase = 1;
+                end_phase = L.r >= NR;
+            }
+        } else if (L.phase == 1) {
+            end_phase = ++L.r >= NR;
+        } else {
+            end_phase = --L.r < 0;
+        }
+    }
+    if (end_phase) {
+        if (L.phase < 2 && L.have) {
+            L.phase = 2;
+            reset_cov(L.st, k);
+            L.chi2 = 0.0f;
+            L.r = L.r_out;
+            L.n = 0;
+            L.miss = 0;
+        } else {
+            lane_finish(L, k, p, gl == 0);
+        }
+    }
+}
+
+// Persistent, dynamically scheduled constructor: idle lane groups take the
+// next entries of the length-sorted schedule (long expected tracks first)
+// from a global counter, with one warp-aggregated atomic per refill.
+template <int G>
+__global__ void __launch_bounds__(256, 3) k_tracklets_sched(KConst k, const float* __restrict__ row_x,
+                                                            DevPtrs p)
 {
     __shared__ float xs[TPC_MAX_ROWS];
     for (int r = threadIdx.x; r < k.n_rows; r += blockDim.x) xs[r] = row_x[r];
     __syncthreads();
+    const unsigned FULL = 0xffffffffu;
     const int T = p.counters[C_T];
     const int lane = threadIdx.x & 31;
+    const int gl = lane % G;
+    const int gbase = lane - gl;
+    const unsigned gmask = (G == 32) ? FULL : (((1u << G) - 1u) << gbase);
+    Lane L;
+    L.t = -1;
+    bool done = false;
     while (true) {
-        int w = 0;
-        if (lane == 0) w = atomicAdd(&p.counters[C_WORK], 32);
-        w = __shfl_sync(0xffffffffu, w, 0);
-        if (w >= T) break;
-        const int i = w + lane;
-        if (i < T) build_tracklet(p.sched[i], k, xs, p);
+        const unsigned need = __ballot_sync(FULL, L.t < 0 && !done && gl == 0);
+        if (need) {
+            const int leader = __ffs(need) - 1;
+            int base = 0;
+            if (lane == leader) base = atomicAdd(&p.counters[C_WORK], __popc(need));
+            base = __shfl_sync(FULL, base, leader);
+            int i = base + __popc(need & ((1u << gbase) - 1u));
+            const bool mine = (need >> gbase) & 1u;
+            if (mine) {
+                if (i < T) lane_init(L, p.sched[i], k, xs, p);
+                else done = true;
+            }
+        }
+        if (__all_sync(FULL, done)) break;
+        if (L.t >= 0) lane_step<G>(L, k, xs, p, gl, gmask);
     }
 }
 
-// Plain form: the tracklets of units [u0, u1) in canonical order, static
-// assignment (one thread per track candidate, Sec. 3).
-__global__ void __launch_bounds__(256) k_tracklets_plain(KConst k, const float* __restrict__ row_x,
-                                                         DevPtrs p, int u0, int u1)
+// Plain form (the Run 1/2 scheme, Sec. 3): the tracklets of units [u0, u1)
+// in canonical order, statically assigned, each thread running one tracklet
+// to completion before the next.
+__global__ void __launch_bounds__(256, 3) k_tracklets_plain(KConst k, const float* __restrict__ row_x,
+                                                            DevPtrs p, int u0, int u1)
 {
     __shared__ float xs[TPC_MAX_ROWS];
     for (int r = threadIdx.x; r < k.n_rows; r += blockDim.x) xs[r] = row_x[r];
     __syncthreads();
     const int t0 = p.start_off[u0 * k.n_rows], t1 = p.start_off[u1 * k.n_rows];
-    for (int t = t0 + blockIdx.x * blockDim.x + threadIdx.x; t < t1; t += gridDim.x * blockDim.x)
-        build_tracklet(t, k, xs, p);
+    const unsigned self = 1u << (threadIdx.x & 31);
+    for (int t = t0 + blockIdx.x * blockDim.x + threadIdx.x; t < t1; t += gridDim.x * blockDim.x) {
+        Lane L;
+        lane_init(L, t, k, xs, p);
+        while (L.t >= 0) lane_step<1>(L, k, xs, p, 0, self);
+    }
 }
 
 // -------------------------------------------------------------- launchers
@@ -455,11 +513,18 @@ cudaError_t launch_neighbours(const KConst& k, const float* row_x_dev, const Dev
 cudaError_t launch_tracklets(const KConst& k, const float* row_x_dev, const DevPtrs& p, int n_sm,
                              int lanes_per_tracklet, int u0, int u1, cudaStream_t s)
 {
-    (void)lanes_per_tracklet;
-    if (u0 < 0) {
-        k_tracklets_sched<<<n_sm * 8, 256, 0, s>>>(k, row_x_dev, p);
-    } else {
+    if (u0 >= 0) {
         k_tracklets_plain<<<n_sm * 2, 256, 0, s>>>(k, row_x_dev, p, u0, u1);
+        return cudaGetLastError();
+    }
+    const int grid = n_sm * 3;  // 3 resident CTAs of 256 per SM
+    switch (lanes_per_tracklet) {
+        case 1: k_tracklets_sched<1><<<grid, 256, 0, s>>>(k, row_x_dev, p); break;
+        case 2: k_tracklets_sched<2><<<grid, 256, 0, s>>>(k, row_x_dev, p); break;
+        case 4: k_tracklets_sched<4><<<grid, 256, 0, s>>>(k, row_x_dev, p); break;
+        case 8: k_tracklets_sched<8><<<grid, 256, 0, s>>>(k, row_x_dev, p); break;
+        case 16: k_tracklets_sched<16><<<grid, 256, 0, s>>>(k, row_x_dev, p); break;
+        default: k_tracklets_sched<32><<<grid, 256, 0, s>>>(k, row_x_dev, p); break;
     }
     return cudaGetLastError();
 }

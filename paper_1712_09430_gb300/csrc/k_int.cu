@@ -324,8 +324,14 @@ __global__ void k_start_write(KConst k, DevPtrs p, int rr0)
         int rank = 0;
         for (int j = 0; j < m; j++) rank += sid[j] < v;
         int t = t0 + rank;
+        int h = sb[i], len = 1;
+        for (int j = p.up2[h]; j >= 0; j = p.up2[j]) {  // walk the seed chain once
+            h = j;
+            len++;
+        }
         p.start[t] = sb[i];
         p.t_row[t] = rr;
+        p.t_end[t] = make_int2(h, len);
         p.sched[s0 + rank] = t;
     }
 }

@@ -71,6 +71,7 @@ struct DevPtrs {
     int* sched_off;            // [R + 1] schedule offsets (row-major order)
     int* start;                // [Tcap] binned index of the start hit of t
     int* t_row;                // [Tcap] row index rr of the start hit of t
+    int2* t_end;               // [Tcap] last hit of the seed chain (binned), chain length
     int* sched;                // [Tcap] tracklets by expected length
     float* tl_f;               // [Tcap][16]
     int* tl_n;                 // [Tcap] Phase-2 cluster count

@@ -236,6 +236,7 @@ size_t tpc_layout(const tpc_tracker* tr, const BatchShape& sh, DevPtrs* p, char*
     q.sched_off = reinterpret_cast<int*>(take((R + 1) * 4));
     q.start = reinterpret_cast<int*>(take(Tc * 4));
     q.t_row = reinterpret_cast<int*>(take(Tc * 4));
+    q.t_end = reinterpret_cast<int2*>(take(Tc * 8));
     q.sched = reinterpret_cast<int*>(take(Tc * 4));
     q.tl_f = reinterpret_cast<float*>(take(Tc * kTlFloats * 4));
     q.tl_n = reinterpret_cast<int*>(take(Tc * 4));
@@ -325,6 +326,14 @@ int tpc_reserve(tpc_tracker* tr, size_t bytes)
 int tpc_enqueue(tpc_tracker* tr, const DevPtrs& p, const BatchShape& sh, cudaStream_t s,
                 bool with_events)
 {
+    // Inside a stream capture, cudaEventRecordExternal adds a real
+    // event-record node, so stage times are also available for graph replays
+    // (a plain record would only become a dependency edge).
+    cudaStreamCaptureStatus cap_status = cudaStreamCaptureStatusNone;
+    TPC_CUDA(cudaStreamIsCapturing(s, &cap_status));
+    const unsigned rec_flags =
+        cap_status == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault;
+#define cudaEventRecord(ev_, s_) cudaEventRecordWithFlags(ev_, s_, rec_flags)
     const KConst& k = tr->kc;
     const tpc_params& P = tr->params;
     const float* xd = tr->row_x_dev;
@@ -370,6 +379,7 @@ int tpc_enqueue(tpc_tracker* tr, const DevPtrs& p, const BatchShape& sh, cudaStr
     }
     TPC_CUDA(tpc_int::launch_emit(k, p, tr->n_sm, s));
     if (with_events) TPC_CUDA(cudaEventRecord(tr->ev[5], s));
+#undef cudaEventRecord
     return TPC_OK;
 }
 
