@@ -191,7 +191,7 @@ def run_ours(args):
     N = len(cl_np)
     tr = Tracker(synth.row_x(), bz=0.5, use_graph=1, exact_fp32=1 if args.exact else 0,
                  bin_target=args.bin_target, threads_per_row=args.threads_per_row,
-                 tracklets_per_warp=args.tracklets_per_warp)
+                 tracklets_per_warp=args.tracklets_per_warp, schedule=args.schedule)
     stream = torch.cuda.Stream()
     sp = C.c_void_p(stream.cuda_stream)
     dev_cl = torch.from_numpy(cl_np).to(f"cuda:{local}")
@@ -276,7 +276,7 @@ def run_ours(args):
                        "tracklets_per_step": int(T), "mode": "exact" if args.exact else "production",
                        "launch": "batched, CUDA graph replay", "bin_target": args.bin_target,
                        "threads_per_row": args.threads_per_row,
-                       "tracklets_per_warp": args.tracklets_per_warp,
+                       "tracklets_per_warp": args.tracklets_per_warp, "schedule": args.schedule,
                        "l2": f"inputs larger than L2 ({N * 16 / 1e6:.0f} MB of clusters per step)",
                        "parallelism": f"events sharded over {world} GPU(s), no collective"},
             "events_per_s": B * world / (ms * 1e-3),
@@ -349,9 +349,10 @@ def main():
     ap.add_argument("--batch", type=int, default=8, help="central events per step (per GPU)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--exact", action="store_true", help="time the -fmad=false build")
-    ap.add_argument("--bin-target", type=float, default=1.0)
+    ap.add_argument("--bin-target", type=float, default=0.25)
     ap.add_argument("--threads-per-row", type=int, default=128)
     ap.add_argument("--tracklets-per-warp", type=int, default=32)
+    ap.add_argument("--schedule", type=int, default=0, help="0 unit by unit, 1 by start row")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling)")

@@ -109,6 +109,10 @@ typedef struct {
                                 (the Run 1/2 scheduling of Sec. 3); 0: all
                                 units in one launch per stage                   */
     int use_graph;           /* 1: replay the batched stages as a CUDA graph    */
+    int schedule;            /* tracklet order of the persistent constructor:
+                                0 unit by unit (canonical order; keeps the
+                                working set of a few sectors in L2), 1 by start
+                                row across all units (longest expected first)  */
 } tpc_params;
 
 /* A selected track: the best tracklet instance (Sec. 2 step 2), with the

@@ -1,8 +1,10 @@
 """Build the tracker's shared library in-tree with nvcc for sm_103a.
 
 libtpcca.so holds the C ABI of include/tpc_tracker.h.  The floating-point
-kernels are compiled twice: -fmad=false (namespace tpc_exact, bit-exact
-against an FP32 CPU evaluation) and with contraction (tpc_fast).  The CUDA
+kernels are compiled twice: -fmad=false (namespace tpc_exact, IEEE division
+and square root, bit-exact against an FP32 CPU evaluation) and a production
+build (tpc_fast: contraction, approximate division and square root, flush
+to zero).  The CUDA
 runtime is linked statically so the library has no runtime-path needs.
 """
 from __future__ import annotations
@@ -24,7 +26,8 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 UNITS = [
     ("k_int.cu", "k_int.o", []),
     ("k_fp.cu", "k_fp_exact.o", ["-fmad=false", "-DTPC_FP_NS=tpc_exact"]),
-    ("k_fp.cu", "k_fp_fast.o", ["-fmad=true", "-DTPC_FP_NS=tpc_fast"]),
+    ("k_fp.cu", "k_fp_fast.o", ["-fmad=true", "-prec-div=false", "-prec-sqrt=false", "-ftz=true",
+                                "-DTPC_FP_NS=tpc_fast", "-DTPC_FAST_MATH=1"]),
     ("tracker.cu", "tracker.o", []),
     ("serve.cu", "serve.o", []),
 ]

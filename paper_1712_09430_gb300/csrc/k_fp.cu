@@ -15,6 +15,13 @@
 #ifndef TPC_FP_NS
 #error "TPC_FP_NS must name the namespace (tpc_exact or tpc_fast)"
 #endif
+// TPC_FAST_MATH (production build only): the same quantities with fewer
+// instructions -- one reciprocal per shared denominator, rsqrt for 1/c and
+// 1/c^3.  Results agree with the FP64 oracle within the production
+// tolerance; the exact build keeps the expressions above verbatim.
+#ifndef TPC_FAST_MATH
+#define TPC_FAST_MATH 0
+#endif
 
 namespace TPC_FP_NS {
 using namespace tpc;
@@ -69,7 +76,10 @@ __global__ void k_neighbours(KConst k, const float* __restrict__ row_x, DevPtrs 
     __syncthreads();
     const RowGrid gu = p.grid[rr + 1], gd = p.grid[rr - 1];
     const int tu = gu.bin_base - bo_d, td = gd.bin_base - bo_d;  // tables in smem
+    const int nyu = grid_ny(gu), nzu = grid_nz(gu), nyd = grid_ny(gd), nzd = grid_nz(gd);
     const float Xr = row_x[r], Xu = row_x[r + 1], Xd = row_x[r - 1];
+    const float yu0 = -(Xu * k.tan_h + k.y_margin), yd0 = -(Xd * k.tan_h + k.y_margin);
+    const float z0 = ((u % k.n_sectors) < k.n_sectors / 2) ? 0.0f : -k.z_max;
     const float Ru = Xu / Xr, Rd = Xd / Xr;
     const float Wu = k.k_win * fabsf(Xu - Xr);
     const float Wd = k.k_win * fabsf(Xd - Xr);
@@ -84,27 +94,27 @@ __global__ void k_neighbours(KConst k, const float* __restrict__ row_x, DevPtrs 
         const float yi = ci.x, zi = ci.y;
         const float ycu = yi * Ru, ycd = yi * Rd;
         // bin windows (widened by kBinEps; the exact test below decides)
-        const int uy0 = bin_index(ycu - Wu - kBinEps, gu.y0, gu.inv_by, gu.ny);
-        const int uy1 = bin_index(ycu + Wu + kBinEps, gu.y0, gu.inv_by, gu.ny);
-        const int uz0 = bin_index(zi - Wu - kBinEps, gu.z0, gu.inv_bz, gu.nz);
-        const int uz1 = bin_index(zi + Wu + kBinEps, gu.z0, gu.inv_bz, gu.nz);
-        const int dy0 = bin_index(ycd - Wd - kBinEps, gd.y0, gd.inv_by, gd.ny);
-        const int dy1 = bin_index(ycd + Wd + kBinEps, gd.y0, gd.inv_by, gd.ny);
-        const int dz0 = bin_index(zi - Wd - kBinEps, gd.z0, gd.inv_bz, gd.nz);
-        const int dz1 = bin_index(zi + Wd + kBinEps, gd.z0, gd.inv_bz, gd.nz);
+        const int uy0 = bin_index(ycu - Wu - kBinEps, yu0, gu.inv_by, nyu);
+        const int uy1 = bin_index(ycu + Wu + kBinEps, yu0, gu.inv_by, nyu);
+        const int uz0 = bin_index(zi - Wu - kBinEps, z0, gu.inv_bz, nzu);
+        const int uz1 = bin_index(zi + Wu + kBinEps, z0, gu.inv_bz, nzu);
+        const int dy0 = bin_index(ycd - Wd - kBinEps, yd0, gd.inv_by, nyd);
+        const int dy1 = bin_index(ycd + Wd + kBinEps, yd0, gd.inv_by, nyd);
+        const int dz0 = bin_index(zi - Wd - kBinEps, z0, gd.inv_bz, nzd);
+        const int dz1 = bin_index(zi + Wd + kBinEps, z0, gd.inv_bz, nzd);
         int bu = -1, bd = -1;
         unsigned bid_u = 0, bid_d = 0;
         float bD = 0.0f;
         for (int bzu = uz0; bzu <= uz1; bzu++) {
-            const int ju0 = bins[tu + bzu * gu.ny + uy0] - off_d;
-            const int ju1 = bins[tu + bzu * gu.ny + uy1 + 1] - off_d;
+            const int ju0 = bins[tu + bzu * nyu + uy0] - off_d;
+            const int ju1 = bins[tu + bzu * nyu + uy1 + 1] - off_d;
             for (int ju = ju0; ju < ju1; ju++) {
                 const float4 cu = rec[ju];
                 if (!(fabsf(cu.x - ycu) <= Wu && fabsf(cu.y - zi) <= Wu)) continue;
                 const unsigned idu = __float_as_uint(cu.z);
                 for (int bzd = dz0; bzd <= dz1; bzd++) {
-                    const int jd0 = bins[td + bzd * gd.ny + dy0] - off_d;
-                    const int jd1 = bins[td + bzd * gd.ny + dy1 + 1] - off_d;
+                    const int jd0 = bins[td + bzd * nyd + dy0] - off_d;
+                    const int jd1 = bins[td + bzd * nyd + dy1 + 1] - off_d;
                     for (int jd = jd0; jd < jd1; jd++) {
                         const float4 cd = rec[jd];
                         if (!(fabsf(cd.x - ycd) <= Wd && fabsf(cd.y - zi) <= Wd)) continue;
@@ -159,17 +169,27 @@ __device__ __forceinline__ bool propagate(State& st, float x1, float kB, float s
     const float s0 = st.s;
     const float s1 = s0 + kk * d;
     if (fabsf(s0) > s_max || fabsf(s1) > s_max) return false;
+#if TPC_FAST_MATH
+    const float e0 = 1.0f - s0 * s0, e1 = 1.0f - s1 * s1;
+    const float ic0 = rsqrtf(e0), ic1 = rsqrtf(e1);
+    const float c0 = e0 * ic0, c1 = e1 * ic1;
+    const float dy = __fdividef(d * (s0 + s1), c0 + c1);
+    const float ci3 = ic0 * ic0 * ic0;
+    const float c1i3 = ic1 * ic1 * ic1;
+#else
     const float c0 = sqrtf(1.0f - s0 * s0);
     const float c1 = sqrtf(1.0f - s1 * s1);
     const float dy = d * (s0 + s1) / (c0 + c1);
+#endif
     const float L = copysignf(sqrtf(d * d + dy * dy), d);
     const float u = kk * L * 0.5f;
     const float u2 = u * u;
     const float arc = L * (1.0f + u2 * ((float)(1.0 / 6.0) + u2 * (float)(3.0 / 40.0)));
     const float dz = st.t * arc;
-
+#if !TPC_FAST_MATH
     const float ci3 = 1.0f / (c0 * c0 * c0);
     const float c1i3 = 1.0f / (c1 * c1 * c1);
+#endif
     const float a = d * (ci3 + c1i3) * 0.5f;
     const float b = kB * d * d * 0.5f * c1i3;
     const float e = kB * d;
@@ -208,7 +228,12 @@ __device__ __forceinline__ void update(State& st, float my, float mz, float sy2,
 {
     const float S = sy2 + st.cy[0];
     const float r = my - st.y;
+#if TPC_FAST_MATH
+    const float iS = __fdividef(1.0f, S);
+    const float K0 = st.cy[0] * iS, K1 = st.cy[1] * iS, K2 = st.cy[3] * iS;
+#else
     const float K0 = st.cy[0] / S, K1 = st.cy[1] / S, K2 = st.cy[3] / S;
+#endif
     const float c00 = st.cy[0], c10 = st.cy[1], c11 = st.cy[2];
     const float c20 = st.cy[3], c21 = st.cy[4], c22 = st.cy[5];
     st.y = st.y + K0 * r;
@@ -220,18 +245,31 @@ __device__ __forceinline__ void update(State& st, float my, float mz, float sy2,
     st.cy[3] = c20 - K2 * c00;
     st.cy[4] = c21 - K2 * c10;
     st.cy[5] = c22 - K2 * c20;
+#if TPC_FAST_MATH
+    const float chi = r * r * iS;
+#else
     const float chi = r * r / S;
+#endif
 
     const float Sz = sz2 + st.cz[0];
     const float rz = mz - st.z;
+#if TPC_FAST_MATH
+    const float iSz = __fdividef(1.0f, Sz);
+    const float L0 = st.cz[0] * iSz, L1 = st.cz[1] * iSz;
+#else
     const float L0 = st.cz[0] / Sz, L1 = st.cz[1] / Sz;
+#endif
     const float z00 = st.cz[0], z10 = st.cz[1], z11 = st.cz[2];
     st.z = st.z + L0 * rz;
     st.t = st.t + L1 * rz;
     st.cz[0] = z00 - L0 * z00;
     st.cz[1] = z10 - L1 * z00;
     st.cz[2] = z11 - L1 * z10;
+#if TPC_FAST_MATH
+    chi2 = chi2 + chi + rz * rz * iSz;
+#else
     chi2 = chi2 + chi + rz * rz / Sz;
+#endif
 }
 
 __device__ __forceinline__ void reset_cov(State& st, const KConst& k)
@@ -259,8 +297,9 @@ __device__ __forceinline__ bool outside(const State& st, float X, const KConst& 
 // reduce the best (d2, id) with warp shuffles; every lane of the group
 // returns the same binned index (or -1).
 template <int G>
-__device__ __forceinline__ int search_row(const State& st, int rr, const KConst& k,
-                                          const DevPtrs& p, int gl, unsigned gmask, int4& work)
+__device__ __forceinline__ int search_row(const State& st, const RowGrid& g, float y0, float z0,
+                                          const KConst& k, const DevPtrs& p, int gl, unsigned gmask,
+                                          int4& work, float2& found)
 {
     const float Sy = k.sy2 + st.cy[0];
     const float Sz = k.sz2 + st.cz[0];
@@ -268,44 +307,67 @@ __device__ __forceinline__ int search_row(const State& st, int rr, const KConst&
     float wz = k.n_sigma * sqrtf(Sz);
     wy = wy < k.w_min ? k.w_min : (wy > k.w_max ? k.w_max : wy);
     wz = wz < k.w_min ? k.w_min : (wz > k.w_max ? k.w_max : wz);
-    const RowGrid g = p.grid[rr];
-    const int y0 = bin_index(st.y - wy - kBinEps, g.y0, g.inv_by, g.ny);
-    const int y1 = bin_index(st.y + wy + kBinEps, g.y0, g.inv_by, g.ny);
-    const int z0 = bin_index(st.z - wz - kBinEps, g.z0, g.inv_bz, g.nz);
-    const int z1 = bin_index(st.z + wz + kBinEps, g.z0, g.inv_bz, g.nz);
+#if TPC_FAST_MATH
+    const float iSy = __fdividef(1.0f, Sy), iSz = __fdividef(1.0f, Sz);
+#endif
+    const int ny = grid_ny(g), nz = grid_nz(g);
+    const int by0 = bin_index(st.y - wy - kBinEps, y0, g.inv_by, ny);
+    const int by1 = bin_index(st.y + wy + kBinEps, y0, g.inv_by, ny);
+    const int bz0 = bin_index(st.z - wz - kBinEps, z0, g.inv_bz, nz);
+    const int bz1 = bin_index(st.z + wz + kBinEps, z0, g.inv_bz, nz);
     int best = -1;
     unsigned bid = 0;
+    bool have_bid = false;  // the best id is read only when a tie needs it
     float bd2 = 0.0f;
     work.x += 1;
-    work.y += z1 - z0 + 1;
-    for (int bz = z0; bz <= z1; bz++) {
-        const int* row_bins = p.bin_off + g.bin_base + bz * g.ny;
-        const int j0 = __ldg(row_bins + y0), j1 = __ldg(row_bins + y1 + 1);
+    work.y += bz1 - bz0 + 1;
+    for (int bz = bz0; bz <= bz1; bz++) {
+        const int* row_bins = p.bin_off + g.bin_base + bz * ny;
+        const int j0 = __ldg(row_bins + by0), j1 = __ldg(row_bins + by1 + 1);
         work.z += j1 - j0;
         for (int j = j0 + gl; j < j1; j += G) {
-            const float4 c = __ldg(p.hits + j);
+            const float2 c = __ldg(p.hyz + j);
             const float dy = c.x - st.y;
             const float dz = c.y - st.z;
             if (!(fabsf(dy) <= wy && fabsf(dz) <= wz)) continue;
+#if TPC_FAST_MATH
+            const float d2 = dy * dy * iSy + dz * dz * iSz;
+#else
             const float d2 = dy * dy / Sy + dz * dz / Sz;
-            const unsigned id = __float_as_uint(c.z);
-            if (best < 0 || d2 < bd2 || (d2 == bd2 && id < bid)) {
+#endif
+            if (best < 0 || d2 < bd2) {
                 best = j;
                 bd2 = d2;
-                bid = id;
+                have_bid = false;
+                found = c;
+            } else if (d2 == bd2) {
+                const unsigned id = __float_as_uint(__ldg(&p.hits[j].z));
+                if (!have_bid) {
+                    bid = __float_as_uint(__ldg(&p.hits[best].z));
+                    have_bid = true;
+                }
+                if (id < bid) {
+                    best = j;
+                    bid = id;
+                    found = c;
+                }
             }
         }
     }
     if (G > 1) {
+        if (best >= 0 && !have_bid) bid = __float_as_uint(__ldg(&p.hits[best].z));
 #pragma unroll
         for (int o = G / 2; o > 0; o >>= 1) {
             const int ob = __shfl_xor_sync(gmask, best, o);
             const float od = __shfl_xor_sync(gmask, bd2, o);
             const unsigned oi = __shfl_xor_sync(gmask, bid, o);
+            const float ofx = __shfl_xor_sync(gmask, found.x, o);
+            const float ofy = __shfl_xor_sync(gmask, found.y, o);
             if (ob >= 0 && (best < 0 || od < bd2 || (od == bd2 && oi < bid))) {
                 best = ob;
                 bd2 = od;
                 bid = oi;
+                found = make_float2(ofx, ofy);
             }
         }
     }
@@ -328,6 +390,8 @@ struct Lane {
     int miss, n;
     bool have;
     float chi2;
+    float z0;     // grid z origin of the unit's side
+    RowGrid g;    // grid record of row r, loaded one step ahead
     State st;
     int4 work;
 };
@@ -340,6 +404,7 @@ __device__ __forceinline__ void lane_init(Lane& L, int t, const KConst& k, const
     const int2 e = p.t_end[t];
     L.t = t;
     L.ubase = rr0 - rr0 % NR;
+    L.z0 = (((rr0 / NR) % k.n_sectors) < k.n_sectors / 2) ? 0.0f : -k.z_max;
     const int r0 = rr0 - L.ubase;
     const int h0 = p.start[t];
     const int rL = r0 + e.y - 1;
@@ -363,6 +428,7 @@ __device__ __forceinline__ void lane_init(Lane& L, int t, const KConst& k, const
     L.miss = 0;
     L.n = 0;
     L.work = make_int4(0, 0, 0, e.y);
+    L.g = p.grid[rr0];
 }
 
 __device__ __forceinline__ void lane_finish(Lane& L, const KConst& k, const DevPtrs& p, bool writer)
@@ -395,10 +461,17 @@ __device__ __forceinline__ void lane_step(Lane& L, const KConst& k, const float*
     const float X = xs[L.r];
     const bool ok = propagate(pr, X, k.kB, k.s_max) && !outside(pr, X, k);
     int j = -1;
-    if (ok) j = L.phase == 0 ? L.h : search_row<G>(pr, L.ubase + L.r, k, p, gl, gmask, L.work);
+    float2 c = make_float2(0.0f, 0.0f);
+    if (ok) {
+        if (L.phase == 0) {
+            j = L.h;
+            c = __ldg(p.hyz + j);
+        } else {
+            j = search_row<G>(pr, L.g, -(X * k.tan_h + k.y_margin), L.z0, k, p, gl, gmask, L.work, c);
+        }
+    }
     bool end_phase = !ok;
     if (j >= 0) {
-        const float4 c = __ldg(p.hits + j);
         update(pr, c.x, c.y, k.sy2, k.sz2, L.chi2);
         L.st = pr;
         if (L.phase == 2) {
@@ -436,16 +509,20 @@ __device__ __forceinline__ void lane_step(Lane& L, const KConst& k, const float*
             L.miss = 0;
         } else {
             lane_finish(L, k, p, gl == 0);
+            return;
         }
     }
+    L.g = p.grid[L.ubase + L.r];  // consumed by the next step; the load overlaps the loop
 }
 
 // Persistent, dynamically scheduled constructor: idle lane groups take the
 // next entries of the length-sorted schedule (long expected tracks first)
 // from a global counter, with one warp-aggregated atomic per refill.
+constexpr int kTrackletCtasPerSm = 4;  // 256 threads each: 32 warps per SM, <= 64 registers
+
 template <int G>
-__global__ void __launch_bounds__(256, 3) k_tracklets_sched(KConst k, const float* __restrict__ row_x,
-                                                            DevPtrs p)
+__global__ void __launch_bounds__(256, kTrackletCtasPerSm)
+    k_tracklets_sched(KConst k, const float* __restrict__ row_x, DevPtrs p, int by_row)
 {
     __shared__ float xs[TPC_MAX_ROWS];
     for (int r = threadIdx.x; r < k.n_rows; r += blockDim.x) xs[r] = row_x[r];
@@ -469,7 +546,7 @@ __global__ void __launch_bounds__(256, 3) k_tracklets_sched(KConst k, const floa
             int i = base + __popc(need & ((1u << gbase) - 1u));
             const bool mine = (need >> gbase) & 1u;
             if (mine) {
-                if (i < T) lane_init(L, p.sched[i], k, xs, p);
+                if (i < T) lane_init(L, by_row ? p.sched[i] : i, k, xs, p);
                 else done = true;
             }
         }
@@ -511,20 +588,20 @@ cudaError_t launch_neighbours(const KConst& k, const float* row_x_dev, const Dev
 }
 
 cudaError_t launch_tracklets(const KConst& k, const float* row_x_dev, const DevPtrs& p, int n_sm,
-                             int lanes_per_tracklet, int u0, int u1, cudaStream_t s)
+                             int lanes_per_tracklet, int schedule, int u0, int u1, cudaStream_t s)
 {
     if (u0 >= 0) {
         k_tracklets_plain<<<n_sm * 2, 256, 0, s>>>(k, row_x_dev, p, u0, u1);
         return cudaGetLastError();
     }
-    const int grid = n_sm * 3;  // 3 resident CTAs of 256 per SM
+    const int grid = n_sm * kTrackletCtasPerSm;  // one wave of resident CTAs
     switch (lanes_per_tracklet) {
-        case 1: k_tracklets_sched<1><<<grid, 256, 0, s>>>(k, row_x_dev, p); break;
-        case 2: k_tracklets_sched<2><<<grid, 256, 0, s>>>(k, row_x_dev, p); break;
-        case 4: k_tracklets_sched<4><<<grid, 256, 0, s>>>(k, row_x_dev, p); break;
-        case 8: k_tracklets_sched<8><<<grid, 256, 0, s>>>(k, row_x_dev, p); break;
-        case 16: k_tracklets_sched<16><<<grid, 256, 0, s>>>(k, row_x_dev, p); break;
-        default: k_tracklets_sched<32><<<grid, 256, 0, s>>>(k, row_x_dev, p); break;
+        case 1: k_tracklets_sched<1><<<grid, 256, 0, s>>>(k, row_x_dev, p, schedule); break;
+        case 2: k_tracklets_sched<2><<<grid, 256, 0, s>>>(k, row_x_dev, p, schedule); break;
+        case 4: k_tracklets_sched<4><<<grid, 256, 0, s>>>(k, row_x_dev, p, schedule); break;
+        case 8: k_tracklets_sched<8><<<grid, 256, 0, s>>>(k, row_x_dev, p, schedule); break;
+        case 16: k_tracklets_sched<16><<<grid, 256, 0, s>>>(k, row_x_dev, p, schedule); break;
+        default: k_tracklets_sched<32><<<grid, 256, 0, s>>>(k, row_x_dev, p, schedule); break;
     }
     return cudaGetLastError();
 }

@@ -88,7 +88,13 @@ __device__ __forceinline__ void flag_error(int* counters, int bits, int rr)
     atomicCAS(&counters[C_BADROW], 0, rr + 1);
 }
 
-__device__ RowGrid make_grid(const KConst& k, int cnt, float X, bool side_a, int bin_base)
+__device__ __forceinline__ float grid_y0(const KConst& k, float X) { return -(X * k.tan_h + k.y_margin); }
+__device__ __forceinline__ float grid_z0(const KConst& k, int rr)
+{
+    return ((rr / k.n_rows) % k.n_sectors) < k.n_sectors / 2 ? 0.0f : -k.z_max;
+}
+
+__device__ RowGrid make_grid(const KConst& k, int cnt, float X, int bin_base)
 {
     RowGrid g;
     float half = X * k.tan_h + k.y_margin;
@@ -102,48 +108,21 @@ __device__ RowGrid make_grid(const KConst& k, int cnt, float X, bool side_a, int
     while (ny * nz > cap) {  // guards rounding at the edge; never loops long
         if (ny >= nz) ny--; else nz--;
     }
-    g.y0 = -half;
-    g.z0 = side_a ? 0.0f : -k.z_max;
     g.inv_by = (float)ny / Ly;
     g.inv_bz = (float)nz / Lz;
-    g.ny = ny;
-    g.nz = nz;
     g.bin_base = bin_base;
-    g.pad = 0;
+    g.nyz = ny | (nz << 16);
     return g;
 }
 
 // ------------------------------------------------------------------- plan
-// One CTA: counters, CSR offsets of rows, bin-table offsets, row grids.
-__global__ void __launch_bounds__(1024) k_plan(KConst k, const float* __restrict__ row_x, DevPtrs p)
+// Row grids of every row (the CSR and bin-table offsets come from the host,
+// which holds the row counts); CTA 0 clears the counters.
+__global__ void k_plan(KConst k, const float* __restrict__ row_x, DevPtrs p)
 {
-    const int tid = threadIdx.x, nt = blockDim.x;
-    if (tid < kNumCounters) p.counters[tid] = 0;
-    const int R = p.R;
-    const int per = (R + nt - 1) / nt;
-    const int r0 = min(R, tid * per), r1 = min(R, r0 + per);
-    int2 s = make_int2(0, 0);
-    for (int r = r0; r < r1; r++) {
-        int c = p.row_cnt[r];
-        s.x += c;
-        s.y += row_bin_slots(c, k.bin_target);
-    }
-    int2 total;
-    int2 ex = block_excl_sum<int2>(s, &total);
-    for (int r = r0; r < r1; r++) {
-        int c = p.row_cnt[r];
-        p.row_off[r] = ex.x;
-        p.bin_cap_off[r] = ex.y;
-        int row = r % k.n_rows;
-        int sector = (r / k.n_rows) % k.n_sectors;
-        p.grid[r] = make_grid(k, c, row_x[row], sector < k.n_sectors / 2, ex.y);
-        ex.x += c;
-        ex.y += row_bin_slots(c, k.bin_target);
-    }
-    if (tid == 0) {
-        p.row_off[R] = total.x;
-        p.bin_cap_off[R] = total.y;
-    }
+    if (blockIdx.x == 0 && threadIdx.x < kNumCounters) p.counters[threadIdx.x] = 0;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < p.R; r += gridDim.x * blockDim.x)
+        p.grid[r] = make_grid(k, p.row_cnt[r], row_x[r % k.n_rows], p.bin_cap_off[r]);
 }
 
 // ------------------------------------------------------------- grid build
@@ -157,7 +136,8 @@ __global__ void k_grid(KConst k, const float* __restrict__ row_x, DevPtrs p, int
     const int cnt = p.row_cnt[rr];
     const int off = p.row_off[rr];
     const RowGrid g = p.grid[rr];
-    const int nb = g.ny * g.nz;
+    const int ny = grid_ny(g), nz = grid_nz(g);
+    const int nb = ny * nz;
     const int tid = threadIdx.x, nt = blockDim.x;
 
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
@@ -184,6 +164,7 @@ __global__ void k_grid(KConst k, const float* __restrict__ row_x, DevPtrs p, int
     }
     const int row = rr % k.n_rows;
     const float X = row_x[row];
+    const float y0 = grid_y0(k, X), z0 = grid_z0(k, rr);
     if (row == 0 || row == k.n_rows - 1) {  // no links of their own
         for (int i = tid; i < cnt; i += nt) {
             p.up[off + i] = -1;
@@ -194,18 +175,18 @@ __global__ void k_grid(KConst k, const float* __restrict__ row_x, DevPtrs p, int
         float4 c = in[i];
         bool ok = fabsf(c.x - X) <= kCoordTol && isfinite(c.y) && isfinite(c.z);
         if (!ok) flag_error(p.counters, E_INPUT, rr);
-        int by = bin_index(c.y, g.y0, g.inv_by, g.ny);
-        int bz = bin_index(c.z, g.z0, g.inv_bz, g.nz);
-        slot[i] = atomicAdd(&hist[bz * g.ny + by], 1);
+        int by = bin_index(c.y, y0, g.inv_by, ny);
+        int bz = bin_index(c.z, z0, g.inv_bz, nz);
+        slot[i] = atomicAdd(&hist[bz * ny + by], 1);
     }
     __syncthreads();
     block_scan_smem(hist, nb + 1);
     for (int b = tid; b <= nb; b += nt) p.bin_off[g.bin_base + b] = off + hist[b];
     for (int i = tid; i < cnt; i += nt) {
         float4 c = in[i];
-        int by = bin_index(c.y, g.y0, g.inv_by, g.ny);
-        int bz = bin_index(c.z, g.z0, g.inv_bz, g.nz);
-        out[hist[bz * g.ny + by] + slot[i]] = make_float4(c.y, c.z, c.w, __int_as_float(off + i));
+        int by = bin_index(c.y, y0, g.inv_by, ny);
+        int bz = bin_index(c.z, z0, g.inv_bz, nz);
+        out[hist[bz * ny + by] + slot[i]] = make_float4(c.y, c.z, c.w, __int_as_float(off + i));
     }
     __syncthreads();
     // order inside each bin by id (insertion sort; bins hold a few clusters)
@@ -227,8 +208,9 @@ __global__ void k_grid(KConst k, const float* __restrict__ row_x, DevPtrs p, int
         fence_async_smem();
         bulk_s2g(p.hits + off, out, (unsigned)cnt * 16u);
         bulk_commit();
-        bulk_wait_all();
     }
+    for (int i = tid; i < cnt; i += nt) p.hyz[off + i] = make_float2(out[i].x, out[i].y);
+    if (tid == 0) bulk_wait_all();
 }
 
 // ------------------------------------------------------ clean + start hits
@@ -265,49 +247,85 @@ __global__ void k_clean(KConst k, DevPtrs p, int rr0)
     if (threadIdx.x == 0) p.row_nstart[rr] = total;
 }
 
-// One CTA: tracklet offsets per row in canonical (unit, row) order and in
-// the schedule order (row, unit): long expected tracks (low start rows) first.
-__global__ void __launch_bounds__(1024) k_start_scan(KConst k, DevPtrs p)
+// Tracklet offsets per row in canonical (unit, row) order and in the
+// schedule order (row, unit): long expected tracks (low start rows) first.
+// Multi-CTA: each CTA scans kScanTile rows of both orders; a one-CTA pass
+// scans the tile sums; k_start_write adds the tile prefix.
+__device__ __forceinline__ int sched_row(int j, int U, int NR) { return (j % U) * NR + j / U; }
+
+__global__ void k_start_tiles(KConst k, DevPtrs p)
 {
-    const int tid = threadIdx.x, nt = blockDim.x;
-    const int R = p.R, NR = k.n_rows, U = p.n_units;
-    const int per = (R + nt - 1) / nt;
-    const int r0 = min(R, tid * per), r1 = min(R, r0 + per);
-    int s = 0;
-    for (int r = r0; r < r1; r++) s += p.row_nstart[r];
-    int total;
-    int ex = block_excl_sum<int>(s, &total);
-    for (int r = r0; r < r1; r++) {
-        p.start_off[r] = ex;
-        ex += p.row_nstart[r];
+    const int R = p.R, U = p.n_units, NR = k.n_rows;
+    const int ntiles = (R + kScanTile - 1) / kScanTile;
+    const int base = blockIdx.x * kScanTile;
+    const int per = kScanTile / blockDim.x;
+    const int i0 = base + threadIdx.x * per;
+    int2 sv = make_int2(0, 0);
+    for (int i = i0; i < i0 + per && i < R; i++) {
+        sv.x += p.row_nstart[i];
+        sv.y += p.row_nstart[sched_row(i, U, NR)];
     }
-    if (tid == 0) {
-        p.start_off[R] = total;
-        p.counters[C_T] = total;
+    int2 total;
+    int2 ex = block_excl_sum<int2>(sv, &total);
+    for (int i = i0; i < i0 + per && i < R; i++) {
+        p.start_off[i] = ex.x;
+        ex.x += p.row_nstart[i];
+        const int rr = sched_row(i, U, NR);
+        p.sched_off[rr] = ex.y;
+        ex.y += p.row_nstart[rr];
     }
-    // schedule order: j = row * U + unit
-    s = 0;
-    for (int j = r0; j < r1; j++) s += p.row_nstart[(j % U) * NR + j / U];
-    ex = block_excl_sum<int>(s, &total);
-    for (int j = r0; j < r1; j++) {
-        int rr = (j % U) * NR + j / U;
-        p.sched_off[rr] = ex;
-        ex += p.row_nstart[rr];
+    if (threadIdx.x == 0) {
+        p.start_part[blockIdx.x] = total.x;
+        p.start_part[ntiles + 1 + blockIdx.x] = total.y;
     }
-    if (tid == 0) p.sched_off[R] = total;
 }
 
-// One CTA per row with start hits: number them by cluster id.
+__global__ void __launch_bounds__(1024) k_start_top(KConst k, DevPtrs p)
+{
+    const int R = p.R;
+    const int ntiles = (R + kScanTile - 1) / kScanTile;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int per = (ntiles + nt - 1) / nt;
+    const int b0 = min(ntiles, tid * per), b1 = min(ntiles, b0 + per);
+    int2 sv = make_int2(0, 0);
+    for (int b = b0; b < b1; b++) sv += make_int2(p.start_part[b], p.start_part[ntiles + 1 + b]);
+    int2 total;
+    int2 ex = block_excl_sum<int2>(sv, &total);
+    for (int b = b0; b < b1; b++) {
+        int2 v = make_int2(p.start_part[b], p.start_part[ntiles + 1 + b]);
+        p.start_part[b] = ex.x;
+        p.start_part[ntiles + 1 + b] = ex.y;
+        ex += v;
+    }
+    if (tid == 0) {
+        p.start_off[R] = total.x;
+        p.sched_off[R] = total.y;
+        p.counters[C_T] = total.x;
+    }
+}
+
+// One CTA per row: finish the row's offsets, then number its start hits by
+// cluster id.
 __global__ void k_start_write(KConst k, DevPtrs p, int rr0)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ int n_sh;
+    __shared__ int n_sh, t0_sh, s0_sh;
     const int rr = rr0 + blockIdx.x;
     const int m = p.row_nstart[rr];
+    if (threadIdx.x == 0) {
+        const int ntiles = (p.R + kScanTile - 1) / kScanTile;
+        const int j = (rr % k.n_rows) * p.n_units + rr / k.n_rows;
+        const int t0 = p.start_off[rr] + p.start_part[rr / kScanTile];
+        const int s0 = p.sched_off[rr] + p.start_part[ntiles + 1 + j / kScanTile];
+        p.start_off[rr] = t0;
+        p.sched_off[rr] = s0;
+        t0_sh = t0;
+        s0_sh = s0;
+        n_sh = 0;
+    }
     if (m == 0) return;
     unsigned* sid = reinterpret_cast<unsigned*>(smem);
     int* sb = reinterpret_cast<int*>(sid + m);
-    if (threadIdx.x == 0) n_sh = 0;
     __syncthreads();
     const int b0 = p.row_off[rr], b1 = p.row_off[rr + 1];
     for (int b = b0 + (int)threadIdx.x; b < b1; b += blockDim.x) {
@@ -318,21 +336,29 @@ __global__ void k_start_write(KConst k, DevPtrs p, int rr0)
         }
     }
     __syncthreads();
-    const int t0 = p.start_off[rr], s0 = p.sched_off[rr];
+    const int t0 = t0_sh, s0 = s0_sh;
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
         unsigned v = sid[i];
         int rank = 0;
         for (int j = 0; j < m; j++) rank += sid[j] < v;
         int t = t0 + rank;
-        int h = sb[i], len = 1;
-        for (int j = p.up2[h]; j >= 0; j = p.up2[j]) {  // walk the seed chain once
+        p.start[t] = sb[i];
+        p.t_row[t] = rr;
+        p.sched[s0 + rank] = t;
+    }
+}
+
+// Last hit and length of every seed chain (one thread per tracklet).
+__global__ void k_chain_end(KConst k, DevPtrs p, int u0, int u1)
+{
+    const int t0 = p.start_off[u0 * k.n_rows], t1 = p.start_off[u1 * k.n_rows];
+    for (int t = t0 + blockIdx.x * blockDim.x + threadIdx.x; t < t1; t += gridDim.x * blockDim.x) {
+        int h = p.start[t], len = 1;
+        for (int j = p.up2[h]; j >= 0; j = p.up2[j]) {
             h = j;
             len++;
         }
-        p.start[t] = sb[i];
-        p.t_row[t] = rr;
         p.t_end[t] = make_int2(h, len);
-        p.sched[s0 + rank] = t;
     }
 }
 
@@ -342,16 +368,19 @@ __device__ __forceinline__ unsigned long long tl_key(int n, int t)
     return ((unsigned long long)(unsigned)n << 32) | (unsigned long long)(0xFFFFFFFFu - (unsigned)t);
 }
 
-// Best instance per cluster: owner[h] = max key over live tracklets.
+// Best instance per cluster: owner[h] = max key over live tracklets.  One
+// warp per tracklet (coalesced reads of its cluster list).
 __global__ void k_owner(KConst k, DevPtrs p, int u0, int u1)
 {
     const int t0 = p.start_off[u0 * k.n_rows], t1 = p.start_off[u1 * k.n_rows];
-    for (int t = t0 + blockIdx.x * blockDim.x + threadIdx.x; t < t1; t += gridDim.x * blockDim.x) {
-        int n = p.tl_n[t];
+    const int lane = threadIdx.x & 31;
+    const int w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+    for (int t = t0 + w0; t < t1; t += nw) {
+        const int n = p.tl_n[t];
         if (n < k.n_min_tracklet) continue;
-        unsigned long long key = tl_key(n, t);
+        const unsigned long long key = tl_key(n, t);
         const int* h = p.tl_hits + (size_t)t * k.n_rows;
-        for (int j = 0; j < n; j++) atomicMax(&p.owner[h[j]], key);
+        for (int j = lane; j < n; j += 32) atomicMax(&p.owner[h[j]], key);
     }
 }
 
@@ -359,19 +388,24 @@ __global__ void k_owner(KConst k, DevPtrs p, int u0, int u1)
 __global__ void k_accept(KConst k, DevPtrs p, int u0, int u1)
 {
     const int t0 = p.start_off[u0 * k.n_rows], t1 = p.start_off[u1 * k.n_rows];
-    for (int t = t0 + blockIdx.x * blockDim.x + threadIdx.x; t < t1; t += gridDim.x * blockDim.x) {
-        int n = p.tl_n[t];
-        int2 a = make_int2(0, 0);
+    const int lane = threadIdx.x & 31;
+    const int w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+    for (int t = t0 + w0; t < t1; t += nw) {
+        const int n = p.tl_n[t];
+        int owned = 0;
         if (n >= k.n_min_tracklet) {
-            unsigned long long key = tl_key(n, t);
+            const unsigned long long key = tl_key(n, t);
             const int* h = p.tl_hits + (size_t)t * k.n_rows;
-            int owned = 0;
-            for (int j = 0; j < n; j++) owned += p.owner[h[j]] == key;
-            if (owned >= k.n_min_track &&
-                (long long)owned * k.own_den >= (long long)k.own_num * n)
-                a = make_int2(1, owned);
+            for (int j0 = 0; j0 < n; j0 += 32) {
+                const bool own = j0 + lane < n && p.owner[h[j0 + lane]] == key;
+                owned += __popc(__ballot_sync(0xffffffffu, own));
+            }
         }
-        p.acc[t] = a;
+        if (lane == 0) {
+            const bool acc = owned >= k.n_min_track &&
+                             (long long)owned * k.own_den >= (long long)k.own_num * n;
+            p.acc[t] = acc ? make_int2(1, owned) : make_int2(0, 0);
+        }
     }
 }
 
@@ -418,37 +452,48 @@ __global__ void __launch_bounds__(1024) k_scan_top(DevPtrs p)
 }
 
 // Write accepted tracks in canonical order with their owned clusters (input
-// positions, rows ascending).
+// positions, rows ascending).  One warp per tracklet: the record is written
+// word by word by 22 lanes, the owned clusters are compacted by ballot.
 __global__ void k_emit(KConst k, DevPtrs p)
 {
     const int T = p.counters[C_T];
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < T; t += gridDim.x * blockDim.x) {
-        int2 a = p.acc[t];
+    const int lane = threadIdx.x & 31;
+    const int w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+    constexpr int kWords = (int)(sizeof(tpc_track) / 4);
+    for (int t = w0; t < T; t += nw) {
+        const int2 a = p.acc[t];
         if (!a.x) continue;
-        int2 ex = p.acc_scan[t] + p.scan_part[t / kScanTile];
-        int m = ex.x, hoff = ex.y;
-        int n = p.tl_n[t];
-        unsigned long long key = tl_key(n, t);
-        const float* f = p.tl_f + (size_t)t * kTlFloats;
-        tpc_track tr;
-        int unit = p.t_row[t] / k.n_rows;
-        tr.event = unit / k.n_sectors;
-        tr.sector = unit % k.n_sectors;
-        tr.tracklet = t;
-        tr.x = f[0];
-        for (int j = 0; j < 5; j++) tr.p[j] = f[1 + j];
-        for (int j = 0; j < 6; j++) tr.cov_y[j] = f[6 + j];
-        for (int j = 0; j < 3; j++) tr.cov_z[j] = f[12 + j];
-        tr.chi2 = f[15];
-        tr.ndf = 2 * n - 5;
-        tr.nhits = a.y;
-        tr.hit_off = hoff;
-        p.out_tracks[m] = tr;
+        const int2 ex = p.acc_scan[t] + p.scan_part[t / kScanTile];
+        const int m = ex.x;
+        const int n = p.tl_n[t];
+        if (lane < kWords) {
+            // word layout of tpc_track: event sector tracklet x p[5] cov_y[6]
+            // cov_z[3] chi2 ndf nhits hit_off
+            int word;
+            const int unit = p.t_row[t] / k.n_rows;
+            if (lane == 0) word = unit / k.n_sectors;
+            else if (lane == 1) word = unit % k.n_sectors;
+            else if (lane == 2) word = t;
+            else if (lane < 19) word = __float_as_int(p.tl_f[(size_t)t * kTlFloats + (lane - 3)]);
+            else if (lane == 19) word = 2 * n - 5;
+            else if (lane == 20) word = a.y;
+            else word = ex.y;
+            reinterpret_cast<int*>(p.out_tracks + m)[lane] = word;
+        }
+        const unsigned long long key = tl_key(n, t);
         const int* h = p.tl_hits + (size_t)t * k.n_rows;
-        int o = hoff;
-        for (int j = n - 1; j >= 0; j--) {
-            int b = h[j];
-            if (p.owner[b] == key) p.out_hits[o++] = __float_as_int(p.hits[b].w);
+        int o = ex.y;
+        for (int j0 = 0; j0 < n; j0 += 32) {
+            const int j = j0 + lane;  // ascending rows: hits are stored descending
+            int b = -1;
+            bool own = false;
+            if (j < n) {
+                b = h[n - 1 - j];
+                own = p.owner[b] == key;
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, own);
+            if (own) p.out_hits[o + __popc(bal & ((1u << lane) - 1u))] = __float_as_int(p.hits[b].w);
+            o += __popc(bal);
         }
     }
 }
@@ -500,9 +545,12 @@ static size_t grid_smem(int max_row)
     return 16 + (size_t)max_row * 36 + (size_t)(kMaxBinsPerRow + 4) * 4;
 }
 
-cudaError_t launch_plan(const KConst& k, const float* row_x_dev, const DevPtrs& p, cudaStream_t s)
+cudaError_t launch_plan(const KConst& k, const float* row_x_dev, const DevPtrs& p, int n_sm,
+                        cudaStream_t s)
 {
-    k_plan<<<1, 1024, 0, s>>>(k, row_x_dev, p);
+    int blocks = (p.R + 255) / 256;
+    blocks = blocks < 1 ? 1 : (blocks > n_sm * 8 ? n_sm * 8 : blocks);
+    k_plan<<<blocks, 256, 0, s>>>(k, row_x_dev, p);
     return cudaGetLastError();
 }
 
@@ -529,7 +577,9 @@ cudaError_t launch_clean(const KConst& k, const DevPtrs& p, int threads, int uni
 
 cudaError_t launch_start_scan(const KConst& k, const DevPtrs& p, cudaStream_t s)
 {
-    k_start_scan<<<1, 1024, 0, s>>>(k, p);
+    int ntiles = (p.R + kScanTile - 1) / kScanTile;
+    k_start_tiles<<<ntiles < 1 ? 1 : ntiles, 256, 0, s>>>(k, p);
+    k_start_top<<<1, 1024, 0, s>>>(k, p);
     return cudaGetLastError();
 }
 
@@ -546,12 +596,18 @@ cudaError_t launch_start_write(const KConst& k, const DevPtrs& p, int threads, i
     return cudaGetLastError();
 }
 
+cudaError_t launch_chain_end(const KConst& k, const DevPtrs& p, int n_sm, int u0, int u1, cudaStream_t s)
+{
+    k_chain_end<<<n_sm * 8, 256, 0, s>>>(k, p, u0, u1);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_select(const KConst& k, const DevPtrs& p, int n_sm, int u0, int u1, cudaStream_t s)
 {
-    k_owner<<<n_sm * 4, 256, 0, s>>>(k, p, u0, u1);
+    k_owner<<<n_sm * 8, 256, 0, s>>>(k, p, u0, u1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_accept<<<n_sm * 4, 256, 0, s>>>(k, p, u0, u1);
+    k_accept<<<n_sm * 8, 256, 0, s>>>(k, p, u0, u1);
     return cudaGetLastError();
 }
 
@@ -561,7 +617,7 @@ cudaError_t launch_emit(const KConst& k, const DevPtrs& p, int n_sm, cudaStream_
     if (nblk < 1) nblk = 1;
     k_scan_tiles<<<nblk, 256, 0, s>>>(p);
     k_scan_top<<<1, 1024, 0, s>>>(p);
-    k_emit<<<n_sm * 4, 256, 0, s>>>(k, p);
+    k_emit<<<n_sm * 8, 256, 0, s>>>(k, p);
     return cudaGetLastError();
 }
 

@@ -46,20 +46,26 @@ struct KConst {
     int n_rows, n_sectors;
 };
 
-// Search grid of one row: nbins = ny * nz, bin = iz * ny + iy.
+// Search grid of one row: nbins = ny * nz, bin = iz * ny + iy.  The grid
+// covers y in [y0, -y0] with y0 = -(X tan_h + y_margin) and z in the drift
+// half of the unit's side (z0 = 0 on side A, -z_max on side C).
 struct RowGrid {
-    float y0, z0, inv_by, inv_bz;
-    int ny, nz, bin_base, pad;
+    float inv_by, inv_bz;
+    int bin_base;  // first entry of the row's bin table in bin_off
+    int nyz;       // ny | nz << 16
 };
+__host__ __device__ __forceinline__ int grid_ny(const RowGrid& g) { return g.nyz & 0xffff; }
+__host__ __device__ __forceinline__ int grid_nz(const RowGrid& g) { return g.nyz >> 16; }
 
 // Device pointers of one call (one batch of events).
 struct DevPtrs {
     const float4* clusters;    // [N] input, (x, y, z, id bits)
     const int* row_cnt;        // [R]
-    int* row_off;              // [R + 1]
-    int* bin_cap_off;          // [R + 1] start of each row's bin table (x4 aligned)
+    const int* row_off;        // [R + 1] (planned on the host)
+    const int* bin_cap_off;    // [R + 1] start of each row's bin table (x4 aligned)
     RowGrid* grid;             // [R]
     float4* hits;              // [N] binned: (y, z, id bits, input position bits)
+    float2* hyz;               // [N] binned (y, z): what the window scans read
     int* bin_off;              // bin tables: absolute binned offsets
     int* up;                   // [N] binned space, before cleaning
     int* dn;
@@ -81,6 +87,7 @@ struct DevPtrs {
     int2* acc;                 // [Tcap] (accepted, owned hits)
     int2* acc_scan;            // [Tcap] exclusive scan of acc
     int2* scan_part;           // [ceil(Tcap / kScanTile) + 1]
+    int* start_part;           // [2 * (ceil(R / kScanTile) + 1)] tile sums of the start scans
     tpc_track* out_tracks;     // [Mcap]
     int* out_hits;             // [MHcap]
     int* counters;             // [kNumCounters]
@@ -186,7 +193,7 @@ __device__ __forceinline__ int bin_index(float v, float lo, float inv, int n)
 // ---------------------------------------------------------------------------
 namespace tpc_int {
 cudaError_t launch_plan(const tpc::KConst& k, const float* row_x_dev, const tpc::DevPtrs& p,
-                        cudaStream_t s);
+                        int n_sm, cudaStream_t s);
 cudaError_t launch_grid(const tpc::KConst& k, const float* row_x_dev, const tpc::DevPtrs& p,
                         int max_row, int threads, int unit0, int n_units, cudaStream_t s);
 cudaError_t launch_clean(const tpc::KConst& k, const tpc::DevPtrs& p, int threads, int unit0,
@@ -194,6 +201,8 @@ cudaError_t launch_clean(const tpc::KConst& k, const tpc::DevPtrs& p, int thread
 cudaError_t launch_start_scan(const tpc::KConst& k, const tpc::DevPtrs& p, cudaStream_t s);
 cudaError_t launch_start_write(const tpc::KConst& k, const tpc::DevPtrs& p, int threads, int unit0,
                                int n_units, cudaStream_t s);
+cudaError_t launch_chain_end(const tpc::KConst& k, const tpc::DevPtrs& p, int n_sm, int u0, int u1,
+                             cudaStream_t s);
 cudaError_t launch_select(const tpc::KConst& k, const tpc::DevPtrs& p, int n_sm, int t0_unit,
                           int t1_unit, cudaStream_t s);
 cudaError_t launch_emit(const tpc::KConst& k, const tpc::DevPtrs& p, int n_sm, cudaStream_t s);
@@ -210,7 +219,7 @@ cudaError_t launch_dump_tl_work(const tpc::DevPtrs& p, int T, int* dst, cudaStre
                                   int n_units, cudaStream_t s);                                   \
     cudaError_t launch_tracklets(const tpc::KConst& k, const float* row_x_dev,                    \
                                  const tpc::DevPtrs& p, int n_sm, int lanes_per_tracklet,         \
-                                 int t_first_unit, int t_last_unit, cudaStream_t s);
+                                 int schedule, int t_first_unit, int t_last_unit, cudaStream_t s);
 
 namespace tpc_exact { TPC_FP_DECLS }
 namespace tpc_fast { TPC_FP_DECLS }

@@ -37,6 +37,8 @@ struct tpc_tracker {
     int last_T = 0, last_M = 0, last_MH = 0;
     cudaStream_t last_stream = nullptr;
     int* counters_host = nullptr;  // pinned
+    int* plan_host = nullptr;      // pinned: row CSR offsets + bin-table offsets of a call
+    size_t plan_cap = 0;           // ints
     cudaEvent_t ev[6] = {};
     // graph replay of the batched stages
     cudaGraphExec_t graph_exec = nullptr;

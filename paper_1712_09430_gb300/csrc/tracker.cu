@@ -83,6 +83,7 @@ static const char* check_params(const tpc_params& P)
     if (t != 32 && t != 64 && t != 128 && t != 256) return "threads_per_row must be 32, 64, 128 or 256";
     int w = P.tracklets_per_warp;
     if (w != 1 && w != 2 && w != 4 && w != 8 && w != 16 && w != 32) return "tracklets_per_warp";
+    if (P.schedule != 0 && P.schedule != 1) return "schedule must be 0 or 1";
     return nullptr;
 }
 
@@ -114,6 +115,7 @@ extern "C" void tpc_params_default(tpc_params* p)
     p->tracklets_per_warp = 32;
     p->plain_per_sector = 0;
     p->use_graph = 0;
+    p->schedule = 0;
 }
 
 extern "C" int tpc_tracker_create(const tpc_geometry* g, double bz, const tpc_params* params,
@@ -180,6 +182,7 @@ extern "C" void tpc_tracker_destroy(tpc_tracker* tr)
     cudaFree(tr->row_x_dev);
     cudaFree(tr->dump_buf);
     cudaFreeHost(tr->counters_host);
+    cudaFreeHost(tr->plan_host);
     for (auto& e : tr->ev) if (e) cudaEventDestroy(e);
     if (tr->own_stream) cudaStreamDestroy(tr->own_stream);
     delete tr;
@@ -221,10 +224,12 @@ size_t tpc_layout(const tpc_tracker* tr, const BatchShape& sh, DevPtrs* p, char*
     DevPtrs q{};
     q.clusters = reinterpret_cast<const float4*>(take(N * 16));
     q.row_cnt = reinterpret_cast<const int*>(take(R * 4));
-    q.row_off = reinterpret_cast<int*>(take((R + 1) * 4));
-    q.bin_cap_off = reinterpret_cast<int*>(take((R + 1) * 4));
+    // row_off and bin_cap_off are adjacent: one H2D of the host plan fills both
+    q.row_off = reinterpret_cast<const int*>(take((R + 1) * 4 * 2));
+    q.bin_cap_off = q.row_off ? q.row_off + (R + 1) : nullptr;
     q.grid = reinterpret_cast<RowGrid*>(take(R * sizeof(RowGrid)));
     q.hits = reinterpret_cast<float4*>(take(N * 16));
+    q.hyz = reinterpret_cast<float2*>(take(N * 8));
     q.bin_off = reinterpret_cast<int*>(take((size_t)sh.bin_slots * 4));
     q.up = reinterpret_cast<int*>(take(N * 4));
     q.dn = reinterpret_cast<int*>(take(N * 4));
@@ -246,6 +251,7 @@ size_t tpc_layout(const tpc_tracker* tr, const BatchShape& sh, DevPtrs* p, char*
     q.acc = reinterpret_cast<int2*>(take(Tc * 8));
     q.acc_scan = reinterpret_cast<int2*>(take(Tc * 8));
     q.scan_part = reinterpret_cast<int2*>(take((Tc / kScanTile + 2) * 8));
+    q.start_part = reinterpret_cast<int*>(take((R / kScanTile + 2) * 2 * 4));
     q.out_tracks = reinterpret_cast<tpc_track*>(take(Tc * sizeof(tpc_track)));
     q.out_hits = reinterpret_cast<int*>(take(N * 4));
     q.counters = reinterpret_cast<int*>(take(kNumCounters * 4));
@@ -267,8 +273,23 @@ int tpc_shape(tpc_tracker* tr, const int32_t* row_counts, int n_events, BatchSha
     if (R > (1 << 28)) return tr->fail(TPC_ERR_INVALID, "too many rows in one call");
     int64_t N = 0, bins = 0;
     int max_row = 0, max3 = 0;
+    if ((size_t)(2 * (R + 1)) > tr->plan_cap) {
+        cudaFreeHost(tr->plan_host);
+        tr->plan_host = nullptr;
+        tr->plan_cap = 0;
+        size_t want = (size_t)(2 * (R + 1)) + (size_t)(R / 4) + 64;
+        if (cudaMallocHost(&tr->plan_host, want * sizeof(int)) != cudaSuccess) {
+            cudaGetLastError();
+            return tr->fail(TPC_ERR_NOMEM, "cannot allocate pinned plan buffer");
+        }
+        tr->plan_cap = want;
+    }
+    int* plan_off = tr->plan_host;           // [R + 1] CSR offsets of rows
+    int* plan_bins = tr->plan_host + R + 1;  // [R + 1] bin-table offsets
     for (int64_t r = 0; r < R; r++) {
         int c = row_counts[r];
+        plan_off[r] = (int)N;
+        plan_bins[r] = (int)bins;
         if (c < 0 || c > TPC_MAX_ROW_CLUSTERS) {
             char m[128];
             std::snprintf(m, sizeof m, "row_counts[%lld] = %d outside [0, %d]", (long long)r, c,
@@ -282,6 +303,9 @@ int tpc_shape(tpc_tracker* tr, const int32_t* row_counts, int n_events, BatchSha
         if (rr >= 1 && rr + 1 < NR) max3 = std::max(max3, row_counts[r - 1] + c + row_counts[r + 1]);
     }
     if (N >= (int64_t)1 << 30) return tr->fail(TPC_ERR_INVALID, "more than 2^30 clusters in one call");
+    if (bins >= (int64_t)1 << 31) return tr->fail(TPC_ERR_INVALID, "search grid too large for one call");
+    plan_off[R] = (int)N;
+    plan_bins[R] = (int)bins;
     sh->n_events = n_events;
     sh->n_units = n_events * S;
     sh->R = (int)R;
@@ -344,12 +368,13 @@ int tpc_enqueue(tpc_tracker* tr, const DevPtrs& p, const BatchShape& sh, cudaStr
                      : tpc_fast::launch_neighbours(kk, x, pp, max3, th, u0, nu, ss);
     };
     auto tl = [&](int u0, int u1) {
-        return exact ? tpc_exact::launch_tracklets(k, xd, p, tr->n_sm, 32 / P.tracklets_per_warp, u0, u1, s)
-                     : tpc_fast::launch_tracklets(k, xd, p, tr->n_sm, 32 / P.tracklets_per_warp, u0, u1, s);
+        const int lpt = 32 / P.tracklets_per_warp;
+        return exact ? tpc_exact::launch_tracklets(k, xd, p, tr->n_sm, lpt, P.schedule, u0, u1, s)
+                     : tpc_fast::launch_tracklets(k, xd, p, tr->n_sm, lpt, P.schedule, u0, u1, s);
     };
     const int th = P.threads_per_row;
     if (with_events) TPC_CUDA(cudaEventRecord(tr->ev[0], s));
-    TPC_CUDA(tpc_int::launch_plan(k, xd, p, s));
+    TPC_CUDA(tpc_int::launch_plan(k, xd, p, tr->n_sm, s));
     if (!P.plain_per_sector) {
         TPC_CUDA(tpc_int::launch_grid(k, xd, p, sh.max_row, th, 0, sh.n_units, s));
         if (with_events) TPC_CUDA(cudaEventRecord(tr->ev[1], s));
@@ -358,6 +383,7 @@ int tpc_enqueue(tpc_tracker* tr, const DevPtrs& p, const BatchShape& sh, cudaStr
         TPC_CUDA(tpc_int::launch_clean(k, p, th, 0, sh.n_units, s));
         TPC_CUDA(tpc_int::launch_start_scan(k, p, s));
         TPC_CUDA(tpc_int::launch_start_write(k, p, th, 0, sh.n_units, s));
+        TPC_CUDA(tpc_int::launch_chain_end(k, p, tr->n_sm, 0, sh.n_units, s));
         if (with_events) TPC_CUDA(cudaEventRecord(tr->ev[3], s));
         TPC_CUDA(tl(-1, -1));
         if (with_events) TPC_CUDA(cudaEventRecord(tr->ev[4], s));
@@ -371,7 +397,9 @@ int tpc_enqueue(tpc_tracker* tr, const DevPtrs& p, const BatchShape& sh, cudaStr
         if (with_events) TPC_CUDA(cudaEventRecord(tr->ev[2], s));
         for (int u = 0; u < sh.n_units; u++) TPC_CUDA(tpc_int::launch_clean(k, p, th, u, 1, s));
         TPC_CUDA(tpc_int::launch_start_scan(k, p, s));
+        // every unit's offsets are final only after all start_write launches
         for (int u = 0; u < sh.n_units; u++) TPC_CUDA(tpc_int::launch_start_write(k, p, th, u, 1, s));
+        for (int u = 0; u < sh.n_units; u++) TPC_CUDA(tpc_int::launch_chain_end(k, p, 1, u, u + 1, s));
         if (with_events) TPC_CUDA(cudaEventRecord(tr->ev[3], s));
         for (int u = 0; u < sh.n_units; u++) TPC_CUDA(tl(u, u + 1));
         if (with_events) TPC_CUDA(cudaEventRecord(tr->ev[4], s));
@@ -386,10 +414,10 @@ int tpc_enqueue(tpc_tracker* tr, const DevPtrs& p, const BatchShape& sh, cudaStr
 static std::string graph_key_of(const tpc_tracker* tr, const BatchShape& sh, const DevPtrs& p)
 {
     char b[256];
-    std::snprintf(b, sizeof b, "%d/%d/%d/%d/%d/%p/%p/%d/%d/%d/%d", sh.N, sh.R, sh.n_units, sh.max_row,
-                  sh.max3, (const void*)p.clusters, (const void*)p.counters, tr->params.exact_fp32,
-                  tr->params.threads_per_row, tr->params.tracklets_per_warp,
-                  tr->params.plain_per_sector);
+    std::snprintf(b, sizeof b, "%d/%d/%d/%d/%d/%p/%p/%d/%d/%d/%d/%d/%g", sh.N, sh.R, sh.n_units,
+                  sh.max_row, sh.max3, (const void*)p.clusters, (const void*)p.counters,
+                  tr->params.exact_fp32, tr->params.threads_per_row, tr->params.tracklets_per_warp,
+                  tr->params.plain_per_sector, tr->params.schedule, (double)tr->params.bin_target);
     return std::string(b);
 }
 
@@ -504,6 +532,8 @@ extern "C" int tpc_track_sectors(tpc_tracker* tr, const tpc_cluster* clusters, c
         p.clusters = reinterpret_cast<const float4*>(clusters);
     }
     TPC_CUDA(cudaMemcpyAsync(const_cast<int*>(p.row_cnt), row_counts, (size_t)sh.R * 4,
+                             cudaMemcpyHostToDevice, s));
+    TPC_CUDA(cudaMemcpyAsync(const_cast<int*>(p.row_off), tr->plan_host, (size_t)(sh.R + 1) * 8,
                              cudaMemcpyHostToDevice, s));
     tr->cur = p;
     tr->cur_shape = sh;

@@ -64,7 +64,8 @@ def test_exact_parity_multi_event_batch(events):
 @pytest.mark.parametrize("over", [dict(bin_target=0.5), dict(bin_target=8.0, threads_per_row=32),
                                   dict(bin_target=2.0, threads_per_row=256),
                                   dict(plain_per_sector=1), dict(use_graph=1),
-                                  dict(tracklets_per_warp=4)])
+                                  dict(tracklets_per_warp=4), dict(schedule=1),
+                                  dict(tracklets_per_warp=16, schedule=1)])
 def test_execution_params_do_not_change_results(events, over):
     ev = events["c3s"]
     base = gpu_run(ev.clusters, ev.row_counts, 1, exact_fp32=1)
