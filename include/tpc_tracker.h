@@ -237,6 +237,46 @@ int tpc_stage_times(tpc_tracker* tr, float* ms, int n);
  * tpc_tracker_create when tr is NULL). */
 const char* tpc_last_error(const tpc_tracker* tr);
 
+/* ---- allocation-free link finding -------------------------------------- *
+ * The paper has no counterpart of this entry point; it exists for callers
+ * that cannot allocate device memory while they run: components of an online
+ * trigger or readout chain whose device memory is divided among components
+ * once at start-up, and latency-critical loops where cudaMalloc or cudaFree
+ * would synchronize the device and add unbounded delays.
+ *
+ * It computes the same cleaned neighbour links as tpc_track_sectors (the
+ * TPC_DUMP_LINKS stage) for ONE event, and allocates nothing: every
+ * intermediate buffer lives in a fixed device array of
+ * TPC_NOALLOC_SCRATCH_BYTES inside the library, which every GPU that loads
+ * the library holds until the process exits.
+ *   g           geometry as for tpc_tracker_create (row_x on the host)
+ *   params      NULL for defaults; uses k_win, d_max2, l_seed, y_margin,
+ *               bin_target, threads_per_row and exact_fp32
+ *   d_clusters  DEVICE, 16-byte aligned, [N] grouped by (sector, row)
+ *   row_counts  HOST, [n_sectors * n_rows]
+ *   d_links     DEVICE output, int32 [2][N]: up links then down links, as
+ *               positions in d_clusters (-1: none)
+ *   cuda_stream stream to run on (NULL: the default stream); the call waits
+ *               for its own work before returning
+ * Limits and errors: at most TPC_NOALLOC_MAX_CLUSTERS clusters and
+ * n_sectors * n_rows <= 16384 rows; larger events return TPC_ERR_INVALID
+ * before any GPU work (use tpc_track_sectors for them).  TPC_ERR_NOMEM if the
+ * bin tables for this bin_target do not fit the fixed scratch,
+ * TPC_ERR_INVALID for bad arguments or input (NaN, x off its row),
+ * TPC_ERR_DEVICE for CUDA errors.
+ * Set-up: the first call on a device looks up the device address of the
+ * scratch with cudaGetSymbolAddress (that device current); make that first
+ * call before any stream capture.
+ * Sharing: all calls in the process use the same scratch, and each call
+ * overwrites what the previous one left there.  Two calls whose GPU work
+ * overlapped would race on it, so the function takes a process-wide lock
+ * and holds it until its GPU work has finished. */
+#define TPC_NOALLOC_MAX_CLUSTERS 65536
+#define TPC_NOALLOC_SCRATCH_BYTES (8u << 20)
+int tpc_links_noalloc(const tpc_geometry* g, const tpc_params* params,
+                      const tpc_cluster* d_clusters, const int32_t* row_counts,
+                      int32_t* d_links, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -30,6 +30,7 @@ UNITS = [
                                 "-DTPC_FP_NS=tpc_fast", "-DTPC_FAST_MATH=1"]),
     ("tracker.cu", "tracker.o", []),
     ("serve.cu", "serve.o", []),
+    ("noalloc.cu", "noalloc.o", []),
 ]
 
 

@@ -32,6 +32,7 @@ TPC_DUMP_TRACKLETS = 3
 TPC_DUMP_TRACKLET_N = 4
 TPC_DUMP_TRACKLET_HITS = 5
 TPC_DUMP_TRACKLET_WORK = 6
+TPC_NOALLOC_MAX_CLUSTERS = 65536
 
 STATUS_NAMES = {0: "TPC_OK", 1: "TPC_PENDING", 2: "TPC_BUSY", -1: "TPC_ERR_INVALID",
                 -2: "TPC_ERR_NOMEM", -3: "TPC_ERR_OUTPUT_TRUNCATED", -4: "TPC_ERR_TIMEOUT",
@@ -97,6 +98,7 @@ def lib() -> C.CDLL:
         L.tpc_stage_times.argtypes = [V, P(C.c_float), C.c_int]
         L.tpc_last_error.argtypes = [V]
         L.tpc_last_error.restype = C.c_char_p
+        L.tpc_links_noalloc.argtypes = [P(tpc_geometry), P(tpc_params), V, V, V, V]
         _LIB = L
     return _LIB
 
