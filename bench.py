@@ -44,19 +44,23 @@ WORKLOAD = "central Pb-Pb-like events: 10,000 primaries (pT exp mean 0.5 GeV/c, 
            "3,000 secondaries + 10% noise, 36 sectors x 159 pad rows, Bz=0.5 T"
 
 
-def _gen_event(seed):
+def _gen_event(job):
+    kind, seed = job
     from paper_1712_09430_gb300 import synth
-    ev = synth.central_event(seed=seed)
+    ev = synth.central_event(seed=seed) if kind == "central" else synth.min_bias_event(seed)
     return ev.clusters, ev.row_counts
 
 
-def make_batch(seeds):
-    # spawn: the pool starts before any CUDA use in this process
-    with mp.get_context("spawn").Pool(min(len(seeds), max(1, os.cpu_count() or 1), 16)) as pool:
-        parts = pool.map(_gen_event, seeds)
-    cl = np.ascontiguousarray(np.concatenate([p[0] for p in parts]))
-    rc = np.ascontiguousarray(np.concatenate([p[1] for p in parts]))
-    return cl, rc
+def make_inputs(central_seeds, mb_seeds):
+    """Central batch and min-bias pool, generated in a spawned process pool
+    (it starts before any CUDA use in this process)."""
+    jobs = [("central", s) for s in central_seeds] + [("minbias", s) for s in mb_seeds]
+    with mp.get_context("spawn").Pool(min(len(jobs), max(1, os.cpu_count() or 1), 16)) as pool:
+        parts = pool.map(_gen_event, jobs)
+    nc = len(central_seeds)
+    cl = np.ascontiguousarray(np.concatenate([p[0] for p in parts[:nc]]))
+    rc = np.ascontiguousarray(np.concatenate([p[1] for p in parts[:nc]]))
+    return cl, rc, parts[nc:]
 
 
 class ClockSampler:
@@ -176,7 +180,8 @@ def run_ours(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     seeds = [3 + rank * args.batch + i for i in range(args.batch)]
-    cl_np, rc_np = make_batch(seeds)           # before any CUDA use (spawned pool)
+    mb_seeds = [1000 + rank * args.pool + i for i in range(args.pool)] if args.stream_rate > 0 else []
+    cl_np, rc_np, mb_pool = make_inputs(seeds, mb_seeds)   # before any CUDA use
     import torch
     import ctypes as C
     dist = None
@@ -244,6 +249,12 @@ def run_ours(args):
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(L, tr, cl_np, rc_ptr, rc_np, B, N, world, sp, cap_t, cap_h, args)
+    plain = None
+    if args.plain_steps > 0:
+        plain = run_plain(L, tr, dev_cl, rc_ptr, B, N, world, sp, out, args)
+    stream_res = None
+    if args.stream_rate > 0:
+        stream_res = run_stream(tr, mb_pool, args)
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -282,11 +293,108 @@ def run_ours(args):
             "events_per_s": B * world / (ms * 1e-3),
             "stage_ms": stage_ms, "wall_s": wall,
             "gpu_launches": LAUNCHES_PER_STEP * args.steps,
-            "clocks": ck, "e2e": e2e, "roofline": rl, "cpu_baseline": cpu}
+            "clocks": ck, "e2e": e2e, "roofline": rl, "cpu_baseline": cpu,
+            "plain_per_sector": plain, "stream": stream_res}
+    if stream_res:
+        line["latency_ms"] = {"p50": stream_res["p50_ms"], "p99": stream_res["p99_ms"],
+                              "rate_hz": stream_res["rate_hz"]}
     print(json.dumps(line), flush=True)
     tr.close()
     if dist:
         dist.destroy_process_group()
+
+
+def run_plain(L, tr, dev_cl, rc_ptr, B, N, world, sp, out, args):
+    """The same batch with every stage launched once per (event, sector) unit
+    on one stream (the Run 1/2 scheduling), for comparison."""
+    import ctypes as C
+    import torch
+    from paper_1712_09430_gb300 import capi
+    tr.set_params(plain_per_sector=1, use_graph=0)
+    try:
+        def step():
+            r = L.tpc_track_sectors(tr.h, C.c_void_p(dev_cl.data_ptr()), rc_ptr, B,
+                                    capi.TPC_MEM_DEVICE, C.byref(out), sp)
+            if r != capi.TPC_OK:
+                raise RuntimeError(f"plain form: {tr.error()}")
+        step()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.plain_steps):
+            step()
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / args.plain_steps
+    finally:
+        tr.set_params(plain_per_sector=0, use_graph=1)
+    units = B * 36
+    return {"value": N * world / dt, "unit": "clusters/s", "ms_per_step": dt * 1e3,
+            "steps": args.plain_steps, "launches_per_step": units * 8 + 6,
+            "note": "every stage launched per (event, sector) unit on one stream"}
+
+
+def run_stream(tr0, pool, args):
+    """Serving: Poisson arrivals of min-bias events (sampled with replacement
+    from the pool) at args.stream_rate Hz for args.stream_seconds, through
+    tpc_stream_submit/poll.  Latency = result in hand - arrival (includes
+    queueing, H2D, the batched stages and D2H)."""
+    from paper_1712_09430_gb300 import synth
+    from paper_1712_09430_gb300.tracker import Tracker
+    p = tr0.params
+    tr = Tracker(synth.row_x(), bz=0.5, exact_fp32=p.exact_fp32, bin_target=p.bin_target,
+                 threads_per_row=p.threads_per_row, tracklets_per_warp=p.tracklets_per_warp,
+                 schedule=p.schedule)
+    try:
+        import torch
+        # events arrive in pinned host memory (as from a readout link) and are
+        # submitted without a copy; each stays untouched until its result is in
+        pool = [(torch.from_numpy(cl).pin_memory(), rc) for cl, rc in pool]
+        tr.stream_configure(arena_bytes=args.stream_arena_gb << 30, max_batch_events=args.stream_batch,
+                            max_inflight=2, no_copy=True)
+        rng = np.random.default_rng(5)
+        n_req = int(args.stream_rate * args.stream_seconds)
+        arrivals = np.cumsum(rng.exponential(1.0 / args.stream_rate, n_req))
+        picks = rng.integers(0, len(pool), n_req)
+        # warm-up: a few requests, drained
+        warm = [tr.submit(pool[i][0], pool[i][1], 1) for i in range(min(8, len(pool)))]
+        for t in warm:
+            while t is not None and tr.poll(t, 1000) is None:
+                pass
+        lat = np.zeros(n_req)
+        clusters = 0
+        nxt, done = 0, 0
+        outstanding = {}
+        backlog = []
+        t0 = time.perf_counter()
+        while done < n_req:
+            now = time.perf_counter() - t0
+            while nxt < n_req and arrivals[nxt] <= now:
+                backlog.append(nxt)
+                nxt += 1
+            while backlog:
+                i = backlog[0]
+                cl, rc = pool[picks[i]]
+                t = tr.submit(cl, rc, 1, tag=i)
+                if t is None:
+                    break               # not admitted now (memory/slots): retry later
+                outstanding[t] = i
+                backlog.pop(0)
+            for t in list(outstanding)[:64]:  # the oldest requests finish first
+                r = tr.poll(t, 0)
+                if r is None:
+                    continue
+                i = outstanding.pop(t)
+                lat[i] = time.perf_counter() - t0 - arrivals[i]
+                clusters += len(pool[picks[i]][0])
+                done += 1
+        wall = time.perf_counter() - t0
+    finally:
+        tr.close()
+    return {"rate_hz": args.stream_rate, "requests": n_req, "p50_ms": float(np.percentile(lat, 50) * 1e3),
+            "p99_ms": float(np.percentile(lat, 99) * 1e3), "max_ms": float(lat.max() * 1e3),
+            "clusters_per_s": clusters / wall, "events_per_s": n_req / wall, "wall_s": wall,
+            "pool_events": len(pool), "mean_clusters_per_event": float(np.mean([len(p[0]) for p in pool])),
+            "workload": "min-bias events (b ~ U[0,15] fm, 10-10,000 primaries + 30% secondaries, "
+                        "10% noise), Poisson arrivals, one event per request"}
 
 
 def run_e2e(L, tr, cl_np, rc_ptr, rc_np, B, N, world, sp, cap_t, cap_h, args):
@@ -356,6 +464,12 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling)")
+    ap.add_argument("--plain-steps", type=int, default=3, help="steps of the plain per-sector form")
+    ap.add_argument("--stream-rate", type=float, default=3000.0, help="Poisson arrivals (Hz); 0 = off")
+    ap.add_argument("--stream-seconds", type=float, default=3.0)
+    ap.add_argument("--stream-batch", type=int, default=64, help="most events per serving batch")
+    ap.add_argument("--stream-arena-gb", type=int, default=16)
+    ap.add_argument("--pool", type=int, default=96, help="min-bias events in the serving pool")
     args = ap.parse_args()
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

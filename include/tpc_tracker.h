@@ -28,6 +28,7 @@
 #ifndef TPC_TRACKER_H
 #define TPC_TRACKER_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -187,7 +188,8 @@ int tpc_track_sectors(tpc_tracker* tr, const tpc_cluster* clusters, const int32_
 int tpc_fetch_output(tpc_tracker* tr, tpc_output* out);
 
 /* Serving (Sec. 3.2, continuous batching).  Submit n_events events; the
- * library copies the input (host memory) before returning.  Events are
+ * library copies the input (host memory) before returning, unless the
+ * tracker was configured with TPC_STREAM_NO_COPY.  Events are
  * admitted while free device memory covers their reservation (input + 3x
  * internal buffers, Sec. 4.1) and a slot is free, else TPC_BUSY is returned
  * and nothing is kept.  Admitted events join the next batched replay; up to
@@ -195,6 +197,19 @@ int tpc_fetch_output(tpc_tracker* tr, tpc_output* out);
  *   ticket  receives an id for tpc_stream_poll. */
 int tpc_stream_submit(tpc_tracker* tr, const tpc_cluster* clusters, const int32_t* row_counts,
                       int n_events, uint64_t tag, uint64_t* ticket);
+
+/* Serving configuration, before the first submit: the device arena that
+ * admission draws on (0: half of the free device memory, at most 24 GiB),
+ * the most events one batch may hold, how many batches may run at once
+ * (1..8; each on its own stream), and flags:
+ *   TPC_STREAM_NO_COPY  tpc_stream_submit does not copy the clusters; the
+ *                       caller keeps the buffer valid and unchanged until the
+ *                       ticket's result has been polled (pinned host memory
+ *                       makes the copy to the device asynchronous).
+ * TPC_BUSY once serving has started. */
+#define TPC_STREAM_NO_COPY 1
+int tpc_stream_configure(tpc_tracker* tr, size_t arena_bytes, int max_batch_events, int max_inflight,
+                         int flags);
 
 /* Poll a ticket, waiting at most timeout_us (0: do not wait).  Returns
  * TPC_PENDING, TPC_OK (out filled; the ticket is released) or an error

@@ -33,6 +33,7 @@ TPC_DUMP_TRACKLET_N = 4
 TPC_DUMP_TRACKLET_HITS = 5
 TPC_DUMP_TRACKLET_WORK = 6
 TPC_NOALLOC_MAX_CLUSTERS = 65536
+TPC_STREAM_NO_COPY = 1
 
 STATUS_NAMES = {0: "TPC_OK", 1: "TPC_PENDING", 2: "TPC_BUSY", -1: "TPC_ERR_INVALID",
                 -2: "TPC_ERR_NOMEM", -3: "TPC_ERR_OUTPUT_TRUNCATED", -4: "TPC_ERR_TIMEOUT",
@@ -94,6 +95,7 @@ def lib() -> C.CDLL:
         L.tpc_fetch_output.argtypes = [V, P(tpc_output)]
         L.tpc_stream_submit.argtypes = [V, V, V, C.c_int, C.c_uint64, P(C.c_uint64)]
         L.tpc_stream_poll.argtypes = [V, C.c_uint64, P(tpc_output), C.c_int]
+        L.tpc_stream_configure.argtypes = [V, C.c_size_t, C.c_int, C.c_int, C.c_int]
         L.tpc_debug_dump.argtypes = [V, C.c_int, V, C.c_int64, P(C.c_int64)]
         L.tpc_stage_times.argtypes = [V, P(C.c_float), C.c_int]
         L.tpc_last_error.argtypes = [V]

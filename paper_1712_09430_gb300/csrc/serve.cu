@@ -1,20 +1,496 @@
-// Request loop (continuous batching): placeholder until the serving path lands.
+// Request loop with continuous batching (Sec. 3.2: independent events share
+// the GPU "as long as the GPU memory suffices").
+//
+// tpc_stream_submit admits a request when the free part of the serving arena
+// covers its reservation and a slot is free; the input is copied to pinned
+// host memory before the call returns.  Admitted requests wait in a FIFO.
+// Whenever fewer than max_inflight batches run, all pending requests (up to
+// max_batch_events events) form the next batch: one H2D per request, the
+// batched stages of tpc_track_sectors on the batch's own stream, and a D2H
+// of the counters and of an estimated output (fetch the rest if the estimate
+// was short, Sec. 3.1).  Requests that arrive while batches run join the
+// next one.  tpc_stream_poll drives the loop and hands out each request's
+// slice of its batch's output.
+#include <algorithm>
+#include <chrono>
+#include <cstdlib>
+#include <cstring>
+#include <thread>
+
 #include "tpc_serve.h"
 
-struct ServeState {};
+using namespace tpc;
 
-void tpc_serve_shutdown(tpc_tracker* tr) { (void)tr; }
-bool tpc_serve_busy(const tpc_tracker* tr) { (void)tr; return false; }
+namespace {
 
-extern "C" int tpc_stream_submit(tpc_tracker* tr, const tpc_cluster*, const int32_t*, int, uint64_t,
-                                 uint64_t*)
+size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
+struct Request {
+    uint64_t ticket = 0, tag = 0;
+    int n_events = 0;
+    int N = 0;
+    std::vector<int32_t> row_counts;
+    size_t pin_off = 0, pin_bytes = 0;  // input copy in the pinned staging
+    const tpc_cluster* src = nullptr;   // caller's buffer when submitted without a copy
+    size_t reserve = 0;                 // arena bytes reserved at admission
+    int state = 0;                      // 0 pending, 1 in flight, 2 done, 3 failed
+    int batch = -1;
+    int err = TPC_OK;
+    // slice of the batch output
+    int e0 = 0, cl0 = 0;                // first event / cluster of the request in the batch
+    int t0 = 0;                         // first canonical tracklet id of the request
+    int m0 = 0, m1 = 0;                 // track range
+    int h0 = 0, h1 = 0;                 // hit range
+};
+
+struct Batch {
+    int id = -1;
+    bool busy = false;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+    size_t arena_off = 0, arena_bytes = 0;
+    BatchShape sh;
+    DevPtrs p{};
+    std::vector<uint64_t> tickets;
+    // pinned per-batch host buffers
+    int* plan = nullptr;                // row counts, row offsets, bin offsets
+    size_t plan_cap = 0;
+    int* counters = nullptr;            // [kNumCounters]
+    tpc_track* tracks = nullptr;
+    int* hits = nullptr;
+    size_t tracks_cap = 0, hits_cap = 0;
+    int est_tracks = 0, est_hits = 0;   // what the D2H enqueued
+    int open_results = 0;               // requests of the batch not yet polled
+};
+
+// First-fit allocator over [0, size) with coalescing.
+struct Arena {
+    size_t size = 0;
+    std::vector<std::pair<size_t, size_t>> free;  // (offset, bytes), sorted
+    void init(size_t s)
+    {
+        size = s;
+        free.clear();
+        if (s) free.push_back({0, s});
+    }
+    bool alloc(size_t bytes, size_t* off)
+    {
+        for (size_t i = 0; i < free.size(); i++) {
+            if (free[i].second >= bytes) {
+                *off = free[i].first;
+                free[i].first += bytes;
+                free[i].second -= bytes;
+                if (!free[i].second) free.erase(free.begin() + (long)i);
+                return true;
+            }
+        }
+        return false;
+    }
+    void release(size_t off, size_t bytes)
+    {
+        auto it = std::lower_bound(free.begin(), free.end(), std::make_pair(off, size_t(0)));
+        it = free.insert(it, {off, bytes});
+        size_t i = (size_t)(it - free.begin());
+        if (i + 1 < free.size() && free[i].first + free[i].second == free[i + 1].first) {
+            free[i].second += free[i + 1].second;
+            free.erase(free.begin() + (long)i + 1);
+        }
+        if (i > 0 && free[i - 1].first + free[i - 1].second == free[i].first) {
+            free[i - 1].second += free[i].second;
+            free.erase(free.begin() + (long)i);
+        }
+    }
+};
+
+bool fault(const char* name)
 {
-    if (!tr) return TPC_ERR_INVALID;
-    return tr->fail(TPC_ERR_INVALID, "serving not available");
+    const char* v = std::getenv(name);
+    return v && *v && std::strcmp(v, "0") != 0;
 }
 
-extern "C" int tpc_stream_poll(tpc_tracker* tr, uint64_t, tpc_output*, int)
+}  // namespace
+
+struct ServeState {
+    size_t arena_bytes = 0;        // 0: choose at first submit
+    int max_batch_events = 64;
+    int max_inflight = 2;
+    int max_requests = 4096;
+    int flags = 0;                 // TPC_STREAM_NO_COPY
+    void* arena_base = nullptr;
+    Arena arena;                   // device workspace of running batches
+    size_t reserved = 0;           // admission: sum of reservations of live requests
+    char* pin = nullptr;           // pinned input staging
+    Arena pin_arena;
+    std::deque<uint64_t> pending;
+    std::map<uint64_t, Request> req;
+    std::vector<Batch> batches;    // slots
+    uint64_t next_ticket = 1;
+    int next_batch = 0;
+    int inflight = 0;
+    double tracks_per_cluster = 0.012, hits_per_cluster = 0.9;  // D2H estimate, adapted
+};
+
+static int serve_init(tpc_tracker* tr)
+{
+    ServeState* S = tr->serve;
+    if (S->arena_base) return TPC_OK;
+    if (!S->arena_bytes) {
+        size_t fr = 0, tot = 0;
+        if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return tr->fail(TPC_ERR_DEVICE, "cudaMemGetInfo");
+        S->arena_bytes = std::min<size_t>(fr / 2, (size_t)24 << 30);
+    }
+    if (fault("TPC_FAULT_ALLOC") || cudaMalloc(&S->arena_base, S->arena_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        S->arena_base = nullptr;
+        return tr->fail(TPC_ERR_NOMEM, "cannot allocate the serving arena");
+    }
+    S->arena.init(S->arena_bytes);
+    const size_t pin_bytes = std::max<size_t>(S->arena_bytes / 8, (size_t)64 << 20);
+    if (cudaMallocHost(&S->pin, pin_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(S->arena_base);
+        S->arena_base = nullptr;
+        return tr->fail(TPC_ERR_NOMEM, "cannot allocate pinned staging");
+    }
+    S->pin_arena.init(pin_bytes);
+    // slots: running batches plus finished ones whose results wait for polls
+    S->batches.resize((size_t)(2 * S->max_inflight + 2));
+    for (auto& b : S->batches) {
+        if (cudaStreamCreateWithFlags(&b.stream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&b.done, cudaEventDisableTiming) != cudaSuccess ||
+            cudaMallocHost(&b.counters, sizeof(int) * kNumCounters) != cudaSuccess)
+            return tr->fail(TPC_ERR_DEVICE, "cannot create serving streams");
+    }
+    return TPC_OK;
+}
+
+static int grow_pinned(tpc_tracker* tr, void** ptr, size_t* cap, size_t want)
+{
+    if (want <= *cap) return TPC_OK;
+    cudaFreeHost(*ptr);
+    *ptr = nullptr;
+    *cap = 0;
+    size_t n = want + want / 4 + 4096;
+    if (cudaMallocHost(ptr, n) != cudaSuccess) {
+        cudaGetLastError();
+        return tr->fail(TPC_ERR_NOMEM, "pinned result buffer");
+    }
+    *cap = n;
+    return TPC_OK;
+}
+
+// Launch all pending requests (up to max_batch_events events) as one batch.
+static int launch_batch(tpc_tracker* tr)
+{
+    ServeState* S = tr->serve;
+    Batch* b = nullptr;
+    for (auto& x : S->batches)
+        if (!x.busy) { b = &x; break; }
+    if (S->pending.empty()) return TPC_OK;
+    if (!b) return TPC_BUSY;  // every slot holds results not yet polled
+    // take requests in arrival order
+    std::vector<uint64_t> take;
+    int ev = 0;
+    for (uint64_t t : S->pending) {
+        const Request& r = S->req[t];
+        if (!take.empty() && ev + r.n_events > S->max_batch_events) break;
+        take.push_back(t);
+        ev += r.n_events;
+    }
+    const int NR = tr->geom.n_rows, NS = tr->geom.n_sectors;
+    const size_t R = (size_t)ev * NS * NR;
+    // the batch's row counts (in a pinned buffer: counts, then the plan)
+    // pinned: counts [R], plan [2 (R + 1)], first tracklet id per event [ev + 1]
+    if (grow_pinned(tr, reinterpret_cast<void**>(&b->plan), &b->plan_cap,
+                    (3 * R + 2 + (size_t)ev + 1) * sizeof(int)) != TPC_OK)
+        return TPC_ERR_NOMEM;
+    int* counts = b->plan;
+    size_t pos = 0;
+    for (uint64_t t : take) {
+        const Request& r = S->req[t];
+        std::memcpy(counts + pos, r.row_counts.data(), r.row_counts.size() * sizeof(int));
+        pos += r.row_counts.size();
+    }
+    BatchShape sh;
+    int rc = tpc_shape(tr, counts, ev, &sh);  // fills tr->plan_host
+    if (rc != TPC_OK) return rc;
+    std::memcpy(counts + R, tr->plan_host, (R + 1) * 2 * sizeof(int));
+    const size_t bytes = align256(tpc_layout(tr, sh, nullptr, nullptr));
+    size_t off = 0;
+    if (!S->arena.alloc(bytes, &off)) return TPC_BUSY;  // wait for a running batch
+    b->id = S->next_batch++;
+    b->busy = true;
+    b->arena_off = off;
+    b->arena_bytes = bytes;
+    b->sh = sh;
+    b->tickets = take;
+    tpc_layout(tr, sh, &b->p, static_cast<char*>(S->arena_base) + off);
+    const DevPtrs& p = b->p;
+    cudaStream_t s = b->stream;
+    int e0 = 0, cl0 = 0;
+    cudaError_t e = cudaSuccess;
+    for (uint64_t t : take) {
+        Request& r = S->req[t];
+        r.state = 1;
+        r.batch = (int)(b - S->batches.data());
+        r.e0 = e0;
+        r.cl0 = cl0;
+        const void* src = r.src ? static_cast<const void*>(r.src) : S->pin + r.pin_off;
+        if (r.N && e == cudaSuccess)
+            e = cudaMemcpyAsync(const_cast<float4*>(p.clusters) + cl0, src, (size_t)r.N * 16,
+                                cudaMemcpyHostToDevice, s);
+        e0 += r.n_events;
+        cl0 += r.N;
+    }
+    S->pending.erase(S->pending.begin(), S->pending.begin() + (long)take.size());
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(const_cast<int*>(p.row_cnt), counts, R * sizeof(int), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(const_cast<int*>(p.row_off), counts + R, (R + 1) * 2 * sizeof(int),
+                            cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return tr->fail(TPC_ERR_DEVICE, cudaGetErrorString(e));
+    S->inflight++;
+    if (sh.N > 0) {
+        rc = tpc_enqueue(tr, p, sh, s, false);
+        if (rc != TPC_OK) return rc;
+        // estimated output, fetched right after the last kernel (Sec. 3.1)
+        b->est_tracks = std::min<int>(sh.t_cap, (int)(S->tracks_per_cluster * sh.N * 1.3) + 256);
+        b->est_hits = std::min<int>(sh.N, (int)(S->hits_per_cluster * sh.N * 1.3) + 4096);
+        if (grow_pinned(tr, reinterpret_cast<void**>(&b->tracks), &b->tracks_cap,
+                        sizeof(tpc_track) * (size_t)b->est_tracks) != TPC_OK ||
+            grow_pinned(tr, reinterpret_cast<void**>(&b->hits), &b->hits_cap,
+                        sizeof(int) * (size_t)b->est_hits) != TPC_OK)
+            return TPC_ERR_NOMEM;
+        e = cudaMemcpyAsync(b->counters, p.counters, sizeof(int) * kNumCounters, cudaMemcpyDeviceToHost, s);
+        // first canonical tracklet id of every event: start_off at each event's first row
+        const size_t ev_rows = (size_t)NS * NR;
+        if (e == cudaSuccess)
+            e = cudaMemcpy2DAsync(b->plan + 3 * R + 2, sizeof(int), p.start_off, ev_rows * sizeof(int),
+                                  sizeof(int), (size_t)ev + 1, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(b->tracks, p.out_tracks, sizeof(tpc_track) * (size_t)b->est_tracks,
+                                cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(b->hits, p.out_hits, sizeof(int) * (size_t)b->est_hits,
+                                cudaMemcpyDeviceToHost, s);
+    } else {
+        std::memset(b->counters, 0, sizeof(int) * kNumCounters);
+        std::memset(b->plan + 3 * R + 2, 0, sizeof(int) * ((size_t)ev + 1));
+        b->est_tracks = b->est_hits = 0;
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(b->done, s);
+    if (e != cudaSuccess) return tr->fail(TPC_ERR_DEVICE, cudaGetErrorString(e));
+    return TPC_OK;
+}
+
+// A finished batch: fetch the rest if the estimate was short, slice the
+// output per request, free the device workspace.
+static void finish_batch(tpc_tracker* tr, Batch& b)
+{
+    ServeState* S = tr->serve;
+    int err = TPC_OK;
+    const int* c = b.counters;
+    const int M = b.sh.N ? c[C_M] : 0, MH = b.sh.N ? c[C_MH] : 0;
+    if (b.sh.N && (c[C_ERR] & E_INPUT)) err = TPC_ERR_INVALID;
+    if (b.sh.N && (c[C_ERR] & E_TIMEOUT)) err = TPC_ERR_TIMEOUT;
+    if (err == TPC_OK && (M > b.est_tracks || MH > b.est_hits)) {
+        // the estimate was short: fetch the remainder now
+        void* tp = b.tracks;
+        void* hp = b.hits;
+        size_t tc = b.tracks_cap, hc = b.hits_cap;
+        std::vector<tpc_track> keep_t(b.tracks, b.tracks + std::min(M, b.est_tracks));
+        std::vector<int> keep_h(b.hits, b.hits + std::min(MH, b.est_hits));
+        if (grow_pinned(tr, &tp, &tc, sizeof(tpc_track) * (size_t)M) != TPC_OK ||
+            grow_pinned(tr, &hp, &hc, sizeof(int) * (size_t)MH) != TPC_OK) {
+            err = TPC_ERR_NOMEM;
+        } else {
+            b.tracks = static_cast<tpc_track*>(tp);
+            b.hits = static_cast<int*>(hp);
+            b.tracks_cap = tc;
+            b.hits_cap = hc;
+            if (cudaMemcpy(b.tracks, b.p.out_tracks, sizeof(tpc_track) * (size_t)M, cudaMemcpyDeviceToHost) !=
+                    cudaSuccess ||
+                cudaMemcpy(b.hits, b.p.out_hits, sizeof(int) * (size_t)MH, cudaMemcpyDeviceToHost) != cudaSuccess)
+                err = TPC_ERR_DEVICE;
+        }
+    }
+    if (b.sh.N > 0) {  // adapt the estimate to what central/min-bias events produce
+        S->tracks_per_cluster = std::max(S->tracks_per_cluster * 0.9, (double)M / b.sh.N);
+        S->hits_per_cluster = std::max(S->hits_per_cluster * 0.9, (double)MH / b.sh.N);
+    }
+    // tracks are in canonical order: grouped by event, so by request
+    int m = 0;
+    b.open_results = 0;
+    const int* tbase = b.plan + 3 * (size_t)b.sh.R + 2;
+    for (uint64_t t : b.tickets) {
+        Request& r = S->req[t];
+        r.t0 = tbase[r.e0];
+        r.err = err;
+        r.state = err == TPC_OK ? 2 : 3;
+        r.m0 = m;
+        while (err == TPC_OK && m < M && b.tracks[m].event < r.e0 + r.n_events) m++;
+        r.m1 = m;
+        r.h0 = r.m1 > r.m0 ? b.tracks[r.m0].hit_off : 0;
+        r.h1 = r.m1 > r.m0 ? b.tracks[r.m1 - 1].hit_off + b.tracks[r.m1 - 1].nhits : 0;
+        if (r.pin_bytes) S->pin_arena.release(r.pin_off, r.pin_bytes);
+        r.pin_bytes = 0;
+        b.open_results++;
+    }
+    S->arena.release(b.arena_off, b.arena_bytes);
+    S->inflight--;
+}
+
+static int progress(tpc_tracker* tr)
+{
+    ServeState* S = tr->serve;
+    for (auto& b : S->batches) {
+        if (!b.busy || b.open_results) continue;
+        if (b.tickets.empty()) continue;
+        cudaError_t q = cudaEventQuery(b.done);
+        if (q == cudaErrorNotReady) continue;
+        if (q != cudaSuccess) return tr->fail(TPC_ERR_DEVICE, cudaGetErrorString(q));
+        finish_batch(tr, b);
+        if (!b.open_results) {
+            b.busy = false;
+            b.tickets.clear();
+        }
+    }
+    while (!S->pending.empty() && S->inflight < S->max_inflight) {
+        int rc = launch_batch(tr);
+        if (rc == TPC_BUSY) break;  // arena fragmented: wait for a running batch
+        if (rc != TPC_OK) return rc;
+    }
+    return TPC_OK;
+}
+
+void tpc_serve_shutdown(tpc_tracker* tr)
+{
+    ServeState* S = tr->serve;
+    if (!S) return;
+    for (auto& b : S->batches) {
+        if (b.stream) cudaStreamSynchronize(b.stream);
+        if (b.stream) cudaStreamDestroy(b.stream);
+        if (b.done) cudaEventDestroy(b.done);
+        cudaFreeHost(b.plan);
+        cudaFreeHost(b.counters);
+        cudaFreeHost(b.tracks);
+        cudaFreeHost(b.hits);
+    }
+    cudaFree(S->arena_base);
+    cudaFreeHost(S->pin);
+    delete S;
+    tr->serve = nullptr;
+}
+
+bool tpc_serve_busy(const tpc_tracker* tr) { return tr->serve && !tr->serve->req.empty(); }
+
+extern "C" int tpc_stream_configure(tpc_tracker* tr, size_t arena_bytes, int max_batch_events,
+                                    int max_inflight, int flags)
 {
     if (!tr) return TPC_ERR_INVALID;
-    return tr->fail(TPC_ERR_INVALID, "serving not available");
+    if (tr->serve && (tr->serve->arena_base || !tr->serve->req.empty()))
+        return tr->fail(TPC_BUSY, "serving already started");
+    if (max_batch_events < 1 || max_inflight < 1 || max_inflight > 8)
+        return tr->fail(TPC_ERR_INVALID, "max_batch_events >= 1, max_inflight in [1, 8]");
+    if (!tr->serve) tr->serve = new ServeState();
+    tr->serve->arena_bytes = arena_bytes;
+    tr->serve->max_batch_events = max_batch_events;
+    tr->serve->max_inflight = max_inflight;
+    tr->serve->flags = flags;
+    return TPC_OK;
+}
+
+extern "C" int tpc_stream_submit(tpc_tracker* tr, const tpc_cluster* clusters, const int32_t* row_counts,
+                                 int n_events, uint64_t tag, uint64_t* ticket)
+{
+    if (!tr) return TPC_ERR_INVALID;
+    if (!row_counts || !ticket || n_events < 1) return tr->fail(TPC_ERR_INVALID, "NULL argument or n_events < 1");
+    if (cudaSetDevice(tr->dev) != cudaSuccess) return tr->fail(TPC_ERR_DEVICE, "cudaSetDevice");
+    if (!tr->serve) tr->serve = new ServeState();
+    int rc = serve_init(tr);
+    if (rc != TPC_OK) return rc;
+    ServeState* S = tr->serve;
+    rc = progress(tr);
+    if (rc != TPC_OK) return rc;
+    BatchShape sh;
+    rc = tpc_shape(tr, row_counts, n_events, &sh);
+    if (rc != TPC_OK) return rc;
+    if (sh.N > 0 && !clusters) return tr->fail(TPC_ERR_INVALID, "NULL clusters");
+    if (n_events > S->max_batch_events) return tr->fail(TPC_ERR_INVALID, "more events than max_batch_events");
+    // admission: the request's own workspace (input + ~3x internal buffers,
+    // Sec. 4.1) must fit the free part of the arena, and a slot must be free
+    const size_t reserve = align256(tpc_layout(tr, sh, nullptr, nullptr)) + ((size_t)1 << 20);
+    if (reserve > S->arena.size) return tr->fail(TPC_ERR_NOMEM, "request larger than the serving arena");
+    if (fault("TPC_FAULT_ADMIT") || S->reserved + reserve > S->arena.size ||
+        (int)S->req.size() >= S->max_requests)
+        return TPC_BUSY;
+    size_t pin_off = 0;
+    const bool no_copy = (S->flags & TPC_STREAM_NO_COPY) != 0;
+    const size_t pin_bytes = no_copy ? 0 : align256((size_t)sh.N * 16);
+    if (pin_bytes && !S->pin_arena.alloc(pin_bytes, &pin_off)) return TPC_BUSY;
+    if (pin_bytes) std::memcpy(S->pin + pin_off, clusters, (size_t)sh.N * 16);
+    Request r;
+    r.ticket = S->next_ticket++;
+    r.tag = tag;
+    r.n_events = n_events;
+    r.N = sh.N;
+    r.row_counts.assign(row_counts, row_counts + sh.R);
+    r.pin_off = pin_off;
+    r.pin_bytes = pin_bytes;
+    r.src = no_copy ? clusters : nullptr;
+    r.reserve = reserve;
+    S->reserved += reserve;
+    S->req[r.ticket] = std::move(r);
+    S->pending.push_back(S->next_ticket - 1);
+    *ticket = S->next_ticket - 1;
+    rc = progress(tr);
+    return rc == TPC_OK ? TPC_OK : rc;
+}
+
+extern "C" int tpc_stream_poll(tpc_tracker* tr, uint64_t ticket, tpc_output* out, int timeout_us)
+{
+    if (!tr) return TPC_ERR_INVALID;
+    if (!out) return tr->fail(TPC_ERR_INVALID, "NULL output");
+    if (!tr->serve) return TPC_ERR_UNKNOWN_TICKET;
+    if (cudaSetDevice(tr->dev) != cudaSuccess) return tr->fail(TPC_ERR_DEVICE, "cudaSetDevice");
+    ServeState* S = tr->serve;
+    const auto t_end = std::chrono::steady_clock::now() + std::chrono::microseconds(std::max(0, timeout_us));
+    while (true) {
+        int rc = progress(tr);
+        if (rc != TPC_OK) return rc;
+        auto it = S->req.find(ticket);
+        if (it == S->req.end()) return TPC_ERR_UNKNOWN_TICKET;
+        Request& r = it->second;
+        if (r.state >= 2) {
+            Batch& b = S->batches[(size_t)r.batch];
+            int result = r.err;
+            if (result == TPC_OK) {
+                const int M = r.m1 - r.m0, MH = r.h1 - r.h0;
+                out->n_tracks = M;
+                out->n_hits = MH;
+                if (M > out->cap_tracks || MH > out->cap_hits)
+                    return tr->fail(TPC_ERR_OUTPUT_TRUNCATED, "output capacity too small");
+                if (out->mem_kind != TPC_MEM_HOST)
+                    return tr->fail(TPC_ERR_INVALID, "stream results are returned in host memory");
+                for (int m = 0; m < M; m++) {
+                    tpc_track t = b.tracks[r.m0 + m];
+                    t.event -= r.e0;
+                    t.tracklet -= r.t0;
+                    t.hit_off -= r.h0;
+                    out->tracks[m] = t;
+                }
+                for (int h = 0; h < MH; h++) out->hit_ids[h] = b.hits[r.h0 + h] - r.cl0;
+            }
+            S->reserved -= r.reserve;
+            S->req.erase(it);
+            if (--b.open_results == 0) {
+                b.busy = false;
+                b.tickets.clear();
+                progress(tr);
+            }
+            return result == TPC_OK ? TPC_OK : tr->fail(result, "batch failed");
+        }
+        if (std::chrono::steady_clock::now() >= t_end) return TPC_PENDING;
+        std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
 }

@@ -144,6 +144,52 @@ class Tracker:
         self.check(rc)
         return Result(tracks[:out.n_tracks], hits[:out.n_hits])
 
+    # ---- serving (continuous batching) -----------------------------------
+    def stream_configure(self, arena_bytes=0, max_batch_events=64, max_inflight=2, no_copy=False):
+        self.check(lib().tpc_stream_configure(self.h, int(arena_bytes), int(max_batch_events),
+                                              int(max_inflight),
+                                              capi.TPC_STREAM_NO_COPY if no_copy else 0))
+
+    def submit(self, clusters, row_counts, n_events=1, tag=0):
+        """Returns a ticket, or None when the request is not admitted now.
+        clusters: numpy float32 [N, 4] or a (pinned) torch CPU tensor; with
+        no_copy the caller keeps it alive until the result is polled."""
+        cl = clusters if hasattr(clusters, "data_ptr") else np.ascontiguousarray(clusters,
+                                                                                 dtype=np.float32)
+        rc_arr = np.ascontiguousarray(row_counts, dtype=np.int32)
+        t = C.c_uint64()
+        rc = lib().tpc_stream_submit(self.h, _ptr(cl), _ptr(rc_arr), int(n_events), int(tag),
+                                     C.byref(t))
+        if rc == capi.TPC_BUSY:
+            return None
+        self.check(rc)
+        return int(t.value)
+
+    def poll(self, ticket, timeout_us=0, cap_tracks=None, cap_hits=None):
+        """Result of a ticket, or None while it is pending.  The output
+        buffers are kept between calls and grown on demand."""
+        ct = cap_tracks if cap_tracks is not None else self._est_tracks
+        ch = cap_hits if cap_hits is not None else self._est_hits
+        while True:
+            buf = getattr(self, "_poll_buf", None)
+            if buf is None or len(buf[0]) < ct or len(buf[1]) < ch:
+                buf = (np.zeros(max(ct, 1), TRACK_DTYPE), np.zeros(max(ch, 1), np.int32))
+                self._poll_buf = buf
+            tracks, hits = buf
+            out = capi.tpc_output(tracks.ctypes.data, hits.ctypes.data, len(tracks), len(hits),
+                                  capi.TPC_MEM_HOST, 0, 0)
+            rc = lib().tpc_stream_poll(self.h, int(ticket), C.byref(out), int(timeout_us))
+            if rc == capi.TPC_PENDING:
+                return None
+            if rc == capi.TPC_ERR_OUTPUT_TRUNCATED and cap_tracks is None:
+                ct, ch = max(out.n_tracks, 1), max(out.n_hits, 1)
+                self._est_tracks = max(self._est_tracks, int(ct * 1.25) + 16)
+                self._est_hits = max(self._est_hits, int(ch * 1.25) + 256)
+                ct, ch = self._est_tracks, self._est_hits
+                continue
+            self.check(rc)
+            return Result(tracks[:out.n_tracks].copy(), hits[:out.n_hits].copy())
+
     def dump(self, what):
         n = C.c_int64()
         # probe the size
