@@ -180,7 +180,7 @@ def run_ours(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     seeds = [3 + rank * args.batch + i for i in range(args.batch)]
-    mb_seeds = [1000 + rank * args.pool + i for i in range(args.pool)] if args.stream_rate > 0 else []
+    mb_seeds = [1000 + rank * args.pool + i for i in range(args.pool)] if args.stream_rates else []
     cl_np, rc_np, mb_pool = make_inputs(seeds, mb_seeds)   # before any CUDA use
     import torch
     import ctypes as C
@@ -212,6 +212,11 @@ def run_ours(args):
         if r != capi.TPC_OK:
             raise RuntimeError(f"tpc_track_sectors: {capi.STATUS_NAMES.get(r)}: {tr.error()}")
 
+    tuned = None
+    if args.autotune:
+        from paper_1712_09430_gb300 import autotune
+        fields, tuned_ms = autotune.tune(tr, dev_cl, rc_np, B, reps=3)
+        tuned = dict(fields, ms=tuned_ms)
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -253,8 +258,8 @@ def run_ours(args):
     if args.plain_steps > 0:
         plain = run_plain(L, tr, dev_cl, rc_ptr, B, N, world, sp, out, args)
     stream_res = None
-    if args.stream_rate > 0:
-        stream_res = run_stream(tr, mb_pool, args)
+    if args.stream_rates:
+        stream_res = [run_stream(tr, mb_pool, args, rate) for rate in args.stream_rates]
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -273,8 +278,12 @@ def run_ours(args):
     rl = None
     if algo is not None:
         achieved = algo["bytes"] / (stage_ms[dom] * 1e-3) / 1e9
+        traffic = None
+        if B == 8 and not args.exact:
+            traffic = measured_traffic(os.path.join(ROOT, "paper_1712_09430_gb300", "csrc", "k_fp.cu"),
+                                       os.path.join(ROOT, "profiles", "k_tracklets_sched_traffic_central8.md"))
         rl = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-              "frac": achieved / hbm, "traffic": None, "kernel": "k_tracklets_sched",
+              "frac": achieved / hbm, "traffic": traffic, "kernel": "k_tracklets_sched",
               "algorithmic_bytes_per_launch": algo["bytes"], "model": algo["model"],
               "counts": {k: v for k, v in algo.items() if k not in ("bytes", "model")},
               "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy) of measured" if peaks else "fallback"}
@@ -285,9 +294,12 @@ def run_ours(args):
             "config": {"workload": WORKLOAD, "events_per_step": B, "events_per_rank": B,
                        "clusters_per_step": int(N) * world, "tracks_per_step": int(M),
                        "tracklets_per_step": int(T), "mode": "exact" if args.exact else "production",
-                       "launch": "batched, CUDA graph replay", "bin_target": args.bin_target,
-                       "threads_per_row": args.threads_per_row,
-                       "tracklets_per_warp": args.tracklets_per_warp, "schedule": args.schedule,
+                       "launch": "batched, CUDA graph replay",
+                       "autotuned": tuned is not None,
+                       "bin_target": float(tr.params.bin_target),
+                       "threads_per_row": int(tr.params.threads_per_row),
+                       "tracklets_per_warp": int(tr.params.tracklets_per_warp),
+                       "schedule": int(tr.params.schedule),
                        "l2": f"inputs larger than L2 ({N * 16 / 1e6:.0f} MB of clusters per step)",
                        "parallelism": f"events sharded over {world} GPU(s), no collective"},
             "events_per_s": B * world / (ms * 1e-3),
@@ -296,8 +308,8 @@ def run_ours(args):
             "clocks": ck, "e2e": e2e, "roofline": rl, "cpu_baseline": cpu,
             "plain_per_sector": plain, "stream": stream_res}
     if stream_res:
-        line["latency_ms"] = {"p50": stream_res["p50_ms"], "p99": stream_res["p99_ms"],
-                              "rate_hz": stream_res["rate_hz"]}
+        line["latency_ms"] = {"p50": stream_res[0]["p50_ms"], "p99": stream_res[0]["p99_ms"],
+                              "rate_hz": stream_res[0]["rate_hz"]}
     print(json.dumps(line), flush=True)
     tr.close()
     if dist:
@@ -332,9 +344,9 @@ def run_plain(L, tr, dev_cl, rc_ptr, B, N, world, sp, out, args):
             "note": "every stage launched per (event, sector) unit on one stream"}
 
 
-def run_stream(tr0, pool, args):
+def run_stream(tr0, pool, args, rate):
     """Serving: Poisson arrivals of min-bias events (sampled with replacement
-    from the pool) at args.stream_rate Hz for args.stream_seconds, through
+    from the pool) at `rate` Hz for args.stream_seconds, through
     tpc_stream_submit/poll.  Latency = result in hand - arrival (includes
     queueing, H2D, the batched stages and D2H)."""
     from paper_1712_09430_gb300 import synth
@@ -351,8 +363,8 @@ def run_stream(tr0, pool, args):
         tr.stream_configure(arena_bytes=args.stream_arena_gb << 30, max_batch_events=args.stream_batch,
                             max_inflight=2, no_copy=True)
         rng = np.random.default_rng(5)
-        n_req = int(args.stream_rate * args.stream_seconds)
-        arrivals = np.cumsum(rng.exponential(1.0 / args.stream_rate, n_req))
+        n_req = int(rate * args.stream_seconds)
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, n_req))
         picks = rng.integers(0, len(pool), n_req)
         # warm-up: a few requests, drained
         warm = [tr.submit(pool[i][0], pool[i][1], 1) for i in range(min(8, len(pool)))]
@@ -389,7 +401,7 @@ def run_stream(tr0, pool, args):
         wall = time.perf_counter() - t0
     finally:
         tr.close()
-    return {"rate_hz": args.stream_rate, "requests": n_req, "p50_ms": float(np.percentile(lat, 50) * 1e3),
+    return {"rate_hz": rate, "requests": n_req, "p50_ms": float(np.percentile(lat, 50) * 1e3),
             "p99_ms": float(np.percentile(lat, 99) * 1e3), "max_ms": float(lat.max() * 1e3),
             "clusters_per_s": clusters / wall, "events_per_s": n_req / wall, "wall_s": wall,
             "pool_events": len(pool), "mean_clusters_per_event": float(np.mean([len(p[0]) for p in pool])),
@@ -432,6 +444,28 @@ def run_e2e(L, tr, cl_np, rc_ptr, rc_np, B, N, world, sp, cap_t, cap_h, args):
             "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_s * 1e3, "steps": k2}
 
 
+def measured_traffic(kernel_source, summary):
+    """DRAM bytes per launch of the tracklet kernel from a committed ncu
+    summary, valid only while the kernel source is the one it was taken on
+    (its SHA-1 is recorded in the summary); None otherwise."""
+    import hashlib
+    try:
+        src = hashlib.sha1(open(kernel_source, "rb").read()).hexdigest()
+        fields = {}
+        for line in open(summary):
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                fields[k.strip().strip("`- ")] = v.strip().strip("`")
+    except OSError:
+        return None
+    if fields.get("source_sha1") != src:
+        return None
+    try:
+        return float(fields["traffic_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
 def algorithmic_bytes(tr, N, T):
     """Bytes the tracklet constructor moves by its own stage structure,
     counted exactly per tracklet by the kernel (TPC_DUMP_TRACKLET_WORK):
@@ -461,12 +495,16 @@ def main():
     ap.add_argument("--threads-per-row", type=int, default=128)
     ap.add_argument("--tracklets-per-warp", type=int, default=32)
     ap.add_argument("--schedule", type=int, default=0, help="0 unit by unit, 1 by start row")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="use the given execution parameters instead of tuning them first")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling)")
     ap.add_argument("--plain-steps", type=int, default=3, help="steps of the plain per-sector form")
-    ap.add_argument("--stream-rate", type=float, default=3000.0, help="Poisson arrivals (Hz); 0 = off")
-    ap.add_argument("--stream-seconds", type=float, default=3.0)
+    ap.add_argument("--stream-rates", type=lambda v: [float(x) for x in v.split(",") if x.strip()],
+                    default=[1000.0, 3000.0, 5000.0],
+                    help="Poisson arrival rates (Hz) of the serving leg, comma separated; '' = off")
+    ap.add_argument("--stream-seconds", type=float, default=2.0)
     ap.add_argument("--stream-batch", type=int, default=64, help="most events per serving batch")
     ap.add_argument("--stream-arena-gb", type=int, default=16)
     ap.add_argument("--pool", type=int, default=96, help="min-bias events in the serving pool")

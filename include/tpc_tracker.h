@@ -187,6 +187,18 @@ int tpc_track_sectors(tpc_tracker* tr, const tpc_cluster* clusters, const int32_
  * example into larger buffers after TPC_ERR_OUTPUT_TRUNCATED). */
 int tpc_fetch_output(tpc_tracker* tr, tpc_output* out);
 
+/* Autotuner of the execution fields (the batched launch of Sec. 3 has no
+ * fixed best shape on a new GPU; the paper tunes its number of command
+ * queues the same way, Fig. 3).  Runs the batch given exactly as
+ * tpc_track_sectors would, for candidate values of schedule, bin_target,
+ * tracklets_per_warp and threads_per_row (coordinate descent, two passes,
+ * each candidate scored by the median device time of `reps` runs), keeps
+ * the fastest in the tracker and writes it to *best (may be NULL).
+ * Results do not depend on these fields, so tuning never changes output.
+ * *best_ms receives the device time of the winner (may be NULL). */
+int tpc_autotune(tpc_tracker* tr, const tpc_cluster* clusters, const int32_t* row_counts,
+                 int n_events, int mem_kind, int reps, tpc_params* best, float* best_ms);
+
 /* Serving (Sec. 3.2, continuous batching).  Submit n_events events; the
  * library copies the input (host memory) before returning, unless the
  * tracker was configured with TPC_STREAM_NO_COPY.  Events are

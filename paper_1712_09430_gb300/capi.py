@@ -93,6 +93,7 @@ def lib() -> C.CDLL:
         L.tpc_tracker_set_params.argtypes = [V, P(tpc_params)]
         L.tpc_track_sectors.argtypes = [V, V, V, C.c_int, C.c_int, P(tpc_output), V]
         L.tpc_fetch_output.argtypes = [V, P(tpc_output)]
+        L.tpc_autotune.argtypes = [V, V, V, C.c_int, C.c_int, C.c_int, P(tpc_params), P(C.c_float)]
         L.tpc_stream_submit.argtypes = [V, V, V, C.c_int, C.c_uint64, P(C.c_uint64)]
         L.tpc_stream_poll.argtypes = [V, C.c_uint64, P(tpc_output), C.c_int]
         L.tpc_stream_configure.argtypes = [V, C.c_size_t, C.c_int, C.c_int, C.c_int]

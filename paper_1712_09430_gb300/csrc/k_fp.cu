@@ -105,38 +105,67 @@ __global__ void k_neighbours(KConst k, const float* __restrict__ row_x, DevPtrs 
         int bu = -1, bd = -1;
         unsigned bid_u = 0, bid_d = 0;
         float bD = 0.0f;
-        for (int bzu = uz0; bzu <= uz1; bzu++) {
-            const int ju0 = bins[tu + bzu * nyu + uy0] - off_d;
-            const int ju1 = bins[tu + bzu * nyu + uy1 + 1] - off_d;
-            for (int ju = ju0; ju < ju1; ju++) {
-                const float4 cu = rec[ju];
-                if (!(fabsf(cu.x - ycu) <= Wu && fabsf(cu.y - zi) <= Wu)) continue;
-                const unsigned idu = __float_as_uint(cu.z);
-                for (int bzd = dz0; bzd <= dz1; bzd++) {
-                    const int jd0 = bins[td + bzd * nyd + dy0] - off_d;
-                    const int jd1 = bins[td + bzd * nyd + dy1 + 1] - off_d;
-                    for (int jd = jd0; jd < jd1; jd++) {
-                        const float4 cd = rec[jd];
-                        if (!(fabsf(cd.x - ycd) <= Wd && fabsf(cd.y - zi) <= Wd)) continue;
-                        const float yp = cd.x + (cu.x - cd.x) * tt;
-                        const float zp = cd.y + (cu.y - cd.y) * tt;
-                        const float ey = yi - yp;
-                        const float ez = zi - zp;
-                        const float D = ey * ey + ez * ez;
-                        if (!(D <= k.d_max2)) continue;
-                        const unsigned idd = __float_as_uint(cd.z);
-                        bool better;
-                        if (bu < 0) better = true;
-                        else if (D < bD) better = true;
-                        else if (D > bD) better = false;
-                        else if (idu != bid_u) better = idu < bid_u;
-                        else better = idd < bid_d;
-                        if (better) {
-                            bu = ju;
-                            bd = jd;
-                            bD = D;
-                            bid_u = idu;
-                            bid_d = idd;
+        // pair (u, d) -> keep the best by (D, id_u, id_d)
+        auto consider = [&](int ju, const float4& cu, int jd, const float4& cd) {
+            const float yp = cd.x + (cu.x - cd.x) * tt;
+            const float zp = cd.y + (cu.y - cd.y) * tt;
+            const float ey = yi - yp;
+            const float ez = zi - zp;
+            const float D = ey * ey + ez * ez;
+            if (!(D <= k.d_max2)) return;
+            const unsigned idu = __float_as_uint(cu.z), idd = __float_as_uint(cd.z);
+            bool better;
+            if (bu < 0) better = true;
+            else if (D < bD) better = true;
+            else if (D > bD) better = false;
+            else if (idu != bid_u) better = idu < bid_u;
+            else better = idd < bid_d;
+            if (better) {
+                bu = ju;
+                bd = jd;
+                bD = D;
+                bid_u = idu;
+                bid_d = idd;
+            }
+        };
+        // down candidates once, into a register list of up to 4
+        int nd = 0;
+        int jd0 = -1, jd1 = -1, jd2 = -1, jd3 = -1;
+        float4 cd0 = make_float4(0.f, 0.f, 0.f, 0.f), cd1 = cd0, cd2 = cd0, cd3 = cd0;
+        for (int bzd = dz0; bzd <= dz1; bzd++) {
+            const int j0 = bins[td + bzd * nyd + dy0] - off_d;
+            const int j1 = bins[td + bzd * nyd + dy1 + 1] - off_d;
+            for (int jd = j0; jd < j1; jd++) {
+                const float4 cd = rec[jd];
+                if (!(fabsf(cd.x - ycd) <= Wd && fabsf(cd.y - zi) <= Wd)) continue;
+                jd3 = jd2; cd3 = cd2;
+                jd2 = jd1; cd2 = cd1;
+                jd1 = jd0; cd1 = cd0;
+                jd0 = jd; cd0 = cd;
+                nd++;
+            }
+        }
+        if (nd > 0) {
+            for (int bzu = uz0; bzu <= uz1; bzu++) {
+                const int ju0 = bins[tu + bzu * nyu + uy0] - off_d;
+                const int ju1 = bins[tu + bzu * nyu + uy1 + 1] - off_d;
+                for (int ju = ju0; ju < ju1; ju++) {
+                    const float4 cu = rec[ju];
+                    if (!(fabsf(cu.x - ycu) <= Wu && fabsf(cu.y - zi) <= Wu)) continue;
+                    if (nd <= 4) {
+                        consider(ju, cu, jd0, cd0);
+                        if (nd > 1) consider(ju, cu, jd1, cd1);
+                        if (nd > 2) consider(ju, cu, jd2, cd2);
+                        if (nd > 3) consider(ju, cu, jd3, cd3);
+                    } else {  // a crowded window: scan the down row again
+                        for (int bzd = dz0; bzd <= dz1; bzd++) {
+                            const int j0 = bins[td + bzd * nyd + dy0] - off_d;
+                            const int j1 = bins[td + bzd * nyd + dy1 + 1] - off_d;
+                            for (int jd = j0; jd < j1; jd++) {
+                                const float4 cd = rec[jd];
+                                if (!(fabsf(cd.x - ycd) <= Wd && fabsf(cd.y - zi) <= Wd)) continue;
+                                consider(ju, cu, jd, cd);
+                            }
                         }
                     }
                 }
@@ -380,6 +409,11 @@ __device__ __forceinline__ int search_row(const State& st, const RowGrid& g, flo
 // (phases 1, 2), filter on a hit.  Phase 0/1: Phase 1 through the seed chain,
 // then outward; phase 2: fresh covariance, inward from the outermost cluster
 // to row 0, collecting the tracklet's clusters.
+// The committed filter state of every lane lives in shared memory (16
+// floats, field-major so a warp's accesses hit distinct banks); registers
+// hold only the prediction of the current step.
+constexpr int kTlThreads = 256;
+
 struct Lane {
     int t;        // tracklet, -1 idle
     int phase;    // 0 chain, 1 outward search, 2 inward search
@@ -389,12 +423,42 @@ struct Lane {
     int r_out;    // row of the outermost filtered cluster
     int miss, n;
     bool have;
-    float chi2;
     float z0;     // grid z origin of the unit's side
     RowGrid g;    // grid record of row r, loaded one step ahead
-    State st;
+    float* sp;    // this lane's state column in shared memory (stride kTlThreads)
     int4 work;
 };
+
+__device__ __forceinline__ State load_state(const float* sp)
+{
+    State s;
+    s.x = sp[0 * kTlThreads];
+    s.y = sp[1 * kTlThreads];
+    s.z = sp[2 * kTlThreads];
+    s.s = sp[3 * kTlThreads];
+    s.t = sp[4 * kTlThreads];
+    s.q = sp[5 * kTlThreads];
+#pragma unroll
+    for (int i = 0; i < 6; i++) s.cy[i] = sp[(6 + i) * kTlThreads];
+#pragma unroll
+    for (int i = 0; i < 3; i++) s.cz[i] = sp[(12 + i) * kTlThreads];
+    return s;
+}
+
+__device__ __forceinline__ void store_state(float* sp, const State& s, float chi2)
+{
+    sp[0 * kTlThreads] = s.x;
+    sp[1 * kTlThreads] = s.y;
+    sp[2 * kTlThreads] = s.z;
+    sp[3 * kTlThreads] = s.s;
+    sp[4 * kTlThreads] = s.t;
+    sp[5 * kTlThreads] = s.q;
+#pragma unroll
+    for (int i = 0; i < 6; i++) sp[(6 + i) * kTlThreads] = s.cy[i];
+#pragma unroll
+    for (int i = 0; i < 3; i++) sp[(12 + i) * kTlThreads] = s.cz[i];
+    sp[15 * kTlThreads] = chi2;
+}
 
 __device__ __forceinline__ void lane_init(Lane& L, int t, const KConst& k, const float* xs,
                                           const DevPtrs& p)
@@ -410,16 +474,17 @@ __device__ __forceinline__ void lane_init(Lane& L, int t, const KConst& k, const
     const int rL = r0 + e.y - 1;
     const float4 c0 = p.hits[h0];
     const float4 cL = p.hits[e.x];
-    L.st.x = xs[r0];
-    L.st.y = c0.x;
-    L.st.z = c0.y;
+    State st;
+    st.x = xs[r0];
+    st.y = c0.x;
+    st.z = c0.y;
     const float dx = xs[rL] - xs[r0], dy = cL.x - c0.x, dz = cL.y - c0.y;
     const float l = sqrtf(dx * dx + dy * dy);
-    L.st.s = dy / l;
-    L.st.t = dz / l;
-    L.st.q = 0.0f;
-    reset_cov(L.st, k);
-    L.chi2 = 0.0f;
+    st.s = dy / l;
+    st.t = dz / l;
+    st.q = 0.0f;
+    reset_cov(st, k);
+    store_state(L.sp, st, 0.0f);
     L.phase = 0;
     L.r = r0;
     L.h = h0;
@@ -434,19 +499,21 @@ __device__ __forceinline__ void lane_init(Lane& L, int t, const KConst& k, const
 __device__ __forceinline__ void lane_finish(Lane& L, const KConst& k, const DevPtrs& p, bool writer)
 {
     if (writer) {
+        // outputs are read only by the selection kernels: evict-first stores
+        // keep the row data of the units in flight in L2
         const int t = L.t;
-        p.tl_n[t] = L.n;
-        p.tl_work[t] = L.work;
+        __stcs(p.tl_n + t, L.n);
+        __stcs(p.tl_work + t, L.work);
         float4* f4 = reinterpret_cast<float4*>(p.tl_f + (size_t)t * kTlFloats);
         if (L.n > 0) {
-            const State& s = L.st;
-            f4[0] = make_float4(s.x, s.y, s.z, s.s);
-            f4[1] = make_float4(s.t, s.q, s.cy[0], s.cy[1]);
-            f4[2] = make_float4(s.cy[2], s.cy[3], s.cy[4], s.cy[5]);
-            f4[3] = make_float4(s.cz[0], s.cz[1], s.cz[2], L.chi2);
+            const float* sp = L.sp;
+#pragma unroll
+            for (int i = 0; i < 4; i++)
+                __stcs(f4 + i, make_float4(sp[(4 * i) * kTlThreads], sp[(4 * i + 1) * kTlThreads],
+                                           sp[(4 * i + 2) * kTlThreads], sp[(4 * i + 3) * kTlThreads]));
         } else {
             const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-            f4[0] = z; f4[1] = z; f4[2] = z; f4[3] = z;
+            __stcs(f4 + 0, z); __stcs(f4 + 1, z); __stcs(f4 + 2, z); __stcs(f4 + 3, z);
         }
     }
     L.t = -1;
@@ -457,7 +524,7 @@ __device__ __forceinline__ void lane_step(Lane& L, const KConst& k, const float*
                                           const DevPtrs& p, int gl, unsigned gmask)
 {
     const int NR = k.n_rows;
-    State pr = L.st;
+    State pr = load_state(L.sp);
     const float X = xs[L.r];
     const bool ok = propagate(pr, X, k.kB, k.s_max) && !outside(pr, X, k);
     int j = -1;
@@ -472,10 +539,11 @@ __device__ __forceinline__ void lane_step(Lane& L, const KConst& k, const float*
     }
     bool end_phase = !ok;
     if (j >= 0) {
-        update(pr, c.x, c.y, k.sy2, k.sz2, L.chi2);
-        L.st = pr;
+        float chi2 = L.sp[15 * kTlThreads];
+        update(pr, c.x, c.y, k.sy2, k.sz2, chi2);
+        store_state(L.sp, pr, chi2);
         if (L.phase == 2) {
-            if (gl == 0) p.tl_hits[(size_t)L.t * NR + L.n] = j;  // rows descending
+            if (gl == 0) __stcs(p.tl_hits + (size_t)L.t * NR + L.n, j);  // rows descending
             L.n++;
         } else {
             L.r_out = L.r;
@@ -502,8 +570,18 @@ __device__ __forceinline__ void lane_step(Lane& L, const KConst& k, const float*
     if (end_phase) {
         if (L.phase < 2 && L.have) {
             L.phase = 2;
-            reset_cov(L.st, k);
-            L.chi2 = 0.0f;
+            // fresh covariance and chi2 at the Phase-1 state
+            float* sp = L.sp;
+            sp[6 * kTlThreads] = k.sy2;
+            sp[7 * kTlThreads] = 0.0f;
+            sp[8 * kTlThreads] = k.var_s;
+            sp[9 * kTlThreads] = 0.0f;
+            sp[10 * kTlThreads] = 0.0f;
+            sp[11 * kTlThreads] = k.var_q;
+            sp[12 * kTlThreads] = k.sz2;
+            sp[13 * kTlThreads] = 0.0f;
+            sp[14 * kTlThreads] = k.var_t;
+            sp[15 * kTlThreads] = 0.0f;
             L.r = L.r_out;
             L.n = 0;
             L.miss = 0;
@@ -521,10 +599,11 @@ __device__ __forceinline__ void lane_step(Lane& L, const KConst& k, const float*
 constexpr int kTrackletCtasPerSm = 4;  // 256 threads each: 32 warps per SM, <= 64 registers
 
 template <int G>
-__global__ void __launch_bounds__(256, kTrackletCtasPerSm)
+__global__ void __launch_bounds__(kTlThreads, kTrackletCtasPerSm)
     k_tracklets_sched(KConst k, const float* __restrict__ row_x, DevPtrs p, int by_row)
 {
     __shared__ float xs[TPC_MAX_ROWS];
+    __shared__ float st_sh[16 * kTlThreads];
     for (int r = threadIdx.x; r < k.n_rows; r += blockDim.x) xs[r] = row_x[r];
     __syncthreads();
     const unsigned FULL = 0xffffffffu;
@@ -535,6 +614,7 @@ __global__ void __launch_bounds__(256, kTrackletCtasPerSm)
     const unsigned gmask = (G == 32) ? FULL : (((1u << G) - 1u) << gbase);
     Lane L;
     L.t = -1;
+    L.sp = st_sh + threadIdx.x;
     bool done = false;
     while (true) {
         const unsigned need = __ballot_sync(FULL, L.t < 0 && !done && gl == 0);
@@ -558,16 +638,18 @@ __global__ void __launch_bounds__(256, kTrackletCtasPerSm)
 // Plain form (the Run 1/2 scheme, Sec. 3): the tracklets of units [u0, u1)
 // in canonical order, statically assigned, each thread running one tracklet
 // to completion before the next.
-__global__ void __launch_bounds__(256, 3) k_tracklets_plain(KConst k, const float* __restrict__ row_x,
-                                                            DevPtrs p, int u0, int u1)
+__global__ void __launch_bounds__(kTlThreads, 3) k_tracklets_plain(KConst k, const float* __restrict__ row_x,
+                                                                   DevPtrs p, int u0, int u1)
 {
     __shared__ float xs[TPC_MAX_ROWS];
+    __shared__ float st_sh[16 * kTlThreads];
     for (int r = threadIdx.x; r < k.n_rows; r += blockDim.x) xs[r] = row_x[r];
     __syncthreads();
     const int t0 = p.start_off[u0 * k.n_rows], t1 = p.start_off[u1 * k.n_rows];
     const unsigned self = 1u << (threadIdx.x & 31);
     for (int t = t0 + blockIdx.x * blockDim.x + threadIdx.x; t < t1; t += gridDim.x * blockDim.x) {
         Lane L;
+        L.sp = st_sh + threadIdx.x;
         lane_init(L, t, k, xs, p);
         while (L.t >= 0) lane_step<1>(L, k, xs, p, 0, self);
     }
@@ -591,17 +673,17 @@ cudaError_t launch_tracklets(const KConst& k, const float* row_x_dev, const DevP
                              int lanes_per_tracklet, int schedule, int u0, int u1, cudaStream_t s)
 {
     if (u0 >= 0) {
-        k_tracklets_plain<<<n_sm * 2, 256, 0, s>>>(k, row_x_dev, p, u0, u1);
+        k_tracklets_plain<<<n_sm * 2, kTlThreads, 0, s>>>(k, row_x_dev, p, u0, u1);
         return cudaGetLastError();
     }
     const int grid = n_sm * kTrackletCtasPerSm;  // one wave of resident CTAs
     switch (lanes_per_tracklet) {
-        case 1: k_tracklets_sched<1><<<grid, 256, 0, s>>>(k, row_x_dev, p, schedule); break;
-        case 2: k_tracklets_sched<2><<<grid, 256, 0, s>>>(k, row_x_dev, p, schedule); break;
-        case 4: k_tracklets_sched<4><<<grid, 256, 0, s>>>(k, row_x_dev, p, schedule); break;
-        case 8: k_tracklets_sched<8><<<grid, 256, 0, s>>>(k, row_x_dev, p, schedule); break;
-        case 16: k_tracklets_sched<16><<<grid, 256, 0, s>>>(k, row_x_dev, p, schedule); break;
-        default: k_tracklets_sched<32><<<grid, 256, 0, s>>>(k, row_x_dev, p, schedule); break;
+        case 1: k_tracklets_sched<1><<<grid, kTlThreads, 0, s>>>(k, row_x_dev, p, schedule); break;
+        case 2: k_tracklets_sched<2><<<grid, kTlThreads, 0, s>>>(k, row_x_dev, p, schedule); break;
+        case 4: k_tracklets_sched<4><<<grid, kTlThreads, 0, s>>>(k, row_x_dev, p, schedule); break;
+        case 8: k_tracklets_sched<8><<<grid, kTlThreads, 0, s>>>(k, row_x_dev, p, schedule); break;
+        case 16: k_tracklets_sched<16><<<grid, kTlThreads, 0, s>>>(k, row_x_dev, p, schedule); break;
+        default: k_tracklets_sched<32><<<grid, kTlThreads, 0, s>>>(k, row_x_dev, p, schedule); break;
     }
     return cudaGetLastError();
 }

@@ -216,12 +216,16 @@ __global__ void k_grid(KConst k, const float* __restrict__ row_x, DevPtrs p, int
 // ------------------------------------------------------ clean + start hits
 // up'[i] = up[i] if dn[up[i]] == i (and symmetric), from the pre-clean
 // arrays; start(i) = up'[i] >= 0, dn'[i] < 0 and a chain of >= l_seed hits.
-__global__ void k_clean(KConst k, DevPtrs p, int rr0)
+__global__ void k_clean(KConst k, DevPtrs p, int rr0, int rows)
 {
-    const int rr = rr0 + blockIdx.x;
+    // one warp per row
+    const int lane = threadIdx.x & 31;
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (w >= rows) return;
+    const int rr = rr0 + w;
     const int b0 = p.row_off[rr], b1 = p.row_off[rr + 1];
     int nstart = 0;
-    for (int b = b0 + (int)threadIdx.x; b < b1; b += blockDim.x) {
+    for (int b = b0 + lane; b < b1; b += 32) {
         int u = p.up[b], d = p.dn[b];
         int u2 = (u >= 0 && p.dn[u] == b) ? u : -1;
         int d2 = (d >= 0 && p.up[d] == b) ? d : -1;
@@ -242,9 +246,8 @@ __global__ void k_clean(KConst k, DevPtrs p, int rr0)
         p.is_start[b] = (unsigned char)st;
         nstart += st;
     }
-    int total;
-    block_excl_sum<int>(nstart, &total);
-    if (threadIdx.x == 0) p.row_nstart[rr] = total;
+    nstart = __reduce_add_sync(0xffffffffu, nstart);
+    if (lane == 0) p.row_nstart[rr] = nstart;
 }
 
 // Tracklet offsets per row in canonical (unit, row) order and in the
@@ -304,47 +307,70 @@ __global__ void __launch_bounds__(1024) k_start_top(KConst k, DevPtrs p)
     }
 }
 
-// One CTA per row: finish the row's offsets, then number its start hits by
-// cluster id.
-__global__ void k_start_write(KConst k, DevPtrs p, int rr0)
+// One warp per row: finish the row's offsets, then number its start hits by
+// cluster id (rank = number of start hits of the row with a smaller id).
+constexpr int kStartWarpBuf = 128;  // start hits ranked in shared memory; more use global reads
+
+__global__ void k_start_write(KConst k, DevPtrs p, int rr0, int rows)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ int n_sh, t0_sh, s0_sh;
-    const int rr = rr0 + blockIdx.x;
+    __shared__ unsigned sid_sh[8][kStartWarpBuf];
+    __shared__ int sb_sh[8][kStartWarpBuf];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (w >= rows) return;
+    const int rr = rr0 + w;
     const int m = p.row_nstart[rr];
-    if (threadIdx.x == 0) {
+    int t0 = 0, s0 = 0;
+    if (lane == 0) {
         const int ntiles = (p.R + kScanTile - 1) / kScanTile;
         const int j = (rr % k.n_rows) * p.n_units + rr / k.n_rows;
-        const int t0 = p.start_off[rr] + p.start_part[rr / kScanTile];
-        const int s0 = p.sched_off[rr] + p.start_part[ntiles + 1 + j / kScanTile];
+        t0 = p.start_off[rr] + p.start_part[rr / kScanTile];
+        s0 = p.sched_off[rr] + p.start_part[ntiles + 1 + j / kScanTile];
         p.start_off[rr] = t0;
         p.sched_off[rr] = s0;
-        t0_sh = t0;
-        s0_sh = s0;
-        n_sh = 0;
     }
     if (m == 0) return;
-    unsigned* sid = reinterpret_cast<unsigned*>(smem);
-    int* sb = reinterpret_cast<int*>(sid + m);
-    __syncthreads();
+    t0 = __shfl_sync(0xffffffffu, t0, 0);
+    s0 = __shfl_sync(0xffffffffu, s0, 0);
+    unsigned* sid = sid_sh[wib];
+    int* sb = sb_sh[wib];
     const int b0 = p.row_off[rr], b1 = p.row_off[rr + 1];
-    for (int b = b0 + (int)threadIdx.x; b < b1; b += blockDim.x) {
-        if (p.is_start[b]) {
-            int pos = atomicAdd(&n_sh, 1);
+    // compact the row's start hits (ballot prefix), in row order
+    int n = 0;
+    for (int c0 = b0; c0 < b1; c0 += 32) {
+        const int b = c0 + lane;
+        const bool st = b < b1 && p.is_start[b];
+        const unsigned bal = __ballot_sync(0xffffffffu, st);
+        const int pos = n + __popc(bal & ((1u << lane) - 1u));
+        if (st && pos < kStartWarpBuf) {
             sid[pos] = __float_as_uint(p.hits[b].z);
             sb[pos] = b;
         }
+        n += __popc(bal);
     }
-    __syncthreads();
-    const int t0 = t0_sh, s0 = s0_sh;
-    for (int i = threadIdx.x; i < m; i += blockDim.x) {
-        unsigned v = sid[i];
-        int rank = 0;
-        for (int j = 0; j < m; j++) rank += sid[j] < v;
-        int t = t0 + rank;
-        p.start[t] = sb[i];
-        p.t_row[t] = rr;
-        p.sched[s0 + rank] = t;
+    __syncwarp();
+    if (m <= kStartWarpBuf) {
+        for (int i = lane; i < m; i += 32) {
+            const unsigned v = sid[i];
+            int rank = 0;
+            for (int j = 0; j < m; j++) rank += sid[j] < v;
+            const int t = t0 + rank;
+            p.start[t] = sb[i];
+            p.t_row[t] = rr;
+            p.sched[s0 + rank] = t;
+        }
+    } else {
+        // many start hits in one row: rank straight from global memory
+        for (int b = b0 + lane; b < b1; b += 32) {
+            if (!p.is_start[b]) continue;
+            const unsigned v = __float_as_uint(p.hits[b].z);
+            int rank = 0;
+            for (int j = b0; j < b1; j++) rank += p.is_start[j] && __float_as_uint(p.hits[j].z) < v;
+            const int t = t0 + rank;
+            p.start[t] = b;
+            p.t_row[t] = rr;
+            p.sched[s0 + rank] = t;
+        }
     }
 }
 
@@ -569,9 +595,10 @@ cudaError_t launch_grid(const KConst& k, const float* row_x_dev, const DevPtrs& 
 cudaError_t launch_clean(const KConst& k, const DevPtrs& p, int threads, int unit0, int n_units,
                          cudaStream_t s)
 {
-    int rows = n_units * k.n_rows;
+    (void)threads;
+    const int rows = n_units * k.n_rows;
     if (rows == 0) return cudaSuccess;
-    k_clean<<<rows, threads, 0, s>>>(k, p, unit0 * k.n_rows);
+    k_clean<<<(rows + 7) / 8, 256, 0, s>>>(k, p, unit0 * k.n_rows, rows);  // a warp per row
     return cudaGetLastError();
 }
 
@@ -586,13 +613,10 @@ cudaError_t launch_start_scan(const KConst& k, const DevPtrs& p, cudaStream_t s)
 cudaError_t launch_start_write(const KConst& k, const DevPtrs& p, int threads, int unit0,
                                int n_units, cudaStream_t s)
 {
-    int rows = n_units * k.n_rows;
+    (void)threads;
+    const int rows = n_units * k.n_rows;
     if (rows == 0) return cudaSuccess;
-    size_t sm = (size_t)TPC_MAX_ROW_CLUSTERS * 8;
-    cudaError_t e =
-        cudaFuncSetAttribute(k_start_write, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    k_start_write<<<rows, threads, sm, s>>>(k, p, unit0 * k.n_rows);
+    k_start_write<<<(rows + 7) / 8, 256, 0, s>>>(k, p, unit0 * k.n_rows, rows);  // a warp per row
     return cudaGetLastError();
 }
 

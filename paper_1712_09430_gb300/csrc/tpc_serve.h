@@ -39,6 +39,8 @@ struct tpc_tracker {
     int* counters_host = nullptr;  // pinned
     int* plan_host = nullptr;      // pinned: row CSR offsets + bin-table offsets of a call
     size_t plan_cap = 0;           // ints
+    std::vector<int> slots_lut;    // bin-table slots per row count (current bin_target)
+    float slots_lut_bt = 0.0f;
     cudaEvent_t ev[6] = {};
     // graph replay of the batched stages
     cudaGraphExec_t graph_exec = nullptr;

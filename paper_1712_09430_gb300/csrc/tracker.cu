@@ -286,21 +286,37 @@ int tpc_shape(tpc_tracker* tr, const int32_t* row_counts, int n_events, BatchSha
     }
     int* plan_off = tr->plan_host;           // [R + 1] CSR offsets of rows
     int* plan_bins = tr->plan_host + R + 1;  // [R + 1] bin-table offsets
-    for (int64_t r = 0; r < R; r++) {
-        int c = row_counts[r];
-        plan_off[r] = (int)N;
-        plan_bins[r] = (int)bins;
-        if (c < 0 || c > TPC_MAX_ROW_CLUSTERS) {
-            char m[128];
-            std::snprintf(m, sizeof m, "row_counts[%lld] = %d outside [0, %d]", (long long)r, c,
-                          TPC_MAX_ROW_CLUSTERS);
-            return tr->fail(TPC_ERR_INVALID, m);
+    // bin-table slots per row count, for the current bin_target
+    if (tr->slots_lut.size() != TPC_MAX_ROW_CLUSTERS + 1 || tr->slots_lut_bt != tr->params.bin_target) {
+        tr->slots_lut.resize(TPC_MAX_ROW_CLUSTERS + 1);
+        for (int c = 0; c <= TPC_MAX_ROW_CLUSTERS; c++)
+            tr->slots_lut[(size_t)c] = row_bin_slots(c, tr->params.bin_target);
+        tr->slots_lut_bt = tr->params.bin_target;
+    }
+    const int* lut = tr->slots_lut.data();
+    for (int64_t u0 = 0; u0 < R; u0 += NR) {  // one (event, sector) unit at a time
+        const int32_t* cnt = row_counts + u0;
+        int ok = 1;
+        for (int r = 0; r < NR; r++) ok &= (unsigned)cnt[r] <= (unsigned)TPC_MAX_ROW_CLUSTERS;
+        if (!ok) {
+            for (int r = 0; r < NR; r++) {
+                if ((unsigned)cnt[r] > (unsigned)TPC_MAX_ROW_CLUSTERS) {
+                    char m[128];
+                    std::snprintf(m, sizeof m, "row_counts[%lld] = %d outside [0, %d]",
+                                  (long long)(u0 + r), cnt[r], TPC_MAX_ROW_CLUSTERS);
+                    return tr->fail(TPC_ERR_INVALID, m);
+                }
+            }
         }
-        N += c;
-        bins += row_bin_slots(c, tr->params.bin_target);
-        max_row = std::max(max_row, c);
-        int rr = (int)(r % NR);
-        if (rr >= 1 && rr + 1 < NR) max3 = std::max(max3, row_counts[r - 1] + c + row_counts[r + 1]);
+        for (int r = 0; r < NR; r++) {
+            const int c = cnt[r];
+            plan_off[u0 + r] = (int)N;
+            plan_bins[u0 + r] = (int)bins;
+            N += c;
+            bins += lut[c];
+            max_row = std::max(max_row, c);
+        }
+        for (int r = 1; r + 1 < NR; r++) max3 = std::max(max3, cnt[r - 1] + cnt[r] + cnt[r + 1]);
     }
     if (N >= (int64_t)1 << 30) return tr->fail(TPC_ERR_INVALID, "more than 2^30 clusters in one call");
     if (bins >= (int64_t)1 << 31) return tr->fail(TPC_ERR_INVALID, "search grid too large for one call");
@@ -621,5 +637,79 @@ extern "C" int tpc_debug_dump(tpc_tracker* tr, int what, void* dst, int64_t cap,
         int* h = static_cast<int*>(dst);
         for (int t = 0; t < T; t++) h[T + t] = h[t] >= tr->params.n_min_tracklet ? 1 : 0;
     }
+    return TPC_OK;
+}
+
+// ---------------------------------------------------------------- autotune
+
+extern "C" int tpc_autotune(tpc_tracker* tr, const tpc_cluster* clusters, const int32_t* row_counts,
+                            int n_events, int mem_kind, int reps, tpc_params* best, float* best_ms)
+{
+    if (!tr) return TPC_ERR_INVALID;
+    if (tpc_serve_busy(tr)) return tr->fail(TPC_BUSY, "stream tickets in flight");
+    if (reps < 1) reps = 3;
+    tpc_output none{};  // capacity 0: the run completes, nothing is copied out
+    auto run_ms = [&](float* ms) -> int {
+        std::vector<float> v;
+        for (int i = 0; i <= reps; i++) {  // the first run warms up (and captures a graph)
+            none.tracks = nullptr;
+            none.hit_ids = nullptr;
+            none.cap_tracks = none.cap_hits = 0;
+            none.mem_kind = TPC_MEM_HOST;
+            int rc = tpc_track_sectors(tr, clusters, row_counts, n_events, mem_kind, &none, nullptr);
+            if (rc != TPC_OK && rc != TPC_ERR_OUTPUT_TRUNCATED) return rc;
+            float t = 0.0f;
+            if (i > 0) {
+                if (!tr->has_result || cudaEventElapsedTime(&t, tr->ev[0], tr->ev[5]) != cudaSuccess) {
+                    cudaGetLastError();
+                    return tr->fail(TPC_ERR_DEVICE, "autotune timing");
+                }
+                v.push_back(t);
+            }
+        }
+        std::sort(v.begin(), v.end());
+        *ms = v.empty() ? 0.0f : v[v.size() / 2];
+        return TPC_OK;
+    };
+    tpc_params cur = tr->params;
+    float cur_ms = 0.0f;
+    int rc = run_ms(&cur_ms);
+    if (rc != TPC_OK) return rc;
+    struct Axis {
+        int kind;  // 0 schedule, 1 bin_target, 2 tracklets_per_warp, 3 threads_per_row
+        std::vector<float> values;
+    };
+    const std::vector<Axis> axes = {{0, {0, 1}},
+                                    {1, {0.25f, 0.5f, 1.0f, 2.0f}},
+                                    {2, {32, 16, 8}},
+                                    {3, {64, 128, 256}}};
+    for (int pass = 0; pass < 2; pass++) {
+        bool changed = false;
+        for (const Axis& ax : axes) {
+            for (float v : ax.values) {
+                tpc_params cand = cur;
+                if (ax.kind == 0) cand.schedule = (int)v;
+                if (ax.kind == 1) cand.bin_target = v;
+                if (ax.kind == 2) cand.tracklets_per_warp = (int)v;
+                if (ax.kind == 3) cand.threads_per_row = (int)v;
+                if (std::memcmp(&cand, &cur, sizeof cand) == 0) continue;
+                rc = tpc_tracker_set_params(tr, &cand);
+                if (rc != TPC_OK) return rc;
+                float ms = 0.0f;
+                rc = run_ms(&ms);
+                if (rc != TPC_OK) return rc;
+                if (ms < cur_ms * 0.99f) {
+                    cur = cand;
+                    cur_ms = ms;
+                    changed = true;
+                }
+            }
+            rc = tpc_tracker_set_params(tr, &cur);
+            if (rc != TPC_OK) return rc;
+        }
+        if (!changed) break;
+    }
+    if (best) *best = cur;
+    if (best_ms) *best_ms = cur_ms;
     return TPC_OK;
 }

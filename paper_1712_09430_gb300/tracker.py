@@ -165,30 +165,23 @@ class Tracker:
         self.check(rc)
         return int(t.value)
 
-    def poll(self, ticket, timeout_us=0, cap_tracks=None, cap_hits=None):
-        """Result of a ticket, or None while it is pending.  The output
-        buffers are kept between calls and grown on demand."""
-        ct = cap_tracks if cap_tracks is not None else self._est_tracks
-        ch = cap_hits if cap_hits is not None else self._est_hits
-        while True:
-            buf = getattr(self, "_poll_buf", None)
-            if buf is None or len(buf[0]) < ct or len(buf[1]) < ch:
-                buf = (np.zeros(max(ct, 1), TRACK_DTYPE), np.zeros(max(ch, 1), np.int32))
-                self._poll_buf = buf
-            tracks, hits = buf
-            out = capi.tpc_output(tracks.ctypes.data, hits.ctypes.data, len(tracks), len(hits),
-                                  capi.TPC_MEM_HOST, 0, 0)
-            rc = lib().tpc_stream_poll(self.h, int(ticket), C.byref(out), int(timeout_us))
-            if rc == capi.TPC_PENDING:
-                return None
-            if rc == capi.TPC_ERR_OUTPUT_TRUNCATED and cap_tracks is None:
-                ct, ch = max(out.n_tracks, 1), max(out.n_hits, 1)
-                self._est_tracks = max(self._est_tracks, int(ct * 1.25) + 16)
-                self._est_hits = max(self._est_hits, int(ch * 1.25) + 256)
-                ct, ch = self._est_tracks, self._est_hits
-                continue
+    def poll(self, ticket, timeout_us=0):
+        """Result of a ticket, or None while it is pending.  A first call
+        with no capacity learns the sizes; the second fills exact arrays."""
+        out = capi.tpc_output(None, None, 0, 0, capi.TPC_MEM_HOST, 0, 0)
+        rc = lib().tpc_stream_poll(self.h, int(ticket), C.byref(out), int(timeout_us))
+        if rc == capi.TPC_PENDING:
+            return None
+        if rc == capi.TPC_OK:       # an empty result
+            return Result(np.zeros(0, TRACK_DTYPE), np.zeros(0, np.int32))
+        if rc != capi.TPC_ERR_OUTPUT_TRUNCATED:
             self.check(rc)
-            return Result(tracks[:out.n_tracks].copy(), hits[:out.n_hits].copy())
+        tracks = np.empty(max(out.n_tracks, 1), TRACK_DTYPE)
+        hits = np.empty(max(out.n_hits, 1), np.int32)
+        out = capi.tpc_output(tracks.ctypes.data, hits.ctypes.data, len(tracks), len(hits),
+                              capi.TPC_MEM_HOST, 0, 0)
+        self.check(lib().tpc_stream_poll(self.h, int(ticket), C.byref(out), 0))
+        return Result(tracks[:out.n_tracks], hits[:out.n_hits])
 
     def dump(self, what):
         n = C.c_int64()

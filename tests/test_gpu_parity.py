@@ -227,3 +227,19 @@ def test_full_size_central_batch_exact():
     g = gpu_run(cl, rc, len(evs), exact_fp32=1, use_graph=1)
     o = oracle_run(cl, rc, len(evs), mode="f32")
     assert_exact_equal(g, o)
+
+
+def test_autotune_keeps_results_and_caches(events, tmp_path):
+    from paper_1712_09430_gb300 import autotune
+    ev = events["c3s"]
+    with Tracker(XR, bz=ev.bz, exact_fp32=1, bin_target=4.0, threads_per_row=32) as tr:
+        before = tr.track(ev.clusters, ev.row_counts, 1)
+        cache = str(tmp_path / "tune.json")
+        fields, ms = autotune.tune(tr, ev.clusters, ev.row_counts, 1, reps=2, cache_path=cache)
+        assert ms > 0 and set(fields) == set(autotune.FIELDS)
+        after = tr.track(ev.clusters, ev.row_counts, 1)
+        np.testing.assert_array_equal(after.tracks.view(np.uint8), before.tracks.view(np.uint8))
+        np.testing.assert_array_equal(after.hit_ids, before.hit_ids)
+    with Tracker(XR, bz=ev.bz, exact_fp32=1) as tr2:   # a cached choice applies without timing
+        f2, _ = autotune.tune(tr2, ev.clusters, ev.row_counts, 1, cache_path=cache)
+        assert f2 == fields and tr2.params.bin_target == fields["bin_target"]
