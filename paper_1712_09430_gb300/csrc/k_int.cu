@@ -231,7 +231,7 @@ __global__ void k_clean(KConst k, DevPtrs p, int rr0, int rows)
         int d2 = (d >= 0 && p.up[d] == b) ? d : -1;
         p.up2[b] = u2;
         p.dn2[b] = d2;
-        p.owner[b] = 0ull;  // selection starts from no owner
+        p.owner[b] = 0u;  // selection starts from no owner
         int st = 0;
         if (u2 >= 0 && d2 < 0) {
             int len = 2, j = u2;
@@ -389,9 +389,16 @@ __global__ void k_chain_end(KConst k, DevPtrs p, int u0, int u1)
 }
 
 // --------------------------------------------------------------- selection
-__device__ __forceinline__ unsigned long long tl_key(int n, int t)
+// Selection key of tracklet t with n clusters: more clusters win, ties go to
+// the lower canonical id.  Keys are compared only within one unit (a cluster
+// belongs to one unit), so the id is taken relative to the unit's first
+// tracklet: n <= 256 takes 9 bits, the local id < 2^23 (a unit holds at most
+// 4096 x 256 / 2 tracklets).
+__device__ __forceinline__ unsigned tl_key(const KConst& k, const DevPtrs& p, int n, int t)
 {
-    return ((unsigned long long)(unsigned)n << 32) | (unsigned long long)(0xFFFFFFFFu - (unsigned)t);
+    const int rr = p.t_row[t];
+    const int t_local = t - p.start_off[rr - rr % k.n_rows];
+    return ((unsigned)n << 23) | (0x7FFFFFu - (unsigned)t_local);
 }
 
 // Best instance per cluster: owner[h] = max key over live tracklets.  One
@@ -404,7 +411,7 @@ __global__ void k_owner(KConst k, DevPtrs p, int u0, int u1)
     for (int t = t0 + w0; t < t1; t += nw) {
         const int n = p.tl_n[t];
         if (n < k.n_min_tracklet) continue;
-        const unsigned long long key = tl_key(n, t);
+        const unsigned key = tl_key(k, p, n, t);
         const int* h = p.tl_hits + (size_t)t * k.n_rows;
         for (int j = lane; j < n; j += 32) atomicMax(&p.owner[h[j]], key);
     }
@@ -420,7 +427,7 @@ __global__ void k_accept(KConst k, DevPtrs p, int u0, int u1)
         const int n = p.tl_n[t];
         int owned = 0;
         if (n >= k.n_min_tracklet) {
-            const unsigned long long key = tl_key(n, t);
+            const unsigned key = tl_key(k, p, n, t);
             const int* h = p.tl_hits + (size_t)t * k.n_rows;
             for (int j0 = 0; j0 < n; j0 += 32) {
                 const bool own = j0 + lane < n && p.owner[h[j0 + lane]] == key;
@@ -506,7 +513,7 @@ __global__ void k_emit(KConst k, DevPtrs p)
             else word = ex.y;
             reinterpret_cast<int*>(p.out_tracks + m)[lane] = word;
         }
-        const unsigned long long key = tl_key(n, t);
+        const unsigned key = tl_key(k, p, n, t);
         const int* h = p.tl_hits + (size_t)t * k.n_rows;
         int o = ex.y;
         for (int j0 = 0; j0 < n; j0 += 32) {

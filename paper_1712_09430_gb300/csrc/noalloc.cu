@@ -122,7 +122,7 @@ extern "C" int tpc_links_noalloc(const tpc_geometry* g, const tpc_params* params
     const size_t o_up = take(n * 4), o_dn = take(n * 4), o_up2 = take(n * 4), o_dn2 = take(n * 4);
     const size_t o_start = take(n);
     const size_t o_nstart = take((size_t)R * 4);
-    const size_t o_owner = take(n * 8);
+    const size_t o_owner = take(n * 4);
     const size_t o_count = take(kNumCounters * 4);
     if (off > kScratchBytes) return TPC_ERR_NOMEM;  // bin tables too large at this bin_target
 
@@ -161,7 +161,7 @@ extern "C" int tpc_links_noalloc(const tpc_geometry* g, const tpc_params* params
     p.dn2 = reinterpret_cast<int*>(base + o_dn2);
     p.is_start = reinterpret_cast<unsigned char*>(base + o_start);
     p.row_nstart = reinterpret_cast<int*>(base + o_nstart);
-    p.owner = reinterpret_cast<unsigned long long*>(base + o_owner);
+    p.owner = reinterpret_cast<unsigned*>(base + o_owner);
     p.counters = reinterpret_cast<int*>(base + o_count);
     p.N = (int)N;
     p.R = R;
