@@ -118,8 +118,9 @@ class ClockSampler:
 
 
 def cpu_baseline(seconds_target=15.0, ev=None):
-    """The FP64 oracle, as it stands, on all host cores over whole central
-    events (OpenMP over (event, sector) units) until ~seconds_target."""
+    """The FP64 oracle, as it stands, on the host cores: all cores over whole
+    central events (OpenMP over (event, sector) units) for ~seconds_target,
+    plus 1 and 4 threads (the paper's four CPU cores) on a 6-sector sample."""
     import oracle
     from paper_1712_09430_gb300 import synth
     if ev is None:
@@ -134,9 +135,24 @@ def cpu_baseline(seconds_target=15.0, ev=None):
         if time.perf_counter() - t0 > seconds_target:
             break
     dt = time.perf_counter() - t0
+    # six sectors (one side's first six) of the same event as one unit set
+    rc = ev.row_counts.reshape(36, 159)
+    sel = np.zeros(36, bool)
+    sel[:6] = True
+    ncl = int(rc[:6].sum())
+    rc6 = np.where(sel[:, None], rc, 0).reshape(-1).astype(np.int32)
+    cl6 = ev.clusters[:ncl]
+    per_threads = {}
+    for th in (1, 4):
+        t1 = time.perf_counter()
+        oracle.run(cl6, rc6, 1, ev.bz, synth.row_x(), mode="f64", threads=th)
+        per_threads[str(th)] = ncl / (time.perf_counter() - t1)
+    per_threads[str(cores)] = done / dt
     return {"value": done / dt, "unit": "clusters/s", "cores": cores, "kind": "oracle",
             "sample": f"{n_ev} x one central Pb-Pb event ({ev.n} clusters), FP64 oracle, "
-                      f"OpenMP over the 36 sectors, {dt:.1f} s wall"}
+                      f"OpenMP over the 36 sectors, {dt:.1f} s wall; 1 and 4 threads on sectors "
+                      f"0-5 of the same event ({ncl} clusters)",
+            "by_threads": per_threads}
 
 
 def run_reference(args):
@@ -170,16 +186,33 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def rank_seeds(rank, batch, base=3):
+    """Event seeds of one rank: ranks track disjoint events (weak scaling,
+    no data-path collective)."""
+    return [base + rank * batch + i for i in range(batch)]
+
+
+def reduce_step_ms(ms, dist, device=None):
+    """Whole-job step time = the slowest rank's (max over ranks)."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 # Launches of our kernels per batched step: plan, grid, neighbours, clean,
-# start scan, start write, tracklets, owner, accept, scan tiles, scan top, emit.
-LAUNCHES_PER_STEP = 12
+# start tiles, start top, start final, start write, chain end, tracklets,
+# owner, accept, scan tiles, scan top, emit.
+LAUNCHES_PER_STEP = 15
 
 
 def run_ours(args):
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    seeds = [3 + rank * args.batch + i for i in range(args.batch)]
+    seeds = rank_seeds(rank, args.batch)
     mb_seeds = [1000 + rank * args.pool + i for i in range(args.pool)] if args.stream_rates else []
     cl_np, rc_np, mb_pool = make_inputs(seeds, mb_seeds)   # before any CUDA use
     import torch
@@ -242,10 +275,7 @@ def run_ours(args):
     ck = clocks.stop()
     ms = sum(s.elapsed_time(e) for s, e in zip(ev_s, ev_e)) / args.steps
     stage /= args.steps
-    if dist:
-        t = torch.tensor([ms], device=dev_cl.device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = reduce_step_ms(ms, dist, dev_cl.device)
     M, MH = out.n_tracks, out.n_hits
     T = len(tr.dump(capi.TPC_DUMP_STARTS)) if rank == 0 else 0
     value = N * world / (ms * 1e-3)
@@ -254,9 +284,10 @@ def run_ours(args):
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(L, tr, cl_np, rc_ptr, rc_np, B, N, world, sp, cap_t, cap_h, args)
-    plain = None
+    plain = multi = None
     if args.plain_steps > 0:
-        plain = run_plain(L, tr, dev_cl, rc_ptr, B, N, world, sp, out, args)
+        plain = run_plain(L, tr, dev_cl, rc_ptr, B, N, world, sp, out, args, mode=1)
+        multi = run_plain(L, tr, dev_cl, rc_ptr, B, N, world, sp, out, args, mode=2)
     stream_res = None
     if args.stream_rates:
         stream_res = [run_stream(tr, mb_pool, args, rate) for rate in args.stream_rates]
@@ -306,7 +337,7 @@ def run_ours(args):
             "stage_ms": stage_ms, "wall_s": wall,
             "gpu_launches": LAUNCHES_PER_STEP * args.steps,
             "clocks": ck, "e2e": e2e, "roofline": rl, "cpu_baseline": cpu,
-            "plain_per_sector": plain, "stream": stream_res}
+            "plain_per_sector": plain, "multi_queue_per_sector": multi, "stream": stream_res}
     if stream_res:
         line["latency_ms"] = {"p50": stream_res[0]["p50_ms"], "p99": stream_res[0]["p99_ms"],
                               "rate_hz": stream_res[0]["rate_hz"]}
@@ -316,13 +347,14 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def run_plain(L, tr, dev_cl, rc_ptr, B, N, world, sp, out, args):
-    """The same batch with every stage launched once per (event, sector) unit
-    on one stream (the Run 1/2 scheduling), for comparison."""
+def run_plain(L, tr, dev_cl, rc_ptr, B, N, world, sp, out, args, mode=1):
+    """The same batch with every stage launched once per (event, sector) unit:
+    mode 1 on one stream (the Run 1/2 scheduling), mode 2 round-robin over 8
+    streams (the multi-queue scheme), for comparison."""
     import ctypes as C
     import torch
     from paper_1712_09430_gb300 import capi
-    tr.set_params(plain_per_sector=1, use_graph=0)
+    tr.set_params(plain_per_sector=mode, use_graph=0, n_queues=8)
     try:
         def step():
             r = L.tpc_track_sectors(tr.h, C.c_void_p(dev_cl.data_ptr()), rc_ptr, B,
@@ -340,8 +372,9 @@ def run_plain(L, tr, dev_cl, rc_ptr, B, N, world, sp, out, args):
         tr.set_params(plain_per_sector=0, use_graph=1)
     units = B * 36
     return {"value": N * world / dt, "unit": "clusters/s", "ms_per_step": dt * 1e3,
-            "steps": args.plain_steps, "launches_per_step": units * 8 + 6,
-            "note": "every stage launched per (event, sector) unit on one stream"}
+            "steps": args.plain_steps, "launches_per_step": units * 9 + 7,
+            "note": "every stage launched per (event, sector) unit, " +
+                    ("on one stream" if mode == 1 else "round-robin over 8 streams")}
 
 
 def run_stream(tr0, pool, args, rate):

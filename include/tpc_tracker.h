@@ -106,10 +106,15 @@ typedef struct {
     int threads_per_row;     /* 32, 64, 128 or 256: CTA size of the row kernels */
     int tracklets_per_warp;  /* 1, 2, 4, 8, 16 or 32: lanes per tracklet =
                                 32 / tracklets_per_warp                         */
-    int plain_per_sector;    /* 1: one launch per (event, sector) per stage
-                                (the Run 1/2 scheduling of Sec. 3); 0: all
-                                units in one launch per stage                   */
+    int plain_per_sector;    /* 0: all units in one launch per stage;
+                                1: one launch per (event, sector) per stage on
+                                one stream (the Run 1/2 scheduling of Sec. 3);
+                                2: the same launches spread round-robin over
+                                n_queues streams, each unit's stages in order
+                                on one stream (the multi-queue scheme of
+                                Sec. 3.1, Fig. 3)                               */
     int use_graph;           /* 1: replay the batched stages as a CUDA graph    */
+    int n_queues;            /* streams of plain_per_sector = 2 (1..64)         */
     int schedule;            /* tracklet order of the persistent constructor:
                                 0 unit by unit (canonical order; keeps the
                                 working set of a few sectors in L2), 1 by start

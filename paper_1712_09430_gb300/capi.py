@@ -55,7 +55,8 @@ class tpc_params(C.Structure):
                 ("own_num", C.c_int), ("own_den", C.c_int),
                 ("exact_fp32", C.c_int), ("bin_target", C.c_float),
                 ("threads_per_row", C.c_int), ("tracklets_per_warp", C.c_int),
-                ("plain_per_sector", C.c_int), ("use_graph", C.c_int), ("schedule", C.c_int)]
+                ("plain_per_sector", C.c_int), ("use_graph", C.c_int), ("n_queues", C.c_int),
+                ("schedule", C.c_int)]
 
 
 class tpc_track(C.Structure):

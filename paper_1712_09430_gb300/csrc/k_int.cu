@@ -307,8 +307,20 @@ __global__ void __launch_bounds__(1024) k_start_top(KConst k, DevPtrs p)
     }
 }
 
-// One warp per row: finish the row's offsets, then number its start hits by
-// cluster id (rank = number of start hits of the row with a smaller id).
+// Final tracklet offsets of every row: the tile-local scans plus the tile
+// prefixes (one thread per row).
+__global__ void k_start_final(KConst k, DevPtrs p)
+{
+    const int ntiles = (p.R + kScanTile - 1) / kScanTile;
+    for (int rr = blockIdx.x * blockDim.x + threadIdx.x; rr < p.R; rr += gridDim.x * blockDim.x) {
+        const int j = (rr % k.n_rows) * p.n_units + rr / k.n_rows;
+        p.start_off[rr] += p.start_part[rr / kScanTile];
+        p.sched_off[rr] += p.start_part[ntiles + 1 + j / kScanTile];
+    }
+}
+
+// One warp per row: number its start hits by cluster id (rank = number of
+// start hits of the row with a smaller id).
 constexpr int kStartWarpBuf = 128;  // start hits ranked in shared memory; more use global reads
 
 __global__ void k_start_write(KConst k, DevPtrs p, int rr0, int rows)
@@ -322,12 +334,8 @@ __global__ void k_start_write(KConst k, DevPtrs p, int rr0, int rows)
     const int m = p.row_nstart[rr];
     int t0 = 0, s0 = 0;
     if (lane == 0) {
-        const int ntiles = (p.R + kScanTile - 1) / kScanTile;
-        const int j = (rr % k.n_rows) * p.n_units + rr / k.n_rows;
-        t0 = p.start_off[rr] + p.start_part[rr / kScanTile];
-        s0 = p.sched_off[rr] + p.start_part[ntiles + 1 + j / kScanTile];
-        p.start_off[rr] = t0;
-        p.sched_off[rr] = s0;
+        t0 = p.start_off[rr];
+        s0 = p.sched_off[rr];
     }
     if (m == 0) return;
     t0 = __shfl_sync(0xffffffffu, t0, 0);
@@ -614,6 +622,8 @@ cudaError_t launch_start_scan(const KConst& k, const DevPtrs& p, cudaStream_t s)
     int ntiles = (p.R + kScanTile - 1) / kScanTile;
     k_start_tiles<<<ntiles < 1 ? 1 : ntiles, 256, 0, s>>>(k, p);
     k_start_top<<<1, 1024, 0, s>>>(k, p);
+    int blocks = (p.R + 255) / 256;
+    k_start_final<<<blocks < 1 ? 1 : (blocks > 4096 ? 4096 : blocks), 256, 0, s>>>(k, p);
     return cudaGetLastError();
 }
 
@@ -633,11 +643,14 @@ cudaError_t launch_chain_end(const KConst& k, const DevPtrs& p, int n_sm, int u0
     return cudaGetLastError();
 }
 
-cudaError_t launch_select(const KConst& k, const DevPtrs& p, int n_sm, int u0, int u1, cudaStream_t s)
+cudaError_t launch_select(const KConst& k, const DevPtrs& p, int n_sm, int u0, int u1, bool owner,
+                          cudaStream_t s)
 {
-    k_owner<<<n_sm * 8, 256, 0, s>>>(k, p, u0, u1);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    if (owner) {  // the persistent constructor claims ownership itself
+        k_owner<<<n_sm * 8, 256, 0, s>>>(k, p, u0, u1);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
     k_accept<<<n_sm * 8, 256, 0, s>>>(k, p, u0, u1);
     return cudaGetLastError();
 }

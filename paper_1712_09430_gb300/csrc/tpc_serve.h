@@ -45,6 +45,10 @@ struct tpc_tracker {
     // graph replay of the batched stages
     cudaGraphExec_t graph_exec = nullptr;
     std::string graph_key;
+    // multi-queue per-sector form: streams and fork/join events
+    std::vector<cudaStream_t> queues;
+    std::vector<cudaEvent_t> queue_ev;
+    cudaEvent_t fork_ev = nullptr;
     // debug dumps
     void* dump_buf = nullptr;
     size_t dump_bytes = 0;

@@ -84,6 +84,8 @@ static const char* check_params(const tpc_params& P)
     int w = P.tracklets_per_warp;
     if (w != 1 && w != 2 && w != 4 && w != 8 && w != 16 && w != 32) return "tracklets_per_warp";
     if (P.schedule != 0 && P.schedule != 1) return "schedule must be 0 or 1";
+    if (P.plain_per_sector < 0 || P.plain_per_sector > 2) return "plain_per_sector must be 0, 1 or 2";
+    if (P.n_queues < 1 || P.n_queues > 64) return "n_queues must be in [1, 64]";
     return nullptr;
 }
 
@@ -115,6 +117,7 @@ extern "C" void tpc_params_default(tpc_params* p)
     p->tracklets_per_warp = 32;
     p->plain_per_sector = 0;
     p->use_graph = 0;
+    p->n_queues = 8;
     p->schedule = 0;
 }
 
@@ -184,6 +187,9 @@ extern "C" void tpc_tracker_destroy(tpc_tracker* tr)
     cudaFreeHost(tr->counters_host);
     cudaFreeHost(tr->plan_host);
     for (auto& e : tr->ev) if (e) cudaEventDestroy(e);
+    for (auto q : tr->queues) cudaStreamDestroy(q);
+    for (auto e : tr->queue_ev) cudaEventDestroy(e);
+    if (tr->fork_ev) cudaEventDestroy(tr->fork_ev);
     if (tr->own_stream) cudaStreamDestroy(tr->own_stream);
     delete tr;
 }
@@ -403,7 +409,61 @@ int tpc_enqueue(tpc_tracker* tr, const DevPtrs& p, const BatchShape& sh, cudaStr
         if (with_events) TPC_CUDA(cudaEventRecord(tr->ev[3], s));
         TPC_CUDA(tl(-1, -1));
         if (with_events) TPC_CUDA(cudaEventRecord(tr->ev[4], s));
-        TPC_CUDA(tpc_int::launch_select(k, p, tr->n_sm, 0, sh.n_units, s));
+        TPC_CUDA(tpc_int::launch_select(k, p, tr->n_sm, 0, sh.n_units, true, s));
+    } else if (P.plain_per_sector == 2) {
+        // Multi-queue scheme (Sec. 3.1, Fig. 3): each unit's stages in order
+        // on one of n_queues streams, units round-robin; the two global steps
+        // (start numbering, output compaction) join all queues.
+        const int nq = P.n_queues;
+        while ((int)tr->queues.size() < nq) {
+            cudaStream_t q;
+            cudaEvent_t e;
+            TPC_CUDA(cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking));
+            TPC_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+            tr->queues.push_back(q);
+            tr->queue_ev.push_back(e);
+        }
+        if (!tr->fork_ev) TPC_CUDA(cudaEventCreateWithFlags(&tr->fork_ev, cudaEventDisableTiming));
+        auto fork = [&]() -> int {
+            TPC_CUDA(cudaEventRecordWithFlags(tr->fork_ev, s, cudaEventRecordDefault));
+            for (int q = 0; q < nq; q++) TPC_CUDA(cudaStreamWaitEvent(tr->queues[(size_t)q], tr->fork_ev, 0));
+            return TPC_OK;
+        };
+        auto join = [&]() -> int {
+            for (int q = 0; q < nq; q++) {
+                TPC_CUDA(cudaEventRecordWithFlags(tr->queue_ev[(size_t)q], tr->queues[(size_t)q], 0));
+                TPC_CUDA(cudaStreamWaitEvent(s, tr->queue_ev[(size_t)q], 0));
+            }
+            return TPC_OK;
+        };
+        int rc = fork();
+        if (rc != TPC_OK) return rc;
+        for (int u = 0; u < sh.n_units; u++) {
+            cudaStream_t q = tr->queues[(size_t)(u % nq)];
+            TPC_CUDA(tpc_int::launch_grid(k, xd, p, sh.max_row, th, u, 1, q));
+            TPC_CUDA(nb(k, xd, p, sh.max3, th, u, 1, q));
+            TPC_CUDA(tpc_int::launch_clean(k, p, th, u, 1, q));
+        }
+        rc = join();
+        if (rc != TPC_OK) return rc;
+        if (with_events) TPC_CUDA(cudaEventRecord(tr->ev[1], s));
+        if (with_events) TPC_CUDA(cudaEventRecord(tr->ev[2], s));
+        TPC_CUDA(tpc_int::launch_start_scan(k, p, s));
+        if (with_events) TPC_CUDA(cudaEventRecord(tr->ev[3], s));
+        rc = fork();
+        if (rc != TPC_OK) return rc;
+        for (int u = 0; u < sh.n_units; u++) {
+            cudaStream_t q = tr->queues[(size_t)(u % nq)];
+            TPC_CUDA(tpc_int::launch_start_write(k, p, th, u, 1, q));
+            TPC_CUDA(tpc_int::launch_chain_end(k, p, 1, u, u + 1, q));
+            const int lpt = 32 / P.tracklets_per_warp;
+            TPC_CUDA(exact ? tpc_exact::launch_tracklets(k, xd, p, tr->n_sm, lpt, P.schedule, u, u + 1, q)
+                           : tpc_fast::launch_tracklets(k, xd, p, tr->n_sm, lpt, P.schedule, u, u + 1, q));
+            TPC_CUDA(tpc_int::launch_select(k, p, tr->n_sm, u, u + 1, true, q));
+        }
+        rc = join();
+        if (rc != TPC_OK) return rc;
+        if (with_events) TPC_CUDA(cudaEventRecord(tr->ev[4], s));
     } else {
         // The Run 1/2 scheduling (Sec. 3): every stage launched per sector.
         for (int u = 0; u < sh.n_units; u++)
@@ -413,13 +473,15 @@ int tpc_enqueue(tpc_tracker* tr, const DevPtrs& p, const BatchShape& sh, cudaStr
         if (with_events) TPC_CUDA(cudaEventRecord(tr->ev[2], s));
         for (int u = 0; u < sh.n_units; u++) TPC_CUDA(tpc_int::launch_clean(k, p, th, u, 1, s));
         TPC_CUDA(tpc_int::launch_start_scan(k, p, s));
-        // every unit's offsets are final only after all start_write launches
-        for (int u = 0; u < sh.n_units; u++) TPC_CUDA(tpc_int::launch_start_write(k, p, th, u, 1, s));
-        for (int u = 0; u < sh.n_units; u++) TPC_CUDA(tpc_int::launch_chain_end(k, p, 1, u, u + 1, s));
+        for (int u = 0; u < sh.n_units; u++) {
+            TPC_CUDA(tpc_int::launch_start_write(k, p, th, u, 1, s));
+            TPC_CUDA(tpc_int::launch_chain_end(k, p, 1, u, u + 1, s));
+        }
         if (with_events) TPC_CUDA(cudaEventRecord(tr->ev[3], s));
         for (int u = 0; u < sh.n_units; u++) TPC_CUDA(tl(u, u + 1));
         if (with_events) TPC_CUDA(cudaEventRecord(tr->ev[4], s));
-        for (int u = 0; u < sh.n_units; u++) TPC_CUDA(tpc_int::launch_select(k, p, tr->n_sm, u, u + 1, s));
+        for (int u = 0; u < sh.n_units; u++)
+            TPC_CUDA(tpc_int::launch_select(k, p, tr->n_sm, u, u + 1, true, s));
     }
     TPC_CUDA(tpc_int::launch_emit(k, p, tr->n_sm, s));
     if (with_events) TPC_CUDA(cudaEventRecord(tr->ev[5], s));
@@ -430,10 +492,11 @@ int tpc_enqueue(tpc_tracker* tr, const DevPtrs& p, const BatchShape& sh, cudaStr
 static std::string graph_key_of(const tpc_tracker* tr, const BatchShape& sh, const DevPtrs& p)
 {
     char b[256];
-    std::snprintf(b, sizeof b, "%d/%d/%d/%d/%d/%p/%p/%d/%d/%d/%d/%d/%g", sh.N, sh.R, sh.n_units,
+    std::snprintf(b, sizeof b, "%d/%d/%d/%d/%d/%p/%p/%d/%d/%d/%d/%d/%g/%d", sh.N, sh.R, sh.n_units,
                   sh.max_row, sh.max3, (const void*)p.clusters, (const void*)p.counters,
                   tr->params.exact_fp32, tr->params.threads_per_row, tr->params.tracklets_per_warp,
-                  tr->params.plain_per_sector, tr->params.schedule, (double)tr->params.bin_target);
+                  tr->params.plain_per_sector, tr->params.schedule, (double)tr->params.bin_target,
+                  tr->params.n_queues);
     return std::string(b);
 }
 

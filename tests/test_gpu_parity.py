@@ -64,6 +64,8 @@ def test_exact_parity_multi_event_batch(events):
 @pytest.mark.parametrize("over", [dict(bin_target=0.5), dict(bin_target=8.0, threads_per_row=32),
                                   dict(bin_target=2.0, threads_per_row=256),
                                   dict(plain_per_sector=1), dict(use_graph=1),
+                                  dict(plain_per_sector=2, n_queues=8),
+                                  dict(plain_per_sector=2, n_queues=3, use_graph=1),
                                   dict(tracklets_per_warp=4), dict(schedule=1),
                                   dict(tracklets_per_warp=16, schedule=1)])
 def test_execution_params_do_not_change_results(events, over):
@@ -243,3 +245,13 @@ def test_autotune_keeps_results_and_caches(events, tmp_path):
     with Tracker(XR, bz=ev.bz, exact_fp32=1) as tr2:   # a cached choice applies without timing
         f2, _ = autotune.tune(tr2, ev.clusters, ev.row_counts, 1, cache_path=cache)
         assert f2 == fields and tr2.params.bin_target == fields["bin_target"]
+
+
+def test_time_frame_uneven_slices_exact():
+    """Continuous-readout time frame cut into uneven slices (different
+    numbers of collisions per slice), all slices in one call."""
+    tf = [S.time_frame(seed=70 + i, n_coll=n, scale=0.5) for i, n in enumerate((2, 5, 9))]
+    cl, rc = S.concat_events(tf)
+    g = gpu_run(cl, rc, len(tf), exact_fp32=1, use_graph=1)
+    o = oracle_run(cl, rc, len(tf), mode="f32")
+    assert_exact_equal(g, o)
