@@ -464,36 +464,31 @@ __device__ __forceinline__ void lane_init(Lane& L, int t, const KConst& k, const
                                           const DevPtrs& p)
 {
     const int NR = k.n_rows;
-    const int rr0 = p.t_row[t];
-    const int2 e = p.t_end[t];
+    const float4 sd = __ldg(p.t_seed + t);  // one 32-byte record per tracklet
+    const int4 info = __ldg(p.t_info + t);
+    const int rr0 = info.x;
     L.t = t;
     L.ubase = rr0 - rr0 % NR;
     L.z0 = (((rr0 / NR) % k.n_sectors) < k.n_sectors / 2) ? 0.0f : -k.z_max;
     const int r0 = rr0 - L.ubase;
-    const int h0 = p.start[t];
-    const int rL = r0 + e.y - 1;
-    const float4 c0 = p.hits[h0];
-    const float4 cL = p.hits[e.x];
     State st;
     st.x = xs[r0];
-    st.y = c0.x;
-    st.z = c0.y;
-    const float dx = xs[rL] - xs[r0], dy = cL.x - c0.x, dz = cL.y - c0.y;
-    const float l = sqrtf(dx * dx + dy * dy);
-    st.s = dy / l;
-    st.t = dz / l;
+    st.y = sd.x;
+    st.z = sd.y;
+    st.s = sd.z;
+    st.t = sd.w;
     st.q = 0.0f;
     reset_cov(st, k);
     store_state(L.sp, st, 0.0f);
     L.phase = 0;
     L.r = r0;
-    L.h = h0;
+    L.h = info.y;
     L.have = false;
     L.r_out = -1;
     L.miss = 0;
     L.n = 0;
-    L.work = make_int4(0, 0, 0, e.y);
-    L.g = p.grid[rr0];
+    L.work = make_int4(0, 0, 0, info.z);
+    L.g = p.grid[rr0];  // not needed before the chain ends; the load overlaps it
 }
 
 __device__ __forceinline__ void lane_finish(Lane& L, const KConst& k, const DevPtrs& p, bool writer)
@@ -655,7 +650,37 @@ __global__ void __launch_bounds__(kTlThreads, 3) k_tracklets_plain(KConst k, con
     }
 }
 
+// Seeds (T1): walk each seed chain to its last hit and compute the initial
+// state at the start hit from the chord to it: sin(phi) = dy / l,
+// tan(lambda) = dz / l, l = sqrt(dx^2 + dy^2).  One thread per tracklet.
+__global__ void k_seeds(KConst k, const float* __restrict__ row_x, DevPtrs p, int u0, int u1)
+{
+    const int t0 = p.start_off[u0 * k.n_rows], t1 = p.start_off[u1 * k.n_rows];
+    for (int t = t0 + blockIdx.x * blockDim.x + threadIdx.x; t < t1; t += gridDim.x * blockDim.x) {
+        const int h0 = p.start[t];
+        int h = h0, len = 1;
+        for (int j = p.up2[h]; j >= 0; j = p.up2[j]) {
+            h = j;
+            len++;
+        }
+        const int rr0 = p.t_row[t];
+        const int r0 = rr0 % k.n_rows, rL = r0 + len - 1;
+        const float2 c0 = p.hyz[h0], cL = p.hyz[h];
+        const float dx = row_x[rL] - row_x[r0], dy = cL.x - c0.x, dz = cL.y - c0.y;
+        const float l = sqrtf(dx * dx + dy * dy);
+        p.t_seed[t] = make_float4(c0.x, c0.y, dy / l, dz / l);
+        p.t_info[t] = make_int4(rr0, h0, len, 0);
+    }
+}
+
 // -------------------------------------------------------------- launchers
+cudaError_t launch_seeds(const KConst& k, const float* row_x_dev, const DevPtrs& p, int n_sm, int u0,
+                         int u1, cudaStream_t s)
+{
+    k_seeds<<<n_sm * 8, 256, 0, s>>>(k, row_x_dev, p, u0, u1);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_neighbours(const KConst& k, const float* row_x_dev, const DevPtrs& p, int max3,
                               int threads, int unit0, int n_units, cudaStream_t s)
 {

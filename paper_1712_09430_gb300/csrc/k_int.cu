@@ -382,20 +382,6 @@ __global__ void k_start_write(KConst k, DevPtrs p, int rr0, int rows)
     }
 }
 
-// Last hit and length of every seed chain (one thread per tracklet).
-__global__ void k_chain_end(KConst k, DevPtrs p, int u0, int u1)
-{
-    const int t0 = p.start_off[u0 * k.n_rows], t1 = p.start_off[u1 * k.n_rows];
-    for (int t = t0 + blockIdx.x * blockDim.x + threadIdx.x; t < t1; t += gridDim.x * blockDim.x) {
-        int h = p.start[t], len = 1;
-        for (int j = p.up2[h]; j >= 0; j = p.up2[j]) {
-            h = j;
-            len++;
-        }
-        p.t_end[t] = make_int2(h, len);
-    }
-}
-
 // --------------------------------------------------------------- selection
 // Selection key of tracklet t with n clusters: more clusters win, ties go to
 // the lower canonical id.  Keys are compared only within one unit (a cluster
@@ -634,12 +620,6 @@ cudaError_t launch_start_write(const KConst& k, const DevPtrs& p, int threads, i
     const int rows = n_units * k.n_rows;
     if (rows == 0) return cudaSuccess;
     k_start_write<<<(rows + 7) / 8, 256, 0, s>>>(k, p, unit0 * k.n_rows, rows);  // a warp per row
-    return cudaGetLastError();
-}
-
-cudaError_t launch_chain_end(const KConst& k, const DevPtrs& p, int n_sm, int u0, int u1, cudaStream_t s)
-{
-    k_chain_end<<<n_sm * 8, 256, 0, s>>>(k, p, u0, u1);
     return cudaGetLastError();
 }
 

@@ -77,7 +77,8 @@ struct DevPtrs {
     int* sched_off;            // [R + 1] schedule offsets (row-major order)
     int* start;                // [Tcap] binned index of the start hit of t
     int* t_row;                // [Tcap] row index rr of the start hit of t
-    int2* t_end;               // [Tcap] last hit of the seed chain (binned), chain length
+    float4* t_seed;            // [Tcap] seed state at the start hit: y, z, sin(phi), tan(lambda)
+    int4* t_info;              // [Tcap] row index rr of the start hit, start hit, chain length, 0
     int* sched;                // [Tcap] tracklets by expected length
     float* tl_f;               // [Tcap][16]
     int* tl_n;                 // [Tcap] Phase-2 cluster count
@@ -201,8 +202,6 @@ cudaError_t launch_clean(const tpc::KConst& k, const tpc::DevPtrs& p, int thread
 cudaError_t launch_start_scan(const tpc::KConst& k, const tpc::DevPtrs& p, cudaStream_t s);
 cudaError_t launch_start_write(const tpc::KConst& k, const tpc::DevPtrs& p, int threads, int unit0,
                                int n_units, cudaStream_t s);
-cudaError_t launch_chain_end(const tpc::KConst& k, const tpc::DevPtrs& p, int n_sm, int u0, int u1,
-                             cudaStream_t s);
 cudaError_t launch_select(const tpc::KConst& k, const tpc::DevPtrs& p, int n_sm, int t0_unit,
                           int t1_unit, bool owner, cudaStream_t s);
 cudaError_t launch_emit(const tpc::KConst& k, const tpc::DevPtrs& p, int n_sm, cudaStream_t s);
@@ -219,7 +218,9 @@ cudaError_t launch_dump_tl_work(const tpc::DevPtrs& p, int T, int* dst, cudaStre
                                   int n_units, cudaStream_t s);                                   \
     cudaError_t launch_tracklets(const tpc::KConst& k, const float* row_x_dev,                    \
                                  const tpc::DevPtrs& p, int n_sm, int lanes_per_tracklet,         \
-                                 int schedule, int t_first_unit, int t_last_unit, cudaStream_t s);
+                                 int schedule, int t_first_unit, int t_last_unit, cudaStream_t s); \
+    cudaError_t launch_seeds(const tpc::KConst& k, const float* row_x_dev, const tpc::DevPtrs& p,   \
+                             int n_sm, int u0, int u1, cudaStream_t s);
 
 namespace tpc_exact { TPC_FP_DECLS }
 namespace tpc_fast { TPC_FP_DECLS }

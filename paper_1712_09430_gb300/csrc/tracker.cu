@@ -247,7 +247,8 @@ size_t tpc_layout(const tpc_tracker* tr, const BatchShape& sh, DevPtrs* p, char*
     q.sched_off = reinterpret_cast<int*>(take((R + 1) * 4));
     q.start = reinterpret_cast<int*>(take(Tc * 4));
     q.t_row = reinterpret_cast<int*>(take(Tc * 4));
-    q.t_end = reinterpret_cast<int2*>(take(Tc * 8));
+    q.t_seed = reinterpret_cast<float4*>(take(Tc * 16));
+    q.t_info = reinterpret_cast<int4*>(take(Tc * 16));
     q.sched = reinterpret_cast<int*>(take(Tc * 4));
     q.tl_f = reinterpret_cast<float*>(take(Tc * kTlFloats * 4));
     q.tl_n = reinterpret_cast<int*>(take(Tc * 4));
@@ -389,6 +390,10 @@ int tpc_enqueue(tpc_tracker* tr, const DevPtrs& p, const BatchShape& sh, cudaStr
         return exact ? tpc_exact::launch_neighbours(kk, x, pp, max3, th, u0, nu, ss)
                      : tpc_fast::launch_neighbours(kk, x, pp, max3, th, u0, nu, ss);
     };
+    auto seeds = [&](int u0, int u1, cudaStream_t ss) {
+        return exact ? tpc_exact::launch_seeds(k, xd, p, tr->n_sm, u0, u1, ss)
+                     : tpc_fast::launch_seeds(k, xd, p, tr->n_sm, u0, u1, ss);
+    };
     auto tl = [&](int u0, int u1) {
         const int lpt = 32 / P.tracklets_per_warp;
         return exact ? tpc_exact::launch_tracklets(k, xd, p, tr->n_sm, lpt, P.schedule, u0, u1, s)
@@ -405,7 +410,7 @@ int tpc_enqueue(tpc_tracker* tr, const DevPtrs& p, const BatchShape& sh, cudaStr
         TPC_CUDA(tpc_int::launch_clean(k, p, th, 0, sh.n_units, s));
         TPC_CUDA(tpc_int::launch_start_scan(k, p, s));
         TPC_CUDA(tpc_int::launch_start_write(k, p, th, 0, sh.n_units, s));
-        TPC_CUDA(tpc_int::launch_chain_end(k, p, tr->n_sm, 0, sh.n_units, s));
+        TPC_CUDA(seeds(0, sh.n_units, s));
         if (with_events) TPC_CUDA(cudaEventRecord(tr->ev[3], s));
         TPC_CUDA(tl(-1, -1));
         if (with_events) TPC_CUDA(cudaEventRecord(tr->ev[4], s));
@@ -455,7 +460,7 @@ int tpc_enqueue(tpc_tracker* tr, const DevPtrs& p, const BatchShape& sh, cudaStr
         for (int u = 0; u < sh.n_units; u++) {
             cudaStream_t q = tr->queues[(size_t)(u % nq)];
             TPC_CUDA(tpc_int::launch_start_write(k, p, th, u, 1, q));
-            TPC_CUDA(tpc_int::launch_chain_end(k, p, 1, u, u + 1, q));
+            TPC_CUDA(seeds(u, u + 1, q));
             const int lpt = 32 / P.tracklets_per_warp;
             TPC_CUDA(exact ? tpc_exact::launch_tracklets(k, xd, p, tr->n_sm, lpt, P.schedule, u, u + 1, q)
                            : tpc_fast::launch_tracklets(k, xd, p, tr->n_sm, lpt, P.schedule, u, u + 1, q));
@@ -475,7 +480,7 @@ int tpc_enqueue(tpc_tracker* tr, const DevPtrs& p, const BatchShape& sh, cudaStr
         TPC_CUDA(tpc_int::launch_start_scan(k, p, s));
         for (int u = 0; u < sh.n_units; u++) {
             TPC_CUDA(tpc_int::launch_start_write(k, p, th, u, 1, s));
-            TPC_CUDA(tpc_int::launch_chain_end(k, p, 1, u, u + 1, s));
+            TPC_CUDA(seeds(u, u + 1, s));
         }
         if (with_events) TPC_CUDA(cudaEventRecord(tr->ev[3], s));
         for (int u = 0; u < sh.n_units; u++) TPC_CUDA(tl(u, u + 1));
