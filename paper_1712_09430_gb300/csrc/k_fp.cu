@@ -80,6 +80,8 @@ __global__ void k_neighbours(KConst k, const float* __restrict__ row_x, DevPtrs 
     const float Xr = row_x[r], Xu = row_x[r + 1], Xd = row_x[r - 1];
     const float yu0 = -(Xu * k.tan_h + k.y_margin), yd0 = -(Xd * k.tan_h + k.y_margin);
     const float z0 = ((u % k.n_sectors) < k.n_sectors / 2) ? 0.0f : -k.z_max;
+    const float cyu = -yu0 * gu.inv_by, czu = -z0 * gu.inv_bz;  // bin_index_fma offsets
+    const float cyd = -yd0 * gd.inv_by, czd = -z0 * gd.inv_bz;
     const float Ru = Xu / Xr, Rd = Xd / Xr;
     const float Wu = k.k_win * fabsf(Xu - Xr);
     const float Wd = k.k_win * fabsf(Xd - Xr);
@@ -94,14 +96,14 @@ __global__ void k_neighbours(KConst k, const float* __restrict__ row_x, DevPtrs 
         const float yi = ci.x, zi = ci.y;
         const float ycu = yi * Ru, ycd = yi * Rd;
         // bin windows (widened by kBinEps; the exact test below decides)
-        const int uy0 = bin_index(ycu - Wu - kBinEps, yu0, gu.inv_by, nyu);
-        const int uy1 = bin_index(ycu + Wu + kBinEps, yu0, gu.inv_by, nyu);
-        const int uz0 = bin_index(zi - Wu - kBinEps, z0, gu.inv_bz, nzu);
-        const int uz1 = bin_index(zi + Wu + kBinEps, z0, gu.inv_bz, nzu);
-        const int dy0 = bin_index(ycd - Wd - kBinEps, yd0, gd.inv_by, nyd);
-        const int dy1 = bin_index(ycd + Wd + kBinEps, yd0, gd.inv_by, nyd);
-        const int dz0 = bin_index(zi - Wd - kBinEps, z0, gd.inv_bz, nzd);
-        const int dz1 = bin_index(zi + Wd + kBinEps, z0, gd.inv_bz, nzd);
+        const int uy0 = bin_index_fma(ycu - Wu - kBinEps, cyu, gu.inv_by, nyu);
+        const int uy1 = bin_index_fma(ycu + Wu + kBinEps, cyu, gu.inv_by, nyu);
+        const int uz0 = bin_index_fma(zi - Wu - kBinEps, czu, gu.inv_bz, nzu);
+        const int uz1 = bin_index_fma(zi + Wu + kBinEps, czu, gu.inv_bz, nzu);
+        const int dy0 = bin_index_fma(ycd - Wd - kBinEps, cyd, gd.inv_by, nyd);
+        const int dy1 = bin_index_fma(ycd + Wd + kBinEps, cyd, gd.inv_by, nyd);
+        const int dz0 = bin_index_fma(zi - Wd - kBinEps, czd, gd.inv_bz, nzd);
+        const int dz1 = bin_index_fma(zi + Wd + kBinEps, czd, gd.inv_bz, nzd);
         int bu = -1, bd = -1;
         unsigned bid_u = 0, bid_d = 0;
         float bD = 0.0f;
@@ -340,10 +342,11 @@ __device__ __forceinline__ int search_row(const State& st, const RowGrid& g, flo
     const float iSy = __fdividef(1.0f, Sy), iSz = __fdividef(1.0f, Sz);
 #endif
     const int ny = grid_ny(g), nz = grid_nz(g);
-    const int by0 = bin_index(st.y - wy - kBinEps, y0, g.inv_by, ny);
-    const int by1 = bin_index(st.y + wy + kBinEps, y0, g.inv_by, ny);
-    const int bz0 = bin_index(st.z - wz - kBinEps, z0, g.inv_bz, nz);
-    const int bz1 = bin_index(st.z + wz + kBinEps, z0, g.inv_bz, nz);
+    const float cy = -y0 * g.inv_by, cz = -z0 * g.inv_bz;
+    const int by0 = bin_index_fma(st.y - wy - kBinEps, cy, g.inv_by, ny);
+    const int by1 = bin_index_fma(st.y + wy + kBinEps, cy, g.inv_by, ny);
+    const int bz0 = bin_index_fma(st.z - wz - kBinEps, cz, g.inv_bz, nz);
+    const int bz1 = bin_index_fma(st.z + wz + kBinEps, cz, g.inv_bz, nz);
     int best = -1;
     unsigned bid = 0;
     bool have_bid = false;  // the best id is read only when a tie needs it

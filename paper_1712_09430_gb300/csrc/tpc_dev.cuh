@@ -186,6 +186,16 @@ __device__ __forceinline__ int bin_index(float v, float lo, float inv, int n)
     return b < 0 ? 0 : (b >= n ? n - 1 : b);
 }
 
+// Search-side bin index: v * inv + c with c = -lo * inv, one fused
+// multiply-add.  It can differ from bin_index only for v within ~1e-6 bins of
+// a bin edge; the search windows are widened by kBinEps (>= 1e-4 bins), so
+// the bins they cover always contain every cluster inside the window.
+__device__ __forceinline__ int bin_index_fma(float v, float c, float inv, int n)
+{
+    int b = __float2int_rd(fmaf(v, inv, c));
+    return min(max(b, 0), n - 1);
+}
+
 }  // namespace tpc
 
 // ---------------------------------------------------------------------------

@@ -255,3 +255,25 @@ def test_time_frame_uneven_slices_exact():
     g = gpu_run(cl, rc, len(tf), exact_fp32=1, use_graph=1)
     o = oracle_run(cl, rc, len(tf), mode="f32")
     assert_exact_equal(g, o)
+
+
+def test_order_inside_rows_and_repeat_calls_do_not_change_results(events):
+    """Clusters may come in any order inside a row (ties break by id), and
+    the dynamic work distribution never shows in the output."""
+    ev = events["c3s"]
+    rng = np.random.default_rng(17)
+    perm = np.arange(ev.n)
+    off = np.concatenate([[0], np.cumsum(ev.row_counts)])
+    for a, b in zip(off[:-1], off[1:]):
+        if b - a > 1:
+            perm[a:b] = a + rng.permutation(b - a)
+    shuffled = ev.clusters[perm]
+    with Tracker(XR, bz=ev.bz) as tr:
+        r1 = tr.track(ev.clusters, ev.row_counts, 1)
+        r2 = tr.track(ev.clusters, ev.row_counts, 1)
+        r3 = tr.track(shuffled, ev.row_counts, 1)
+    np.testing.assert_array_equal(r1.tracks.view(np.uint8), r2.tracks.view(np.uint8))
+    np.testing.assert_array_equal(r1.hit_ids, r2.hit_ids)
+    # same tracks; hit ids refer to positions, so map the shuffled ones back
+    np.testing.assert_array_equal(r3.tracks.view(np.uint8), r1.tracks.view(np.uint8))
+    np.testing.assert_array_equal(perm[r3.hit_ids], r1.hit_ids)
