@@ -353,38 +353,52 @@ __device__ __forceinline__ int search_row(const State& st, const RowGrid& g, flo
     float bd2 = 0.0f;
     work.x += 1;
     work.y += bz1 - bz0 + 1;
-    for (int bz = bz0; bz <= bz1; bz++) {
-        const int* row_bins = p.bin_off + g.bin_base + bz * ny;
-        const int j0 = __ldg(row_bins + by0), j1 = __ldg(row_bins + by1 + 1);
-        work.z += j1 - j0;
-        for (int j = j0 + gl; j < j1; j += G) {
-            const float2 c = __ldg(p.hyz + j);
-            const float dy = c.x - st.y;
-            const float dz = c.y - st.z;
-            if (!(fabsf(dy) <= wy && fabsf(dz) <= wz)) continue;
+    // One flat loop over the candidates of the first two z rows of the window
+    // (their bin-table reads go out together), so that lanes with different
+    // numbers of z rows and candidates diverge as little as possible; a
+    // window over more z rows (rare) continues in the general loop below.
+    const int* rb = p.bin_off + g.bin_base + by0;
+    const int ja0 = __ldg(rb + bz0 * ny), ja1 = __ldg(rb + bz0 * ny + (by1 - by0) + 1);
+    int jb0 = 0, jb1 = 0;
+    if (bz1 > bz0) {
+        jb0 = __ldg(rb + (bz0 + 1) * ny);
+        jb1 = __ldg(rb + (bz0 + 1) * ny + (by1 - by0) + 1);
+    }
+    const int na = ja1 - ja0, ntot = na + (jb1 - jb0);
+    work.z += ntot;
+    auto consider = [&](int j) {
+        const float2 c = __ldg(p.hyz + j);
+        const float dy = c.x - st.y;
+        const float dz = c.y - st.z;
+        if (!(fabsf(dy) <= wy && fabsf(dz) <= wz)) return;
 #if TPC_FAST_MATH
-            const float d2 = dy * dy * iSy + dz * dz * iSz;
+        const float d2 = dy * dy * iSy + dz * dz * iSz;
 #else
-            const float d2 = dy * dy / Sy + dz * dz / Sz;
+        const float d2 = dy * dy / Sy + dz * dz / Sz;
 #endif
-            if (best < 0 || d2 < bd2) {
+        if (best < 0 || d2 < bd2) {
+            best = j;
+            bd2 = d2;
+            have_bid = false;
+            found = c;
+        } else if (d2 == bd2) {
+            const unsigned id = __float_as_uint(__ldg(&p.hits[j].z));
+            if (!have_bid) {
+                bid = __float_as_uint(__ldg(&p.hits[best].z));
+                have_bid = true;
+            }
+            if (id < bid) {
                 best = j;
-                bd2 = d2;
-                have_bid = false;
+                bid = id;
                 found = c;
-            } else if (d2 == bd2) {
-                const unsigned id = __float_as_uint(__ldg(&p.hits[j].z));
-                if (!have_bid) {
-                    bid = __float_as_uint(__ldg(&p.hits[best].z));
-                    have_bid = true;
-                }
-                if (id < bid) {
-                    best = j;
-                    bid = id;
-                    found = c;
-                }
             }
         }
+    };
+    for (int i = gl; i < ntot; i += G) consider(i < na ? ja0 + i : jb0 + (i - na));
+    for (int bz = bz0 + 2; bz <= bz1; bz++) {
+        const int j0 = __ldg(rb + bz * ny), j1 = __ldg(rb + bz * ny + (by1 - by0) + 1);
+        work.z += j1 - j0;
+        for (int j = j0 + gl; j < j1; j += G) consider(j);
     }
     if (G > 1) {
         if (best >= 0 && !have_bid) bid = __float_as_uint(__ldg(&p.hits[best].z));
