@@ -350,7 +350,7 @@ __device__ __forceinline__ int search_row(const State& st, const RowGrid& g, flo
     int best = -1;
     unsigned bid = 0;
     bool have_bid = false;  // the best id is read only when a tie needs it
-    float bd2 = 0.0f;
+    float bd2 = __int_as_float(0x7f800000);  // +inf: the first candidate in the window wins
     work.x += 1;
     work.y += bz1 - bz0 + 1;
     // One flat loop over the candidates of the first two z rows of the window
@@ -366,39 +366,51 @@ __device__ __forceinline__ int search_row(const State& st, const RowGrid& g, flo
     }
     const int na = ja1 - ja0, ntot = na + (jb1 - jb0);
     work.z += ntot;
-    auto consider = [&](int j) {
-        const float2 c = __ldg(p.hyz + j);
+    // one candidate: the window test and the distance, then a branch taken
+    // only for an improvement or a tie inside the window
+    auto consider = [&](int j, const float2 c) {
         const float dy = c.x - st.y;
         const float dz = c.y - st.z;
-        if (!(fabsf(dy) <= wy && fabsf(dz) <= wz)) return;
 #if TPC_FAST_MATH
         const float d2 = dy * dy * iSy + dz * dz * iSz;
 #else
         const float d2 = dy * dy / Sy + dz * dz / Sz;
 #endif
-        if (best < 0 || d2 < bd2) {
-            best = j;
-            bd2 = d2;
-            have_bid = false;
-            found = c;
-        } else if (d2 == bd2) {
-            const unsigned id = __float_as_uint(__ldg(&p.hits[j].z));
-            if (!have_bid) {
-                bid = __float_as_uint(__ldg(&p.hits[best].z));
-                have_bid = true;
-            }
-            if (id < bid) {
+        if (fabsf(dy) <= wy && fabsf(dz) <= wz && d2 <= bd2) {
+            if (d2 < bd2) {
                 best = j;
-                bid = id;
+                bd2 = d2;
+                have_bid = false;
                 found = c;
+            } else {  // exact tie: smaller cluster id
+                const unsigned id = __float_as_uint(__ldg(&p.hits[j].z));
+                if (!have_bid) {
+                    bid = __float_as_uint(__ldg(&p.hits[best].z));
+                    have_bid = true;
+                }
+                if (id < bid) {
+                    best = j;
+                    bid = id;
+                    found = c;
+                }
             }
         }
     };
-    for (int i = gl; i < ntot; i += G) consider(i < na ? ja0 + i : jb0 + (i - na));
+    // candidates in pairs: both loads go out before either is tested
+    for (int i0 = gl; i0 < ntot; i0 += 2 * G) {
+        const int i1 = i0 + G;
+        const int j0 = i0 < na ? ja0 + i0 : jb0 + (i0 - na);
+        const int j1 = i1 < na ? ja0 + i1 : jb0 + (i1 - na);
+        const float2 c0 = __ldg(p.hyz + j0);
+        float2 c1 = c0;
+        if (i1 < ntot) c1 = __ldg(p.hyz + j1);
+        consider(j0, c0);
+        if (i1 < ntot) consider(j1, c1);
+    }
     for (int bz = bz0 + 2; bz <= bz1; bz++) {
         const int j0 = __ldg(rb + bz * ny), j1 = __ldg(rb + bz * ny + (by1 - by0) + 1);
         work.z += j1 - j0;
-        for (int j = j0 + gl; j < j1; j += G) consider(j);
+        for (int j = j0 + gl; j < j1; j += G) consider(j, __ldg(p.hyz + j));
     }
     if (G > 1) {
         if (best >= 0 && !have_bid) bid = __float_as_uint(__ldg(&p.hits[best].z));
