@@ -699,6 +699,7 @@ __global__ void k_seeds(KConst k, const float* __restrict__ row_x, DevPtrs p, in
         const float l = sqrtf(dx * dx + dy * dy);
         p.t_seed[t] = make_float4(c0.x, c0.y, dy / l, dz / l);
         p.t_info[t] = make_int4(rr0, h0, len, 0);
+        p.owned[t] = 0;  // counted by the selection
     }
 }
 

@@ -411,28 +411,33 @@ __global__ void k_owner(KConst k, DevPtrs p, int u0, int u1)
     }
 }
 
+// Clusters owned per tracklet: one pass over the clusters (a warp per row,
+// coalesced reads of the owner keys); the winner is decoded from its key.
+__global__ void k_owned_count(KConst k, DevPtrs p, int rr0, int rows)
+{
+    const int lane = threadIdx.x & 31;
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (w >= rows) return;
+    const int rr = rr0 + w;
+    const int b0 = p.row_off[rr], b1 = p.row_off[rr + 1];
+    if (b0 == b1) return;
+    const int tb = p.start_off[rr - rr % k.n_rows];  // first tracklet of the unit
+    for (int b = b0 + lane; b < b1; b += 32) {
+        const unsigned key = p.owner[b];
+        if (key) atomicAdd(&p.owned[tb + (int)(0x7FFFFFu - (key & 0x7FFFFFu))], 1);
+    }
+}
+
 // A tracklet keeps the clusters it owns; accepted if enough remain.
 __global__ void k_accept(KConst k, DevPtrs p, int u0, int u1)
 {
     const int t0 = p.start_off[u0 * k.n_rows], t1 = p.start_off[u1 * k.n_rows];
-    const int lane = threadIdx.x & 31;
-    const int w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
-    for (int t = t0 + w0; t < t1; t += nw) {
+    for (int t = t0 + blockIdx.x * blockDim.x + threadIdx.x; t < t1; t += gridDim.x * blockDim.x) {
         const int n = p.tl_n[t];
-        int owned = 0;
-        if (n >= k.n_min_tracklet) {
-            const unsigned key = tl_key(k, p, n, t);
-            const int* h = p.tl_hits + (size_t)t * k.n_rows;
-            for (int j0 = 0; j0 < n; j0 += 32) {
-                const bool own = j0 + lane < n && p.owner[h[j0 + lane]] == key;
-                owned += __popc(__ballot_sync(0xffffffffu, own));
-            }
-        }
-        if (lane == 0) {
-            const bool acc = owned >= k.n_min_track &&
-                             (long long)owned * k.own_den >= (long long)k.own_num * n;
-            p.acc[t] = acc ? make_int2(1, owned) : make_int2(0, 0);
-        }
+        const int owned = p.owned[t];
+        const bool acc = n >= k.n_min_tracklet && owned >= k.n_min_track &&
+                         (long long)owned * k.own_den >= (long long)k.own_num * n;
+        p.acc[t] = acc ? make_int2(1, owned) : make_int2(0, 0);
     }
 }
 
@@ -631,6 +636,8 @@ cudaError_t launch_select(const KConst& k, const DevPtrs& p, int n_sm, int u0, i
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
+    const int rows = (u1 - u0) * k.n_rows;
+    if (rows > 0) k_owned_count<<<(rows + 7) / 8, 256, 0, s>>>(k, p, u0 * k.n_rows, rows);
     k_accept<<<n_sm * 8, 256, 0, s>>>(k, p, u0, u1);
     return cudaGetLastError();
 }

@@ -85,6 +85,7 @@ struct DevPtrs {
     int* tl_hits;              // [Tcap][n_rows] binned, rows DESCENDING
     int4* tl_work;             // [Tcap] row steps, bin-table rows, candidates, chain length
     unsigned* owner;           // [N] best key (n << 23 | 0x7FFFFF - t_local), 0 = none
+    int* owned;                // [Tcap] clusters each tracklet owns after selection
     int2* acc;                 // [Tcap] (accepted, owned hits)
     int2* acc_scan;            // [Tcap] exclusive scan of acc
     int2* scan_part;           // [ceil(Tcap / kScanTile) + 1]

@@ -255,6 +255,7 @@ size_t tpc_layout(const tpc_tracker* tr, const BatchShape& sh, DevPtrs* p, char*
     q.tl_hits = reinterpret_cast<int*>(take(Tc * NR * 4));
     q.tl_work = reinterpret_cast<int4*>(take(Tc * 16));
     q.owner = reinterpret_cast<unsigned*>(take(N * 4));
+    q.owned = reinterpret_cast<int*>(take(Tc * 4));
     q.acc = reinterpret_cast<int2*>(take(Tc * 8));
     q.acc_scan = reinterpret_cast<int2*>(take(Tc * 8));
     q.scan_part = reinterpret_cast<int2*>(take((Tc / kScanTile + 2) * 8));
