@@ -130,48 +130,55 @@ __global__ void k_neighbours(KConst k, const float* __restrict__ row_x, DevPtrs 
                 bid_d = idd;
             }
         };
+        // Candidates of a window: one flat loop over its first two z rows (so
+        // threads with different numbers of z rows and candidates diverge as
+        // little as possible), then any further z rows.
+        auto for_window = [&](int tab, int ny, int y0b, int y1b, int z0b, int z1b, auto&& f) {
+            const int* rb = bins + tab + y0b;
+            const int span = y1b - y0b + 1;
+            const int a0 = rb[z0b * ny] - off_d, a1 = rb[z0b * ny + span] - off_d;
+            int b0 = 0, b1 = 0;
+            if (z1b > z0b) {
+                b0 = rb[(z0b + 1) * ny] - off_d;
+                b1 = rb[(z0b + 1) * ny + span] - off_d;
+            }
+            const int na = a1 - a0, nt = na + (b1 - b0);
+            for (int c = 0; c < nt; c++) f(c < na ? a0 + c : b0 + (c - na));
+            for (int bz = z0b + 2; bz <= z1b; bz++) {
+                const int j0 = rb[bz * ny] - off_d, j1 = rb[bz * ny + span] - off_d;
+                for (int j = j0; j < j1; j++) f(j);
+            }
+        };
         // down candidates once, into a register list of up to 4
         int nd = 0;
         int jd0 = -1, jd1 = -1, jd2 = -1, jd3 = -1;
         float4 cd0 = make_float4(0.f, 0.f, 0.f, 0.f), cd1 = cd0, cd2 = cd0, cd3 = cd0;
-        for (int bzd = dz0; bzd <= dz1; bzd++) {
-            const int j0 = bins[td + bzd * nyd + dy0] - off_d;
-            const int j1 = bins[td + bzd * nyd + dy1 + 1] - off_d;
-            for (int jd = j0; jd < j1; jd++) {
-                const float4 cd = rec[jd];
-                if (!(fabsf(cd.x - ycd) <= Wd && fabsf(cd.y - zi) <= Wd)) continue;
+        for_window(td, nyd, dy0, dy1, dz0, dz1, [&](int jd) {
+            const float4 cd = rec[jd];
+            if (fabsf(cd.x - ycd) <= Wd && fabsf(cd.y - zi) <= Wd) {
                 jd3 = jd2; cd3 = cd2;
                 jd2 = jd1; cd2 = cd1;
                 jd1 = jd0; cd1 = cd0;
                 jd0 = jd; cd0 = cd;
                 nd++;
             }
-        }
+        });
         if (nd > 0) {
-            for (int bzu = uz0; bzu <= uz1; bzu++) {
-                const int ju0 = bins[tu + bzu * nyu + uy0] - off_d;
-                const int ju1 = bins[tu + bzu * nyu + uy1 + 1] - off_d;
-                for (int ju = ju0; ju < ju1; ju++) {
-                    const float4 cu = rec[ju];
-                    if (!(fabsf(cu.x - ycu) <= Wu && fabsf(cu.y - zi) <= Wu)) continue;
-                    if (nd <= 4) {
-                        consider(ju, cu, jd0, cd0);
-                        if (nd > 1) consider(ju, cu, jd1, cd1);
-                        if (nd > 2) consider(ju, cu, jd2, cd2);
-                        if (nd > 3) consider(ju, cu, jd3, cd3);
-                    } else {  // a crowded window: scan the down row again
-                        for (int bzd = dz0; bzd <= dz1; bzd++) {
-                            const int j0 = bins[td + bzd * nyd + dy0] - off_d;
-                            const int j1 = bins[td + bzd * nyd + dy1 + 1] - off_d;
-                            for (int jd = j0; jd < j1; jd++) {
-                                const float4 cd = rec[jd];
-                                if (!(fabsf(cd.x - ycd) <= Wd && fabsf(cd.y - zi) <= Wd)) continue;
-                                consider(ju, cu, jd, cd);
-                            }
-                        }
-                    }
+            for_window(tu, nyu, uy0, uy1, uz0, uz1, [&](int ju) {
+                const float4 cu = rec[ju];
+                if (!(fabsf(cu.x - ycu) <= Wu && fabsf(cu.y - zi) <= Wu)) return;
+                if (nd <= 4) {
+                    consider(ju, cu, jd0, cd0);
+                    if (nd > 1) consider(ju, cu, jd1, cd1);
+                    if (nd > 2) consider(ju, cu, jd2, cd2);
+                    if (nd > 3) consider(ju, cu, jd3, cd3);
+                } else {  // a crowded window: scan the down row again
+                    for_window(td, nyd, dy0, dy1, dz0, dz1, [&](int jd) {
+                        const float4 cd = rec[jd];
+                        if (fabsf(cd.x - ycd) <= Wd && fabsf(cd.y - zi) <= Wd) consider(ju, cu, jd, cd);
+                    });
                 }
-            }
+            });
         }
         p.up[off_m + i] = bu >= 0 ? off_d + bu : -1;
         p.dn[off_m + i] = bd >= 0 ? off_d + bd : -1;
