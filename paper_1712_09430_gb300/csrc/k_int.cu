@@ -3,6 +3,7 @@
 // start hits (the CA's second and third steps, Sec. 2 step 1), canonical and
 // length-sorted tracklet numbering, tracklet selection (Sec. 2 step 2: the
 // best instance is kept, the others removed) and output compaction.
+#include <algorithm>
 #include <cstdint>
 
 #include "tpc_dev.cuh"
@@ -411,6 +412,40 @@ __global__ void k_owner(KConst k, DevPtrs p, int u0, int u1)
     }
 }
 
+// Ownership of one unit's clusters in shared memory: a CTA per (unit, chunk
+// of kOwnerChunk clusters) scans the cluster lists of the unit's live
+// tracklets (a warp per tracklet), applies atomicMax in shared memory to the
+// clusters of its chunk, then writes the chunk's keys out coalesced.
+// Ownership never crosses units, so no global atomics are needed.
+constexpr int kOwnerChunk = 48 * 1024;
+
+__global__ void __launch_bounds__(1024) k_owner_units(KConst k, DevPtrs p, int chunks)
+{
+    extern __shared__ unsigned keys[];
+    const int u = blockIdx.x / chunks, c = blockIdx.x % chunks;
+    const int NR = k.n_rows;
+    const int ub0 = p.row_off[u * NR], ub1 = p.row_off[(u + 1) * NR];
+    const int lo = ub0 + c * kOwnerChunk;
+    const int hi = min(ub1, lo + kOwnerChunk);
+    if (lo >= hi) return;
+    for (int i = threadIdx.x; i < hi - lo; i += blockDim.x) keys[i] = 0u;
+    __syncthreads();
+    const int t0 = p.start_off[u * NR], t1 = p.start_off[(u + 1) * NR];
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int t = t0 + (int)(threadIdx.x >> 5); t < t1; t += nw) {
+        const int n = p.tl_n[t];
+        if (n < k.n_min_tracklet) continue;
+        const unsigned key = ((unsigned)n << 23) | (0x7FFFFFu - (unsigned)(t - t0));
+        const int* h = p.tl_hits + (size_t)t * NR;
+        for (int j = lane; j < n; j += 32) {
+            const int b = h[j];
+            if (b >= lo && b < hi) atomicMax(&keys[b - lo], key);
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < hi - lo; i += blockDim.x) p.owner[lo + i] = keys[i];
+}
+
 // Clusters owned per tracklet: one pass over the clusters (a warp per row,
 // coalesced reads of the owner keys); the winner is decoded from its key.
 __global__ void k_owned_count(KConst k, DevPtrs p, int rr0, int rows)
@@ -639,6 +674,18 @@ cudaError_t launch_select(const KConst& k, const DevPtrs& p, int n_sm, int u0, i
     const int rows = (u1 - u0) * k.n_rows;
     if (rows > 0) k_owned_count<<<(rows + 7) / 8, 256, 0, s>>>(k, p, u0 * k.n_rows, rows);
     k_accept<<<n_sm * 8, 256, 0, s>>>(k, p, u0, u1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_owner_units(const KConst& k, const DevPtrs& p, int n_units, int max_unit,
+                               cudaStream_t s)
+{
+    if (n_units == 0 || max_unit == 0) return cudaSuccess;
+    const int chunks = (max_unit + kOwnerChunk - 1) / kOwnerChunk;
+    const size_t sm = (size_t)std::min(max_unit, kOwnerChunk) * 4;
+    cudaError_t e = cudaFuncSetAttribute(k_owner_units, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k_owner_units<<<n_units * chunks, 1024, sm, s>>>(k, p, chunks);
     return cudaGetLastError();
 }
 

@@ -215,6 +215,8 @@ cudaError_t launch_start_write(const tpc::KConst& k, const tpc::DevPtrs& p, int 
                                int n_units, cudaStream_t s);
 cudaError_t launch_select(const tpc::KConst& k, const tpc::DevPtrs& p, int n_sm, int t0_unit,
                           int t1_unit, bool owner, cudaStream_t s);
+cudaError_t launch_owner_units(const tpc::KConst& k, const tpc::DevPtrs& p, int n_units, int max_unit,
+                               cudaStream_t s);
 cudaError_t launch_emit(const tpc::KConst& k, const tpc::DevPtrs& p, int n_sm, cudaStream_t s);
 cudaError_t launch_dump_links(const tpc::DevPtrs& p, int cleaned, int* dst, cudaStream_t s);
 cudaError_t launch_dump_starts(const tpc::DevPtrs& p, int T, int* dst, cudaStream_t s);

@@ -13,6 +13,7 @@ struct BatchShape {
     int n_events = 0, n_units = 0, R = 0, N = 0, t_cap = 0;
     int64_t bin_slots = 0;
     int max_row = 1, max3 = 1;
+    int max_unit = 0;  // clusters of the largest (event, sector) unit
 };
 
 struct ServeState;  // defined in serve.cu

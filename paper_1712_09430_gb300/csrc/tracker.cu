@@ -279,7 +279,7 @@ int tpc_shape(tpc_tracker* tr, const int32_t* row_counts, int n_events, BatchSha
     const int NR = tr->geom.n_rows, S = tr->geom.n_sectors;
     const int64_t R = (int64_t)n_events * S * NR;
     if (R > (1 << 28)) return tr->fail(TPC_ERR_INVALID, "too many rows in one call");
-    int64_t N = 0, bins = 0;
+    int64_t N = 0, bins = 0, max_unit = 0;
     int max_row = 0, max3 = 0;
     if ((size_t)(2 * (R + 1)) > tr->plan_cap) {
         cudaFreeHost(tr->plan_host);
@@ -316,6 +316,7 @@ int tpc_shape(tpc_tracker* tr, const int32_t* row_counts, int n_events, BatchSha
                 }
             }
         }
+        const int64_t n_before = N;
         for (int r = 0; r < NR; r++) {
             const int c = cnt[r];
             plan_off[u0 + r] = (int)N;
@@ -324,6 +325,7 @@ int tpc_shape(tpc_tracker* tr, const int32_t* row_counts, int n_events, BatchSha
             bins += lut[c];
             max_row = std::max(max_row, c);
         }
+        max_unit = std::max<int64_t>(max_unit, N - n_before);
         for (int r = 1; r + 1 < NR; r++) max3 = std::max(max3, cnt[r - 1] + cnt[r] + cnt[r + 1]);
     }
     if (N >= (int64_t)1 << 30) return tr->fail(TPC_ERR_INVALID, "more than 2^30 clusters in one call");
@@ -339,6 +341,7 @@ int tpc_shape(tpc_tracker* tr, const int32_t* row_counts, int n_events, BatchSha
     sh->bin_slots = bins;
     sh->max_row = std::max(max_row, 1);
     sh->max3 = std::max(max3, 1);
+    sh->max_unit = (int)max_unit;
     return TPC_OK;
 }
 
@@ -415,7 +418,8 @@ int tpc_enqueue(tpc_tracker* tr, const DevPtrs& p, const BatchShape& sh, cudaStr
         if (with_events) TPC_CUDA(cudaEventRecord(tr->ev[3], s));
         TPC_CUDA(tl(-1, -1));
         if (with_events) TPC_CUDA(cudaEventRecord(tr->ev[4], s));
-        TPC_CUDA(tpc_int::launch_select(k, p, tr->n_sm, 0, sh.n_units, true, s));
+        TPC_CUDA(tpc_int::launch_owner_units(k, p, sh.n_units, sh.max_unit, s));
+        TPC_CUDA(tpc_int::launch_select(k, p, tr->n_sm, 0, sh.n_units, false, s));
     } else if (P.plain_per_sector == 2) {
         // Multi-queue scheme (Sec. 3.1, Fig. 3): each unit's stages in order
         // on one of n_queues streams, units round-robin; the two global steps
