@@ -1,9 +1,10 @@
-"""CPU oracle of the per-sector TPC tracker (test infrastructure only).
+"""CPU oracle of the per-sector TPC tracker and of the final track fit
+(test infrastructure only).
 
 Only tests/, the package smoke check and the CPU-baseline leg of the
 benchmark load this module.  The CUDA path never imports it, and it imports
 nothing from the CUDA path.  See tpc_oracle.c for what each function follows
-and what pins it.
+and what pins it; tpc_refit.c holds the full Kalman filter refit.
 
 Two builds of the same C source:
   mode="f64"  FP64 accuracy reference
@@ -18,11 +19,12 @@ import subprocess
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "tpc_oracle.c")
+_SRCS = [os.path.join(_HERE, "tpc_oracle.c"), os.path.join(_HERE, "tpc_refit.c")]
 _BUILD = os.path.join(_HERE, "_build")
 _LIBS = {}
 
 N_TL_F = 16  # x y z s t q cy[6] cz[3] chi2
+N_FIT = 24   # x p[5] cov[15] chi2 ndf status
 
 
 class Params(C.Structure):
@@ -31,6 +33,11 @@ class Params(C.Structure):
                                           "var_q", "var_t")] + \
                [(n, C.c_int) for n in ("g_max", "l_seed", "n_min_tracklet", "n_min_track",
                                        "own_num", "own_den")]
+
+
+class FitParams(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("sigma_y", "sigma_z", "var_s", "var_t", "var_q", "s_max",
+                                          "bz")] + [("b", C.c_double * 5)]
 
 
 class Geom(C.Structure):
@@ -47,10 +54,11 @@ def build(force=False):
     os.makedirs(_BUILD, exist_ok=True)
     for mode, real in (("f64", "double"), ("f32", "float")):
         out = _lib_path(mode)
-        if not force and os.path.exists(out) and os.path.getmtime(out) >= os.path.getmtime(_SRC):
+        if not force and os.path.exists(out) and \
+                os.path.getmtime(out) >= max(os.path.getmtime(f) for f in _SRCS):
             continue
         base = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
-                "-shared", f"-DORACLE_REAL={real}", _SRC, "-o", out + ".tmp", "-lm"]
+                "-shared", f"-DORACLE_REAL={real}", *_SRCS, "-o", out + ".tmp", "-lm"]
         try:
             subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True, capture_output=True)
         except subprocess.CalledProcessError:
@@ -74,6 +82,9 @@ def lib(mode="f64"):
         L.orc_propagate.argtypes = [P(Params), C.c_double, V, C.c_double]
         L.orc_update_state.argtypes = [P(Params), V, C.c_double, C.c_double, P(C.c_double)]
         L.orc_fit_hits.argtypes = [P(Params), C.c_double, V, C.c_int, V, V, V, P(C.c_double)]
+        L.orc_refit_tracks.argtypes = [P(FitParams), C.c_int, V, V, V, V, V, C.c_int]
+        L.orc_refit_propagate.argtypes = [P(FitParams), V, C.c_double]
+        L.orc_refit_update.argtypes = [P(FitParams), V, C.c_double, C.c_double, P(C.c_double)]
         L.orc_max_threads.restype = C.c_int
         L.orc_real_size.restype = C.c_int
         _LIBS[mode] = L
@@ -187,3 +198,75 @@ def fit_hits(v, x, y, z, bz, params=None, mode="f64"):
 
 def max_threads():
     return int(lib("f64").orc_max_threads())
+
+
+# final track fit (tpc_refit.c) ---------------------------------------------
+
+def fit_params(bz, field=None, params=None, **over) -> FitParams:
+    """Constants of the refit: cluster errors, reset variances and s_max from
+    the tracker params, the constant field bz and the polynomial terms
+    field = (b1..b5) of Bz = bz + z (b1 + z b2) + rho^2 (b3 + z (b4 + z b5))."""
+    p = params if params is not None else default_params()
+    f = FitParams()
+    for k in ("sigma_y", "sigma_z", "var_s", "var_t", "var_q", "s_max"):
+        setattr(f, k, getattr(p, k))
+    f.bz = bz
+    for j, v in enumerate(field if field is not None else (0.0,) * 5):
+        f.b[j] = v
+    for k, v in over.items():
+        setattr(f, k, v)
+    return f
+
+
+def refit_tracks(o, clusters, bz, field=None, params=None, mode="f64", threads=0, fp=None):
+    """Refit the selected tracks of an oracle result `o` (run()): start state
+    from each track's tracklet (tl_f x..q), clusters from `clusters` by the
+    track's hit positions.  Returns float64 [M, N_FIT]."""
+    f = fp if fp is not None else fit_params(bz, field, params)
+    st6 = np.ascontiguousarray(o["tl_f"][o["trk_t"], :6], np.float64)
+    return refit_lists(st6, o["trk_hit_off"], o["trk_hits"], clusters, f, mode, threads)
+
+
+def refit_lists(st6, hit_off, hits, clusters, fp, mode="f64", threads=0):
+    st6 = np.ascontiguousarray(st6, np.float64).reshape(-1, 6)
+    M = len(st6)
+    off = np.ascontiguousarray(hit_off, np.int64)
+    h = np.ascontiguousarray(hits, np.int32)
+    cl = np.ascontiguousarray(clusters, np.float32)
+    out = np.zeros((M, N_FIT), np.float64)
+    lib(mode).orc_refit_tracks(C.byref(fp), M, _ptr(st6), _ptr(off), _ptr(h), _ptr(cl), _ptr(out),
+                               int(threads))
+    return out
+
+
+def fit_vec(x, p, C5=None):
+    """21-vector of the single-step refit entries: x, p[5], packed lower C."""
+    v = np.zeros(21)
+    v[0] = x
+    v[1:6] = p
+    if C5 is not None:
+        v[6:] = [C5[i][j] for i in range(5) for j in range(i + 1)]
+    return v
+
+
+def unpack_cov(v, at=6):
+    C5 = np.zeros((5, 5))
+    k = at
+    for i in range(5):
+        for j in range(i + 1):
+            C5[i, j] = C5[j, i] = v[k]
+            k += 1
+    return C5
+
+
+def refit_propagate(v, x1, fp, mode="f64"):
+    v = np.array(v, dtype=np.float64)
+    ok = lib(mode).orc_refit_propagate(C.byref(fp), _ptr(v), float(x1))
+    return bool(ok), v
+
+
+def refit_update(v, my, mz, fp, mode="f64", chi2=0.0):
+    v = np.array(v, dtype=np.float64)
+    c = C.c_double(chi2)
+    lib(mode).orc_refit_update(C.byref(fp), _ptr(v), float(my), float(mz), C.byref(c))
+    return v, c.value

@@ -1,0 +1,334 @@
+/*
+ * CPU oracle of the final track fit: the full Kalman filter refit of each
+ * selected track (Sec. 2, "Track fit"; Table 1 row 4), with the magnetic
+ * field given as a polynomial instead of a field map (Sec. 2: the polynomial
+ * approximation avoids slow field-map reads).
+ *
+ * TEST INFRASTRUCTURE ONLY, like tpc_oracle.c (built into the same library):
+ * loaded by the tests, the package smoke check and the benchmark's
+ * CPU-baseline leg, never by the CUDA path; it shares no source with it.
+ *
+ * The paper names the step but gives no equations; the readings (F1-F6 in
+ * the design notes) are:
+ *   F1 state p = (y, z, s = sin phi, t = tan lambda, q = q/pT) at the plane
+ *      x, with a full symmetric 5x5 covariance (15 packed lower entries,
+ *      C[i][j] at i (i + 1) / 2 + j for i >= j);
+ *   F2 propagation is the exact helix step of the tracklet filter (signed
+ *      chord, arc series to u^4), the covariance is transported with the full
+ *      analytic Jacobian of that step (all cross terms kept), no process noise;
+ *   F3 the field is Bz(rho, z) = bz + z (b1 + z b2) + rho^2 (b3 + z (b4 + z b5)),
+ *      rho^2 = x^2 + y^2 (frame independent), evaluated once per step at the
+ *      straight-line midpoint and held constant over the step; the Jacobian
+ *      ignores the field's derivatives;
+ *   F4 update with the 2-D measurement (y, z) of variance diag(sy^2, sz^2):
+ *      S = H C H^T + V, K = C H^T S^-1, p += K r, C -= K H C,
+ *      chi2 += r^T S^-1 r;
+ *   F5 two passes over the track's clusters, each cluster on its own x:
+ *      outward (rows ascending) from the tracklet state, then inward from the
+ *      outermost cluster; each pass starts at its first cluster with y, z set
+ *      to that measurement, C = diag(sy^2, sz^2, var_s, var_t, var_q) and
+ *      chi2 = 0 (an infinite prior on y and z), then filters the rest.  The
+ *      output is the inward pass's state at the innermost cluster,
+ *      chi2, ndf = 2 n - 5;
+ *   F6 a step with |sin phi| above s_max before or after it fails the fit:
+ *      status 1, the output holds the state reached, ndf counts the clusters
+ *      filtered in the failing pass.
+ *
+ * Parity status (tests/test_oracle_refit.py):
+ *   propagate   closed-form helix (textbook arcsine form, not the series)
+ *   Jacobian    every column against central finite differences of propagate
+ *   update      Bayesian posterior in information form (numpy.linalg)
+ *   refit       small-noise limit equals one Gauss-Newton step of least
+ *               squares on the closed-form helix, estimate and covariance;
+ *               noise-free tracks: fixed point = truth; pulls and chi2/ndf on
+ *               smeared tracks; non-uniform field: truth recovered on tracks
+ *               integrated numerically through the same polynomial field
+ *
+ * Written with plain 5x5 matrices and loops; every product runs its sum in
+ * increasing index order.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#ifndef ORACLE_REAL
+#define ORACLE_REAL double
+#endif
+typedef ORACLE_REAL rreal;
+
+#define RF(c) ((rreal)(c))
+#define RF_IS_FLOAT (sizeof(rreal) == sizeof(float))
+#define RF_KAPPA 0.00299792458 /* curvature [1/cm] per (T * c/GeV) */
+#define RF_NOUT 24             /* x p[5] cov[15] chi2 ndf status */
+
+static inline rreal f_sqrt(rreal v) { return RF_IS_FLOAT ? (rreal)sqrtf((float)v) : (rreal)sqrt((double)v); }
+static inline rreal f_fabs(rreal v) { return RF_IS_FLOAT ? (rreal)fabsf((float)v) : (rreal)fabs((double)v); }
+static inline rreal f_copysign(rreal v, rreal s)
+{
+    return RF_IS_FLOAT ? (rreal)copysignf((float)v, (float)s) : (rreal)copysign((double)v, (double)s);
+}
+
+/* Constants of the fit in working precision. */
+typedef struct {
+    double sigma_y, sigma_z, var_s, var_t, var_q, s_max;
+    double bz;       /* constant term of the field (T)                          */
+    double b[5];     /* field polynomial: z, z^2, rho^2, rho^2 z, rho^2 z^2       */
+} orc_fit_params;
+
+typedef struct {
+    rreal sy2, sz2, var_s, var_t, var_q, s_max;
+    rreal kB0;       /* -kappa * bz, rounded once from double                   */
+    rreal kP;        /* -kappa                                                  */
+    rreal b[5];
+} rf_ctx;
+
+static void rf_ctx_init(rf_ctx* c, const orc_fit_params* p)
+{
+    rreal sy = RF(p->sigma_y), sz = RF(p->sigma_z);
+    c->sy2 = sy * sy;
+    c->sz2 = sz * sz;
+    c->var_s = RF(p->var_s);
+    c->var_t = RF(p->var_t);
+    c->var_q = RF(p->var_q);
+    c->s_max = RF(p->s_max);
+    c->kB0 = RF(-RF_KAPPA * p->bz);
+    c->kP = RF(-RF_KAPPA);
+    for (int j = 0; j < 5; j++) c->b[j] = RF(p->b[j]);
+}
+
+typedef struct {
+    rreal x;
+    rreal p[5];      /* y z s t q */
+    rreal C[5][5];   /* full symmetric */
+} rf_state;
+
+/* F2, F3: one step to the plane x1.  Returns 1 on success, 0 when |sin phi|
+ * exceeds s_max before or after the step (state untouched). */
+static int rf_prop(const rf_ctx* c, rf_state* st, rreal x1)
+{
+    rreal d = x1 - st->x;
+    if (d == RF(0)) return 1;
+    rreal y = st->p[0], z = st->p[1], s0 = st->p[2], t = st->p[3], q = st->p[4];
+    if (f_fabs(s0) > c->s_max) return 0;
+    rreal c0 = f_sqrt(RF(1) - s0 * s0);
+
+    /* field at the straight-line midpoint of the step */
+    rreal h = d * RF(0.5);
+    rreal xm = st->x + h;
+    rreal ym = y + h * (s0 / c0);
+    rreal zm = z + h * (t / c0);
+    rreal r2 = xm * xm + ym * ym;
+    rreal poly = zm * (c->b[0] + zm * c->b[1]) + r2 * (c->b[2] + zm * (c->b[3] + zm * c->b[4]));
+    rreal kB = c->kB0 + c->kP * poly;
+
+    rreal k = kB * q;
+    rreal s1 = s0 + k * d;
+    if (f_fabs(s1) > c->s_max) return 0;
+    rreal c1 = f_sqrt(RF(1) - s1 * s1);
+    rreal A = s0 + s1;
+    rreal B = c0 + c1;
+    rreal dy = d * A / B;
+    rreal L = f_copysign(f_sqrt(d * d + dy * dy), d);
+    rreal u = k * L * RF(0.5);
+    rreal u2 = u * u;
+    rreal arc = L * (RF(1) + u2 * (RF(1.0 / 6.0) + u2 * RF(3.0 / 40.0)));
+    rreal dz = t * arc;
+
+    /* Jacobian of (y1, z1, s1, t1, q1) by (y, z, s, t, q):
+     *   dy1/ds = d (2 B + A (s0/c0 + s1/c1)) / B^2
+     *   dy1/dq = d (kB d) (B + A s1/c1) / B^2
+     *   ds1/dq = kB d
+     *   arc(L, k): d arc/dL = 1 + u^2/2 + 3 u^4/8, d arc/dk = L^2/2 (u/3 + 3 u^3/10)
+     *   dL/d(dy) = dy / L
+     *   dz1/ds = t (d arc/dL) (dy/L) dy1/ds
+     *   dz1/dq = t ((d arc/dL) (dy/L) dy1/dq + (d arc/dk) kB)
+     *   dz1/dt = arc                                                        */
+    rreal iB2 = RF(1) / (B * B);
+    rreal hq = kB * d;
+    rreal ja_in = RF(2) * B + A * (s0 / c0 + s1 / c1);
+    rreal ja = d * ja_in * iB2;
+    rreal jb_in = B + A * (s1 / c1);
+    rreal jb = d * hq * jb_in * iB2;
+    rreal g = RF(1) + u2 * (RF(0.5) + u2 * RF(0.375));
+    rreal w = dy / L;
+    rreal jcs = t * g * w * ja;
+    rreal fp = u * (RF(1.0 / 3.0) + u2 * RF(0.3));
+    rreal jcq = t * (g * w * jb + L * L * RF(0.5) * fp * kB);
+
+    rreal J[5][5];
+    memset(J, 0, sizeof J);
+    for (int i = 0; i < 5; i++) J[i][i] = RF(1);
+    J[0][2] = ja;  J[0][4] = jb;
+    J[1][2] = jcs; J[1][3] = arc; J[1][4] = jcq;
+    J[2][4] = hq;
+
+    /* C1 = J C J^T: F = J C, then C1 = F J^T */
+    rreal F[5][5], C1[5][5];
+    for (int i = 0; i < 5; i++)
+        for (int j = 0; j < 5; j++) {
+            rreal acc = J[i][0] * st->C[0][j];
+            for (int m = 1; m < 5; m++) acc = acc + J[i][m] * st->C[m][j];
+            F[i][j] = acc;
+        }
+    for (int i = 0; i < 5; i++)
+        for (int j = 0; j < 5; j++) {
+            rreal acc = F[i][0] * J[j][0];
+            for (int m = 1; m < 5; m++) acc = acc + F[i][m] * J[j][m];
+            C1[i][j] = acc;
+        }
+    /* keep the lower triangle as computed, mirror it */
+    for (int i = 0; i < 5; i++)
+        for (int j = 0; j <= i; j++) { st->C[i][j] = C1[i][j]; st->C[j][i] = C1[i][j]; }
+
+    st->x = x1;
+    st->p[0] = y + dy;
+    st->p[1] = z + dz;
+    st->p[2] = s1;
+    return 1;
+}
+
+/* F4: measurement update with (my, mz). */
+static void rf_update(const rf_ctx* c, rf_state* st, rreal my, rreal mz, rreal* chi2)
+{
+    rreal r0 = my - st->p[0];
+    rreal r1 = mz - st->p[1];
+    rreal S00 = st->C[0][0] + c->sy2;
+    rreal S10 = st->C[1][0];
+    rreal S11 = st->C[1][1] + c->sz2;
+    rreal det = S00 * S11 - S10 * S10;
+    rreal inv = RF(1) / det;
+    rreal Si00 = S11 * inv, Si10 = -(S10 * inv), Si11 = S00 * inv;
+    rreal Si[2][2] = {{Si00, Si10}, {Si10, Si11}};
+    /* K = C H^T S^-1: C H^T holds the first two columns of C */
+    rreal K[5][2];
+    for (int i = 0; i < 5; i++)
+        for (int a = 0; a < 2; a++) K[i][a] = st->C[i][0] * Si[0][a] + st->C[i][1] * Si[1][a];
+    /* C1 = C - K (H C), H C holds the first two rows of C */
+    rreal C1[5][5];
+    for (int i = 0; i < 5; i++)
+        for (int j = 0; j < 5; j++)
+            C1[i][j] = st->C[i][j] - (K[i][0] * st->C[0][j] + K[i][1] * st->C[1][j]);
+    for (int i = 0; i < 5; i++) st->p[i] = st->p[i] + (K[i][0] * r0 + K[i][1] * r1);
+    for (int i = 0; i < 5; i++)
+        for (int j = 0; j <= i; j++) { st->C[i][j] = C1[i][j]; st->C[j][i] = C1[i][j]; }
+    *chi2 = *chi2 + (r0 * (Si00 * r0 + Si10 * r1) + r1 * (Si10 * r0 + Si11 * r1));
+}
+
+/* F5: start of a pass at a cluster */
+static void rf_init_pass(const rf_ctx* c, rf_state* st, rreal my, rreal mz, rreal* chi2)
+{
+    st->p[0] = my;
+    st->p[1] = mz;
+    memset(st->C, 0, sizeof st->C);
+    st->C[0][0] = c->sy2;
+    st->C[1][1] = c->sz2;
+    st->C[2][2] = c->var_s;
+    st->C[3][3] = c->var_t;
+    st->C[4][4] = c->var_q;
+    *chi2 = RF(0);
+}
+
+static void rf_store(const rf_state* st, rreal chi2, int ndf, int status, double* out)
+{
+    out[0] = (double)st->x;
+    for (int i = 0; i < 5; i++) out[1 + i] = (double)st->p[i];
+    for (int i = 0, k = 0; i < 5; i++)
+        for (int j = 0; j <= i; j++, k++) out[6 + k] = (double)st->C[i][j];
+    out[21] = (double)chi2;
+    out[22] = (double)ndf;
+    out[23] = (double)status;
+}
+
+/* One track: start state st6 = (x, y, z, s, t, q); n clusters (x, y, z, id)
+ * in row-ascending order.  out[RF_NOUT]. */
+static void rf_refit(const rf_ctx* c, const double* st6, int n, const float* const* cl, double* out)
+{
+    rf_state st;
+    memset(&st, 0, sizeof st);
+    st.x = RF(st6[0]);
+    for (int i = 0; i < 5; i++) st.p[i] = RF(st6[1 + i]);
+    rreal chi2 = RF(0);
+    if (n <= 0) { rf_store(&st, chi2, -5, 1, out); return; }
+    /* outward pass */
+    for (int k = 0; k < n; k++) {
+        if (!rf_prop(c, &st, RF(cl[k][0]))) { rf_store(&st, chi2, 2 * k - 5, 1, out); return; }
+        if (k == 0) rf_init_pass(c, &st, RF(cl[k][1]), RF(cl[k][2]), &chi2);
+        else rf_update(c, &st, RF(cl[k][1]), RF(cl[k][2]), &chi2);
+    }
+    /* inward pass, from the outermost cluster */
+    for (int j = 0; j < n; j++) {
+        int k = n - 1 - j;
+        if (!rf_prop(c, &st, RF(cl[k][0]))) { rf_store(&st, chi2, 2 * j - 5, 1, out); return; }
+        if (j == 0) rf_init_pass(c, &st, RF(cl[k][1]), RF(cl[k][2]), &chi2);
+        else rf_update(c, &st, RF(cl[k][1]), RF(cl[k][2]), &chi2);
+    }
+    rf_store(&st, chi2, 2 * n - 5, 0, out);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Entry points                                                              */
+/* ------------------------------------------------------------------------ */
+
+/* Refit M tracks.  st6[M][6] start states; hit_off[M + 1] into hits; hits are
+ * positions in clusters[.][4] (x, y, z, id bits); out[M][RF_NOUT]. */
+void orc_refit_tracks(const orc_fit_params* p, int M, const double* st6, const int64_t* hit_off,
+                      const int32_t* hits, const float* clusters, double* out, int n_threads)
+{
+    rf_ctx c;
+    rf_ctx_init(&c, p);
+#ifdef _OPENMP
+    if (n_threads > 0) omp_set_num_threads(n_threads);
+#pragma omp parallel for schedule(dynamic, 64)
+#endif
+    for (int m = 0; m < M; m++) {
+        int n = (int)(hit_off[m + 1] - hit_off[m]);
+        const float* cl[512];
+        if (n > 512) n = 512;
+        for (int k = 0; k < n; k++) cl[k] = clusters + (size_t)hits[hit_off[m] + k] * 4;
+        rf_refit(&c, st6 + (size_t)m * 6, n, cl, out + (size_t)m * RF_NOUT);
+    }
+    (void)n_threads;
+}
+
+/* A fit vector for the single-step entry points: x, p[5], cov[15] (21). */
+static void rf_unpack(const double* v, rf_state* st)
+{
+    st->x = RF(v[0]);
+    for (int i = 0; i < 5; i++) st->p[i] = RF(v[1 + i]);
+    for (int i = 0, k = 0; i < 5; i++)
+        for (int j = 0; j <= i; j++, k++) { st->C[i][j] = RF(v[6 + k]); st->C[j][i] = RF(v[6 + k]); }
+}
+
+static void rf_pack(const rf_state* st, double* v)
+{
+    v[0] = (double)st->x;
+    for (int i = 0; i < 5; i++) v[1 + i] = (double)st->p[i];
+    for (int i = 0, k = 0; i < 5; i++)
+        for (int j = 0; j <= i; j++, k++) v[6 + k] = (double)st->C[i][j];
+}
+
+int orc_refit_propagate(const orc_fit_params* p, double* v, double x1)
+{
+    rf_ctx c;
+    rf_ctx_init(&c, p);
+    rf_state st;
+    rf_unpack(v, &st);
+    int ok = rf_prop(&c, &st, RF(x1));
+    rf_pack(&st, v);
+    return ok;
+}
+
+void orc_refit_update(const orc_fit_params* p, double* v, double my, double mz, double* chi2)
+{
+    rf_ctx c;
+    rf_ctx_init(&c, p);
+    rf_state st;
+    rf_unpack(v, &st);
+    rreal c2 = RF(*chi2);
+    rf_update(&c, &st, RF(my), RF(mz), &c2);
+    rf_pack(&st, v);
+    *chi2 = (double)c2;
+}
