@@ -239,17 +239,29 @@ def refit_lists(st6, hit_off, hits, clusters, fp, mode="f64", threads=0):
     return out
 
 
-def fit_vec(x, p, C5=None):
-    """21-vector of the single-step refit entries: x, p[5], packed lower C."""
-    v = np.zeros(21)
+def fit_vec(x, p, S5=None):
+    """31-vector of the single-step refit entries: x, p[5], the covariance
+    factor S (C = S S^T) row-major."""
+    v = np.zeros(31)
     v[0] = x
     v[1:6] = p
-    if C5 is not None:
-        v[6:] = [C5[i][j] for i in range(5) for j in range(i + 1)]
+    if S5 is not None:
+        v[6:] = np.asarray(S5, dtype=np.float64).reshape(25)
     return v
 
 
+def factor_of(v):
+    return v[6:31].reshape(5, 5)
+
+
+def cov_of(v):
+    """C = S S^T of a 31-vector."""
+    S5 = factor_of(v)
+    return S5 @ S5.T
+
+
 def unpack_cov(v, at=6):
+    """Symmetric 5x5 from 15 packed lower entries (a refit output row)."""
     C5 = np.zeros((5, 5))
     k = at
     for i in range(5):

@@ -67,8 +67,8 @@ def refit_double(st6, x, y, z, fp, mode="f64"):
     def init(v, k):
         v = v.copy()
         v[1], v[2] = y[k], z[k]
-        C5 = np.diag([fp.sigma_y ** 2, fp.sigma_z ** 2, fp.var_s, fp.var_t, fp.var_q])
-        v[6:] = [C5[i][j] for i in range(5) for j in range(i + 1)]
+        v[6:] = np.diag(np.sqrt([fp.sigma_y ** 2, fp.sigma_z ** 2, fp.var_s, fp.var_t,
+                                 fp.var_q])).reshape(25)
         return v
 
     chi2 = 0.0
@@ -125,9 +125,9 @@ def test_refit_propagate_follows_exact_helix(inward):
 
 @pytest.mark.parametrize("bz", [0.0, 0.5])
 def test_refit_jacobian_matches_finite_differences(bz):
-    """Every entry of the transport Jacobian: with C = e_k e_k^T the
-    transported covariance's column k is J[:, k]; compare with central
-    differences of the propagated state (uniform field)."""
+    """Every entry of the transport Jacobian: with the factor S = e_k e_k^T
+    (C = e_k e_k^T) the transported covariance's column k is J[:, k]; compare
+    with central differences of the propagated state (uniform field)."""
     rng = np.random.default_rng(22)
     fp = oracle.fit_params(bz)
     names = ["y", "z", "s", "t", "q"]
@@ -141,7 +141,7 @@ def test_refit_jacobian_matches_finite_differences(bz):
             C5[kcol, kcol] = 1.0
             ok, w = oracle.refit_propagate(oracle.fit_vec(x, p0, C5), x + d, fp)
             assert ok
-            Jk = oracle.unpack_cov(w)[:, kcol]
+            Jk = oracle.cov_of(w)[:, kcol]
             h = 1e-6 * max(1.0, abs(p0[kcol]))
             pp, pm = p0.copy(), p0.copy()
             pp[kcol] += h
@@ -191,12 +191,12 @@ def test_refit_update_equals_bayesian_posterior():
         C0 = A @ A.T + 0.05 * np.eye(5)
         p0 = rng.normal(size=5)
         m = rng.normal(size=2)
-        w, chi2 = oracle.refit_update(oracle.fit_vec(100.0, p0, C0), m[0], m[1], fp)
+        w, chi2 = oracle.refit_update(oracle.fit_vec(100.0, p0, np.linalg.cholesky(C0)), m[0], m[1], fp)
         Ci = np.linalg.inv(C0)
         Cp = np.linalg.inv(Ci + H.T @ np.linalg.inv(V) @ H)
         pp = Cp @ (Ci @ p0 + H.T @ np.linalg.inv(V) @ m)
         assert np.allclose(w[1:6], pp, rtol=1e-9, atol=1e-11)
-        assert np.allclose(oracle.unpack_cov(w), Cp, rtol=1e-8, atol=1e-11)
+        assert np.allclose(oracle.cov_of(w), Cp, rtol=1e-8, atol=1e-11)
         dp = pp - p0
         r = m - H @ pp
         obj = dp @ Ci @ dp + r @ np.linalg.inv(V) @ r
@@ -261,7 +261,7 @@ def test_refit_small_noise_is_gauss_newton(bz):
         cov = np.linalg.inv(info)
         step = cov @ (A.T @ (W * r))
         got = v[1:6] - th0
-        C5 = oracle.unpack_cov(v)
+        C5 = oracle.cov_of(v)
         nk = A.shape[1]
         scale = np.sqrt(np.diag(cov))
         # the estimate: deviations agree to 1e-3 of their own size (sigma-scaled)
@@ -313,7 +313,7 @@ def test_refit_pulls_and_chi2_on_smeared_tracks():
         y = c["y"] + S.SIGMA * rng.normal(size=len(xs))
         z = c["z"] + S.SIGMA * rng.normal(size=len(xs))
         v, chi2 = refit_double(truth, xs, y, z, fp)
-        C5 = oracle.unpack_cov(v)
+        C5 = oracle.cov_of(v)
         pulls.append((v[1:6] - truth[1:]) / np.sqrt(np.diag(C5)))
         chi.append(chi2 / (2 * len(xs) - 5))
     pulls = np.array(pulls)
@@ -411,7 +411,15 @@ def test_refit_tracks_equals_step_sequence():
         s[0] = np.float32(s[0])
         st6.append(s)
         v, chi2 = refit_double(s, xs.astype(np.float64), y.astype(np.float64), z.astype(np.float64), fp)
-        ref.append(np.concatenate([v, [chi2, 2 * len(xs) - 5, 0]]))
+        F = oracle.factor_of(v)
+        packed = []
+        for i in range(5):
+            for j in range(i + 1):
+                acc = F[i, 0] * F[j, 0]
+                for m_ in range(1, 5):
+                    acc = acc + F[i, m_] * F[j, m_]
+                packed.append(acc)
+        ref.append(np.concatenate([v[:6], packed, [chi2, 2 * len(xs) - 5, 0]]))
     out = oracle.refit_lists(np.array(st6), np.array(off), np.arange(off[-1]), np.array(cl, np.float32), fp)
     np.testing.assert_array_equal(out, np.array(ref))
 
