@@ -119,6 +119,16 @@ typedef struct {
                                 0 unit by unit (canonical order; keeps the
                                 working set of a few sectors in L2), 1 by start
                                 row across all units (longest expected first)  */
+    /* final track fit (Sec. 2 "Track fit", Table 1 row 4) */
+    int refit;               /* 1: refit every selected track with the full
+                                Kalman filter after selection (tpc_fit output);
+                                0: no refit (default)                           */
+    float field[5];          /* the field of the refit as a polynomial
+                                (Sec. 2: avoids field-map reads):
+                                Bz(rho, z) = bz + z (b1 + z b2)
+                                           + rho^2 (b3 + z (b4 + z b5)),
+                                rho^2 = x^2 + y^2, field = {b1..b5} in T/cm^n;
+                                all zero (default): the uniform field bz       */
 } tpc_params;
 
 /* A selected track: the best tracklet instance (Sec. 2 step 2), with the
@@ -136,9 +146,28 @@ typedef struct {
     int32_t hit_off;         /* first entry of this track in hit_ids            */
 } tpc_track;
 
-/* Output buffers, caller-owned.  mem_kind says where tracks and hit_ids
- * live.  hit_ids are positions in the call's cluster array, rows ascending
- * within a track; tracks are in canonical tracklet order. */
+/* The full Kalman filter refit of a selected track (Sec. 2 "Track fit",
+ * Table 1 row 4): state, full covariance and chi2 of the inward pass at the
+ * track's innermost cluster.  Two passes over the track's clusters, each on
+ * its own x: outward from the tracklet state, then inward from the
+ * outermost cluster; each pass starts at its first cluster with y, z set to
+ * the measurement and the covariance reset to diag(sigma_y^2, sigma_z^2,
+ * var_s, var_t, var_q).  Exact helix steps in the polynomial field held at
+ * each step's midpoint, full 5x5 Jacobian transport, 2-D (y, z) update. */
+typedef struct {
+    float x;                 /* plane of the innermost cluster                  */
+    float p[5];              /* y, z, sin(phi), tan(lambda), q/pT               */
+    float cov[15];           /* C[i][j], i >= j, at i (i + 1) / 2 + j, in the
+                                order of p                                      */
+    float chi2;
+    int32_t ndf;             /* 2 * clusters - 5 (of the failing pass if any)   */
+    int32_t status;          /* 0 ok; 1 |sin phi| > s_max on a step: the state
+                                reached is kept                                 */
+} tpc_fit;
+
+/* Output buffers, caller-owned.  mem_kind says where tracks, hit_ids and
+ * fits live.  hit_ids are positions in the call's cluster array, rows
+ * ascending within a track; tracks are in canonical tracklet order. */
 typedef struct {
     tpc_track* tracks;
     int32_t* hit_ids;
@@ -147,6 +176,9 @@ typedef struct {
     int32_t mem_kind;        /* TPC_MEM_HOST or TPC_MEM_DEVICE                  */
     int32_t n_tracks;        /* written: tracks found (required capacity)       */
     int32_t n_hits;          /* written: hit ids found (required capacity)      */
+    tpc_fit* fits;           /* optional, [cap_tracks]: fits[m] is the refit of
+                                tracks[m]; written only when params.refit = 1
+                                (NULL: not copied)                              */
 } tpc_output;
 
 typedef struct tpc_tracker tpc_tracker;
@@ -262,7 +294,8 @@ int tpc_debug_dump(tpc_tracker* tr, int what, void* dst, int64_t cap, int64_t* n
 /* Device time of each stage of the last call, in milliseconds, measured
  * with CUDA events on the launching stream: [0] grid build, [1] neighbours,
  * [2] clean + start hits, [3] tracklet construction, [4] selection + output,
- * [5] whole call.  n = entries wanted (<= 6). */
+ * [5] whole call, [6] final refit (0 when params.refit = 0).  n = entries
+ * wanted (<= 7). */
 int tpc_stage_times(tpc_tracker* tr, float* ms, int n);
 
 /* One-line description of the last error on tr (or of the last failed

@@ -28,6 +28,9 @@ UNITS = [
     ("k_fp.cu", "k_fp_exact.o", ["-fmad=false", "-DTPC_FP_NS=tpc_exact"]),
     ("k_fp.cu", "k_fp_fast.o", ["-fmad=true", "-prec-div=false", "-prec-sqrt=false", "-ftz=true",
                                 "-DTPC_FP_NS=tpc_fast", "-DTPC_FAST_MATH=1"]),
+    ("k_refit.cu", "k_refit_exact.o", ["-fmad=false", "-DTPC_FP_NS=tpc_exact"]),
+    ("k_refit.cu", "k_refit_fast.o", ["-fmad=true", "-prec-div=false", "-prec-sqrt=false", "-ftz=true",
+                                      "-DTPC_FP_NS=tpc_fast", "-DTPC_FAST_MATH=1"]),
     ("tracker.cu", "tracker.o", []),
     ("serve.cu", "serve.o", []),
     ("noalloc.cu", "noalloc.o", []),

@@ -56,7 +56,7 @@ class tpc_params(C.Structure):
                 ("exact_fp32", C.c_int), ("bin_target", C.c_float),
                 ("threads_per_row", C.c_int), ("tracklets_per_warp", C.c_int),
                 ("plain_per_sector", C.c_int), ("use_graph", C.c_int), ("n_queues", C.c_int),
-                ("schedule", C.c_int)]
+                ("schedule", C.c_int), ("refit", C.c_int), ("field", C.c_float * 5)]
 
 
 class tpc_track(C.Structure):
@@ -66,10 +66,15 @@ class tpc_track(C.Structure):
                 ("nhits", C.c_int32), ("hit_off", C.c_int32)]
 
 
+class tpc_fit(C.Structure):
+    _fields_ = [("x", C.c_float), ("p", C.c_float * 5), ("cov", C.c_float * 15),
+                ("chi2", C.c_float), ("ndf", C.c_int32), ("status", C.c_int32)]
+
+
 class tpc_output(C.Structure):
     _fields_ = [("tracks", C.c_void_p), ("hit_ids", C.c_void_p), ("cap_tracks", C.c_int32),
                 ("cap_hits", C.c_int32), ("mem_kind", C.c_int32), ("n_tracks", C.c_int32),
-                ("n_hits", C.c_int32)]
+                ("n_hits", C.c_int32), ("fits", C.c_void_p)]
 
 
 _LIB = None

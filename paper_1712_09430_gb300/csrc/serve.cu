@@ -58,7 +58,8 @@ struct Batch {
     int* counters = nullptr;            // [kNumCounters]
     tpc_track* tracks = nullptr;
     int* hits = nullptr;
-    size_t tracks_cap = 0, hits_cap = 0;
+    tpc_fit* fits = nullptr;            // with params.refit
+    size_t tracks_cap = 0, hits_cap = 0, fits_cap = 0;
     int est_tracks = 0, est_hits = 0;   // what the D2H enqueued
     int open_results = 0;               // requests of the batch not yet polled
 };
@@ -261,6 +262,10 @@ static int launch_batch(tpc_tracker* tr)
             grow_pinned(tr, reinterpret_cast<void**>(&b->hits), &b->hits_cap,
                         sizeof(int) * (size_t)b->est_hits) != TPC_OK)
             return TPC_ERR_NOMEM;
+        if (tr->params.refit &&
+            grow_pinned(tr, reinterpret_cast<void**>(&b->fits), &b->fits_cap,
+                        sizeof(tpc_fit) * (size_t)b->est_tracks) != TPC_OK)
+            return TPC_ERR_NOMEM;
         e = cudaMemcpyAsync(b->counters, p.counters, sizeof(int) * kNumCounters, cudaMemcpyDeviceToHost, s);
         // first canonical tracklet id of every event: start_off at each event's first row
         const size_t ev_rows = (size_t)NS * NR;
@@ -272,6 +277,9 @@ static int launch_batch(tpc_tracker* tr)
                                 cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(b->hits, p.out_hits, sizeof(int) * (size_t)b->est_hits,
+                                cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess && tr->params.refit)
+            e = cudaMemcpyAsync(b->fits, p.out_fits, sizeof(tpc_fit) * (size_t)b->est_tracks,
                                 cudaMemcpyDeviceToHost, s);
     } else {
         std::memset(b->counters, 0, sizeof(int) * kNumCounters);
@@ -312,6 +320,19 @@ static void finish_batch(tpc_tracker* tr, Batch& b)
                     cudaSuccess ||
                 cudaMemcpy(b.hits, b.p.out_hits, sizeof(int) * (size_t)MH, cudaMemcpyDeviceToHost) != cudaSuccess)
                 err = TPC_ERR_DEVICE;
+            if (err == TPC_OK && tr->params.refit) {
+                void* fp = b.fits;
+                size_t fc = b.fits_cap;
+                if (grow_pinned(tr, &fp, &fc, sizeof(tpc_fit) * (size_t)M) != TPC_OK) {
+                    err = TPC_ERR_NOMEM;
+                } else {
+                    b.fits = static_cast<tpc_fit*>(fp);
+                    b.fits_cap = fc;
+                    if (cudaMemcpy(b.fits, b.p.out_fits, sizeof(tpc_fit) * (size_t)M, cudaMemcpyDeviceToHost) !=
+                        cudaSuccess)
+                        err = TPC_ERR_DEVICE;
+                }
+            }
         }
     }
     if (b.sh.N > 0) {  // adapt the estimate to what central/min-bias events produce
@@ -375,6 +396,7 @@ void tpc_serve_shutdown(tpc_tracker* tr)
         cudaFreeHost(b.counters);
         cudaFreeHost(b.tracks);
         cudaFreeHost(b.hits);
+        cudaFreeHost(b.fits);
     }
     cudaFree(S->arena_base);
     cudaFreeHost(S->pin);
@@ -480,6 +502,8 @@ extern "C" int tpc_stream_poll(tpc_tracker* tr, uint64_t ticket, tpc_output* out
                     out->tracks[m] = t;
                 }
                 for (int h = 0; h < MH; h++) out->hit_ids[h] = b.hits[r.h0 + h] - r.cl0;
+                if (out->fits && tr->params.refit)
+                    for (int m = 0; m < M; m++) out->fits[m] = b.fits[r.m0 + m];
             }
             S->reserved -= r.reserve;
             S->req.erase(it);

@@ -30,6 +30,7 @@ enum {
     C_M = 3,        // accepted tracks
     C_MH = 4,       // hits of accepted tracks
     C_BADROW = 5,   // first row index with invalid input (+1), 0 = none
+    C_FIT = 6,      // persistent refit kernel work counter
 };
 enum { E_INPUT = 1, E_TIMEOUT = 2, E_TOO_DENSE = 4 };
 
@@ -40,6 +41,8 @@ struct KConst {
     float sy2, sz2, var_s, var_q, var_t;
     float n_sigma, w_min, w_max, s_max, y_margin;
     float kB;            // (float)(-kappa * Bz) rounded once from double
+    float kP;            // (float)(-kappa): curvature per tesla of the field polynomial
+    float fb[5];         // field polynomial terms b1..b5 of the refit
     float tan_h, z_max;
     float bin_target;
     int l_seed, g_max, n_min_tracklet, n_min_track, own_num, own_den;
@@ -92,6 +95,7 @@ struct DevPtrs {
     int* start_part;           // [2 * (ceil(R / kScanTile) + 1)] tile sums of the start scans
     tpc_track* out_tracks;     // [Mcap]
     int* out_hits;             // [MHcap]
+    tpc_fit* out_fits;         // [Mcap] refit of each track
     int* counters;             // [kNumCounters]
     int N, R, n_units, t_cap, m_cap, mh_cap;
 };
@@ -233,7 +237,8 @@ cudaError_t launch_dump_tl_work(const tpc::DevPtrs& p, int T, int* dst, cudaStre
                                  const tpc::DevPtrs& p, int n_sm, int lanes_per_tracklet,         \
                                  int schedule, int t_first_unit, int t_last_unit, cudaStream_t s); \
     cudaError_t launch_seeds(const tpc::KConst& k, const float* row_x_dev, const tpc::DevPtrs& p,   \
-                             int n_sm, int u0, int u1, cudaStream_t s);
+                             int n_sm, int u0, int u1, cudaStream_t s);                             \
+    cudaError_t launch_refit(const tpc::KConst& k, const tpc::DevPtrs& p, int n_sm, cudaStream_t s);
 
 namespace tpc_exact { TPC_FP_DECLS }
 namespace tpc_fast { TPC_FP_DECLS }

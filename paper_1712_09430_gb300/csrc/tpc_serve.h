@@ -42,7 +42,7 @@ struct tpc_tracker {
     size_t plan_cap = 0;           // ints
     std::vector<int> slots_lut;    // bin-table slots per row count (current bin_target)
     float slots_lut_bt = 0.0f;
-    cudaEvent_t ev[6] = {};
+    cudaEvent_t ev[7] = {};
     // graph replay of the batched stages
     cudaGraphExec_t graph_exec = nullptr;
     std::string graph_key;

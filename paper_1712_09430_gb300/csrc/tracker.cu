@@ -55,6 +55,8 @@ static KConst make_kconst(const tpc_params& P, const tpc_geometry& G, double bz)
     k.s_max = P.s_max;
     k.y_margin = P.y_margin;
     k.kB = (float)(-0.00299792458 * bz);
+    k.kP = (float)(-0.00299792458);
+    for (int i = 0; i < 5; i++) k.fb[i] = P.field[i];
     k.tan_h = G.tan_half_open;
     k.z_max = G.z_max;
     k.bin_target = P.bin_target;
@@ -86,6 +88,9 @@ static const char* check_params(const tpc_params& P)
     if (P.schedule != 0 && P.schedule != 1) return "schedule must be 0 or 1";
     if (P.plain_per_sector < 0 || P.plain_per_sector > 2) return "plain_per_sector must be 0, 1 or 2";
     if (P.n_queues < 1 || P.n_queues > 64) return "n_queues must be in [1, 64]";
+    if (P.refit != 0 && P.refit != 1) return "refit must be 0 or 1";
+    for (int i = 0; i < 5; i++)
+        if (!std::isfinite(P.field[i])) return "field terms must be finite";
     return nullptr;
 }
 
@@ -262,6 +267,7 @@ size_t tpc_layout(const tpc_tracker* tr, const BatchShape& sh, DevPtrs* p, char*
     q.start_part = reinterpret_cast<int*>(take((R / kScanTile + 2) * 2 * 4));
     q.out_tracks = reinterpret_cast<tpc_track*>(take(Tc * sizeof(tpc_track)));
     q.out_hits = reinterpret_cast<int*>(take(N * 4));
+    q.out_fits = reinterpret_cast<tpc_fit*>(take(Tc * sizeof(tpc_fit)));
     q.counters = reinterpret_cast<int*>(take(kNumCounters * 4));
     q.N = sh.N;
     q.R = sh.R;
@@ -495,6 +501,9 @@ int tpc_enqueue(tpc_tracker* tr, const DevPtrs& p, const BatchShape& sh, cudaStr
     }
     TPC_CUDA(tpc_int::launch_emit(k, p, tr->n_sm, s));
     if (with_events) TPC_CUDA(cudaEventRecord(tr->ev[5], s));
+    if (P.refit)
+        TPC_CUDA(exact ? tpc_exact::launch_refit(k, p, tr->n_sm, s) : tpc_fast::launch_refit(k, p, tr->n_sm, s));
+    if (with_events) TPC_CUDA(cudaEventRecord(tr->ev[6], s));
 #undef cudaEventRecord
     return TPC_OK;
 }
@@ -583,6 +592,8 @@ int tpc_copy_out(tpc_tracker* tr, const DevPtrs& p, int M, int MH, tpc_output* o
         if (!out->hit_ids) return tr->fail(TPC_ERR_INVALID, "NULL hit_ids buffer");
         TPC_CUDA(cudaMemcpyAsync(out->hit_ids, p.out_hits, sizeof(int) * mh, kind, s));
     }
+    if (mt > 0 && out->fits && tr->params.refit)
+        TPC_CUDA(cudaMemcpyAsync(out->fits, p.out_fits, sizeof(tpc_fit) * mt, kind, s));
     TPC_CUDA(cudaStreamSynchronize(s));
     if (mt < M || mh < MH) return tr->fail(TPC_ERR_OUTPUT_TRUNCATED, "output capacity too small");
     return TPC_OK;
@@ -648,9 +659,9 @@ extern "C" int tpc_stage_times(tpc_tracker* tr, float* ms, int n)
 {
     if (!tr || !ms) return TPC_ERR_INVALID;
     if (!tr->has_result) return tr->fail(TPC_ERR_INVALID, "no result");
-    for (int i = 0; i < n && i < 6; i++) {
+    for (int i = 0; i < n && i < 7; i++) {
         float v = 0.0f;
-        int a = i < 5 ? i : 0, b = i < 5 ? i + 1 : 5;
+        int a = i < 5 ? i : (i == 5 ? 0 : 5), b = i < 5 ? i + 1 : 6;
         if (cudaEventElapsedTime(&v, tr->ev[a], tr->ev[b]) != cudaSuccess) {
             cudaGetLastError();
             v = -1.0f;

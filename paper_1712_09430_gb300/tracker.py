@@ -17,6 +17,9 @@ TRACK_DTYPE = np.dtype([("event", np.int32), ("sector", np.int32), ("tracklet", 
                         ("cov_z", np.float32, 3), ("chi2", np.float32), ("ndf", np.int32),
                         ("nhits", np.int32), ("hit_off", np.int32)])
 assert TRACK_DTYPE.itemsize == C.sizeof(capi.tpc_track)
+FIT_DTYPE = np.dtype([("x", np.float32), ("p", np.float32, 5), ("cov", np.float32, 15),
+                      ("chi2", np.float32), ("ndf", np.int32), ("status", np.int32)])
+assert FIT_DTYPE.itemsize == C.sizeof(capi.tpc_fit)
 
 
 class TrackerError(RuntimeError):
@@ -25,11 +28,17 @@ class TrackerError(RuntimeError):
         self.code = code
 
 
+def _set(p, k, v):
+    if k == "field":
+        v = (C.c_float * 5)(*[float(x) for x in v])
+    setattr(p, k, v)
+
+
 def default_params(**over) -> capi.tpc_params:
     p = capi.tpc_params()
     lib().tpc_params_default(C.byref(p))
     for k, v in over.items():
-        setattr(p, k, v)
+        _set(p, k, v)
     return p
 
 
@@ -42,11 +51,13 @@ def _ptr(a):
 
 
 class Result:
-    """Tracks (structured numpy array, TRACK_DTYPE) and their hit ids."""
+    """Tracks (structured numpy array, TRACK_DTYPE), their hit ids and, with
+    params.refit, the full Kalman filter refit of each track (FIT_DTYPE)."""
 
-    def __init__(self, tracks, hit_ids):
+    def __init__(self, tracks, hit_ids, fits=None):
         self.tracks = tracks
         self.hit_ids = hit_ids
+        self.fits = fits
 
     def hits_of(self, m):
         t = self.tracks[m]
@@ -112,7 +123,7 @@ class Tracker:
         p = capi.tpc_params()
         C.memmove(C.byref(p), C.byref(self.params), C.sizeof(p))
         for k, v in over.items():
-            setattr(p, k, v)
+            _set(p, k, v)
         self.check(lib().tpc_tracker_set_params(self.h, C.byref(p)))
         self.params = p
 
@@ -127,9 +138,12 @@ class Tracker:
         fixed = cap_tracks is not None or cap_hits is not None
         ct = cap_tracks if cap_tracks is not None else self._est_tracks
         ch = cap_hits if cap_hits is not None else self._est_hits
+        refit = bool(self.params.refit)
         tracks = np.zeros(max(ct, 1), TRACK_DTYPE)
         hits = np.zeros(max(ch, 1), np.int32)
-        out = capi.tpc_output(tracks.ctypes.data, hits.ctypes.data, ct, ch, capi.TPC_MEM_HOST, 0, 0)
+        fits = np.zeros(max(ct, 1), FIT_DTYPE) if refit else None
+        out = capi.tpc_output(tracks.ctypes.data, hits.ctypes.data, ct, ch, capi.TPC_MEM_HOST, 0, 0,
+                              fits.ctypes.data if refit else None)
         rc = lib().tpc_track_sectors(self.h, _ptr(clusters), _ptr(rc_arr), int(n_events), kind,
                                      C.byref(out), stream)
         if rc == capi.TPC_ERR_OUTPUT_TRUNCATED and not fixed:
@@ -138,11 +152,13 @@ class Tracker:
             self._est_tracks, self._est_hits = int(ct * 1.25) + 16, int(ch * 1.25) + 256
             tracks = np.zeros(ct, TRACK_DTYPE)
             hits = np.zeros(ch, np.int32)
+            fits = np.zeros(ct, FIT_DTYPE) if refit else None
             out = capi.tpc_output(tracks.ctypes.data, hits.ctypes.data, ct, ch, capi.TPC_MEM_HOST,
-                                  0, 0)
+                                  0, 0, fits.ctypes.data if refit else None)
             rc = lib().tpc_fetch_output(self.h, C.byref(out))
         self.check(rc)
-        return Result(tracks[:out.n_tracks], hits[:out.n_hits])
+        return Result(tracks[:out.n_tracks], hits[:out.n_hits],
+                      fits[:out.n_tracks] if refit else None)
 
     # ---- serving (continuous batching) -----------------------------------
     def stream_configure(self, arena_bytes=0, max_batch_events=64, max_inflight=2, no_copy=False):
@@ -172,16 +188,20 @@ class Tracker:
         rc = lib().tpc_stream_poll(self.h, int(ticket), C.byref(out), int(timeout_us))
         if rc == capi.TPC_PENDING:
             return None
+        refit = bool(self.params.refit)
         if rc == capi.TPC_OK:       # an empty result
-            return Result(np.zeros(0, TRACK_DTYPE), np.zeros(0, np.int32))
+            return Result(np.zeros(0, TRACK_DTYPE), np.zeros(0, np.int32),
+                          np.zeros(0, FIT_DTYPE) if refit else None)
         if rc != capi.TPC_ERR_OUTPUT_TRUNCATED:
             self.check(rc)
         tracks = np.empty(max(out.n_tracks, 1), TRACK_DTYPE)
         hits = np.empty(max(out.n_hits, 1), np.int32)
+        fits = np.empty(max(out.n_tracks, 1), FIT_DTYPE) if refit else None
         out = capi.tpc_output(tracks.ctypes.data, hits.ctypes.data, len(tracks), len(hits),
-                              capi.TPC_MEM_HOST, 0, 0)
+                              capi.TPC_MEM_HOST, 0, 0, fits.ctypes.data if refit else None)
         self.check(lib().tpc_stream_poll(self.h, int(ticket), C.byref(out), 0))
-        return Result(tracks[:out.n_tracks], hits[:out.n_hits])
+        return Result(tracks[:out.n_tracks], hits[:out.n_hits],
+                      fits[:out.n_tracks] if refit else None)
 
     def dump(self, what):
         n = C.c_int64()
@@ -204,6 +224,8 @@ class Tracker:
         return a
 
     def stage_times(self):
-        ms = (C.c_float * 6)()
-        self.check(lib().tpc_stage_times(self.h, ms, 6))
+        """ms of: grid, neighbours, clean + start hits, tracklets, selection +
+        output, whole call, final refit."""
+        ms = (C.c_float * 7)()
+        self.check(lib().tpc_stage_times(self.h, ms, 7))
         return list(ms)
