@@ -261,7 +261,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     ev_s = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ev_e = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    stage = np.zeros(6)
+    stage = np.zeros(7)
     t0 = time.perf_counter()
     for i in range(args.steps):
         ev_s[i].record(stream)
@@ -291,6 +291,9 @@ def run_ours(args):
     stream_res = None
     if args.stream_rates:
         stream_res = [run_stream(tr, mb_pool, args, rate) for rate in args.stream_rates]
+    refit = None
+    if args.refit_steps > 0:
+        refit = run_refit(L, tr, dev_cl, rc_ptr, B, sp, out, out_tr, args)
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -337,7 +340,8 @@ def run_ours(args):
             "stage_ms": stage_ms, "wall_s": wall,
             "gpu_launches": LAUNCHES_PER_STEP * args.steps,
             "clocks": ck, "e2e": e2e, "roofline": rl, "cpu_baseline": cpu,
-            "plain_per_sector": plain, "multi_queue_per_sector": multi, "stream": stream_res}
+            "plain_per_sector": plain, "multi_queue_per_sector": multi, "stream": stream_res,
+            "refit": refit}
     if stream_res:
         line["latency_ms"] = {"p50": stream_res[0]["p50_ms"], "p99": stream_res[0]["p99_ms"],
                               "rate_hz": stream_res[0]["rate_hz"]}
@@ -345,6 +349,61 @@ def run_ours(args):
     tr.close()
     if dist:
         dist.destroy_process_group()
+
+
+# Algorithmic FP32 operations of one refit step (k_refit.cu; a division or a
+# square root counts as one): the helix step with its midpoint field and
+# Jacobian (85) plus the square-root transport S <- J S (60), and two scalar
+# Potter updates of 129 each.
+REFIT_FLOPS_PROPAGATE = 145
+REFIT_FLOPS_UPDATE = 258
+FP32_LANES_PER_SM = 128  # Blackwell SM: 4 x 32 FP32 lanes, one FMA (2 flops) per lane per clock
+
+
+def run_refit(L, tr, dev_cl, rc_ptr, B, sp, out, out_tr, args):
+    """The final full Kalman filter refit (Sec. 2 "Track fit") over the same
+    batch: the batched step with params.refit = 1, the refit stage timed by
+    its own CUDA events (stage 6).  Roofline: FP32 ALU (the refit does ~20
+    flops per byte it moves)."""
+    import ctypes as C
+    import torch
+    from paper_1712_09430_gb300 import capi
+    from paper_1712_09430_gb300.tracker import TRACK_DTYPE
+    tr.set_params(refit=1)
+
+    def step():
+        r = L.tpc_track_sectors(tr.h, C.c_void_p(dev_cl.data_ptr()), rc_ptr, B,
+                                capi.TPC_MEM_DEVICE, C.byref(out), sp)
+        if r != capi.TPC_OK:
+            raise RuntimeError(f"tpc_track_sectors: {capi.STATUS_NAMES.get(r)}: {tr.error()}")
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(args.refit_steps):
+        step()
+        ms.append(tr.stage_times()[6])
+    torch.cuda.synchronize()
+    tr.set_params(refit=0)
+    M = out.n_tracks
+    tracks = out_tr[:M * TRACK_DTYPE.itemsize].cpu().numpy().view(TRACK_DTYPE)
+    n = tracks["nhits"].astype(np.int64)
+    steps = int(np.sum(2 * (n - 1)))
+    flops = float(steps) * (REFIT_FLOPS_PROPAGATE + REFIT_FLOPS_UPDATE)
+    t = statistics.median(ms) * 1e-3
+    props = torch.cuda.get_device_properties(dev_cl.device)
+    peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * 2.07e9 / 1e12
+    achieved = flops / t / 1e12
+    return {"ms": t * 1e3, "tracks": int(M), "filter_steps": steps,
+            "tracks_per_s": M / t, "clusters_per_s": float(n.sum()) / t,
+            "mode": "exact" if args.exact else "production",
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None, "kernel": "k_refit",
+                         "algorithmic_flops_per_launch": flops,
+                         "model": f"2*(n-1) steps per track x ({REFIT_FLOPS_PROPAGATE} propagate + "
+                                  f"{REFIT_FLOPS_UPDATE} update) FP32 ops",
+                         "peak_source": f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 "
+                                        "lanes x 2 flops (FMA) x 2.07 GHz max SM clock (derived)"}}
 
 
 def run_plain(L, tr, dev_cl, rc_ptr, B, N, world, sp, out, args, mode=1):
@@ -538,6 +597,8 @@ def main():
                     default=[1000.0, 3000.0, 5000.0],
                     help="Poisson arrival rates (Hz) of the serving leg, comma separated; '' = off")
     ap.add_argument("--stream-seconds", type=float, default=2.0)
+    ap.add_argument("--refit-steps", type=int, default=10,
+                    help="steps of the final-refit leg (0: skip)")
     ap.add_argument("--stream-batch", type=int, default=64, help="most events per serving batch")
     ap.add_argument("--stream-arena-gb", type=int, default=16)
     ap.add_argument("--pool", type=int, default=96, help="min-bias events in the serving pool")

@@ -43,7 +43,7 @@ using namespace tpc;
 namespace {
 
 constexpr int kRefitThreads = 128;
-constexpr int kRefitCtasPerSm = 4;
+constexpr int kRefitCtasPerSm = 6;  // 80 registers: 6 x 128 threads fit the register file
 
 // State, covariance factor S (row-major, C = S S^T) and chi2 of one track.
 struct Fit {
@@ -217,18 +217,28 @@ __device__ __forceinline__ void fit_store(tpc_fit* dst, const Fit& f, int ndf, i
 
 }  // namespace
 
-// Persistent refit: one track per lane.  A lane's track m runs 2 n steps:
-// j = 0..n-1 of pass 0 (clusters ascending), then of pass 1 (descending).
+// Persistent refit: one track per lane.  A lane's track m runs 2 n steps
+// g = 0 .. 2n-1 on cluster idx(g) = g (pass 0, ascending) or 2n-1-g (pass 1,
+// descending); steps 0 and n start a pass.  The cluster of step g + 1 and
+// the hit id of step g + 2 are loaded while step g computes.
+__device__ __forceinline__ int fit_idx(int g, int n) { return g < n ? g : 2 * n - 1 - g; }
+
 __global__ void __launch_bounds__(kRefitThreads, kRefitCtasPerSm) k_refit(KConst k, DevPtrs p)
 {
     const unsigned FULL = 0xffffffffu;
-    const int M = p.counters[C_M];
+    const int M = p.counters[C_FIT_M];
     const int lane = threadIdx.x & 31;
-    int m = -1, n = 0, off = 0, j = 0, pass = 0;
+    int m = -1, n = 0, off = 0, g = 0;
     bool done = false;
     Fit f;
-    float4 cl = make_float4(0.f, 0.f, 0.f, 0.f);
-    while (true) {
+    // Two register sets for the in-flight loads, used alternately by the two
+    // halves of the loop body, so no register copy waits on a load.
+    float4 clA = make_float4(0.f, 0.f, 0.f, 0.f), clB = clA;
+    int hA = 0, hB = 0;
+    // One step: take the next track if idle, then filter cluster idx(g) held
+    // in c (h1 holds the hit id of step g + 1); loads cn and h2 for the steps
+    // after.  Returns false once every lane of the warp is done.
+    auto half = [&](float4& c, float4& cn, int& h1, int& h2) -> bool {
         const unsigned need = __ballot_sync(FULL, m < 0 && !done);
         if (need) {
             const int leader = __ffs(need) - 1;
@@ -238,9 +248,9 @@ __global__ void __launch_bounds__(kRefitThreads, kRefitCtasPerSm) k_refit(KConst
             if (m < 0 && !done) {
                 const int i = base + __popc(need & ((1u << lane) - 1u));
                 if (i < M) {
-                    const int* tw = reinterpret_cast<const int*>(p.out_tracks + i);
+                    m = p.sched[i];  // tracks by decreasing cluster count
+                    const int* tw = reinterpret_cast<const int*>(p.out_tracks + m);
                     const float* tf = reinterpret_cast<const float*>(tw);
-                    m = i;
                     n = tw[20];
                     off = tw[21];
                     f.x = tf[3];
@@ -249,45 +259,92 @@ __global__ void __launch_bounds__(kRefitThreads, kRefitCtasPerSm) k_refit(KConst
                     f.chi2 = 0.0f;
 #pragma unroll
                     for (int q = 0; q < 25; q++) f.S[q] = 0.0f;
-                    j = 0;
-                    pass = 0;
+                    g = 0;
                     if (n <= 0) {
                         fit_store(p.out_fits + m, f, -5, 1);
                         m = -1;
                     } else {
-                        cl = p.clusters[p.out_hits[off]];
+                        c = p.clusters[p.out_hits[off]];
+                        h1 = p.out_hits[off + fit_idx(1, n)];
                     }
                 } else {
                     done = true;
                 }
             }
         }
-        if (__all_sync(FULL, done)) break;
-        if (m < 0) continue;
-        if (!fit_propagate(f, cl.x, k)) {
+        if (__all_sync(FULL, done)) return false;
+        if (m < 0) return true;
+        const int n2 = 2 * n;
+        if (g + 1 < n2) cn = p.clusters[h1];
+        if (g + 2 < n2) h2 = p.out_hits[off + fit_idx(g + 2, n)];
+        const int j = g < n ? g : g - n;  // step within the pass
+        if (!fit_propagate(f, c.x, k)) {
             fit_store(p.out_fits + m, f, 2 * j - 5, 1);
             m = -1;
-            continue;
+            return true;
         }
-        if (j == 0) fit_init_pass(f, cl.y, cl.z, k);
-        else fit_update(f, cl.y, cl.z, k);
-        j++;
-        if (j == n) {
-            if (pass == 1) {
-                fit_store(p.out_fits + m, f, 2 * n - 5, 0);
-                m = -1;
-                continue;
-            }
-            pass = 1;
-            j = 0;
+        if (j == 0) fit_init_pass(f, c.y, c.z, k);
+        else fit_update(f, c.y, c.z, k);
+        if (++g == n2) {
+            fit_store(p.out_fits + m, f, n2 - 5, 0);
+            m = -1;
         }
-        const int idx = pass == 0 ? j : n - 1 - j;
-        cl = p.clusters[p.out_hits[off + idx]];
+        return true;
+    };
+    while (half(clA, clB, hA, hB) && half(clB, clA, hB, hA)) {
+    }
+}
+
+// Longest tracks first (the persistent kernel then ends with short ones):
+// counting sort of the tracks by cluster count, descending, into sched (the
+// tracklet schedule, free once the tracklets are built).
+// bins[0 .. kFitBins) counts, bins[kFitBins .. 2 kFitBins) running offsets.
+constexpr int kFitBins = TPC_MAX_ROWS + 1;
+
+__global__ void k_fit_hist(DevPtrs p, int* bins)
+{
+    __shared__ int h[kFitBins];
+    for (int i = threadIdx.x; i < kFitBins; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    const int M = p.counters[C_M];
+    for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < M; m += gridDim.x * blockDim.x) {
+        const int n = min(max(p.out_tracks[m].nhits, 0), kFitBins - 1);
+        atomicAdd(&h[n], 1);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kFitBins; i += blockDim.x)
+        if (h[i]) atomicAdd(&bins[i], h[i]);
+}
+
+__global__ void k_fit_offsets(DevPtrs p, int* bins)
+{
+    if (threadIdx.x == 0) {
+        int acc = 0;
+        for (int n = kFitBins - 1; n >= 0; n--) {
+            bins[kFitBins + n] = acc;
+            acc += bins[n];
+        }
+        p.counters[C_FIT_M] = acc;  // tracks to refit
+    }
+}
+
+__global__ void k_fit_scatter(DevPtrs p, int* bins)
+{
+    const int M = p.counters[C_M];
+    for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < M; m += gridDim.x * blockDim.x) {
+        const int n = min(max(p.out_tracks[m].nhits, 0), kFitBins - 1);
+        p.sched[atomicAdd(&bins[kFitBins + n], 1)] = m;
     }
 }
 
 cudaError_t launch_refit(const KConst& k, const DevPtrs& p, int n_sm, cudaStream_t s)
 {
+    int* bins = p.fit_bins;
+    cudaError_t e = cudaMemsetAsync(bins, 0, sizeof(int) * kFitBins, s);
+    if (e != cudaSuccess) return e;
+    k_fit_hist<<<n_sm, 256, 0, s>>>(p, bins);
+    k_fit_offsets<<<1, 32, 0, s>>>(p, bins);
+    k_fit_scatter<<<n_sm * 2, 256, 0, s>>>(p, bins);
     k_refit<<<n_sm * kRefitCtasPerSm, kRefitThreads, 0, s>>>(k, p);
     return cudaGetLastError();
 }

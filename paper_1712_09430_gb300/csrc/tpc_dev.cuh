@@ -31,6 +31,7 @@ enum {
     C_MH = 4,       // hits of accepted tracks
     C_BADROW = 5,   // first row index with invalid input (+1), 0 = none
     C_FIT = 6,      // persistent refit kernel work counter
+    C_FIT_M = 7,    // tracks in the refit schedule
 };
 enum { E_INPUT = 1, E_TIMEOUT = 2, E_TOO_DENSE = 4 };
 
@@ -96,6 +97,7 @@ struct DevPtrs {
     tpc_track* out_tracks;     // [Mcap]
     int* out_hits;             // [MHcap]
     tpc_fit* out_fits;         // [Mcap] refit of each track
+    int* fit_bins;             // [2 * (TPC_MAX_ROWS + 1)] refit order: counts, offsets
     int* counters;             // [kNumCounters]
     int N, R, n_units, t_cap, m_cap, mh_cap;
 };

@@ -268,6 +268,7 @@ size_t tpc_layout(const tpc_tracker* tr, const BatchShape& sh, DevPtrs* p, char*
     q.out_tracks = reinterpret_cast<tpc_track*>(take(Tc * sizeof(tpc_track)));
     q.out_hits = reinterpret_cast<int*>(take(N * 4));
     q.out_fits = reinterpret_cast<tpc_fit*>(take(Tc * sizeof(tpc_fit)));
+    q.fit_bins = reinterpret_cast<int*>(take(2 * (TPC_MAX_ROWS + 1) * 4));
     q.counters = reinterpret_cast<int*>(take(kNumCounters * 4));
     q.N = sh.N;
     q.R = sh.R;
