@@ -458,16 +458,20 @@ def run_stream(tr0, pool, args, rate):
         n_req = int(rate * args.stream_seconds)
         arrivals = np.cumsum(rng.exponential(1.0 / rate, n_req))
         picks = rng.integers(0, len(pool), n_req)
-        # warm-up: a few requests, drained
-        warm = [tr.submit(pool[i][0], pool[i][1], 1) for i in range(min(8, len(pool)))]
-        for t in warm:
-            while t is not None and tr.poll(t, 1000) is None:
-                pass
+        # warm-up: one burst of a full batch (the result buffers reach their
+        # working size), then a few single requests, drained
+        for burst in (min(args.stream_batch, len(pool)), 1, 1, 1, 1):
+            warm = [tr.submit(pool[i][0], pool[i][1], 1) for i in range(burst)]
+            for t in warm:
+                while t is not None and tr.poll(t, 1000) is None:
+                    pass
         lat = np.zeros(n_req)
         clusters = 0
         nxt, done = 0, 0
         outstanding = {}
         backlog = []
+        t_submit = t_poll = 0.0
+        n_tracks = 0
         t0 = time.perf_counter()
         while done < n_req:
             now = time.perf_counter() - t0
@@ -477,25 +481,46 @@ def run_stream(tr0, pool, args, rate):
             while backlog:
                 i = backlog[0]
                 cl, rc = pool[picks[i]]
+                ts = time.perf_counter()
                 t = tr.submit(cl, rc, 1, tag=i)
+                t_submit += time.perf_counter() - ts
                 if t is None:
                     break               # not admitted now (memory/slots): retry later
                 outstanding[t] = i
                 backlog.pop(0)
-            for t in list(outstanding)[:64]:  # the oldest requests finish first
-                r = tr.poll(t, 0)
+            # the oldest requests finish first: poll from the oldest and stop
+            # after a few pending ones (each poll of a pending ticket costs a
+            # pass of the request loop)
+            misses = 0
+            for t in list(outstanding)[:64]:
+                ts = time.perf_counter()
+                r = tr.poll_view(t, 0)   # no copy: the tracks are read in place
+                if r is not None:
+                    n_tracks += len(r.tracks)
+                    tr.release(t)
+                t_poll += time.perf_counter() - ts
                 if r is None:
+                    misses += 1
+                    if misses >= 4:
+                        break
                     continue
                 i = outstanding.pop(t)
                 lat[i] = time.perf_counter() - t0 - arrivals[i]
                 clusters += len(pool[picks[i]][0])
                 done += 1
         wall = time.perf_counter() - t0
+        st = tr.stream_stats()
     finally:
         tr.close()
+    st["gpu_busy_frac"] = st["gpu_ms"] / (wall * 1e3)
+    st["client_submit_s"] = t_submit
+    st["client_poll_s"] = t_poll
+    st["mean_batch_events"] = st["events"] / max(st["batches"], 1)
     return {"rate_hz": rate, "requests": n_req, "p50_ms": float(np.percentile(lat, 50) * 1e3),
+            "loop": st,
             "p99_ms": float(np.percentile(lat, 99) * 1e3), "max_ms": float(lat.max() * 1e3),
             "clusters_per_s": clusters / wall, "events_per_s": n_req / wall, "wall_s": wall,
+            "tracks": n_tracks, "client": "tpc_stream_poll_view + tpc_stream_release (results read in place)",
             "pool_events": len(pool), "mean_clusters_per_event": float(np.mean([len(p[0]) for p in pool])),
             "workload": "min-bias events (b ~ U[0,15] fm, 10-10,000 primaries + 30% secondaries, "
                         "10% noise), Poisson arrivals, one event per request"}

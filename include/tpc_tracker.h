@@ -267,6 +267,44 @@ int tpc_stream_configure(tpc_tracker* tr, size_t arena_bytes, int max_batch_even
  * when the device has room. */
 int tpc_stream_poll(tpc_tracker* tr, uint64_t ticket, tpc_output* out, int timeout_us);
 
+/* A finished ticket's result without a copy: pointers into the library's
+ * pinned host buffers, with the ids and offsets already relative to the
+ * request (as tpc_stream_poll returns them).  Valid until
+ * tpc_stream_release(ticket); the batch slot stays held until then, so a
+ * caller that keeps many views open holds back new batches (TPC_BUSY). */
+typedef struct {
+    const tpc_track* tracks;
+    const int32_t* hit_ids;
+    const tpc_fit* fits;     /* NULL unless params.refit = 1                    */
+    int32_t n_tracks;
+    int32_t n_hits;
+} tpc_stream_view;
+
+/* TPC_PENDING, TPC_OK (view filled; the ticket stays valid) or an error (the
+ * ticket is released). */
+int tpc_stream_poll_view(tpc_tracker* tr, uint64_t ticket, tpc_stream_view* view, int timeout_us);
+
+/* Release a finished ticket (after tpc_stream_poll_view).  TPC_ERR_INVALID
+ * while it is still pending, TPC_ERR_UNKNOWN_TICKET if unknown. */
+int tpc_stream_release(tpc_tracker* tr, uint64_t ticket);
+
+/* Counters of the request loop since tpc_stream_configure (observability
+ * of the serving path; no counterpart in the paper). */
+typedef struct {
+    int64_t batches;         /* batches launched                                */
+    int64_t events;          /* events in them                                  */
+    int64_t clusters;
+    int64_t refetches;       /* batches whose estimated output was short        */
+    int64_t max_batch_events;
+    double gpu_ms;           /* sum over finished batches: first H2D to the last
+                                D2H on the batch's stream                       */
+    double host_launch_ms;   /* host time spent forming and enqueueing batches  */
+    double host_finish_ms;   /* host time spent slicing finished batches        */
+    double host_copy_ms;     /* host time spent copying results in polls        */
+} tpc_stream_stats;
+
+int tpc_stream_get_stats(const tpc_tracker* tr, tpc_stream_stats* stats);
+
 /* Per-stage results of the last tpc_track_sectors call, for the step-by-step
  * comparison against a CPU implementation (Sec. 4.1: results of all steps
  * can be compared individually).  what:

@@ -77,6 +77,18 @@ class tpc_output(C.Structure):
                 ("n_hits", C.c_int32), ("fits", C.c_void_p)]
 
 
+class tpc_stream_stats(C.Structure):
+    _fields_ = [("batches", C.c_int64), ("events", C.c_int64), ("clusters", C.c_int64),
+                ("refetches", C.c_int64), ("max_batch_events", C.c_int64), ("gpu_ms", C.c_double),
+                ("host_launch_ms", C.c_double), ("host_finish_ms", C.c_double),
+                ("host_copy_ms", C.c_double)]
+
+
+class tpc_stream_view(C.Structure):
+    _fields_ = [("tracks", C.c_void_p), ("hit_ids", C.c_void_p), ("fits", C.c_void_p),
+                ("n_tracks", C.c_int32), ("n_hits", C.c_int32)]
+
+
 _LIB = None
 
 
@@ -103,6 +115,9 @@ def lib() -> C.CDLL:
         L.tpc_stream_submit.argtypes = [V, V, V, C.c_int, C.c_uint64, P(C.c_uint64)]
         L.tpc_stream_poll.argtypes = [V, C.c_uint64, P(tpc_output), C.c_int]
         L.tpc_stream_configure.argtypes = [V, C.c_size_t, C.c_int, C.c_int, C.c_int]
+        L.tpc_stream_get_stats.argtypes = [V, P(tpc_stream_stats)]
+        L.tpc_stream_poll_view.argtypes = [V, C.c_uint64, P(tpc_stream_view), C.c_int]
+        L.tpc_stream_release.argtypes = [V, C.c_uint64]
         L.tpc_debug_dump.argtypes = [V, C.c_int, V, C.c_int64, P(C.c_int64)]
         L.tpc_stage_times.argtypes = [V, P(C.c_float), C.c_int]
         L.tpc_last_error.argtypes = [V]

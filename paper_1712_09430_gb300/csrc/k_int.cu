@@ -533,11 +533,11 @@ __global__ void k_emit(KConst k, DevPtrs p)
         const int2 ex = p.acc_scan[t] + p.scan_part[t / kScanTile];
         const int m = ex.x;
         const int n = p.tl_n[t];
+        const int unit = p.t_row[t] / k.n_rows;
         if (lane < kWords) {
             // word layout of tpc_track: event sector tracklet x p[5] cov_y[6]
             // cov_z[3] chi2 ndf nhits hit_off
             int word;
-            const int unit = p.t_row[t] / k.n_rows;
             if (lane == 0) word = unit / k.n_sectors;
             else if (lane == 1) word = unit % k.n_sectors;
             else if (lane == 2) word = t;
@@ -562,6 +562,44 @@ __global__ void k_emit(KConst k, DevPtrs p)
             if (own) p.out_hits[o + __popc(bal & ((1u << lane) - 1u))] = __float_as_int(p.hits[b].w);
             o += __popc(bal);
         }
+    }
+}
+
+// Serving, after every other stage: event, tracklet, hit offset and cluster
+// positions of each track made relative to the track's request (its first
+// event, canonical tracklet, hit and cluster).  A warp per track.
+__global__ void k_rebase(KConst k, DevPtrs p)
+{
+    const int M = p.counters[C_M];
+    const int lane = threadIdx.x & 31;
+    const int w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+    for (int m = w0; m < M; m += nw) {
+        tpc_track& tk = p.out_tracks[m];
+        const int ev = tk.event, n = tk.nhits, h0 = tk.hit_off;
+        const int b_ev = p.req_first_event[ev];
+        const int rr0 = b_ev * k.n_sectors * k.n_rows;
+        const int b_cl = p.row_off[rr0];
+        const int b_t = p.start_off[rr0];
+        const int b_h = (p.acc_scan[b_t] + p.scan_part[b_t / kScanTile]).y;
+        for (int j = lane; j < n; j += 32) p.out_hits[h0 + j] -= b_cl;
+        __syncwarp();
+        if (lane == 0) {
+            tk.event = ev - b_ev;
+            tk.tracklet -= b_t;
+            tk.hit_off = h0 - b_h;
+        }
+    }
+}
+
+// Serving: first (track, hit) of every event of the batch, from the
+// exclusive scan at the event's first canonical tracklet; entry E is (M, MH).
+__global__ void k_ev_first(KConst k, DevPtrs p, int E)
+{
+    const int T = p.counters[C_T];
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e <= E; e += gridDim.x * blockDim.x) {
+        const int t = p.start_off[e * k.n_sectors * k.n_rows];
+        p.ev_first[e] = t < T ? p.acc_scan[t] + p.scan_part[t / kScanTile]
+                              : make_int2(p.counters[C_M], p.counters[C_MH]);
     }
 }
 
@@ -696,6 +734,14 @@ cudaError_t launch_emit(const KConst& k, const DevPtrs& p, int n_sm, cudaStream_
     k_scan_tiles<<<nblk, 256, 0, s>>>(p);
     k_scan_top<<<1, 1024, 0, s>>>(p);
     k_emit<<<n_sm * 8, 256, 0, s>>>(k, p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rebase(const KConst& k, const DevPtrs& p, int n_sm, cudaStream_t s)
+{
+    const int E = p.R / (k.n_sectors * k.n_rows);
+    k_ev_first<<<(E + 256) / 256, 256, 0, s>>>(k, p, E);
+    k_rebase<<<n_sm * 8, 256, 0, s>>>(k, p);
     return cudaGetLastError();
 }
 

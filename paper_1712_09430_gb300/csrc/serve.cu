@@ -36,11 +36,11 @@ struct Request {
     int state = 0;                      // 0 pending, 1 in flight, 2 done, 3 failed
     int batch = -1;
     int err = TPC_OK;
-    // slice of the batch output
+    // slice of the batch output (rebased to the request on the device)
     int e0 = 0, cl0 = 0;                // first event / cluster of the request in the batch
-    int t0 = 0;                         // first canonical tracklet id of the request
     int m0 = 0, m1 = 0;                 // track range
     int h0 = 0, h1 = 0;                 // hit range
+    bool viewed = false;                // handed out by tpc_stream_poll_view
 };
 
 struct Batch {
@@ -48,6 +48,7 @@ struct Batch {
     bool busy = false;
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
+    cudaEvent_t start = nullptr;        // timing: first H2D of the batch
     size_t arena_off = 0, arena_bytes = 0;
     BatchShape sh;
     DevPtrs p{};
@@ -129,7 +130,15 @@ struct ServeState {
     int next_batch = 0;
     int inflight = 0;
     double tracks_per_cluster = 0.012, hits_per_cluster = 0.9;  // D2H estimate, adapted
+    tpc_stream_stats stats{};
 };
+
+namespace {
+double ms_since(std::chrono::steady_clock::time_point t0)
+{
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+}
+}  // namespace
 
 static int serve_init(tpc_tracker* tr)
 {
@@ -158,7 +167,7 @@ static int serve_init(tpc_tracker* tr)
     S->batches.resize((size_t)(2 * S->max_inflight + 2));
     for (auto& b : S->batches) {
         if (cudaStreamCreateWithFlags(&b.stream, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&b.done, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreate(&b.done) != cudaSuccess || cudaEventCreate(&b.start) != cudaSuccess ||
             cudaMallocHost(&b.counters, sizeof(int) * kNumCounters) != cudaSuccess)
             return tr->fail(TPC_ERR_DEVICE, "cannot create serving streams");
     }
@@ -170,8 +179,11 @@ static int grow_pinned(tpc_tracker* tr, void** ptr, size_t* cap, size_t want)
     if (want <= *cap) return TPC_OK;
     cudaFreeHost(*ptr);
     *ptr = nullptr;
+    const size_t old = *cap;
     *cap = 0;
-    size_t n = want + want / 4 + 4096;
+    // grow at least twofold: pinned reallocation is slow and can synchronize
+    // the device, so it must stay rare under a growing load
+    size_t n = std::max(want + want / 4, 2 * old) + 4096;
     if (cudaMallocHost(ptr, n) != cudaSuccess) {
         cudaGetLastError();
         return tr->fail(TPC_ERR_NOMEM, "pinned result buffer");
@@ -181,7 +193,17 @@ static int grow_pinned(tpc_tracker* tr, void** ptr, size_t* cap, size_t want)
 }
 
 // Launch all pending requests (up to max_batch_events events) as one batch.
+static int launch_batch_impl(tpc_tracker* tr);
+
 static int launch_batch(tpc_tracker* tr)
+{
+    const auto t0 = std::chrono::steady_clock::now();
+    const int rc = launch_batch_impl(tr);
+    tr->serve->stats.host_launch_ms += ms_since(t0);
+    return rc;
+}
+
+static int launch_batch_impl(tpc_tracker* tr)
 {
     ServeState* S = tr->serve;
     Batch* b = nullptr;
@@ -200,10 +222,11 @@ static int launch_batch(tpc_tracker* tr)
     }
     const int NR = tr->geom.n_rows, NS = tr->geom.n_sectors;
     const size_t R = (size_t)ev * NS * NR;
-    // the batch's row counts (in a pinned buffer: counts, then the plan)
-    // pinned: counts [R], plan [2 (R + 1)], first tracklet id per event [ev + 1]
+    // the batch's pinned host buffer: row counts [R], plan [2 (R + 1)], first
+    // event of each event's request [ev], first (track, hit) of each event
+    // [2 (ev + 1)] (filled by the device)
     if (grow_pinned(tr, reinterpret_cast<void**>(&b->plan), &b->plan_cap,
-                    (3 * R + 2 + (size_t)ev + 1) * sizeof(int)) != TPC_OK)
+                    (3 * R + 2 + 3 * (size_t)ev + 2) * sizeof(int)) != TPC_OK)
         return TPC_ERR_NOMEM;
     int* counts = b->plan;
     size_t pos = 0;
@@ -226,16 +249,23 @@ static int launch_batch(tpc_tracker* tr)
     b->sh = sh;
     b->tickets = take;
     tpc_layout(tr, sh, &b->p, static_cast<char*>(S->arena_base) + off);
+    b->p.req_first_event = b->p.req_area;
+    int* req_first = counts + 3 * R + 2;
     const DevPtrs& p = b->p;
     cudaStream_t s = b->stream;
     int e0 = 0, cl0 = 0;
-    cudaError_t e = cudaSuccess;
+    cudaError_t e = cudaEventRecord(b->start, s);
+    S->stats.batches++;
+    S->stats.events += ev;
+    S->stats.clusters += sh.N;
+    S->stats.max_batch_events = std::max<int64_t>(S->stats.max_batch_events, ev);
     for (uint64_t t : take) {
         Request& r = S->req[t];
         r.state = 1;
         r.batch = (int)(b - S->batches.data());
         r.e0 = e0;
         r.cl0 = cl0;
+        for (int q = 0; q < r.n_events; q++) req_first[e0 + q] = e0;
         const void* src = r.src ? static_cast<const void*>(r.src) : S->pin + r.pin_off;
         if (r.N && e == cudaSuccess)
             e = cudaMemcpyAsync(const_cast<float4*>(p.clusters) + cl0, src, (size_t)r.N * 16,
@@ -249,6 +279,8 @@ static int launch_batch(tpc_tracker* tr)
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(const_cast<int*>(p.row_off), counts + R, (R + 1) * 2 * sizeof(int),
                             cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && ev > 0)
+        e = cudaMemcpyAsync(p.req_area, req_first, (size_t)ev * sizeof(int), cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return tr->fail(TPC_ERR_DEVICE, cudaGetErrorString(e));
     S->inflight++;
     if (sh.N > 0) {
@@ -267,11 +299,10 @@ static int launch_batch(tpc_tracker* tr)
                         sizeof(tpc_fit) * (size_t)b->est_tracks) != TPC_OK)
             return TPC_ERR_NOMEM;
         e = cudaMemcpyAsync(b->counters, p.counters, sizeof(int) * kNumCounters, cudaMemcpyDeviceToHost, s);
-        // first canonical tracklet id of every event: start_off at each event's first row
-        const size_t ev_rows = (size_t)NS * NR;
+        // first (track, hit) of every event, to slice the output per request
         if (e == cudaSuccess)
-            e = cudaMemcpy2DAsync(b->plan + 3 * R + 2, sizeof(int), p.start_off, ev_rows * sizeof(int),
-                                  sizeof(int), (size_t)ev + 1, cudaMemcpyDeviceToHost, s);
+            e = cudaMemcpyAsync(req_first + ev, p.ev_first, ((size_t)ev + 1) * sizeof(int2),
+                                cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(b->tracks, p.out_tracks, sizeof(tpc_track) * (size_t)b->est_tracks,
                                 cudaMemcpyDeviceToHost, s);
@@ -283,7 +314,7 @@ static int launch_batch(tpc_tracker* tr)
                                 cudaMemcpyDeviceToHost, s);
     } else {
         std::memset(b->counters, 0, sizeof(int) * kNumCounters);
-        std::memset(b->plan + 3 * R + 2, 0, sizeof(int) * ((size_t)ev + 1));
+        std::memset(req_first + ev, 0, sizeof(int2) * ((size_t)ev + 1));
         b->est_tracks = b->est_hits = 0;
     }
     if (e == cudaSuccess) e = cudaEventRecord(b->done, s);
@@ -296,6 +327,12 @@ static int launch_batch(tpc_tracker* tr)
 static void finish_batch(tpc_tracker* tr, Batch& b)
 {
     ServeState* S = tr->serve;
+    const auto t_host = std::chrono::steady_clock::now();
+    {
+        float gms = 0.0f;
+        if (cudaEventElapsedTime(&gms, b.start, b.done) == cudaSuccess) S->stats.gpu_ms += gms;
+        else cudaGetLastError();
+    }
     int err = TPC_OK;
     const int* c = b.counters;
     const int M = b.sh.N ? c[C_M] : 0, MH = b.sh.N ? c[C_MH] : 0;
@@ -303,6 +340,7 @@ static void finish_batch(tpc_tracker* tr, Batch& b)
     if (b.sh.N && (c[C_ERR] & E_TIMEOUT)) err = TPC_ERR_TIMEOUT;
     if (err == TPC_OK && (M > b.est_tracks || MH > b.est_hits)) {
         // the estimate was short: fetch the remainder now
+        S->stats.refetches++;
         void* tp = b.tracks;
         void* hp = b.hits;
         size_t tc = b.tracks_cap, hc = b.hits_cap;
@@ -339,26 +377,27 @@ static void finish_batch(tpc_tracker* tr, Batch& b)
         S->tracks_per_cluster = std::max(S->tracks_per_cluster * 0.9, (double)M / b.sh.N);
         S->hits_per_cluster = std::max(S->hits_per_cluster * 0.9, (double)MH / b.sh.N);
     }
-    // tracks are in canonical order: grouped by event, so by request
-    int m = 0;
+    // tracks are in canonical order, grouped by event, so by request; the
+    // device wrote the first (track, hit) of every event
     b.open_results = 0;
-    const int* tbase = b.plan + 3 * (size_t)b.sh.R + 2;
+    const int ev = b.sh.n_events;
+    const int2* evf = reinterpret_cast<const int2*>(b.plan + 3 * (size_t)b.sh.R + 2 + ev);
     for (uint64_t t : b.tickets) {
         Request& r = S->req[t];
-        r.t0 = tbase[r.e0];
         r.err = err;
         r.state = err == TPC_OK ? 2 : 3;
-        r.m0 = m;
-        while (err == TPC_OK && m < M && b.tracks[m].event < r.e0 + r.n_events) m++;
-        r.m1 = m;
-        r.h0 = r.m1 > r.m0 ? b.tracks[r.m0].hit_off : 0;
-        r.h1 = r.m1 > r.m0 ? b.tracks[r.m1 - 1].hit_off + b.tracks[r.m1 - 1].nhits : 0;
+        const int2 f0 = evf[r.e0], f1 = evf[r.e0 + r.n_events];
+        r.m0 = err == TPC_OK ? f0.x : 0;
+        r.m1 = err == TPC_OK ? f1.x : 0;
+        r.h0 = err == TPC_OK ? f0.y : 0;
+        r.h1 = err == TPC_OK ? f1.y : 0;
         if (r.pin_bytes) S->pin_arena.release(r.pin_off, r.pin_bytes);
         r.pin_bytes = 0;
         b.open_results++;
     }
     S->arena.release(b.arena_off, b.arena_bytes);
     S->inflight--;
+    S->stats.host_finish_ms += ms_since(t_host);
 }
 
 static int progress(tpc_tracker* tr)
@@ -392,6 +431,7 @@ void tpc_serve_shutdown(tpc_tracker* tr)
         if (b.stream) cudaStreamSynchronize(b.stream);
         if (b.stream) cudaStreamDestroy(b.stream);
         if (b.done) cudaEventDestroy(b.done);
+        if (b.start) cudaEventDestroy(b.start);
         cudaFreeHost(b.plan);
         cudaFreeHost(b.counters);
         cudaFreeHost(b.tracks);
@@ -469,12 +509,9 @@ extern "C" int tpc_stream_submit(tpc_tracker* tr, const tpc_cluster* clusters, c
     return rc == TPC_OK ? TPC_OK : rc;
 }
 
-extern "C" int tpc_stream_poll(tpc_tracker* tr, uint64_t ticket, tpc_output* out, int timeout_us)
+// Drive the loop until the ticket's batch is done or the time runs out.
+static int wait_ticket(tpc_tracker* tr, uint64_t ticket, int timeout_us, Request** out)
 {
-    if (!tr) return TPC_ERR_INVALID;
-    if (!out) return tr->fail(TPC_ERR_INVALID, "NULL output");
-    if (!tr->serve) return TPC_ERR_UNKNOWN_TICKET;
-    if (cudaSetDevice(tr->dev) != cudaSuccess) return tr->fail(TPC_ERR_DEVICE, "cudaSetDevice");
     ServeState* S = tr->serve;
     const auto t_end = std::chrono::steady_clock::now() + std::chrono::microseconds(std::max(0, timeout_us));
     while (true) {
@@ -482,39 +519,106 @@ extern "C" int tpc_stream_poll(tpc_tracker* tr, uint64_t ticket, tpc_output* out
         if (rc != TPC_OK) return rc;
         auto it = S->req.find(ticket);
         if (it == S->req.end()) return TPC_ERR_UNKNOWN_TICKET;
-        Request& r = it->second;
-        if (r.state >= 2) {
-            Batch& b = S->batches[(size_t)r.batch];
-            int result = r.err;
-            if (result == TPC_OK) {
-                const int M = r.m1 - r.m0, MH = r.h1 - r.h0;
-                out->n_tracks = M;
-                out->n_hits = MH;
-                if (M > out->cap_tracks || MH > out->cap_hits)
-                    return tr->fail(TPC_ERR_OUTPUT_TRUNCATED, "output capacity too small");
-                if (out->mem_kind != TPC_MEM_HOST)
-                    return tr->fail(TPC_ERR_INVALID, "stream results are returned in host memory");
-                for (int m = 0; m < M; m++) {
-                    tpc_track t = b.tracks[r.m0 + m];
-                    t.event -= r.e0;
-                    t.tracklet -= r.t0;
-                    t.hit_off -= r.h0;
-                    out->tracks[m] = t;
-                }
-                for (int h = 0; h < MH; h++) out->hit_ids[h] = b.hits[r.h0 + h] - r.cl0;
-                if (out->fits && tr->params.refit)
-                    for (int m = 0; m < M; m++) out->fits[m] = b.fits[r.m0 + m];
-            }
-            S->reserved -= r.reserve;
-            S->req.erase(it);
-            if (--b.open_results == 0) {
-                b.busy = false;
-                b.tickets.clear();
-                progress(tr);
-            }
-            return result == TPC_OK ? TPC_OK : tr->fail(result, "batch failed");
+        if (it->second.state >= 2) {
+            *out = &it->second;
+            return TPC_OK;
         }
         if (std::chrono::steady_clock::now() >= t_end) return TPC_PENDING;
         std::this_thread::sleep_for(std::chrono::microseconds(20));
     }
+}
+
+// Forget a finished request; its batch slot frees with its last request.
+static void release_ticket(tpc_tracker* tr, uint64_t ticket)
+{
+    ServeState* S = tr->serve;
+    auto it = S->req.find(ticket);
+    Batch& b = S->batches[(size_t)it->second.batch];
+    S->reserved -= it->second.reserve;
+    S->req.erase(it);
+    if (--b.open_results == 0) {
+        b.busy = false;
+        b.tickets.clear();
+        progress(tr);
+    }
+}
+
+extern "C" int tpc_stream_poll(tpc_tracker* tr, uint64_t ticket, tpc_output* out, int timeout_us)
+{
+    if (!tr) return TPC_ERR_INVALID;
+    if (!out) return tr->fail(TPC_ERR_INVALID, "NULL output");
+    if (!tr->serve) return TPC_ERR_UNKNOWN_TICKET;
+    if (cudaSetDevice(tr->dev) != cudaSuccess) return tr->fail(TPC_ERR_DEVICE, "cudaSetDevice");
+    ServeState* S = tr->serve;
+    Request* r = nullptr;
+    int rc = wait_ticket(tr, ticket, timeout_us, &r);
+    if (rc != TPC_OK) return rc;
+    Batch& b = S->batches[(size_t)r->batch];
+    const int result = r->err;
+    if (result == TPC_OK) {
+        const int M = r->m1 - r->m0, MH = r->h1 - r->h0;
+        out->n_tracks = M;
+        out->n_hits = MH;
+        if (M > out->cap_tracks || MH > out->cap_hits)
+            return tr->fail(TPC_ERR_OUTPUT_TRUNCATED, "output capacity too small");
+        if (out->mem_kind != TPC_MEM_HOST)
+            return tr->fail(TPC_ERR_INVALID, "stream results are returned in host memory");
+        const auto t_copy = std::chrono::steady_clock::now();
+        if (M) std::memcpy(out->tracks, b.tracks + r->m0, sizeof(tpc_track) * (size_t)M);
+        if (MH) std::memcpy(out->hit_ids, b.hits + r->h0, sizeof(int32_t) * (size_t)MH);
+        if (M && out->fits && tr->params.refit)
+            std::memcpy(out->fits, b.fits + r->m0, sizeof(tpc_fit) * (size_t)M);
+        S->stats.host_copy_ms += ms_since(t_copy);
+    }
+    release_ticket(tr, ticket);
+    return result == TPC_OK ? TPC_OK : tr->fail(result, "batch failed");
+}
+
+extern "C" int tpc_stream_poll_view(tpc_tracker* tr, uint64_t ticket, tpc_stream_view* view, int timeout_us)
+{
+    if (!tr) return TPC_ERR_INVALID;
+    if (!view) return tr->fail(TPC_ERR_INVALID, "NULL view");
+    if (!tr->serve) return TPC_ERR_UNKNOWN_TICKET;
+    if (cudaSetDevice(tr->dev) != cudaSuccess) return tr->fail(TPC_ERR_DEVICE, "cudaSetDevice");
+    ServeState* S = tr->serve;
+    Request* r = nullptr;
+    int rc = wait_ticket(tr, ticket, timeout_us, &r);
+    if (rc != TPC_OK) return rc;
+    if (r->err != TPC_OK) {
+        const int result = r->err;
+        release_ticket(tr, ticket);
+        return tr->fail(result, "batch failed");
+    }
+    const Batch& b = S->batches[(size_t)r->batch];
+    view->tracks = b.tracks + r->m0;
+    view->hit_ids = b.hits + r->h0;
+    view->fits = tr->params.refit ? b.fits + r->m0 : nullptr;
+    view->n_tracks = r->m1 - r->m0;
+    view->n_hits = r->h1 - r->h0;
+    r->viewed = true;
+    return TPC_OK;
+}
+
+extern "C" int tpc_stream_release(tpc_tracker* tr, uint64_t ticket)
+{
+    if (!tr) return TPC_ERR_INVALID;
+    if (!tr->serve) return TPC_ERR_UNKNOWN_TICKET;
+    ServeState* S = tr->serve;
+    auto it = S->req.find(ticket);
+    if (it == S->req.end()) return TPC_ERR_UNKNOWN_TICKET;
+    if (it->second.state < 2) return tr->fail(TPC_ERR_INVALID, "ticket still pending");
+    if (cudaSetDevice(tr->dev) != cudaSuccess) return tr->fail(TPC_ERR_DEVICE, "cudaSetDevice");
+    release_ticket(tr, ticket);
+    return TPC_OK;
+}
+
+extern "C" int tpc_stream_get_stats(const tpc_tracker* tr, tpc_stream_stats* stats)
+{
+    if (!tr || !stats) return TPC_ERR_INVALID;
+    if (!tr->serve) {
+        *stats = tpc_stream_stats{};
+        return TPC_OK;
+    }
+    *stats = tr->serve->stats;
+    return TPC_OK;
 }

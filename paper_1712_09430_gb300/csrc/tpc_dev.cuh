@@ -98,6 +98,11 @@ struct DevPtrs {
     int* out_hits;             // [MHcap]
     tpc_fit* out_fits;         // [Mcap] refit of each track
     int* fit_bins;             // [2 * (TPC_MAX_ROWS + 1)] refit order: counts, offsets
+    // serving batches only (nullptr otherwise): the output is rebased per
+    // request on the device
+    const int* req_first_event;  // [E] first event of each event's request
+    int2* ev_first;              // [E + 1] first (track, hit) of each event
+    int* req_area;               // [E] device storage for req_first_event
     int* counters;             // [kNumCounters]
     int N, R, n_units, t_cap, m_cap, mh_cap;
 };
@@ -223,6 +228,7 @@ cudaError_t launch_select(const tpc::KConst& k, const tpc::DevPtrs& p, int n_sm,
                           int t1_unit, bool owner, cudaStream_t s);
 cudaError_t launch_owner_units(const tpc::KConst& k, const tpc::DevPtrs& p, int n_units, int max_unit,
                                cudaStream_t s);
+cudaError_t launch_rebase(const tpc::KConst& k, const tpc::DevPtrs& p, int n_sm, cudaStream_t s);
 cudaError_t launch_emit(const tpc::KConst& k, const tpc::DevPtrs& p, int n_sm, cudaStream_t s);
 cudaError_t launch_dump_links(const tpc::DevPtrs& p, int cleaned, int* dst, cudaStream_t s);
 cudaError_t launch_dump_starts(const tpc::DevPtrs& p, int T, int* dst, cudaStream_t s);

@@ -269,6 +269,10 @@ size_t tpc_layout(const tpc_tracker* tr, const BatchShape& sh, DevPtrs* p, char*
     q.out_hits = reinterpret_cast<int*>(take(N * 4));
     q.out_fits = reinterpret_cast<tpc_fit*>(take(Tc * sizeof(tpc_fit)));
     q.fit_bins = reinterpret_cast<int*>(take(2 * (TPC_MAX_ROWS + 1) * 4));
+    q.ev_first = reinterpret_cast<int2*>(take(((size_t)sh.n_events + 1) * 8));
+    q.req_area = reinterpret_cast<int*>(take((size_t)sh.n_events * 4));
+    // set by the serving loop for its batches; the synchronous call does not rebase
+    q.req_first_event = nullptr;
     q.counters = reinterpret_cast<int*>(take(kNumCounters * 4));
     q.N = sh.N;
     q.R = sh.R;
@@ -504,6 +508,7 @@ int tpc_enqueue(tpc_tracker* tr, const DevPtrs& p, const BatchShape& sh, cudaStr
     if (with_events) TPC_CUDA(cudaEventRecord(tr->ev[5], s));
     if (P.refit)
         TPC_CUDA(exact ? tpc_exact::launch_refit(k, p, tr->n_sm, s) : tpc_fast::launch_refit(k, p, tr->n_sm, s));
+    if (p.req_first_event) TPC_CUDA(tpc_int::launch_rebase(k, p, tr->n_sm, s));
     if (with_events) TPC_CUDA(cudaEventRecord(tr->ev[6], s));
 #undef cudaEventRecord
     return TPC_OK;

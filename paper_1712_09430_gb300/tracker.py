@@ -166,6 +166,12 @@ class Tracker:
                                               int(max_inflight),
                                               capi.TPC_STREAM_NO_COPY if no_copy else 0))
 
+    def stream_stats(self):
+        """Counters of the request loop (batches, events, device and host ms)."""
+        st = capi.tpc_stream_stats()
+        self.check(lib().tpc_stream_get_stats(self.h, C.byref(st)))
+        return {k: getattr(st, k) for k, _ in st._fields_}
+
     def submit(self, clusters, row_counts, n_events=1, tag=0):
         """Returns a ticket, or None when the request is not admitted now.
         clusters: numpy float32 [N, 4] or a (pinned) torch CPU tensor; with
@@ -202,6 +208,27 @@ class Tracker:
         self.check(lib().tpc_stream_poll(self.h, int(ticket), C.byref(out), 0))
         return Result(tracks[:out.n_tracks], hits[:out.n_hits],
                       fits[:out.n_tracks] if refit else None)
+
+    def poll_view(self, ticket, timeout_us=0):
+        """Result of a ticket without a copy (numpy views of the library's
+        pinned buffers), or None while pending.  The views stay valid until
+        release(ticket)."""
+        v = capi.tpc_stream_view()
+        rc = lib().tpc_stream_poll_view(self.h, int(ticket), C.byref(v), int(timeout_us))
+        if rc == capi.TPC_PENDING:
+            return None
+        self.check(rc)
+
+        def arr(ptr, n, dt):
+            if n == 0 or not ptr:
+                return np.zeros(0, dt)
+            return np.frombuffer((C.c_char * (n * dt.itemsize)).from_address(ptr), dtype=dt)
+        fits = arr(v.fits, v.n_tracks, FIT_DTYPE) if self.params.refit else None
+        return Result(arr(v.tracks, v.n_tracks, TRACK_DTYPE), arr(v.hit_ids, v.n_hits, np.dtype(np.int32)),
+                      fits)
+
+    def release(self, ticket):
+        self.check(lib().tpc_stream_release(self.h, int(ticket)))
 
     def dump(self, what):
         n = C.c_int64()

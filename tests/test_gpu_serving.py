@@ -156,3 +156,41 @@ def test_stream_rejects_invalid_input(pool):
         # the loop keeps serving
         t = tr.submit(ev.clusters, ev.row_counts, 1)
         assert _drain(tr, [t])[t] is not None
+
+
+def test_stream_poll_view_equals_poll_and_release(pool):
+    evs = pool[:6]
+    with Tracker(XR, exact_fp32=1) as a:
+        a.stream_configure(arena_bytes=2 << 30, max_batch_events=4, max_inflight=2)
+        ta = [a.submit(e.clusters, e.row_counts, 1) for e in evs]
+        res = _drain(a, ta)
+        ref = [res[t] for t in ta]
+    with Tracker(XR, exact_fp32=1) as tr:
+        tr.stream_configure(arena_bytes=2 << 30, max_batch_events=4, max_inflight=2)
+        tickets = [tr.submit(e.clusters, e.row_counts, 1) for e in evs]
+        seen = set()
+        t_end = time.time() + 60
+        while len(seen) < len(tickets):
+            for i, t in enumerate(tickets):
+                if i not in seen:
+                    v = tr.poll_view(t, timeout_us=200)
+                    if v is not None:
+                        _same(v, ref[i])
+                        tr.release(t)
+                        seen.add(i)
+            assert time.time() < t_end
+        with pytest.raises(TrackerError) as e:
+            tr.release(tickets[0])
+        assert e.value.code == capi.TPC_ERR_UNKNOWN_TICKET
+
+
+def test_stream_release_of_pending_ticket_is_refused(pool):
+    ev = pool[10]
+    with Tracker(XR) as tr:
+        tr.stream_configure(arena_bytes=2 << 30)
+        t = tr.submit(ev.clusters, ev.row_counts, 1)
+        # a central-size event cannot be done within microseconds of submission
+        with pytest.raises(TrackerError) as e:
+            tr.release(t)
+        assert e.value.code == capi.TPC_ERR_INVALID
+        assert _drain(tr, [t])[t] is not None
