@@ -40,6 +40,10 @@ class FitParams(C.Structure):
                                           "bz")] + [("b", C.c_double * 5)]
 
 
+class MergeParams(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("chi2_max", "gap", "overlap", "cos_t", "sin_t")]
+
+
 class Geom(C.Structure):
     _fields_ = [("n_rows", C.c_int), ("n_sectors", C.c_int), ("row_x", C.POINTER(C.c_float)),
                 ("tan_half_open", C.c_float), ("z_max", C.c_float)]
@@ -85,6 +89,11 @@ def lib(mode="f64"):
         L.orc_refit_tracks.argtypes = [P(FitParams), C.c_int, V, V, V, V, V, C.c_int]
         L.orc_refit_propagate.argtypes = [P(FitParams), V, C.c_double]
         L.orc_refit_update.argtypes = [P(FitParams), V, C.c_double, C.c_double, P(C.c_double)]
+        L.orc_merge_tracks.argtypes = [P(FitParams), P(MergeParams), C.c_int, C.c_int, V, V, V, V, V,
+                                       C.c_int]
+        L.orc_merge_rotate.argtypes = [P(FitParams), V, C.c_double, C.c_double]
+        L.orc_merge_propagate.argtypes = [P(FitParams), V, C.c_double]
+        L.orc_merge_chi2.argtypes = [V, V, P(C.c_double)]
         L.orc_max_threads.restype = C.c_int
         L.orc_real_size.restype = C.c_int
         _LIBS[mode] = L
@@ -282,3 +291,60 @@ def refit_update(v, my, mz, fp, mode="f64", chi2=0.0):
     c = C.c_double(chi2)
     lib(mode).orc_refit_update(C.byref(fp), _ptr(v), float(my), float(mz), C.byref(c))
     return v, c.value
+
+
+# track merging (tpc_refit.c, Phase II) -------------------------------------
+
+def merge_params(chi2_max=30.0, gap=50.0, overlap=5.0, angle_deg=20.0) -> MergeParams:
+    import math
+    m = MergeParams()
+    m.chi2_max, m.gap, m.overlap = chi2_max, gap, overlap
+    m.cos_t = float(np.float32(math.cos(math.radians(angle_deg))))
+    m.sin_t = float(np.float32(math.sin(math.radians(angle_deg))))
+    return m
+
+
+def merge_tracks(unit, fits, x_last, fp, mp=None, n_sectors=36, mode="f64"):
+    """Merge links of refitted tracks (canonical order).  unit[M] = event *
+    n_sectors + sector; fits [M, N_FIT] (refit outputs); x_last[M].  Returns
+    (next[M] int32, chi2[M])."""
+    mp = mp if mp is not None else merge_params()
+    u = np.ascontiguousarray(unit, np.int32)
+    f = np.ascontiguousarray(fits, np.float64)
+    xl = np.ascontiguousarray(x_last, np.float64)
+    M = len(u)
+    nxt = np.full(M, -1, np.int32)
+    chi = np.zeros(M, np.float64)
+    lib(mode).orc_merge_tracks(C.byref(fp), C.byref(mp), M, n_sectors, _ptr(u), _ptr(f), _ptr(xl),
+                               _ptr(nxt), _ptr(chi), 0)
+    return nxt, chi
+
+
+def merge_vec(x, p, C5=None):
+    """31-vector of the merge entries: x, p[5], C[5][5] row-major."""
+    v = np.zeros(31)
+    v[0] = x
+    v[1:6] = p
+    if C5 is not None:
+        v[6:] = np.asarray(C5, np.float64).reshape(25)
+    return v
+
+
+def merge_rotate(v, cos_t, sin_t, fp, mode="f64"):
+    v = np.array(v, dtype=np.float64)
+    ok = lib(mode).orc_merge_rotate(C.byref(fp), _ptr(v), float(cos_t), float(sin_t))
+    return bool(ok), v
+
+
+def merge_propagate(v, x1, fp, mode="f64"):
+    v = np.array(v, dtype=np.float64)
+    ok = lib(mode).orc_merge_propagate(C.byref(fp), _ptr(v), float(x1))
+    return bool(ok), v
+
+
+def merge_chi2(va, vb, mode="f64"):
+    va = np.ascontiguousarray(va, np.float64)
+    vb = np.ascontiguousarray(vb, np.float64)
+    c = C.c_double()
+    ok = lib(mode).orc_merge_chi2(_ptr(va), _ptr(vb), C.byref(c))
+    return bool(ok), c.value

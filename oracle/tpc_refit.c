@@ -117,19 +117,22 @@ typedef struct {
     rreal S[5][5];   /* covariance factor: C = S S^T */
 } rf_state;
 
-/* F2, F3: one step to the plane x1.  Returns 1 on success, 0 when |sin phi|
- * exceeds s_max before or after the step (state untouched). */
-static int rf_prop(const rf_ctx* c, rf_state* st, rreal x1)
+/* F2, F3: one step of the state (x, p) to the plane x1 and its Jacobian J.
+ * Returns 1 on success, 0 when |sin phi| exceeds s_max before or after the
+ * step (x, p untouched). */
+static int rf_step(const rf_ctx* c, rreal* x, rreal* p, rreal J[5][5], rreal x1)
 {
-    rreal d = x1 - st->x;
+    memset(J, 0, sizeof(rreal) * 25);
+    for (int i = 0; i < 5; i++) J[i][i] = RF(1);
+    rreal d = x1 - *x;
     if (d == RF(0)) return 1;
-    rreal y = st->p[0], z = st->p[1], s0 = st->p[2], t = st->p[3], q = st->p[4];
+    rreal y = p[0], z = p[1], s0 = p[2], t = p[3], q = p[4];
     if (f_fabs(s0) > c->s_max) return 0;
     rreal c0 = f_sqrt(RF(1) - s0 * s0);
 
     /* field at the straight-line midpoint of the step */
     rreal h = d * RF(0.5);
-    rreal xm = st->x + h;
+    rreal xm = *x + h;
     rreal ym = y + h * (s0 / c0);
     rreal zm = z + h * (t / c0);
     rreal r2 = xm * xm + ym * ym;
@@ -170,13 +173,24 @@ static int rf_prop(const rf_ctx* c, rf_state* st, rreal x1)
     rreal fp = u * (RF(1.0 / 3.0) + u2 * RF(0.3));
     rreal jcq = t * (g * w * jb + L * L * RF(0.5) * fp * kB);
 
-    rreal J[5][5];
-    memset(J, 0, sizeof J);
-    for (int i = 0; i < 5; i++) J[i][i] = RF(1);
     J[0][2] = ja;  J[0][4] = jb;
     J[1][2] = jcs; J[1][3] = arc; J[1][4] = jcq;
     J[2][4] = hq;
 
+    *x = x1;
+    p[0] = y + dy;
+    p[1] = z + dz;
+    p[2] = s1;
+    return 1;
+}
+
+static int rf_prop(const rf_ctx* c, rf_state* st, rreal x1)
+{
+    if (x1 - st->x == RF(0)) return 1;
+    rreal J[5][5];
+    rreal x = st->x, p[5];
+    for (int i = 0; i < 5; i++) p[i] = st->p[i];
+    if (!rf_step(c, &x, p, J, x1)) return 0;
     /* S1 = J S */
     rreal S1[5][5];
     for (int i = 0; i < 5; i++)
@@ -186,11 +200,8 @@ static int rf_prop(const rf_ctx* c, rf_state* st, rreal x1)
             S1[i][j] = acc;
         }
     memcpy(st->S, S1, sizeof S1);
-
-    st->x = x1;
-    st->p[0] = y + dy;
-    st->p[1] = z + dz;
-    st->p[2] = s1;
+    st->x = x;
+    for (int i = 0; i < 5; i++) st->p[i] = p[i];
     return 1;
 }
 
@@ -346,4 +357,285 @@ void orc_refit_update(const orc_fit_params* p, double* v, double my, double mz, 
     rf_update(&c, &st, RF(my), RF(mz), &c2);
     rf_pack(&st, v);
     *chi2 = (double)c2;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Phase II track merging (Sec. 2 step 3; Table 1 row 3: "matching           */
+/* covariance").  Readings M1-M6 of the design notes:                        */
+/*   M1 candidates: two refitted tracks (status 0) of one event, A inner, B  */
+/*      outer: in one sector with x_last(A) < x_first(B) <= x_last(A) + gap  */
+/*      (a gap the track following did not cover), or in adjacent sectors of */
+/*      one side with x_last(A) - overlap <= x_first(B) <= x_last(A) + gap   */
+/*      (the sector border);                                                 */
+/*   M2 A's refit state (at its innermost cluster) is propagated with its    */
+/*      covariance (C <- J C J^T) to x_first(B); across a border it is first */
+/*      propagated to x_last(A), rotated into B's frame (M3), then to        */
+/*      x_first(B);                                                          */
+/*   M3 rotation by theta = alpha_B - alpha_A (+-20 deg): the point and the  */
+/*      direction rotate (x' = x cos + y sin, y' = y cos - x sin,            */
+/*      phi' = phi - theta), the state is referred to the plane through the  */
+/*      rotated point; Jacobian dy'/dy = cos phi / cos phi',                  */
+/*      dz'/dy = -t sin(theta) / cos phi', ds'/dy = -k sin(theta) (k of the  */
+/*      uniform field), ds'/ds = cos phi' / cos phi; fails unless cos phi' > 0*/
+/*      and |sin phi'| <= s_max;                                             */
+/*   M4 compatibility chi2 = d^T (C_A + C_B)^-1 d, d = p_A - p_B, by a       */
+/*      Cholesky factorisation and a forward solve; compatible iff every     */
+/*      step succeeds, the sum is positive definite and chi2 <= chi2_max;    */
+/*   M5 A and B are merged iff B is A's best outer candidate and A is B's    */
+/*      best inner candidate (smallest chi2, ties by the smaller track       */
+/*      index): each track has at most one outer and one inner partner, the  */
+/*      links form chains ordered by x_first;                                */
+/*   M6 output per track: the index of its outer partner (-1: none) and the */
+/*      link's chi2.                                                         */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    double chi2_max;
+    double gap;        /* cm */
+    double overlap;    /* cm */
+    double cos_t;      /* cos and sin of the angle between adjacent sectors */
+    double sin_t;
+} orc_merge_params;
+
+typedef struct {
+    rreal x;
+    rreal p[5];
+    rreal C[5][5];
+} mg_state;
+
+/* C <- J C J^T, sums in index order */
+static void mg_transport(rreal C[5][5], rreal J[5][5])
+{
+    rreal F[5][5], C1[5][5];
+    for (int i = 0; i < 5; i++)
+        for (int j = 0; j < 5; j++) {
+            rreal acc = J[i][0] * C[0][j];
+            for (int m = 1; m < 5; m++) acc = acc + J[i][m] * C[m][j];
+            F[i][j] = acc;
+        }
+    for (int i = 0; i < 5; i++)
+        for (int j = 0; j < 5; j++) {
+            rreal acc = F[i][0] * J[j][0];
+            for (int m = 1; m < 5; m++) acc = acc + F[i][m] * J[j][m];
+            C1[i][j] = acc;
+        }
+    for (int i = 0; i < 5; i++)
+        for (int j = 0; j <= i; j++) { C[i][j] = C1[i][j]; C[j][i] = C1[i][j]; }
+}
+
+static int mg_prop(const rf_ctx* c, mg_state* st, rreal x1)
+{
+    if (x1 - st->x == RF(0)) return 1;
+    rreal J[5][5];
+    if (!rf_step(c, &st->x, st->p, J, x1)) return 0;
+    mg_transport(st->C, J);
+    return 1;
+}
+
+/* M3: rotate the state into the frame turned by theta (cos ct, sin st_). */
+static int mg_rotate(const rf_ctx* c, mg_state* st, rreal ct, rreal stt)
+{
+    rreal x = st->x, y = st->p[0], s = st->p[2], t = st->p[3], q = st->p[4];
+    if (f_fabs(s) > c->s_max) return 0;
+    rreal cs = f_sqrt(RF(1) - s * s);
+    rreal xb = x * ct + y * stt;
+    rreal yb = y * ct - x * stt;
+    rreal sb = s * ct - cs * stt;
+    rreal cb = cs * ct + s * stt;
+    if (!(cb > RF(0)) || f_fabs(sb) > c->s_max) return 0;
+    rreal J[5][5];
+    memset(J, 0, sizeof J);
+    for (int i = 0; i < 5; i++) J[i][i] = RF(1);
+    J[0][0] = cs / cb;
+    J[1][0] = -(t * stt) / cb;
+    J[2][0] = -(c->kB0 * q * stt);
+    J[2][2] = cb / cs;
+    mg_transport(st->C, J);
+    st->x = xb;
+    st->p[0] = yb;
+    st->p[2] = sb;
+    return 1;
+}
+
+/* M4: chi2 of d = pa - pb with covariance Ca + Cb; 0 when not positive
+ * definite. */
+static int mg_chi2(const mg_state* a, const mg_state* b, rreal* chi2)
+{
+    rreal C[5][5], L[5][5], d[5], w[5];
+    memset(L, 0, sizeof L);
+    for (int i = 0; i < 5; i++) {
+        d[i] = a->p[i] - b->p[i];
+        for (int j = 0; j < 5; j++) C[i][j] = a->C[i][j] + b->C[i][j];
+    }
+    for (int j = 0; j < 5; j++) {
+        rreal acc = C[j][j];
+        for (int m = 0; m < j; m++) acc = acc - L[j][m] * L[j][m];
+        if (!(acc > RF(0))) return 0;
+        L[j][j] = f_sqrt(acc);
+        for (int i = j + 1; i < 5; i++) {
+            rreal v = C[i][j];
+            for (int m = 0; m < j; m++) v = v - L[i][m] * L[j][m];
+            L[i][j] = v / L[j][j];
+        }
+    }
+    rreal sum = RF(0);
+    for (int i = 0; i < 5; i++) {
+        rreal v = d[i];
+        for (int m = 0; m < i; m++) v = v - L[i][m] * w[m];
+        w[i] = v / L[i][i];
+        sum = sum + w[i] * w[i];
+    }
+    *chi2 = sum;
+    return 1;
+}
+
+static void mg_from_fit(const double* f, mg_state* st)
+{
+    st->x = RF(f[0]);
+    for (int i = 0; i < 5; i++) st->p[i] = RF(f[1 + i]);
+    for (int i = 0, k = 0; i < 5; i++)
+        for (int j = 0; j <= i; j++, k++) { st->C[i][j] = RF(f[6 + k]); st->C[j][i] = RF(f[6 + k]); }
+}
+
+/* M1-M4 for one candidate pair; rot = 0 (same sector), +1 (B is the next
+ * sector, theta = +20 deg), -1 (previous sector).  Returns 1 if compatible. */
+static int mg_pair(const rf_ctx* c, const orc_merge_params* mp, const double* fa, double xa_last,
+                   const double* fb, int rot, rreal* chi2)
+{
+    mg_state a, b;
+    mg_from_fit(fa, &a);
+    mg_from_fit(fb, &b);
+    if (rot != 0) {
+        if (!mg_prop(c, &a, RF(xa_last))) return 0;
+        rreal ct = RF(mp->cos_t), stt = rot > 0 ? RF(mp->sin_t) : -RF(mp->sin_t);
+        if (!mg_rotate(c, &a, ct, stt)) return 0;
+    }
+    if (!mg_prop(c, &a, b.x)) return 0;
+    if (!mg_chi2(&a, &b, chi2)) return 0;
+    return *chi2 <= RF(mp->chi2_max);
+}
+
+/* M1: is B a candidate outer partner of A?  Returns rot + 2 (1..3) or 0. */
+static int mg_candidate(const orc_merge_params* mp, int n_sectors, int ua, int ub, const double* fa,
+                        double xa_last, const double* fb)
+{
+    if (fa[23] != 0.0 || fb[23] != 0.0) return 0;
+    int half = n_sectors / 2;
+    int ea = ua / n_sectors, eb = ub / n_sectors;
+    if (ea != eb) return 0;
+    int sa = ua % n_sectors, sb = ub % n_sectors;
+    if (sa / half != sb / half) return 0;  /* same side */
+    rreal xl = RF(xa_last), xf = RF(fb[0]);
+    rreal gap = RF(mp->gap), ov = RF(mp->overlap);
+    if (sa == sb) return (xl < xf && xf <= xl + gap) ? 2 : 0;
+    int la = sa % half, lb = sb % half;
+    int rot = 0;
+    if (lb == (la + 1) % half) rot = 1;
+    else if (lb == (la + half - 1) % half) rot = -1;
+    else return 0;
+    return (xl - ov <= xf && xf <= xl + gap) ? rot + 2 : 0;
+}
+
+/* Merge links of M refitted tracks (canonical order: grouped by unit).
+ * unit[M] = event * n_sectors + sector; fits[M][RF_NOUT]; x_last[M] = x of
+ * each track's outermost cluster.  next[M]: outer partner or -1; chi2[M]. */
+void orc_merge_tracks(const orc_fit_params* p, const orc_merge_params* mp, int M, int n_sectors,
+                      const int32_t* unit, const double* fits, const double* x_last, int32_t* next,
+                      double* chi2, int n_threads)
+{
+    rf_ctx c;
+    rf_ctx_init(&c, p);
+    int n_units = M ? unit[M - 1] + 1 : 0;
+    int* first = (int*)calloc((size_t)n_units + 2, sizeof(int));
+    for (int u = 0, m = 0; u <= n_units; u++) {
+        while (m < M && unit[m] < u) m++;
+        first[u] = m;
+    }
+    double* bo = (double*)malloc(sizeof(double) * ((size_t)M + 1));
+    double* bi = (double*)malloc(sizeof(double) * ((size_t)M + 1));
+    int* io = (int*)malloc(sizeof(int) * ((size_t)M + 1));
+    int* ii = (int*)malloc(sizeof(int) * ((size_t)M + 1));
+    for (int m = 0; m < M; m++) { io[m] = -1; ii[m] = -1; }
+    int half = n_sectors / 2;
+    (void)n_threads;
+    /* candidate units of A's outer partners: its own and the two neighbours */
+    for (int a = 0; a < M; a++) {
+        int ua = unit[a], e = ua / n_sectors, sa = ua % n_sectors;
+        int base = (sa / half) * half, la = sa % half;
+        int us[3] = {ua, e * n_sectors + base + (la + 1) % half, e * n_sectors + base + (la + half - 1) % half};
+        for (int k = 0; k < 3; k++) {
+            int ub = us[k];
+            if (k > 0 && (ub >= n_units || us[2] == us[1] && k == 2)) continue;
+            for (int b = first[ub]; b < first[ub + 1]; b++) {
+                if (b == a) continue;
+                int cnd = mg_candidate(mp, n_sectors, ua, ub, fits + (size_t)a * RF_NOUT, x_last[a],
+                                       fits + (size_t)b * RF_NOUT);
+                if (!cnd) continue;
+                rreal x2;
+                if (!mg_pair(&c, mp, fits + (size_t)a * RF_NOUT, x_last[a], fits + (size_t)b * RF_NOUT,
+                             cnd - 2, &x2))
+                    continue;
+                double v = (double)x2;
+                if (io[a] < 0 || v < bo[a] || (v == bo[a] && b < io[a])) { bo[a] = v; io[a] = b; }
+                if (ii[b] < 0 || v < bi[b] || (v == bi[b] && a < ii[b])) { bi[b] = v; ii[b] = a; }
+            }
+        }
+    }
+    for (int a = 0; a < M; a++) {
+        int b = io[a];
+        if (b >= 0 && ii[b] == a) { next[a] = b; chi2[a] = bo[a]; }
+        else { next[a] = -1; chi2[a] = 0.0; }
+    }
+    free(first); free(bo); free(bi); free(io); free(ii);
+}
+
+/* Single-step entries for the pins: a merge vector is x, p[5], C[5][5]
+ * row-major (31 doubles). */
+static void mg_unpack(const double* v, mg_state* st)
+{
+    st->x = RF(v[0]);
+    for (int i = 0; i < 5; i++) st->p[i] = RF(v[1 + i]);
+    for (int i = 0; i < 5; i++)
+        for (int j = 0; j < 5; j++) st->C[i][j] = RF(v[6 + 5 * i + j]);
+}
+
+static void mg_pack(const mg_state* st, double* v)
+{
+    v[0] = (double)st->x;
+    for (int i = 0; i < 5; i++) v[1 + i] = (double)st->p[i];
+    for (int i = 0; i < 5; i++)
+        for (int j = 0; j < 5; j++) v[6 + 5 * i + j] = (double)st->C[i][j];
+}
+
+int orc_merge_rotate(const orc_fit_params* p, double* v, double cos_t, double sin_t)
+{
+    rf_ctx c;
+    rf_ctx_init(&c, p);
+    mg_state st;
+    mg_unpack(v, &st);
+    int ok = mg_rotate(&c, &st, RF(cos_t), RF(sin_t));
+    mg_pack(&st, v);
+    return ok;
+}
+
+int orc_merge_propagate(const orc_fit_params* p, double* v, double x1)
+{
+    rf_ctx c;
+    rf_ctx_init(&c, p);
+    mg_state st;
+    mg_unpack(v, &st);
+    int ok = mg_prop(&c, &st, RF(x1));
+    mg_pack(&st, v);
+    return ok;
+}
+
+int orc_merge_chi2(const double* va, const double* vb, double* chi2)
+{
+    mg_state a, b;
+    mg_unpack(va, &a);
+    mg_unpack(vb, &b);
+    rreal x2 = RF(0);
+    int ok = mg_chi2(&a, &b, &x2);
+    *chi2 = (double)x2;
+    return ok;
 }
