@@ -41,7 +41,7 @@ class FitParams(C.Structure):
 
 
 class MergeParams(C.Structure):
-    _fields_ = [(n, C.c_double) for n in ("chi2_max", "gap", "overlap", "cos_t", "sin_t")]
+    _fields_ = [(n, C.c_double) for n in ("chi2_max", "gap", "overlap", "window", "cos_t", "sin_t")]
 
 
 class Geom(C.Structure):
@@ -295,10 +295,10 @@ def refit_update(v, my, mz, fp, mode="f64", chi2=0.0):
 
 # track merging (tpc_refit.c, Phase II) -------------------------------------
 
-def merge_params(chi2_max=30.0, gap=50.0, overlap=5.0, angle_deg=20.0) -> MergeParams:
+def merge_params(chi2_max=30.0, gap=50.0, overlap=5.0, window=5.0, angle_deg=20.0) -> MergeParams:
     import math
     m = MergeParams()
-    m.chi2_max, m.gap, m.overlap = chi2_max, gap, overlap
+    m.chi2_max, m.gap, m.overlap, m.window = chi2_max, gap, overlap, window
     m.cos_t = float(np.float32(math.cos(math.radians(angle_deg))))
     m.sin_t = float(np.float32(math.sin(math.radians(angle_deg))))
     return m

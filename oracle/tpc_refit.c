@@ -380,7 +380,8 @@ void orc_refit_update(const orc_fit_params* p, double* v, double my, double mz, 
 /*      and |sin phi'| <= s_max;                                             */
 /*   M4 compatibility chi2 = d^T (C_A + C_B)^-1 d, d = p_A - p_B, by a       */
 /*      Cholesky factorisation and a forward solve; compatible iff every     */
-/*      step succeeds, the sum is positive definite and chi2 <= chi2_max;    */
+/*      step succeeds, |d_y| <= window and |d_z| <= window (cm), the sum is  */
+/*      positive definite and chi2 <= chi2_max;                              */
 /*   M5 A and B are merged iff B is A's best outer candidate and A is B's    */
 /*      best inner candidate (smallest chi2, ties by the smaller track       */
 /*      index): each track has at most one outer and one inner partner, the  */
@@ -393,6 +394,7 @@ typedef struct {
     double chi2_max;
     double gap;        /* cm */
     double overlap;    /* cm */
+    double window;     /* cm */
     double cos_t;      /* cos and sin of the angle between adjacent sectors */
     double sin_t;
 } orc_merge_params;
@@ -511,6 +513,8 @@ static int mg_pair(const rf_ctx* c, const orc_merge_params* mp, const double* fa
         if (!mg_rotate(c, &a, ct, stt)) return 0;
     }
     if (!mg_prop(c, &a, b.x)) return 0;
+    rreal w = RF(mp->window);
+    if (!(f_fabs(a.p[0] - b.p[0]) <= w) || !(f_fabs(a.p[1] - b.p[1]) <= w)) return 0;
     if (!mg_chi2(&a, &b, chi2)) return 0;
     return *chi2 <= RF(mp->chi2_max);
 }

@@ -267,6 +267,15 @@ def test_candidate_geometry():
     for ub in (36, 18, 2):
         nxt, _ = oracle.merge_tracks(np.array([0, ub]), fits, np.array([120.0, 190.0]), fp)
         assert nxt[0] == -1
+    # outside the y window (5 cm) after propagation: never, whatever the chi2
+    far = pb.copy()
+    far[0] += 5.5
+    fw = np.array([_fit_row(100.0, pa), _fit_row(xb, far, var=100.0)])
+    nxt, _ = oracle.merge_tracks(np.zeros(2, np.int32), fw, np.array([120.0, 190.0]), fp)
+    assert nxt[0] == -1
+    nxt, _ = oracle.merge_tracks(np.zeros(2, np.int32), fw, np.array([120.0, 190.0]), fp,
+                                 mp=oracle.merge_params(window=6.0))
+    assert nxt[0] == 1
     # a failed fit never merges
     f2 = fits.copy()
     f2[1, 23] = 1
