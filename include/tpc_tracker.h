@@ -129,6 +129,15 @@ typedef struct {
                                            + rho^2 (b3 + z (b4 + z b5)),
                                 rho^2 = x^2 + y^2, field = {b1..b5} in T/cm^n;
                                 all zero (default): the uniform field bz       */
+    /* track merging (Sec. 2 Phase II step 3, Table 1 row 3); needs refit = 1 */
+    int merge;               /* 1: link track segments after the refit (tpc_merge
+                                output); 0: no merging (default)                */
+    float merge_chi2;        /* compatibility cut on the matching chi2 (30)     */
+    float merge_gap;         /* an outer partner starts at most this far (cm)
+                                beyond the inner segment's last cluster (50)    */
+    float merge_overlap;     /* across a sector border the outer segment may
+                                start this much (cm) before the inner one ends (5) */
+    float merge_window;      /* |dy| and |dz| of the propagated states (cm) (5) */
 } tpc_params;
 
 /* A selected track: the best tracklet instance (Sec. 2 step 2), with the
@@ -165,8 +174,25 @@ typedef struct {
                                 reached is kept                                 */
 } tpc_fit;
 
-/* Output buffers, caller-owned.  mem_kind says where tracks, hit_ids and
- * fits live.  hit_ids are positions in the call's cluster array, rows
+/* Merge link of a track (Sec. 2 Phase II step 3: track segments merged in a
+ * sector across a gap the following did not cover, and across sector
+ * borders, by comparing parameters with their covariances).  Candidates: an
+ * outer segment B of the same event, in the same sector with
+ * x_last(A) < x_first(B) <= x_last(A) + merge_gap, or in an adjacent sector of
+ * the same side with x_last(A) - merge_overlap <= x_first(B) <= x_last(A) +
+ * merge_gap.  A's refit state is propagated with its covariance to
+ * x_first(B) (across a border: to its last cluster, rotated by 20 degrees into
+ * B's frame, then on); compatible when |dy|, |dz| <= merge_window and
+ * chi2 = d^T (C_A + C_B)^-1 d <= merge_chi2.  A and B are linked when each is
+ * the other's best compatible candidate (smallest chi2, ties by the smaller
+ * track index), so the links form chains of segments ordered outward. */
+typedef struct {
+    int32_t next;            /* index of the outer partner track, -1: none      */
+    float chi2;              /* chi2 of that link (0 without one)               */
+} tpc_merge;
+
+/* Output buffers, caller-owned.  mem_kind says where tracks, hit_ids, fits
+ * and merges live.  hit_ids are positions in the call's cluster array, rows
  * ascending within a track; tracks are in canonical tracklet order. */
 typedef struct {
     tpc_track* tracks;
@@ -179,6 +205,8 @@ typedef struct {
     tpc_fit* fits;           /* optional, [cap_tracks]: fits[m] is the refit of
                                 tracks[m]; written only when params.refit = 1
                                 (NULL: not copied)                              */
+    tpc_merge* merges;       /* optional, [cap_tracks]: merge link of tracks[m];
+                                written only when params.merge = 1              */
 } tpc_output;
 
 typedef struct tpc_tracker tpc_tracker;
@@ -276,6 +304,7 @@ typedef struct {
     const tpc_track* tracks;
     const int32_t* hit_ids;
     const tpc_fit* fits;     /* NULL unless params.refit = 1                    */
+    const tpc_merge* merges; /* NULL unless params.merge = 1                    */
     int32_t n_tracks;
     int32_t n_hits;
 } tpc_stream_view;
@@ -332,8 +361,8 @@ int tpc_debug_dump(tpc_tracker* tr, int what, void* dst, int64_t cap, int64_t* n
 /* Device time of each stage of the last call, in milliseconds, measured
  * with CUDA events on the launching stream: [0] grid build, [1] neighbours,
  * [2] clean + start hits, [3] tracklet construction, [4] selection + output,
- * [5] whole call, [6] final refit (0 when params.refit = 0).  n = entries
- * wanted (<= 7). */
+ * [5] whole call, [6] final refit and merging (0 when params.refit = 0).
+ * n = entries wanted (<= 7). */
 int tpc_stage_times(tpc_tracker* tr, float* ms, int n);
 
 /* One-line description of the last error on tr (or of the last failed

@@ -56,7 +56,9 @@ class tpc_params(C.Structure):
                 ("exact_fp32", C.c_int), ("bin_target", C.c_float),
                 ("threads_per_row", C.c_int), ("tracklets_per_warp", C.c_int),
                 ("plain_per_sector", C.c_int), ("use_graph", C.c_int), ("n_queues", C.c_int),
-                ("schedule", C.c_int), ("refit", C.c_int), ("field", C.c_float * 5)]
+                ("schedule", C.c_int), ("refit", C.c_int), ("field", C.c_float * 5),
+                ("merge", C.c_int), ("merge_chi2", C.c_float), ("merge_gap", C.c_float),
+                ("merge_overlap", C.c_float), ("merge_window", C.c_float)]
 
 
 class tpc_track(C.Structure):
@@ -71,10 +73,14 @@ class tpc_fit(C.Structure):
                 ("chi2", C.c_float), ("ndf", C.c_int32), ("status", C.c_int32)]
 
 
+class tpc_merge(C.Structure):
+    _fields_ = [("next", C.c_int32), ("chi2", C.c_float)]
+
+
 class tpc_output(C.Structure):
     _fields_ = [("tracks", C.c_void_p), ("hit_ids", C.c_void_p), ("cap_tracks", C.c_int32),
                 ("cap_hits", C.c_int32), ("mem_kind", C.c_int32), ("n_tracks", C.c_int32),
-                ("n_hits", C.c_int32), ("fits", C.c_void_p)]
+                ("n_hits", C.c_int32), ("fits", C.c_void_p), ("merges", C.c_void_p)]
 
 
 class tpc_stream_stats(C.Structure):
@@ -86,7 +92,7 @@ class tpc_stream_stats(C.Structure):
 
 class tpc_stream_view(C.Structure):
     _fields_ = [("tracks", C.c_void_p), ("hit_ids", C.c_void_p), ("fits", C.c_void_p),
-                ("n_tracks", C.c_int32), ("n_hits", C.c_int32)]
+                ("merges", C.c_void_p), ("n_tracks", C.c_int32), ("n_hits", C.c_int32)]
 
 
 _LIB = None

@@ -580,13 +580,14 @@ __global__ void k_rebase(KConst k, DevPtrs p)
         const int rr0 = b_ev * k.n_sectors * k.n_rows;
         const int b_cl = p.row_off[rr0];
         const int b_t = p.start_off[rr0];
-        const int b_h = (p.acc_scan[b_t] + p.scan_part[b_t / kScanTile]).y;
+        const int2 b_mh = p.acc_scan[b_t] + p.scan_part[b_t / kScanTile];
         for (int j = lane; j < n; j += 32) p.out_hits[h0 + j] -= b_cl;
         __syncwarp();
         if (lane == 0) {
             tk.event = ev - b_ev;
             tk.tracklet -= b_t;
-            tk.hit_off = h0 - b_h;
+            tk.hit_off = h0 - b_mh.y;
+            if (k.mg_on && p.out_merges[m].next >= 0) p.out_merges[m].next -= b_mh.x;
         }
     }
 }

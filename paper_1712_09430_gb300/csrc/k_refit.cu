@@ -53,13 +53,19 @@ struct Fit {
     float chi2;
 };
 
-// One step to the plane x1.  false (state untouched) when |sin phi| exceeds
-// s_max before or after the step.
-__device__ __forceinline__ bool fit_propagate(Fit& f, float x1, const KConst& k)
+// Off-identity entries of the step's Jacobian (rows y, z, s; columns by
+// name): dy/ds ja, dy/dq jb, dz/ds jcs, dz/dt arc, dz/dq jcq, ds/dq hq.
+struct StepJ {
+    float ja, jb, jcs, arc, jcq, hq;
+};
+
+// One step of the state (x, p) to the plane x1 and its Jacobian.  false
+// (state untouched) when |sin phi| exceeds s_max before or after the step.
+// Call only with x1 != x.
+__device__ __forceinline__ bool fit_step(float& x, float* p, float x1, const KConst& k, StepJ& J)
 {
-    const float d = x1 - f.x;
-    if (d == 0.0f) return true;
-    const float y = f.p[0], z = f.p[1], s0 = f.p[2], t = f.p[3], q = f.p[4];
+    const float d = x1 - x;
+    const float y = p[0], z = p[1], s0 = p[2], t = p[3], q = p[4];
     if (fabsf(s0) > k.s_max) return false;
 #if TPC_FAST_MATH
     const float e0 = 1.0f - s0 * s0;
@@ -72,7 +78,7 @@ __device__ __forceinline__ bool fit_propagate(Fit& f, float x1, const KConst& k)
 #endif
     // field at the straight-line midpoint of the step
     const float h = d * 0.5f;
-    const float xm = f.x + h;
+    const float xm = x + h;
     const float ym = y + h * s0c0;
     const float zm = z + h * tc0;
     const float r2 = xm * xm + ym * ym;
@@ -123,19 +129,33 @@ __device__ __forceinline__ bool fit_propagate(Fit& f, float x1, const KConst& k)
     const float fpu = u * ((float)(1.0 / 3.0) + u2 * 0.3f);
     const float jcq = t * (g * w * jb + L * L * 0.5f * fpu * kB);
 
-    // S <- J S: rows y, z, s change (rows y and z read the old row s)
+    J.ja = ja;
+    J.jb = jb;
+    J.jcs = jcs;
+    J.arc = arc;
+    J.jcq = jcq;
+    J.hq = hq;
+    x = x1;
+    p[0] = y + dy;
+    p[1] = z + dz;
+    p[2] = s1;
+    return true;
+}
+
+// Refit step: the state and the covariance factor, S <- J S (rows y, z, s
+// change; rows y and z read the old row s).
+__device__ __forceinline__ bool fit_propagate(Fit& f, float x1, const KConst& k)
+{
+    if (x1 - f.x == 0.0f) return true;
+    StepJ J;
+    if (!fit_step(f.x, f.p, x1, k, J)) return false;
 #pragma unroll
     for (int j = 0; j < 5; j++) {
         const float s2 = f.S[10 + j], s3 = f.S[15 + j], s4 = f.S[20 + j];
-        f.S[j] = f.S[j] + ja * s2 + jb * s4;
-        f.S[5 + j] = f.S[5 + j] + jcs * s2 + arc * s3 + jcq * s4;
-        f.S[10 + j] = s2 + hq * s4;
+        f.S[j] = f.S[j] + J.ja * s2 + J.jb * s4;
+        f.S[5 + j] = f.S[5 + j] + J.jcs * s2 + J.arc * s3 + J.jcq * s4;
+        f.S[10 + j] = s2 + J.hq * s4;
     }
-
-    f.x = x1;
-    f.p[0] = y + dy;
-    f.p[1] = z + dz;
-    f.p[2] = s1;
     return true;
 }
 
@@ -346,6 +366,300 @@ cudaError_t launch_refit(const KConst& k, const DevPtrs& p, int n_sm, cudaStream
     k_fit_offsets<<<1, 32, 0, s>>>(p, bins);
     k_fit_scatter<<<n_sm * 2, 256, 0, s>>>(p, bins);
     k_refit<<<n_sm * kRefitCtasPerSm, kRefitThreads, 0, s>>>(k, p);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ track merging
+// Sec. 2 Phase II step 3 (Table 1 row 3, "matching covariance"): segments of
+// one track, split by a gap the following did not cover or by a sector
+// border, are linked by comparing their refitted parameters with the
+// covariances.  For an inner segment A and an outer candidate B (same event;
+// same sector with x_last(A) < x_first(B) <= x_last(A) + gap, or an adjacent
+// sector of the same side with x_last(A) - overlap <= x_first(B) <=
+// x_last(A) + gap), A's refit state is carried with C <- J C J^T to
+// x_first(B) (across a border: to x_last(A), rotated into B's frame, then on);
+// compatible when |dy|, |dz| <= window and chi2 = d^T (C_A + C_B)^-1 d <=
+// chi2_max (Cholesky and a forward solve).  A and B are linked when each is
+// the other's best compatible candidate (smallest chi2, ties by the smaller
+// track index).  Every sum runs in index order, as in an FP32 CPU evaluation.
+
+// Full symmetric 5x5 covariance in packed lower storage (i (i + 1) / 2 + j).
+struct Cov {
+    float c[15];
+};
+
+__device__ __forceinline__ float cget(const Cov& C, int i, int j)
+{
+    return i >= j ? C.c[i * (i + 1) / 2 + j] : C.c[j * (j + 1) / 2 + i];
+}
+
+// C <- J C J^T for a step's Jacobian (F = J C: rows y, z, s change).
+__device__ __forceinline__ void cov_step(Cov& C, const StepJ& J)
+{
+    const float* c = C.c;
+    const float C00 = c[0], C10 = c[1], C11 = c[2], C20 = c[3], C21 = c[4], C22 = c[5];
+    const float C30 = c[6], C31 = c[7], C32 = c[8], C33 = c[9];
+    const float C40 = c[10], C41 = c[11], C42 = c[12], C43 = c[13], C44 = c[14];
+    const float ja = J.ja, jb = J.jb, jcs = J.jcs, arc = J.arc, jcq = J.jcq, hq = J.hq;
+    const float F00 = C00 + ja * C20 + jb * C40;
+    const float F02 = C20 + ja * C22 + jb * C42;
+    const float F04 = C40 + ja * C42 + jb * C44;
+    const float F10 = C10 + jcs * C20 + arc * C30 + jcq * C40;
+    const float F11 = C11 + jcs * C21 + arc * C31 + jcq * C41;
+    const float F12 = C21 + jcs * C22 + arc * C32 + jcq * C42;
+    const float F13 = C31 + jcs * C32 + arc * C33 + jcq * C43;
+    const float F14 = C41 + jcs * C42 + arc * C43 + jcq * C44;
+    const float F20 = C20 + hq * C40;
+    const float F21 = C21 + hq * C41;
+    const float F22 = C22 + hq * C42;
+    const float F23 = C32 + hq * C43;
+    const float F24 = C42 + hq * C44;
+    C.c[0] = F00 + ja * F02 + jb * F04;
+    C.c[1] = F10 + ja * F12 + jb * F14;
+    C.c[2] = F11 + jcs * F12 + arc * F13 + jcq * F14;
+    C.c[3] = F20 + ja * F22 + jb * F24;
+    C.c[4] = F21 + jcs * F22 + arc * F23 + jcq * F24;
+    C.c[5] = F22 + hq * F24;
+    C.c[6] = C30 + ja * C32 + jb * C43;
+    C.c[7] = C31 + jcs * C32 + arc * C33 + jcq * C43;
+    C.c[8] = C32 + hq * C43;
+    C.c[9] = C33;
+    C.c[10] = C40 + ja * C42 + jb * C44;
+    C.c[11] = C41 + jcs * C42 + arc * C43 + jcq * C44;
+    C.c[12] = C42 + hq * C44;
+    C.c[13] = C43;
+    C.c[14] = C44;
+}
+
+// State and covariance to x1.
+__device__ __forceinline__ bool mg_prop(float& x, float* p, Cov& C, float x1, const KConst& k)
+{
+    if (x1 - x == 0.0f) return true;
+    StepJ J;
+    if (!fit_step(x, p, x1, k, J)) return false;
+    cov_step(C, J);
+    return true;
+}
+
+// Rotation into the frame turned by theta (cos ct, sin st): the point and the
+// direction turn, the state refers to the plane through the rotated point;
+// Jacobian: dy'/dy = c / c', dz'/dy = -t st / c', ds'/dy = -k st (uniform
+// field), ds'/ds = c' / c.
+__device__ __forceinline__ bool mg_rotate(float& x, float* p, Cov& C, float ct, float st, const KConst& k)
+{
+    const float y = p[0], s = p[2], t = p[3], q = p[4];
+    if (fabsf(s) > k.s_max) return false;
+    const float cs = sqrtf(1.0f - s * s);
+    const float xb = x * ct + y * st;
+    const float yb = y * ct - x * st;
+    const float sb = s * ct - cs * st;
+    const float cb = cs * ct + s * st;
+    if (!(cb > 0.0f) || fabsf(sb) > k.s_max) return false;
+#if TPC_FAST_MATH
+    const float icb = __fdividef(1.0f, cb);
+    const float j00 = cs * icb;
+    const float j10 = -(t * st) * icb;
+    const float j22 = __fdividef(cb, cs);
+#else
+    const float j00 = cs / cb;
+    const float j10 = -(t * st) / cb;
+    const float j22 = cb / cs;
+#endif
+    const float j20 = -(k.kB * q * st);
+    // F = J C: F0j = j00 C0j, F1j = j10 C0j + C1j, F2j = j20 C0j + j22 C2j,
+    // F3j = C3j, F4j = C4j; C' = F J^T
+    float F[5][5];
+#pragma unroll
+    for (int j = 0; j < 5; j++) {
+        const float c0 = cget(C, 0, j), c1 = cget(C, 1, j), c2 = cget(C, 2, j);
+        F[0][j] = j00 * c0;
+        F[1][j] = j10 * c0 + c1;
+        F[2][j] = j20 * c0 + j22 * c2;
+        F[3][j] = cget(C, 3, j);
+        F[4][j] = cget(C, 4, j);
+    }
+#pragma unroll
+    for (int i = 0; i < 5; i++) {
+        C.c[i * (i + 1) / 2 + 0] = F[i][0] * j00;
+        if (i >= 1) C.c[i * (i + 1) / 2 + 1] = F[i][0] * j10 + F[i][1];
+        if (i >= 2) C.c[i * (i + 1) / 2 + 2] = F[i][0] * j20 + F[i][2] * j22;
+        if (i >= 3) C.c[i * (i + 1) / 2 + 3] = F[i][3];
+        if (i >= 4) C.c[i * (i + 1) / 2 + 4] = F[i][4];
+    }
+    x = xb;
+    p[0] = yb;
+    p[2] = sb;
+    return true;
+}
+
+// chi2 of d = pa - pb with covariance Ca + Cb; false unless positive definite.
+__device__ __forceinline__ bool mg_chi2(const float* pa, const Cov& Ca, const float* pb, const Cov& Cb,
+                                        float& chi2)
+{
+    float L[15];
+    float d[5];
+#pragma unroll
+    for (int i = 0; i < 5; i++) d[i] = pa[i] - pb[i];
+#pragma unroll
+    for (int j = 0; j < 5; j++) {
+        float acc = Ca.c[j * (j + 1) / 2 + j] + Cb.c[j * (j + 1) / 2 + j];
+#pragma unroll
+        for (int m = 0; m < j; m++) acc = acc - L[j * (j + 1) / 2 + m] * L[j * (j + 1) / 2 + m];
+        if (!(acc > 0.0f)) return false;
+        const float ljj = sqrtf(acc);
+        L[j * (j + 1) / 2 + j] = ljj;
+#pragma unroll
+        for (int i = j + 1; i < 5; i++) {
+            float v = Ca.c[i * (i + 1) / 2 + j] + Cb.c[i * (i + 1) / 2 + j];
+#pragma unroll
+            for (int m = 0; m < j; m++) v = v - L[i * (i + 1) / 2 + m] * L[j * (j + 1) / 2 + m];
+            L[i * (i + 1) / 2 + j] = v / ljj;
+        }
+    }
+    float w[5];
+    float sum = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 5; i++) {
+        float v = d[i];
+#pragma unroll
+        for (int m = 0; m < i; m++) v = v - L[i * (i + 1) / 2 + m] * w[m];
+        w[i] = v / L[i * (i + 1) / 2 + i];
+        sum = sum + w[i] * w[i];
+    }
+    chi2 = sum;
+    return true;
+}
+
+// First track of every (event, sector) unit: the exclusive scan of accepted
+// tracklets at the unit's first canonical tracklet.
+__global__ void k_unit_first(KConst k, DevPtrs p)
+{
+    const int T = p.counters[C_T], M = p.counters[C_M];
+    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u <= p.n_units; u += gridDim.x * blockDim.x) {
+        const int t = p.start_off[u * k.n_rows];
+        p.unit_first[u] = t < T ? p.acc_scan[t].x + p.scan_part[t / kScanTile].x : M;
+    }
+}
+
+__global__ void k_merge_init(DevPtrs p)
+{
+    const int M = p.counters[C_M];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 2 * M; i += gridDim.x * blockDim.x)
+        p.mg_best[i] = ~0ull;
+}
+
+// A warp per inner segment A; its lanes take the candidates B of A's unit and
+// of the two adjacent units of the same side.
+__global__ void __launch_bounds__(256) k_merge_pairs(KConst k, DevPtrs p)
+{
+    const int M = p.counters[C_M];
+    const int lane = threadIdx.x & 31;
+    const int S = k.n_sectors, half = S / 2;
+    const int w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+    for (int a = w0; a < M; a += nw) {
+        const tpc_fit& fa = p.out_fits[a];
+        if (fa.status != 0) continue;
+        const tpc_track& ta = p.out_tracks[a];
+        const float xa_last = p.clusters[p.out_hits[ta.hit_off + ta.nhits - 1]].x;
+        const int ua = ta.event * S + ta.sector;
+        const int base = (ta.sector / half) * half, la = ta.sector % half;
+        const int un = ta.event * S + base + (la + 1) % half;
+        const int up = ta.event * S + base + (la + half - 1) % half;
+        for (int kk = 0; kk < 3; kk++) {
+            const int ub = kk == 0 ? ua : (kk == 1 ? un : up);
+            if (kk == 2 && up == un) continue;
+            if (kk > 0 && ub == ua) continue;
+            const int rot = kk == 0 ? 0 : (kk == 1 ? 1 : -1);
+            // source state of the candidates: A at its innermost cluster, or
+            // at its outermost one rotated into B's frame
+            float xs = fa.x;
+            float ps[5];
+            Cov Cs;
+#pragma unroll
+            for (int i = 0; i < 5; i++) ps[i] = fa.p[i];
+#pragma unroll
+            for (int i = 0; i < 15; i++) Cs.c[i] = fa.cov[i];
+            if (rot != 0) {
+                if (!mg_prop(xs, ps, Cs, xa_last, k)) continue;
+                if (!mg_rotate(xs, ps, Cs, k.mg_cos, rot > 0 ? k.mg_sin : -k.mg_sin, k)) continue;
+            }
+            const int b0 = p.unit_first[ub], b1 = p.unit_first[ub + 1];
+            for (int b = b0 + lane; b < b1; b += 32) {
+                if (b == a) continue;
+                const tpc_fit& fb = p.out_fits[b];
+                const float xf = fb.x;
+                const bool geom = rot == 0 ? (xa_last < xf && xf <= xa_last + k.mg_gap)
+                                           : (xa_last - k.mg_overlap <= xf && xf <= xa_last + k.mg_gap);
+                if (!geom || fb.status != 0) continue;
+                float x = xs;
+                float pp[5];
+#pragma unroll
+                for (int i = 0; i < 5; i++) pp[i] = ps[i];
+                if (xf - x == 0.0f) {
+                } else {
+                    StepJ J;
+                    if (!fit_step(x, pp, xf, k, J)) continue;
+                    float pb[5];
+#pragma unroll
+                    for (int i = 0; i < 5; i++) pb[i] = fb.p[i];
+                    if (!(fabsf(pp[0] - pb[0]) <= k.mg_window) || !(fabsf(pp[1] - pb[1]) <= k.mg_window)) continue;
+                    Cov Cp = Cs;
+                    cov_step(Cp, J);
+                    Cov Cb;
+#pragma unroll
+                    for (int i = 0; i < 15; i++) Cb.c[i] = fb.cov[i];
+                    float chi2;
+                    if (!mg_chi2(pp, Cp, pb, Cb, chi2) || !(chi2 <= k.mg_chi2)) continue;
+                    const unsigned long long hi = (unsigned long long)__float_as_uint(chi2) << 32;
+                    atomicMin(&p.mg_best[a], hi | (unsigned)b);
+                    atomicMin(&p.mg_best[M + b], hi | (unsigned)a);
+                    continue;
+                }
+                // same plane (x_first(B) == x of the source): no step
+                float pb[5];
+#pragma unroll
+                for (int i = 0; i < 5; i++) pb[i] = fb.p[i];
+                if (!(fabsf(pp[0] - pb[0]) <= k.mg_window) || !(fabsf(pp[1] - pb[1]) <= k.mg_window)) continue;
+                Cov Cb;
+#pragma unroll
+                for (int i = 0; i < 15; i++) Cb.c[i] = fb.cov[i];
+                float chi2;
+                if (!mg_chi2(pp, Cs, pb, Cb, chi2) || !(chi2 <= k.mg_chi2)) continue;
+                const unsigned long long hi = (unsigned long long)__float_as_uint(chi2) << 32;
+                atomicMin(&p.mg_best[a], hi | (unsigned)b);
+                atomicMin(&p.mg_best[M + b], hi | (unsigned)a);
+            }
+        }
+    }
+}
+
+// Mutual best candidates are linked.
+__global__ void k_merge_link(DevPtrs p)
+{
+    const int M = p.counters[C_M];
+    for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < M; a += gridDim.x * blockDim.x) {
+        const unsigned long long ka = p.mg_best[a];
+        tpc_merge out;
+        out.next = -1;
+        out.chi2 = 0.0f;
+        if (ka != ~0ull) {
+            const int b = (int)(unsigned)(ka & 0xffffffffu);
+            const unsigned long long kb = p.mg_best[M + b];
+            if ((int)(unsigned)(kb & 0xffffffffu) == a) {
+                out.next = b;
+                out.chi2 = __uint_as_float((unsigned)(ka >> 32));
+            }
+        }
+        p.out_merges[a] = out;
+    }
+}
+
+cudaError_t launch_merge(const KConst& k, const DevPtrs& p, int n_sm, cudaStream_t s)
+{
+    k_unit_first<<<(p.n_units + 256) / 256, 256, 0, s>>>(k, p);
+    k_merge_init<<<n_sm * 2, 256, 0, s>>>(p);
+    k_merge_pairs<<<n_sm * 8, 256, 0, s>>>(k, p);
+    k_merge_link<<<n_sm * 2, 256, 0, s>>>(p);
     return cudaGetLastError();
 }
 

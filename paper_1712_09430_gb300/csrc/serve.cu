@@ -60,7 +60,8 @@ struct Batch {
     tpc_track* tracks = nullptr;
     int* hits = nullptr;
     tpc_fit* fits = nullptr;            // with params.refit
-    size_t tracks_cap = 0, hits_cap = 0, fits_cap = 0;
+    tpc_merge* merges = nullptr;        // with params.merge
+    size_t tracks_cap = 0, hits_cap = 0, fits_cap = 0, merges_cap = 0;
     int est_tracks = 0, est_hits = 0;   // what the D2H enqueued
     int open_results = 0;               // requests of the batch not yet polled
 };
@@ -298,6 +299,10 @@ static int launch_batch_impl(tpc_tracker* tr)
             grow_pinned(tr, reinterpret_cast<void**>(&b->fits), &b->fits_cap,
                         sizeof(tpc_fit) * (size_t)b->est_tracks) != TPC_OK)
             return TPC_ERR_NOMEM;
+        if (tr->params.merge &&
+            grow_pinned(tr, reinterpret_cast<void**>(&b->merges), &b->merges_cap,
+                        sizeof(tpc_merge) * (size_t)b->est_tracks) != TPC_OK)
+            return TPC_ERR_NOMEM;
         e = cudaMemcpyAsync(b->counters, p.counters, sizeof(int) * kNumCounters, cudaMemcpyDeviceToHost, s);
         // first (track, hit) of every event, to slice the output per request
         if (e == cudaSuccess)
@@ -311,6 +316,9 @@ static int launch_batch_impl(tpc_tracker* tr)
                                 cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess && tr->params.refit)
             e = cudaMemcpyAsync(b->fits, p.out_fits, sizeof(tpc_fit) * (size_t)b->est_tracks,
+                                cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess && tr->params.merge)
+            e = cudaMemcpyAsync(b->merges, p.out_merges, sizeof(tpc_merge) * (size_t)b->est_tracks,
                                 cudaMemcpyDeviceToHost, s);
     } else {
         std::memset(b->counters, 0, sizeof(int) * kNumCounters);
@@ -368,6 +376,19 @@ static void finish_batch(tpc_tracker* tr, Batch& b)
                     b.fits_cap = fc;
                     if (cudaMemcpy(b.fits, b.p.out_fits, sizeof(tpc_fit) * (size_t)M, cudaMemcpyDeviceToHost) !=
                         cudaSuccess)
+                        err = TPC_ERR_DEVICE;
+                }
+            }
+            if (err == TPC_OK && tr->params.merge) {
+                void* mp = b.merges;
+                size_t mc = b.merges_cap;
+                if (grow_pinned(tr, &mp, &mc, sizeof(tpc_merge) * (size_t)M) != TPC_OK) {
+                    err = TPC_ERR_NOMEM;
+                } else {
+                    b.merges = static_cast<tpc_merge*>(mp);
+                    b.merges_cap = mc;
+                    if (cudaMemcpy(b.merges, b.p.out_merges, sizeof(tpc_merge) * (size_t)M,
+                                   cudaMemcpyDeviceToHost) != cudaSuccess)
                         err = TPC_ERR_DEVICE;
                 }
             }
@@ -437,6 +458,7 @@ void tpc_serve_shutdown(tpc_tracker* tr)
         cudaFreeHost(b.tracks);
         cudaFreeHost(b.hits);
         cudaFreeHost(b.fits);
+        cudaFreeHost(b.merges);
     }
     cudaFree(S->arena_base);
     cudaFreeHost(S->pin);
@@ -568,6 +590,8 @@ extern "C" int tpc_stream_poll(tpc_tracker* tr, uint64_t ticket, tpc_output* out
         if (MH) std::memcpy(out->hit_ids, b.hits + r->h0, sizeof(int32_t) * (size_t)MH);
         if (M && out->fits && tr->params.refit)
             std::memcpy(out->fits, b.fits + r->m0, sizeof(tpc_fit) * (size_t)M);
+        if (M && out->merges && tr->params.merge)
+            std::memcpy(out->merges, b.merges + r->m0, sizeof(tpc_merge) * (size_t)M);
         S->stats.host_copy_ms += ms_since(t_copy);
     }
     release_ticket(tr, ticket);
@@ -593,6 +617,7 @@ extern "C" int tpc_stream_poll_view(tpc_tracker* tr, uint64_t ticket, tpc_stream
     view->tracks = b.tracks + r->m0;
     view->hit_ids = b.hits + r->h0;
     view->fits = tr->params.refit ? b.fits + r->m0 : nullptr;
+    view->merges = tr->params.merge ? b.merges + r->m0 : nullptr;
     view->n_tracks = r->m1 - r->m0;
     view->n_hits = r->h1 - r->h0;
     r->viewed = true;

@@ -44,6 +44,9 @@ struct KConst {
     float kB;            // (float)(-kappa * Bz) rounded once from double
     float kP;            // (float)(-kappa): curvature per tesla of the field polynomial
     float fb[5];         // field polynomial terms b1..b5 of the refit
+    float mg_chi2, mg_gap, mg_overlap, mg_window;  // merging cuts
+    float mg_cos, mg_sin;  // rotation between adjacent sectors, rounded once from double
+    int mg_on;             // merge links are computed (params.merge)
     float tan_h, z_max;
     float bin_target;
     int l_seed, g_max, n_min_tracklet, n_min_track, own_num, own_den;
@@ -103,6 +106,9 @@ struct DevPtrs {
     const int* req_first_event;  // [E] first event of each event's request
     int2* ev_first;              // [E + 1] first (track, hit) of each event
     int* req_area;               // [E] device storage for req_first_event
+    tpc_merge* out_merges;       // [Mcap] merge links
+    unsigned long long* mg_best; // [2 Mcap] best outer / inner candidate keys
+    int* unit_first;             // [n_units + 1] first track of each unit
     int* counters;             // [kNumCounters]
     int N, R, n_units, t_cap, m_cap, mh_cap;
 };
@@ -246,7 +252,8 @@ cudaError_t launch_dump_tl_work(const tpc::DevPtrs& p, int T, int* dst, cudaStre
                                  int schedule, int t_first_unit, int t_last_unit, cudaStream_t s); \
     cudaError_t launch_seeds(const tpc::KConst& k, const float* row_x_dev, const tpc::DevPtrs& p,   \
                              int n_sm, int u0, int u1, cudaStream_t s);                             \
-    cudaError_t launch_refit(const tpc::KConst& k, const tpc::DevPtrs& p, int n_sm, cudaStream_t s);
+    cudaError_t launch_refit(const tpc::KConst& k, const tpc::DevPtrs& p, int n_sm, cudaStream_t s); \
+    cudaError_t launch_merge(const tpc::KConst& k, const tpc::DevPtrs& p, int n_sm, cudaStream_t s);
 
 namespace tpc_exact { TPC_FP_DECLS }
 namespace tpc_fast { TPC_FP_DECLS }

@@ -57,6 +57,16 @@ static KConst make_kconst(const tpc_params& P, const tpc_geometry& G, double bz)
     k.kB = (float)(-0.00299792458 * bz);
     k.kP = (float)(-0.00299792458);
     for (int i = 0; i < 5; i++) k.fb[i] = P.field[i];
+    k.mg_chi2 = P.merge_chi2;
+    k.mg_gap = P.merge_gap;
+    k.mg_overlap = P.merge_overlap;
+    k.mg_window = P.merge_window;
+    k.mg_on = P.merge;
+    // angle between adjacent sectors of one side: 360 deg / (n_sectors / 2)
+    const double deg = 720.0 / (double)G.n_sectors;
+    const double th = deg * (3.14159265358979323846 / 180.0);
+    k.mg_cos = (float)std::cos(th);
+    k.mg_sin = (float)std::sin(th);
     k.tan_h = G.tan_half_open;
     k.z_max = G.z_max;
     k.bin_target = P.bin_target;
@@ -89,6 +99,10 @@ static const char* check_params(const tpc_params& P)
     if (P.plain_per_sector < 0 || P.plain_per_sector > 2) return "plain_per_sector must be 0, 1 or 2";
     if (P.n_queues < 1 || P.n_queues > 64) return "n_queues must be in [1, 64]";
     if (P.refit != 0 && P.refit != 1) return "refit must be 0 or 1";
+    if (P.merge != 0 && P.merge != 1) return "merge must be 0 or 1";
+    if (P.merge && !P.refit) return "merge needs refit = 1 (it compares refitted states)";
+    if (!(P.merge_chi2 > 0) || !(P.merge_gap > 0) || !(P.merge_overlap >= 0) || !(P.merge_window > 0))
+        return "merge cuts must be positive";
     for (int i = 0; i < 5; i++)
         if (!std::isfinite(P.field[i])) return "field terms must be finite";
     return nullptr;
@@ -124,6 +138,12 @@ extern "C" void tpc_params_default(tpc_params* p)
     p->use_graph = 0;
     p->n_queues = 8;
     p->schedule = 0;
+    p->refit = 0;
+    p->merge = 0;
+    p->merge_chi2 = 30.0f;
+    p->merge_gap = 50.0f;
+    p->merge_overlap = 5.0f;
+    p->merge_window = 5.0f;
 }
 
 extern "C" int tpc_tracker_create(const tpc_geometry* g, double bz, const tpc_params* params,
@@ -271,6 +291,9 @@ size_t tpc_layout(const tpc_tracker* tr, const BatchShape& sh, DevPtrs* p, char*
     q.fit_bins = reinterpret_cast<int*>(take(2 * (TPC_MAX_ROWS + 1) * 4));
     q.ev_first = reinterpret_cast<int2*>(take(((size_t)sh.n_events + 1) * 8));
     q.req_area = reinterpret_cast<int*>(take((size_t)sh.n_events * 4));
+    q.out_merges = reinterpret_cast<tpc_merge*>(take(Tc * sizeof(tpc_merge)));
+    q.mg_best = reinterpret_cast<unsigned long long*>(take(Tc * 16));
+    q.unit_first = reinterpret_cast<int*>(take(((size_t)sh.n_units + 1) * 4));
     // set by the serving loop for its batches; the synchronous call does not rebase
     q.req_first_event = nullptr;
     q.counters = reinterpret_cast<int*>(take(kNumCounters * 4));
@@ -508,6 +531,8 @@ int tpc_enqueue(tpc_tracker* tr, const DevPtrs& p, const BatchShape& sh, cudaStr
     if (with_events) TPC_CUDA(cudaEventRecord(tr->ev[5], s));
     if (P.refit)
         TPC_CUDA(exact ? tpc_exact::launch_refit(k, p, tr->n_sm, s) : tpc_fast::launch_refit(k, p, tr->n_sm, s));
+    if (P.merge)
+        TPC_CUDA(exact ? tpc_exact::launch_merge(k, p, tr->n_sm, s) : tpc_fast::launch_merge(k, p, tr->n_sm, s));
     if (p.req_first_event) TPC_CUDA(tpc_int::launch_rebase(k, p, tr->n_sm, s));
     if (with_events) TPC_CUDA(cudaEventRecord(tr->ev[6], s));
 #undef cudaEventRecord
@@ -600,6 +625,8 @@ int tpc_copy_out(tpc_tracker* tr, const DevPtrs& p, int M, int MH, tpc_output* o
     }
     if (mt > 0 && out->fits && tr->params.refit)
         TPC_CUDA(cudaMemcpyAsync(out->fits, p.out_fits, sizeof(tpc_fit) * mt, kind, s));
+    if (mt > 0 && out->merges && tr->params.merge)
+        TPC_CUDA(cudaMemcpyAsync(out->merges, p.out_merges, sizeof(tpc_merge) * mt, kind, s));
     TPC_CUDA(cudaStreamSynchronize(s));
     if (mt < M || mh < MH) return tr->fail(TPC_ERR_OUTPUT_TRUNCATED, "output capacity too small");
     return TPC_OK;
