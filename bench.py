@@ -384,7 +384,16 @@ def run_refit(L, tr, dev_cl, rc_ptr, B, sp, out, out_tr, args):
         step()
         ms.append(tr.stage_times()[6])
     torch.cuda.synchronize()
-    tr.set_params(refit=0)
+    # the same with merging after the refit (Sec. 2 Phase II step 3)
+    tr.set_params(merge=1)
+    for _ in range(3):
+        step()
+    ms_merge = []
+    for _ in range(args.refit_steps):
+        step()
+        ms_merge.append(tr.stage_times()[6])
+    torch.cuda.synchronize()
+    tr.set_params(refit=0, merge=0)
     M = out.n_tracks
     tracks = out_tr[:M * TRACK_DTYPE.itemsize].cpu().numpy().view(TRACK_DTYPE)
     n = tracks["nhits"].astype(np.int64)
@@ -394,7 +403,8 @@ def run_refit(L, tr, dev_cl, rc_ptr, B, sp, out, out_tr, args):
     props = torch.cuda.get_device_properties(dev_cl.device)
     peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * 2.07e9 / 1e12
     achieved = flops / t / 1e12
-    return {"ms": t * 1e3, "tracks": int(M), "filter_steps": steps,
+    merge_ms = statistics.median(ms_merge) - t * 1e3
+    return {"ms": t * 1e3, "merge_ms": merge_ms, "tracks": int(M), "filter_steps": steps,
             "tracks_per_s": M / t, "clusters_per_s": float(n.sum()) / t,
             "mode": "exact" if args.exact else "production",
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",

@@ -541,11 +541,15 @@ __global__ void k_unit_first(KConst k, DevPtrs p)
     }
 }
 
+// Best-candidate keys reset; compact candidate keys (x_first, refit ok) so
+// the candidate scan reads 8 bytes per track, coalesced.
 __global__ void k_merge_init(DevPtrs p)
 {
     const int M = p.counters[C_M];
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 2 * M; i += gridDim.x * blockDim.x)
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 2 * M; i += gridDim.x * blockDim.x) {
         p.mg_best[i] = ~0ull;
+        if (i < M) p.mg_keys[i] = make_float2(p.out_fits[i].x, p.out_fits[i].status == 0 ? 1.0f : 0.0f);
+    }
 }
 
 // A warp per inner segment A; its lanes take the candidates B of A's unit and
@@ -585,12 +589,12 @@ __global__ void __launch_bounds__(256) k_merge_pairs(KConst k, DevPtrs p)
             }
             const int b0 = p.unit_first[ub], b1 = p.unit_first[ub + 1];
             for (int b = b0 + lane; b < b1; b += 32) {
-                if (b == a) continue;
-                const tpc_fit& fb = p.out_fits[b];
-                const float xf = fb.x;
+                const float2 key = p.mg_keys[b];
+                const float xf = key.x;
                 const bool geom = rot == 0 ? (xa_last < xf && xf <= xa_last + k.mg_gap)
                                            : (xa_last - k.mg_overlap <= xf && xf <= xa_last + k.mg_gap);
-                if (!geom || fb.status != 0) continue;
+                if (!geom || key.y == 0.0f || b == a) continue;
+                const tpc_fit& fb = p.out_fits[b];
                 float x = xs;
                 float pp[5];
 #pragma unroll

@@ -109,6 +109,7 @@ struct DevPtrs {
     tpc_merge* out_merges;       // [Mcap] merge links
     unsigned long long* mg_best; // [2 Mcap] best outer / inner candidate keys
     int* unit_first;             // [n_units + 1] first track of each unit
+    float2* mg_keys;             // [Mcap] (x of the innermost cluster, 1 if the refit succeeded)
     int* counters;             // [kNumCounters]
     int N, R, n_units, t_cap, m_cap, mh_cap;
 };

@@ -294,6 +294,7 @@ size_t tpc_layout(const tpc_tracker* tr, const BatchShape& sh, DevPtrs* p, char*
     q.out_merges = reinterpret_cast<tpc_merge*>(take(Tc * sizeof(tpc_merge)));
     q.mg_best = reinterpret_cast<unsigned long long*>(take(Tc * 16));
     q.unit_first = reinterpret_cast<int*>(take(((size_t)sh.n_units + 1) * 4));
+    q.mg_keys = reinterpret_cast<float2*>(take(Tc * 8));
     // set by the serving loop for its batches; the synchronous call does not rebase
     q.req_first_event = nullptr;
     q.counters = reinterpret_cast<int*>(take(kNumCounters * 4));
