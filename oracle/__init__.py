@@ -44,6 +44,11 @@ class MergeParams(C.Structure):
     _fields_ = [(n, C.c_double) for n in ("chi2_max", "gap", "overlap", "window", "cos_t", "sin_t")]
 
 
+class T0Params(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("y_cut", "bin", "z_max", "radius")] + \
+               [("window", C.c_int), ("n_min", C.c_int)]
+
+
 class Geom(C.Structure):
     _fields_ = [("n_rows", C.c_int), ("n_sectors", C.c_int), ("row_x", C.POINTER(C.c_float)),
                 ("tan_half_open", C.c_float), ("z_max", C.c_float)]
@@ -94,6 +99,7 @@ def lib(mode="f64"):
         L.orc_merge_rotate.argtypes = [P(FitParams), V, C.c_double, C.c_double]
         L.orc_merge_propagate.argtypes = [P(FitParams), V, C.c_double]
         L.orc_merge_chi2.argtypes = [V, V, P(C.c_double)]
+        L.orc_t0_tracks.argtypes = [P(FitParams), P(T0Params), C.c_int, C.c_int, V, V, V]
         L.orc_max_threads.restype = C.c_int
         L.orc_real_size.restype = C.c_int
         _LIBS[mode] = L
@@ -348,3 +354,22 @@ def merge_chi2(va, vb, mode="f64"):
     c = C.c_double()
     ok = lib(mode).orc_merge_chi2(_ptr(va), _ptr(vb), C.byref(c))
     return bool(ok), c.value
+
+
+# continuous readout: collision offsets (tpc_refit.c) ------------------------
+
+def t0_params(y_cut=1.0, bin=0.25, z_max=250.0, radius=1.0, window=8, n_min=8) -> T0Params:
+    t = T0Params()
+    t.y_cut, t.bin, t.z_max, t.radius, t.window, t.n_min = y_cut, bin, z_max, radius, window, n_min
+    return t
+
+
+def t0_tracks(unit, fits, fp, tp=None, n_sectors=36, mode="f64"):
+    """Per refitted track: (collision, u, D) of the continuous-readout
+    readings; returns float64 [M, 3]."""
+    tp = tp if tp is not None else t0_params()
+    u = np.ascontiguousarray(unit, np.int32)
+    f = np.ascontiguousarray(fits, np.float64)
+    out = np.zeros((len(u), 3))
+    lib(mode).orc_t0_tracks(C.byref(fp), C.byref(tp), len(u), n_sectors, _ptr(u), _ptr(f), _ptr(out))
+    return out

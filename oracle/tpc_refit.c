@@ -61,6 +61,7 @@
  */
 #include <math.h>
 #include <stdint.h>
+#include <stdlib.h>
 #include <string.h>
 #ifdef _OPENMP
 #include <omp.h>
@@ -642,4 +643,141 @@ int orc_merge_chi2(const double* va, const double* vb, double* chi2)
     int ok = mg_chi2(&a, &b, &x2);
     *chi2 = (double)x2;
     return ok;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Continuous readout (Sec. 3.3, Run 3 conditions): the drift coordinate z'  */
+/* of a cluster is its spatial z only once the collision time is known, so   */
+/* transformation and tracking are coupled.  Readings T01-T05:               */
+/*   T01 the tracker runs on z' (a collision's unknown time shifts all its   */
+/*       clusters by sign(side) dz, which the track model absorbs);          */
+/*   T02 each refitted track (status 0) is stepped to the beam line x = 0 of */
+/*       its sector frame in 16 equal steps (targets x0 - i (x0 / 16), the   */
+/*       last exactly 0: short enough for the arc series); it is a primary   */
+/*       candidate if every step succeeds and |y(0)| <= y_cut; its offset   */
+/*       estimate is u = sign(side) z'(0), sign = +1 on side A (sectors <    */
+/*       n_sectors / 2), -1 on side C;                                       */
+/*   T03 per time frame (one event of the batch) the candidates' u in        */
+/*       [-z_max, z_max) are binned, h[b] with b = floor((u + z_max) / w);  */
+/*       n[b] = sum of h over b-2..b+2, s[b] the same with weights 1 2 3 2 1;*/
+/*       bin b is a collision peak if n[b] >= n_min, s[b] > s[b'] for b' in  */
+/*       [b - W, b) and s[b] >= s[b'] for b' in (b, b + W] (the lowest of    */
+/*       equal maxima); collisions are numbered by increasing peak bin;      */
+/*       centre c = -z_max + (b + 1/2) w;                                    */
+/*   T04 a candidate belongs to the collision whose centre is nearest, if    */
+/*       |u - c| <= r (ties: the lower one); the collision's offset D is the */
+/*       mean u of its tracks, summed as integers (u in units of 1e-4 cm,    */
+/*       rounded to nearest) so the sum does not depend on order:            */
+/*       D = (sum / n) 1e-4;                                                 */
+/*   T05 per track: its collision (-1: none), u, and D (0 without one); the  */
+/*       track's spatial z is z' - sign(side) D.                             */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    double y_cut;      /* cm */
+    double bin;        /* cm */
+    double z_max;      /* cm */
+    double radius;     /* r, cm */
+    int window;        /* W, bins */
+    int n_min;
+} orc_t0_params;
+
+/* out[M][3]: collision, u, D (collision -1: none) */
+void orc_t0_tracks(const orc_fit_params* p, const orc_t0_params* tp, int M, int n_sectors,
+                   const int32_t* unit, const double* fits, double* out)
+{
+    rf_ctx c;
+    rf_ctx_init(&c, p);
+    rreal zmax = RF(tp->z_max), w = RF(tp->bin), ycut = RF(tp->y_cut);
+    int nb = (int)ceil(2.0 * tp->z_max / tp->bin);
+    int n_events = M ? unit[M - 1] / n_sectors + 1 : 0;
+    int* bin = (int*)malloc(sizeof(int) * ((size_t)M + 1));
+    rreal* u = (rreal*)malloc(sizeof(rreal) * ((size_t)M + 1));
+    int* hist = (int*)calloc((size_t)nb, sizeof(int));
+    int* grp = (int*)malloc(sizeof(int) * (size_t)nb);
+    int64_t* gsum = (int64_t*)malloc(sizeof(int64_t) * (size_t)nb);
+    int* gcnt = (int*)malloc(sizeof(int) * (size_t)nb);
+    /* T02 */
+    for (int m = 0; m < M; m++) {
+        const double* f = fits + (size_t)m * RF_NOUT;
+        bin[m] = -1;
+        out[(size_t)m * 3 + 0] = -1.0;
+        out[(size_t)m * 3 + 1] = 0.0;
+        out[(size_t)m * 3 + 2] = 0.0;
+        if (f[23] != 0.0) continue;
+        rreal x = RF(f[0]), pp[5], J[5][5];
+        for (int i = 0; i < 5; i++) pp[i] = RF(f[1 + i]);
+        rreal h = x * RF(0.0625);
+        rreal x0 = x;
+        int ok = 1;
+        for (int i = 1; i <= 16 && ok; i++) {
+            rreal xt = i == 16 ? RF(0) : x0 - (rreal)i * h;
+            if (xt - x != RF(0)) ok = rf_step(&c, &x, pp, J, xt);
+        }
+        if (!ok) continue;
+        if (!(f_fabs(pp[0]) <= ycut)) continue;
+        int side_a = (unit[m] % n_sectors) < n_sectors / 2;
+        rreal um = side_a ? pp[1] : -pp[1];
+        u[m] = um;
+        out[(size_t)m * 3 + 1] = (double)um;
+        if (!(um >= -zmax && um < zmax)) continue;
+        int b = (int)floor((double)((um + zmax) / w));
+        if (b < 0) b = 0;
+        if (b >= nb) b = nb - 1;
+        bin[m] = b;
+    }
+    /* T03, T04 per event */
+    int* sm = (int*)malloc(sizeof(int) * (size_t)nb);
+    int* peak = (int*)malloc(sizeof(int) * (size_t)nb);
+    for (int e = 0, m0 = 0; e < n_events; e++) {
+        int m1 = m0;
+        while (m1 < M && unit[m1] / n_sectors == e) m1++;
+        memset(hist, 0, sizeof(int) * (size_t)nb);
+        for (int m = m0; m < m1; m++)
+            if (bin[m] >= 0) hist[bin[m]]++;
+        for (int b = 0; b < nb; b++) {
+            int acc = 0, cnt = 0;
+            for (int j = b - 2; j <= b + 2; j++)
+                if (j >= 0 && j < nb) {
+                    acc += (3 - abs(j - b)) * hist[j];
+                    cnt += hist[j];
+                }
+            sm[b] = acc;
+            grp[b] = cnt;  /* n[b] */
+        }
+        int np_ = 0;
+        for (int b = 0; b < nb; b++) {
+            if (grp[b] < tp->n_min) continue;
+            int is_peak = 1;
+            for (int j = b - tp->window; j < b && is_peak; j++)
+                if (j >= 0 && !(sm[b] > sm[j])) is_peak = 0;
+            for (int j = b + 1; j <= b + tp->window && is_peak; j++)
+                if (j < nb && !(sm[b] >= sm[j])) is_peak = 0;
+            if (is_peak) peak[np_++] = b;
+        }
+        for (int k = 0; k < np_; k++) { gsum[k] = 0; gcnt[k] = 0; }
+        for (int m = m0; m < m1; m++) {
+            if (bin[m] < 0) continue;
+            int best = -1;
+            rreal bd = RF(0);
+            for (int k = 0; k < np_; k++) {
+                rreal cen = -zmax + ((rreal)peak[k] + RF(0.5)) * w;
+                rreal dd = f_fabs(u[m] - cen);
+                if (dd <= RF(tp->radius) && (best < 0 || dd < bd)) { best = k; bd = dd; }
+            }
+            bin[m] = best < 0 ? -1 : nb + best;  /* reuse: nb + collision */
+            if (best < 0) continue;
+            gsum[best] += (int64_t)llrint((double)u[m] * 1e4);
+            gcnt[best]++;
+        }
+        for (int m = m0; m < m1; m++) {
+            if (bin[m] < nb) continue;
+            int k = bin[m] - nb;
+            out[(size_t)m * 3 + 0] = (double)k;
+            out[(size_t)m * 3 + 2] = (double)(float)((double)gsum[k] / (double)gcnt[k] * 1e-4);
+        }
+        m0 = m1;
+    }
+    free(sm); free(peak);
+    free(bin); free(u); free(hist); free(grp); free(gsum); free(gcnt);
 }

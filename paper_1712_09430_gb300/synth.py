@@ -354,6 +354,7 @@ def time_frame(seed=4, n_coll=50, scale=1.0) -> Event:
     rng = np.random.default_rng(seed)
     secs, rows, ys, zs, labs, tys, tzs, tss, trks = [], [], [], [], [], [], [], [], []
     lab_off = 0
+    coll_dz, track_coll = [], []
     for c in range(n_coll):
         n = max(1, int(round(min_bias_tracks(rng) * scale)))
         ev = make_event(int(rng.integers(1 << 62)), n, int(round(0.3 * n)), pt_mean=0.5,
@@ -368,6 +369,8 @@ def time_frame(seed=4, n_coll=50, scale=1.0) -> Event:
         labs.append(np.where(lab[keep] >= 0, lab[keep] + lab_off, -1))
         tys.append(ty[keep]); tzs.append(tz2[keep]); tss.append(ts[keep])
         trks.append(ev.tracks)
+        coll_dz.append(dz)
+        track_coll.append(np.full(len(ev.tracks), c, np.int32))
         lab_off += len(ev.tracks)
     tracks = Tracks.concat(trks)
     base = Event(np.zeros((0, 4), np.float32), np.zeros(N_SECTORS * N_ROWS, np.int32),
@@ -375,7 +378,11 @@ def time_frame(seed=4, n_coll=50, scale=1.0) -> Event:
     ev = _rebuild(rng, base, np.concatenate(secs), np.concatenate(rows), np.concatenate(ys),
                   np.concatenate(zs), np.concatenate(labs), np.concatenate(tys),
                   np.concatenate(tzs), np.concatenate(tss))
-    return _add_noise(rng, ev, int(round(0.10 * ev.n)))
+    ev = _add_noise(rng, ev, int(round(0.10 * ev.n)))
+    # truth of the overlay: each collision's drift offset, each track's collision
+    ev.coll_dz = np.array(coll_dz)
+    ev.track_coll = np.concatenate(track_coll) if track_coll else np.zeros(0, np.int32)
+    return ev
 
 
 def concat_events(events):
