@@ -138,6 +138,14 @@ typedef struct {
     float merge_overlap;     /* across a sector border the outer segment may
                                 start this much (cm) before the inner one ends (5) */
     float merge_window;      /* |dy| and |dz| of the propagated states (cm) (5) */
+    /* continuous readout (Sec. 3.3 Run 3 conditions): collision offsets of a
+       time frame estimated from its tracks; needs refit = 1                 */
+    int t0;                  /* 1: estimate them (tpc_t0 output); 0: no (default) */
+    float t0_y_cut;          /* primary candidate: |y| at the beam line (1 cm)  */
+    float t0_bin;            /* histogram bin of the offsets (0.25 cm)          */
+    float t0_radius;         /* a track joins a collision within this (1 cm)    */
+    int t0_window;           /* peak suppression half-width in bins (8)         */
+    int t0_n_min;            /* candidates within +-2 bins of a peak (8)        */
 } tpc_params;
 
 /* A selected track: the best tracklet instance (Sec. 2 step 2), with the
@@ -191,8 +199,27 @@ typedef struct {
     float chi2;              /* chi2 of that link (0 without one)               */
 } tpc_merge;
 
-/* Output buffers, caller-owned.  mem_kind says where tracks, hit_ids, fits
- * and merges live.  hit_ids are positions in the call's cluster array, rows
+/* Continuous readout (Sec. 3.3, Run 3 conditions): in a time frame a
+ * cluster's drift coordinate z' is its spatial z only once its collision's
+ * time is known, so transformation and tracking are coupled.  The tracker
+ * runs on z'; afterwards each refitted track is stepped to the beam line
+ * x = 0 of its sector frame (16 equal steps); with |y(0)| <= t0_y_cut it
+ * estimates its collision's offset u = sign(side) z'(0) (+1 side A, -1 side
+ * C).  Per time frame (event of the batch) the estimates are binned
+ * (t0_bin); a bin is a collision if at least t0_n_min estimates lie within
+ * +-2 bins and its 1-2-3-2-1 smoothed count is the largest within
+ * +-t0_window bins (the lowest of equal maxima); a track joins the nearest
+ * collision centre within t0_radius; a collision's offset dz is the mean u of
+ * its tracks.  A track's spatial z is z' - sign(side) dz. */
+typedef struct {
+    int32_t collision;       /* collision index in its event, by increasing
+                                offset; -1: none                              */
+    float u;                 /* the track's own offset estimate (cm)            */
+    float dz;                /* its collision's offset (0 without one)          */
+} tpc_t0;
+
+/* Output buffers, caller-owned.  mem_kind says where tracks, hit_ids, fits,
+ * merges and t0s live.  hit_ids are positions in the call's cluster array, rows
  * ascending within a track; tracks are in canonical tracklet order. */
 typedef struct {
     tpc_track* tracks;
@@ -207,6 +234,8 @@ typedef struct {
                                 (NULL: not copied)                              */
     tpc_merge* merges;       /* optional, [cap_tracks]: merge link of tracks[m];
                                 written only when params.merge = 1              */
+    tpc_t0* t0s;             /* optional, [cap_tracks]: collision of tracks[m];
+                                written only when params.t0 = 1                 */
 } tpc_output;
 
 typedef struct tpc_tracker tpc_tracker;
@@ -305,6 +334,7 @@ typedef struct {
     const int32_t* hit_ids;
     const tpc_fit* fits;     /* NULL unless params.refit = 1                    */
     const tpc_merge* merges; /* NULL unless params.merge = 1                    */
+    const tpc_t0* t0s;       /* NULL unless params.t0 = 1                       */
     int32_t n_tracks;
     int32_t n_hits;
 } tpc_stream_view;

@@ -58,7 +58,9 @@ class tpc_params(C.Structure):
                 ("plain_per_sector", C.c_int), ("use_graph", C.c_int), ("n_queues", C.c_int),
                 ("schedule", C.c_int), ("refit", C.c_int), ("field", C.c_float * 5),
                 ("merge", C.c_int), ("merge_chi2", C.c_float), ("merge_gap", C.c_float),
-                ("merge_overlap", C.c_float), ("merge_window", C.c_float)]
+                ("merge_overlap", C.c_float), ("merge_window", C.c_float),
+                ("t0", C.c_int), ("t0_y_cut", C.c_float), ("t0_bin", C.c_float),
+                ("t0_radius", C.c_float), ("t0_window", C.c_int), ("t0_n_min", C.c_int)]
 
 
 class tpc_track(C.Structure):
@@ -77,10 +79,15 @@ class tpc_merge(C.Structure):
     _fields_ = [("next", C.c_int32), ("chi2", C.c_float)]
 
 
+class tpc_t0(C.Structure):
+    _fields_ = [("collision", C.c_int32), ("u", C.c_float), ("dz", C.c_float)]
+
+
 class tpc_output(C.Structure):
     _fields_ = [("tracks", C.c_void_p), ("hit_ids", C.c_void_p), ("cap_tracks", C.c_int32),
                 ("cap_hits", C.c_int32), ("mem_kind", C.c_int32), ("n_tracks", C.c_int32),
-                ("n_hits", C.c_int32), ("fits", C.c_void_p), ("merges", C.c_void_p)]
+                ("n_hits", C.c_int32), ("fits", C.c_void_p), ("merges", C.c_void_p),
+                ("t0s", C.c_void_p)]
 
 
 class tpc_stream_stats(C.Structure):
@@ -92,7 +99,8 @@ class tpc_stream_stats(C.Structure):
 
 class tpc_stream_view(C.Structure):
     _fields_ = [("tracks", C.c_void_p), ("hit_ids", C.c_void_p), ("fits", C.c_void_p),
-                ("merges", C.c_void_p), ("n_tracks", C.c_int32), ("n_hits", C.c_int32)]
+                ("merges", C.c_void_p), ("t0s", C.c_void_p), ("n_tracks", C.c_int32),
+                ("n_hits", C.c_int32)]
 
 
 _LIB = None

@@ -667,4 +667,158 @@ cudaError_t launch_merge(const KConst& k, const DevPtrs& p, int n_sm, cudaStream
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------- continuous readout
+// Sec. 3.3 (Run 3 conditions): a time frame's clusters carry drift
+// coordinates z'; each collision's unknown time shifts its clusters by
+// sign(side) dz.  Each refitted track is stepped to the beam line x = 0 in 16
+// equal steps; with |y(0)| <= y_cut it estimates u = sign(side) z'(0).  Per
+// time frame the estimates are binned; a bin is a collision peak if >= n_min
+// estimates lie within +-2 bins and its 1-2-3-2-1 smoothed count is the
+// largest within +-W bins (the lowest of equal maxima); tracks join the
+// nearest peak centre within r; the offset is the mean of the members' u,
+// summed as integers (1e-4 cm) so the result does not depend on order.
+
+__global__ void k_t0_clear(KConst k, DevPtrs p, int E)
+{
+    const int n = E * k.t0_nb;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        p.t0_hist[i] = 0;
+        p.t0_sum[i] = 0ull;
+        p.t0_cnt[i] = 0;
+    }
+}
+
+// A thread per track: offset estimate, bin, histogram.
+__global__ void k_t0_track(KConst k, DevPtrs p)
+{
+    const int M = p.counters[C_M];
+    const int half = k.n_sectors / 2, nb = k.t0_nb;
+    for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < M; m += gridDim.x * blockDim.x) {
+        p.t0_bin[m] = -1;
+        p.t0_u[m] = 0.0f;
+        const tpc_fit& f = p.out_fits[m];
+        if (f.status != 0) continue;
+        float x = f.x, pp[5];
+#pragma unroll
+        for (int i = 0; i < 5; i++) pp[i] = f.p[i];
+        const float h = x * 0.0625f, x0 = x;
+        bool ok = true;
+        for (int i = 1; i <= 16 && ok; i++) {
+            const float xt = i == 16 ? 0.0f : x0 - (float)i * h;
+            if (xt - x != 0.0f) {
+                StepJ J;
+                ok = fit_step(x, pp, xt, k, J);
+            }
+        }
+        if (!ok || !(fabsf(pp[0]) <= k.t0_ycut)) continue;
+        const tpc_track& t = p.out_tracks[m];
+        const float u = t.sector < half ? pp[1] : -pp[1];
+        p.t0_u[m] = u;
+        if (!(u >= -k.z_max && u < k.z_max)) continue;
+        int b = (int)floorf((u + k.z_max) / k.t0_bin);
+        b = min(max(b, 0), nb - 1);
+        p.t0_bin[m] = b;
+        atomicAdd(&p.t0_hist[t.event * nb + b], 1);
+    }
+}
+
+// A warp per event: peaks by increasing bin (each lane tests bins, ballot
+// compaction keeps the order).
+__global__ void k_t0_peaks(KConst k, DevPtrs p, int E)
+{
+    const int lane = threadIdx.x & 31;
+    const int nb = k.t0_nb, W = k.t0_window;
+    for (int e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; e < E; e += (gridDim.x * blockDim.x) >> 5) {
+        const int* h = p.t0_hist + (size_t)e * nb;
+        int np = 0;
+        for (int b0 = 0; b0 < nb; b0 += 32) {
+            const int b = b0 + lane;
+            bool peak = false;
+            if (b < nb) {
+                int cnt = 0;
+                for (int j = b - 2; j <= b + 2; j++)
+                    if (j >= 0 && j < nb) cnt += h[j];
+                if (cnt >= k.t0_nmin) {
+                    auto sm = [&](int c) {
+                        int acc = 0;
+                        for (int j = c - 2; j <= c + 2; j++)
+                            if (j >= 0 && j < nb) acc += (3 - abs(j - c)) * h[j];
+                        return acc;
+                    };
+                    const int sb = sm(b);
+                    peak = true;
+                    for (int j = b - W; j < b && peak; j++)
+                        if (j >= 0 && !(sb > sm(j))) peak = false;
+                    for (int j = b + 1; j <= b + W && peak; j++)
+                        if (j < nb && !(sb >= sm(j))) peak = false;
+                }
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, peak);
+            if (peak) p.t0_peak[(size_t)e * nb + np + __popc(bal & ((1u << lane) - 1u))] = b;
+            np += __popc(bal);
+        }
+        if (lane == 0) p.t0_npeak[e] = np;
+    }
+}
+
+// A thread per track: nearest peak centre within r (ties: the lower), sums.
+__global__ void k_t0_assign(KConst k, DevPtrs p)
+{
+    const int M = p.counters[C_M];
+    const int nb = k.t0_nb;
+    for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < M; m += gridDim.x * blockDim.x) {
+        if (p.t0_bin[m] < 0) continue;
+        const int e = p.out_tracks[m].event;
+        const float u = p.t0_u[m];
+        const int np = p.t0_npeak[e];
+        const int* pk = p.t0_peak + (size_t)e * nb;
+        int best = -1;
+        float bd = 0.0f;
+        for (int q = 0; q < np; q++) {
+            const float cen = -k.z_max + ((float)pk[q] + 0.5f) * k.t0_bin;
+            const float dd = fabsf(u - cen);
+            if (dd <= k.t0_radius && (best < 0 || dd < bd)) {
+                best = q;
+                bd = dd;
+            }
+        }
+        p.t0_bin[m] = best < 0 ? -1 : nb + best;
+        if (best < 0) continue;
+        const long long uq = __double2ll_rn((double)u * 1e4);
+        atomicAdd(&p.t0_sum[(size_t)e * nb + best], (unsigned long long)uq);
+        atomicAdd(&p.t0_cnt[(size_t)e * nb + best], 1);
+    }
+}
+
+__global__ void k_t0_out(KConst k, DevPtrs p)
+{
+    const int M = p.counters[C_M];
+    const int nb = k.t0_nb;
+    for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < M; m += gridDim.x * blockDim.x) {
+        tpc_t0 o;
+        o.collision = -1;
+        o.u = p.t0_u[m];
+        o.dz = 0.0f;
+        const int b = p.t0_bin[m];
+        if (b >= nb) {
+            const int q = b - nb;
+            const size_t i = (size_t)p.out_tracks[m].event * nb + q;
+            o.collision = q;
+            o.dz = (float)((double)(long long)p.t0_sum[i] / (double)p.t0_cnt[i] * 1e-4);
+        }
+        p.out_t0s[m] = o;
+    }
+}
+
+cudaError_t launch_t0(const KConst& k, const DevPtrs& p, int n_sm, int n_events, cudaStream_t s)
+{
+    if (n_events <= 0) return cudaSuccess;
+    k_t0_clear<<<n_sm * 2, 256, 0, s>>>(k, p, n_events);
+    k_t0_track<<<n_sm * 4, 128, 0, s>>>(k, p);
+    k_t0_peaks<<<(n_events * 32 + 255) / 256, 256, 0, s>>>(k, p, n_events);
+    k_t0_assign<<<n_sm * 4, 128, 0, s>>>(k, p);
+    k_t0_out<<<n_sm * 4, 128, 0, s>>>(k, p);
+    return cudaGetLastError();
+}
+
 }  // namespace TPC_FP_NS

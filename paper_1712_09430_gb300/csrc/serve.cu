@@ -61,7 +61,8 @@ struct Batch {
     int* hits = nullptr;
     tpc_fit* fits = nullptr;            // with params.refit
     tpc_merge* merges = nullptr;        // with params.merge
-    size_t tracks_cap = 0, hits_cap = 0, fits_cap = 0, merges_cap = 0;
+    tpc_t0* t0s = nullptr;              // with params.t0
+    size_t tracks_cap = 0, hits_cap = 0, fits_cap = 0, merges_cap = 0, t0s_cap = 0;
     int est_tracks = 0, est_hits = 0;   // what the D2H enqueued
     int open_results = 0;               // requests of the batch not yet polled
 };
@@ -303,6 +304,10 @@ static int launch_batch_impl(tpc_tracker* tr)
             grow_pinned(tr, reinterpret_cast<void**>(&b->merges), &b->merges_cap,
                         sizeof(tpc_merge) * (size_t)b->est_tracks) != TPC_OK)
             return TPC_ERR_NOMEM;
+        if (tr->params.t0 &&
+            grow_pinned(tr, reinterpret_cast<void**>(&b->t0s), &b->t0s_cap,
+                        sizeof(tpc_t0) * (size_t)b->est_tracks) != TPC_OK)
+            return TPC_ERR_NOMEM;
         e = cudaMemcpyAsync(b->counters, p.counters, sizeof(int) * kNumCounters, cudaMemcpyDeviceToHost, s);
         // first (track, hit) of every event, to slice the output per request
         if (e == cudaSuccess)
@@ -319,6 +324,9 @@ static int launch_batch_impl(tpc_tracker* tr)
                                 cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess && tr->params.merge)
             e = cudaMemcpyAsync(b->merges, p.out_merges, sizeof(tpc_merge) * (size_t)b->est_tracks,
+                                cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess && tr->params.t0)
+            e = cudaMemcpyAsync(b->t0s, p.out_t0s, sizeof(tpc_t0) * (size_t)b->est_tracks,
                                 cudaMemcpyDeviceToHost, s);
     } else {
         std::memset(b->counters, 0, sizeof(int) * kNumCounters);
@@ -375,6 +383,19 @@ static void finish_batch(tpc_tracker* tr, Batch& b)
                     b.fits = static_cast<tpc_fit*>(fp);
                     b.fits_cap = fc;
                     if (cudaMemcpy(b.fits, b.p.out_fits, sizeof(tpc_fit) * (size_t)M, cudaMemcpyDeviceToHost) !=
+                        cudaSuccess)
+                        err = TPC_ERR_DEVICE;
+                }
+            }
+            if (err == TPC_OK && tr->params.t0) {
+                void* tp0 = b.t0s;
+                size_t tc0 = b.t0s_cap;
+                if (grow_pinned(tr, &tp0, &tc0, sizeof(tpc_t0) * (size_t)M) != TPC_OK) {
+                    err = TPC_ERR_NOMEM;
+                } else {
+                    b.t0s = static_cast<tpc_t0*>(tp0);
+                    b.t0s_cap = tc0;
+                    if (cudaMemcpy(b.t0s, b.p.out_t0s, sizeof(tpc_t0) * (size_t)M, cudaMemcpyDeviceToHost) !=
                         cudaSuccess)
                         err = TPC_ERR_DEVICE;
                 }
@@ -459,6 +480,7 @@ void tpc_serve_shutdown(tpc_tracker* tr)
         cudaFreeHost(b.hits);
         cudaFreeHost(b.fits);
         cudaFreeHost(b.merges);
+        cudaFreeHost(b.t0s);
     }
     cudaFree(S->arena_base);
     cudaFreeHost(S->pin);
@@ -592,6 +614,7 @@ extern "C" int tpc_stream_poll(tpc_tracker* tr, uint64_t ticket, tpc_output* out
             std::memcpy(out->fits, b.fits + r->m0, sizeof(tpc_fit) * (size_t)M);
         if (M && out->merges && tr->params.merge)
             std::memcpy(out->merges, b.merges + r->m0, sizeof(tpc_merge) * (size_t)M);
+        if (M && out->t0s && tr->params.t0) std::memcpy(out->t0s, b.t0s + r->m0, sizeof(tpc_t0) * (size_t)M);
         S->stats.host_copy_ms += ms_since(t_copy);
     }
     release_ticket(tr, ticket);
@@ -618,6 +641,7 @@ extern "C" int tpc_stream_poll_view(tpc_tracker* tr, uint64_t ticket, tpc_stream
     view->hit_ids = b.hits + r->h0;
     view->fits = tr->params.refit ? b.fits + r->m0 : nullptr;
     view->merges = tr->params.merge ? b.merges + r->m0 : nullptr;
+    view->t0s = tr->params.t0 ? b.t0s + r->m0 : nullptr;
     view->n_tracks = r->m1 - r->m0;
     view->n_hits = r->h1 - r->h0;
     r->viewed = true;

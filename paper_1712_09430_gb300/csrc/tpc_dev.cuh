@@ -47,6 +47,8 @@ struct KConst {
     float mg_chi2, mg_gap, mg_overlap, mg_window;  // merging cuts
     float mg_cos, mg_sin;  // rotation between adjacent sectors, rounded once from double
     int mg_on;             // merge links are computed (params.merge)
+    float t0_ycut, t0_bin, t0_radius;  // collision offsets (continuous readout)
+    int t0_window, t0_nmin, t0_nb;     // t0_nb: bins over [-z_max, z_max)
     float tan_h, z_max;
     float bin_target;
     int l_seed, g_max, n_min_tracklet, n_min_track, own_num, own_den;
@@ -110,6 +112,14 @@ struct DevPtrs {
     unsigned long long* mg_best; // [2 Mcap] best outer / inner candidate keys
     int* unit_first;             // [n_units + 1] first track of each unit
     float2* mg_keys;             // [Mcap] (x of the innermost cluster, 1 if the refit succeeded)
+    tpc_t0* out_t0s;             // [Mcap] collision of each track
+    float* t0_u;                 // [Mcap] offset estimate
+    int* t0_bin;                 // [Mcap] its bin (-1: not a candidate), then nb + collision
+    int* t0_hist;                // [E * nb] counts
+    int* t0_peak;                // [E * nb] peak bins by increasing bin, then
+    int* t0_npeak;               // [E] their number
+    unsigned long long* t0_sum;  // [E * nb] integer sums of the members' offsets
+    int* t0_cnt;                 // [E * nb] member counts
     int* counters;             // [kNumCounters]
     int N, R, n_units, t_cap, m_cap, mh_cap;
 };
@@ -254,7 +264,8 @@ cudaError_t launch_dump_tl_work(const tpc::DevPtrs& p, int T, int* dst, cudaStre
     cudaError_t launch_seeds(const tpc::KConst& k, const float* row_x_dev, const tpc::DevPtrs& p,   \
                              int n_sm, int u0, int u1, cudaStream_t s);                             \
     cudaError_t launch_refit(const tpc::KConst& k, const tpc::DevPtrs& p, int n_sm, cudaStream_t s); \
-    cudaError_t launch_merge(const tpc::KConst& k, const tpc::DevPtrs& p, int n_sm, cudaStream_t s);
+    cudaError_t launch_merge(const tpc::KConst& k, const tpc::DevPtrs& p, int n_sm, cudaStream_t s);   \
+    cudaError_t launch_t0(const tpc::KConst& k, const tpc::DevPtrs& p, int n_sm, int n_events, cudaStream_t s);
 
 namespace tpc_exact { TPC_FP_DECLS }
 namespace tpc_fast { TPC_FP_DECLS }

@@ -62,6 +62,12 @@ static KConst make_kconst(const tpc_params& P, const tpc_geometry& G, double bz)
     k.mg_overlap = P.merge_overlap;
     k.mg_window = P.merge_window;
     k.mg_on = P.merge;
+    k.t0_ycut = P.t0_y_cut;
+    k.t0_bin = P.t0_bin;
+    k.t0_radius = P.t0_radius;
+    k.t0_window = P.t0_window;
+    k.t0_nmin = P.t0_n_min;
+    k.t0_nb = P.t0_bin > 0 ? (int)std::ceil(2.0 * (double)G.z_max / (double)P.t0_bin) : 1;
     // angle between adjacent sectors of one side: 360 deg / (n_sectors / 2)
     const double deg = 720.0 / (double)G.n_sectors;
     const double th = deg * (3.14159265358979323846 / 180.0);
@@ -103,6 +109,10 @@ static const char* check_params(const tpc_params& P)
     if (P.merge && !P.refit) return "merge needs refit = 1 (it compares refitted states)";
     if (!(P.merge_chi2 > 0) || !(P.merge_gap > 0) || !(P.merge_overlap >= 0) || !(P.merge_window > 0))
         return "merge cuts must be positive";
+    if (P.t0 != 0 && P.t0 != 1) return "t0 must be 0 or 1";
+    if (P.t0 && !P.refit) return "t0 needs refit = 1 (it extrapolates refitted states)";
+    if (!(P.t0_y_cut > 0) || !(P.t0_bin >= 0.01f) || !(P.t0_radius > 0) || P.t0_window < 0 || P.t0_n_min < 1)
+        return "t0 parameters";
     for (int i = 0; i < 5; i++)
         if (!std::isfinite(P.field[i])) return "field terms must be finite";
     return nullptr;
@@ -144,6 +154,12 @@ extern "C" void tpc_params_default(tpc_params* p)
     p->merge_gap = 50.0f;
     p->merge_overlap = 5.0f;
     p->merge_window = 5.0f;
+    p->t0 = 0;
+    p->t0_y_cut = 1.0f;
+    p->t0_bin = 0.25f;
+    p->t0_radius = 1.0f;
+    p->t0_window = 8;
+    p->t0_n_min = 8;
 }
 
 extern "C" int tpc_tracker_create(const tpc_geometry* g, double bz, const tpc_params* params,
@@ -295,6 +311,17 @@ size_t tpc_layout(const tpc_tracker* tr, const BatchShape& sh, DevPtrs* p, char*
     q.mg_best = reinterpret_cast<unsigned long long*>(take(Tc * 16));
     q.unit_first = reinterpret_cast<int*>(take(((size_t)sh.n_units + 1) * 4));
     q.mg_keys = reinterpret_cast<float2*>(take(Tc * 8));
+    {
+        const size_t E = (size_t)sh.n_events, nb = (size_t)std::max(tr->kc.t0_nb, 1);
+        q.out_t0s = reinterpret_cast<tpc_t0*>(take(Tc * sizeof(tpc_t0)));
+        q.t0_u = reinterpret_cast<float*>(take(Tc * 4));
+        q.t0_bin = reinterpret_cast<int*>(take(Tc * 4));
+        q.t0_hist = reinterpret_cast<int*>(take(E * nb * 4));
+        q.t0_peak = reinterpret_cast<int*>(take(E * nb * 4));
+        q.t0_npeak = reinterpret_cast<int*>(take(E * 4));
+        q.t0_sum = reinterpret_cast<unsigned long long*>(take(E * nb * 8));
+        q.t0_cnt = reinterpret_cast<int*>(take(E * nb * 4));
+    }
     // set by the serving loop for its batches; the synchronous call does not rebase
     q.req_first_event = nullptr;
     q.counters = reinterpret_cast<int*>(take(kNumCounters * 4));
@@ -534,6 +561,9 @@ int tpc_enqueue(tpc_tracker* tr, const DevPtrs& p, const BatchShape& sh, cudaStr
         TPC_CUDA(exact ? tpc_exact::launch_refit(k, p, tr->n_sm, s) : tpc_fast::launch_refit(k, p, tr->n_sm, s));
     if (P.merge)
         TPC_CUDA(exact ? tpc_exact::launch_merge(k, p, tr->n_sm, s) : tpc_fast::launch_merge(k, p, tr->n_sm, s));
+    if (P.t0)
+        TPC_CUDA(exact ? tpc_exact::launch_t0(k, p, tr->n_sm, sh.n_events, s)
+                       : tpc_fast::launch_t0(k, p, tr->n_sm, sh.n_events, s));
     if (p.req_first_event) TPC_CUDA(tpc_int::launch_rebase(k, p, tr->n_sm, s));
     if (with_events) TPC_CUDA(cudaEventRecord(tr->ev[6], s));
 #undef cudaEventRecord
@@ -628,6 +658,8 @@ int tpc_copy_out(tpc_tracker* tr, const DevPtrs& p, int M, int MH, tpc_output* o
         TPC_CUDA(cudaMemcpyAsync(out->fits, p.out_fits, sizeof(tpc_fit) * mt, kind, s));
     if (mt > 0 && out->merges && tr->params.merge)
         TPC_CUDA(cudaMemcpyAsync(out->merges, p.out_merges, sizeof(tpc_merge) * mt, kind, s));
+    if (mt > 0 && out->t0s && tr->params.t0)
+        TPC_CUDA(cudaMemcpyAsync(out->t0s, p.out_t0s, sizeof(tpc_t0) * mt, kind, s));
     TPC_CUDA(cudaStreamSynchronize(s));
     if (mt < M || mh < MH) return tr->fail(TPC_ERR_OUTPUT_TRUNCATED, "output capacity too small");
     return TPC_OK;

@@ -22,6 +22,8 @@ FIT_DTYPE = np.dtype([("x", np.float32), ("p", np.float32, 5), ("cov", np.float3
 assert FIT_DTYPE.itemsize == C.sizeof(capi.tpc_fit)
 MERGE_DTYPE = np.dtype([("next", np.int32), ("chi2", np.float32)])
 assert MERGE_DTYPE.itemsize == C.sizeof(capi.tpc_merge)
+T0_DTYPE = np.dtype([("collision", np.int32), ("u", np.float32), ("dz", np.float32)])
+assert T0_DTYPE.itemsize == C.sizeof(capi.tpc_t0)
 
 
 class TrackerError(RuntimeError):
@@ -57,11 +59,12 @@ class Result:
     params.refit the full Kalman filter refit of each track (FIT_DTYPE), and
     with params.merge each track's merge link (MERGE_DTYPE)."""
 
-    def __init__(self, tracks, hit_ids, fits=None, merges=None):
+    def __init__(self, tracks, hit_ids, fits=None, merges=None, t0s=None):
         self.tracks = tracks
         self.hit_ids = hit_ids
         self.fits = fits
         self.merges = merges
+        self.t0s = t0s
 
     def hits_of(self, m):
         t = self.tracks[m]
@@ -142,13 +145,11 @@ class Tracker:
         fixed = cap_tracks is not None or cap_hits is not None
         ct = cap_tracks if cap_tracks is not None else self._est_tracks
         ch = cap_hits if cap_hits is not None else self._est_hits
-        refit, merge = bool(self.params.refit), bool(self.params.merge)
         tracks = np.zeros(max(ct, 1), TRACK_DTYPE)
         hits = np.zeros(max(ch, 1), np.int32)
-        fits = np.zeros(max(ct, 1), FIT_DTYPE) if refit else None
-        merges = np.zeros(max(ct, 1), MERGE_DTYPE) if merge else None
+        opt = self._optional(max(ct, 1))
         out = capi.tpc_output(tracks.ctypes.data, hits.ctypes.data, ct, ch, capi.TPC_MEM_HOST, 0, 0,
-                              fits.ctypes.data if refit else None, merges.ctypes.data if merge else None)
+                              *self._ptrs(opt))
         rc = lib().tpc_track_sectors(self.h, _ptr(clusters), _ptr(rc_arr), int(n_events), kind,
                                      C.byref(out), stream)
         if rc == capi.TPC_ERR_OUTPUT_TRUNCATED and not fixed:
@@ -157,15 +158,25 @@ class Tracker:
             self._est_tracks, self._est_hits = int(ct * 1.25) + 16, int(ch * 1.25) + 256
             tracks = np.zeros(ct, TRACK_DTYPE)
             hits = np.zeros(ch, np.int32)
-            fits = np.zeros(ct, FIT_DTYPE) if refit else None
-            merges = np.zeros(ct, MERGE_DTYPE) if merge else None
+            opt = self._optional(ct)
             out = capi.tpc_output(tracks.ctypes.data, hits.ctypes.data, ct, ch, capi.TPC_MEM_HOST,
-                                  0, 0, fits.ctypes.data if refit else None,
-                                  merges.ctypes.data if merge else None)
+                                  0, 0, *self._ptrs(opt))
             rc = lib().tpc_fetch_output(self.h, C.byref(out))
         self.check(rc)
         return Result(tracks[:out.n_tracks], hits[:out.n_hits],
-                      fits[:out.n_tracks] if refit else None, merges[:out.n_tracks] if merge else None)
+                      *[a[:out.n_tracks] if a is not None else None for a in opt])
+
+    def _optional(self, n):
+        """Buffers of the optional per-track outputs the params switch on:
+        fits (refit), merges (merge), t0s (t0)."""
+        p = self.params
+        return (np.zeros(n, FIT_DTYPE) if p.refit else None,
+                np.zeros(n, MERGE_DTYPE) if p.merge else None,
+                np.zeros(n, T0_DTYPE) if p.t0 else None)
+
+    @staticmethod
+    def _ptrs(opt):
+        return [a.ctypes.data if a is not None else None for a in opt]
 
     # ---- serving (continuous batching) -----------------------------------
     def stream_configure(self, arena_bytes=0, max_batch_events=64, max_inflight=2, no_copy=False):
@@ -201,23 +212,18 @@ class Tracker:
         rc = lib().tpc_stream_poll(self.h, int(ticket), C.byref(out), int(timeout_us))
         if rc == capi.TPC_PENDING:
             return None
-        refit, merge = bool(self.params.refit), bool(self.params.merge)
         if rc == capi.TPC_OK:       # an empty result
-            return Result(np.zeros(0, TRACK_DTYPE), np.zeros(0, np.int32),
-                          np.zeros(0, FIT_DTYPE) if refit else None,
-                          np.zeros(0, MERGE_DTYPE) if merge else None)
+            return Result(np.zeros(0, TRACK_DTYPE), np.zeros(0, np.int32), *self._optional(0))
         if rc != capi.TPC_ERR_OUTPUT_TRUNCATED:
             self.check(rc)
         tracks = np.empty(max(out.n_tracks, 1), TRACK_DTYPE)
         hits = np.empty(max(out.n_hits, 1), np.int32)
-        fits = np.empty(max(out.n_tracks, 1), FIT_DTYPE) if refit else None
-        merges = np.empty(max(out.n_tracks, 1), MERGE_DTYPE) if merge else None
+        opt = self._optional(max(out.n_tracks, 1))
         out = capi.tpc_output(tracks.ctypes.data, hits.ctypes.data, len(tracks), len(hits),
-                              capi.TPC_MEM_HOST, 0, 0, fits.ctypes.data if refit else None,
-                              merges.ctypes.data if merge else None)
+                              capi.TPC_MEM_HOST, 0, 0, *self._ptrs(opt))
         self.check(lib().tpc_stream_poll(self.h, int(ticket), C.byref(out), 0))
         return Result(tracks[:out.n_tracks], hits[:out.n_hits],
-                      fits[:out.n_tracks] if refit else None, merges[:out.n_tracks] if merge else None)
+                      *[a[:out.n_tracks] if a is not None else None for a in opt])
 
     def poll_view(self, ticket, timeout_us=0):
         """Result of a ticket without a copy (numpy views of the library's
@@ -235,8 +241,9 @@ class Tracker:
             return np.frombuffer((C.c_char * (n * dt.itemsize)).from_address(ptr), dtype=dt)
         fits = arr(v.fits, v.n_tracks, FIT_DTYPE) if self.params.refit else None
         merges = arr(v.merges, v.n_tracks, MERGE_DTYPE) if self.params.merge else None
+        t0s = arr(v.t0s, v.n_tracks, T0_DTYPE) if self.params.t0 else None
         return Result(arr(v.tracks, v.n_tracks, TRACK_DTYPE), arr(v.hit_ids, v.n_hits, np.dtype(np.int32)),
-                      fits, merges)
+                      fits, merges, t0s)
 
     def release(self, ticket):
         self.check(lib().tpc_stream_release(self.h, int(ticket)))
