@@ -16,6 +16,10 @@ e2e        the same metric through the C ABI with pinned HOST buffers: H2D of
 roofline   the dominant kernel (tracklet constructor) against the measured HBM
            copy bandwidth
 cpu_baseline  the FP64 CPU oracle on the host cores, bounded sample
+refit      the final refit and the track merging on the same batch (Sec. 2
+           Phase II): device time, tracks/s, FP32 ALU roofline of the refit
+time_frame a continuous-readout time frame (Sec. 3.3): overlaid shifted
+           collisions, the whole chain with the per-collision offsets
 --impl reference  times the CPU oracle as the reference arm (same metric)
 
 Multi-GPU: events shard across ranks with no collective (weak scaling), one
@@ -47,19 +51,27 @@ WORKLOAD = "central Pb-Pb-like events: 10,000 primaries (pT exp mean 0.5 GeV/c, 
 def _gen_event(job):
     kind, seed = job
     from paper_1712_09430_gb300 import synth
+    if kind == "timeframe":
+        ev = synth.time_frame(seed=seed[0], n_coll=seed[1])
+        return ev.clusters, ev.row_counts, ev.label, ev.track_coll, ev.coll_dz
     ev = synth.central_event(seed=seed) if kind == "central" else synth.min_bias_event(seed)
     return ev.clusters, ev.row_counts
 
 
-def make_inputs(central_seeds, mb_seeds):
-    """Central batch and min-bias pool, generated in a spawned process pool
-    (it starts before any CUDA use in this process)."""
-    jobs = [("central", s) for s in central_seeds] + [("minbias", s) for s in mb_seeds]
+def make_inputs(central_seeds, mb_seeds, tf=None):
+    """Central batch, min-bias pool and (tf = (seed, collisions)) a
+    continuous-readout time frame, generated in a spawned process pool (it
+    starts before any CUDA use in this process)."""
+    jobs = [("timeframe", tf)] if tf else []
+    jobs += [("central", s) for s in central_seeds] + [("minbias", s) for s in mb_seeds]
     with mp.get_context("spawn").Pool(min(len(jobs), max(1, os.cpu_count() or 1), 16)) as pool:
         parts = pool.map(_gen_event, jobs)
+    frame = parts.pop(0) if tf else None
     nc = len(central_seeds)
     cl = np.ascontiguousarray(np.concatenate([p[0] for p in parts[:nc]]))
     rc = np.ascontiguousarray(np.concatenate([p[1] for p in parts[:nc]]))
+    if tf:
+        return cl, rc, parts[nc:], frame
     return cl, rc, parts[nc:]
 
 
@@ -214,7 +226,9 @@ def run_ours(args):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     seeds = rank_seeds(rank, args.batch)
     mb_seeds = [1000 + rank * args.pool + i for i in range(args.pool)] if args.stream_rates else []
-    cl_np, rc_np, mb_pool = make_inputs(seeds, mb_seeds)   # before any CUDA use
+    tf_job = (4 + rank, args.tf_collisions) if args.tf_collisions > 0 else None
+    cl_np, rc_np, mb_pool, *frame = make_inputs(seeds, mb_seeds, tf_job)   # before any CUDA use
+    frame = frame[0] if frame else None
     import torch
     import ctypes as C
     dist = None
@@ -294,6 +308,9 @@ def run_ours(args):
     refit = None
     if args.refit_steps > 0:
         refit = run_refit(L, tr, dev_cl, rc_ptr, B, sp, out, out_tr, args)
+    tframe = None
+    if frame is not None:
+        tframe = run_time_frame(frame, tr, args, dev_cl.device)
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -341,7 +358,7 @@ def run_ours(args):
             "gpu_launches": LAUNCHES_PER_STEP * args.steps,
             "clocks": ck, "e2e": e2e, "roofline": rl, "cpu_baseline": cpu,
             "plain_per_sector": plain, "multi_queue_per_sector": multi, "stream": stream_res,
-            "refit": refit}
+            "refit": refit, "time_frame": tframe}
     if stream_res:
         line["latency_ms"] = {"p50": stream_res[0]["p50_ms"], "p99": stream_res[0]["p99_ms"],
                               "rate_hz": stream_res[0]["rate_hz"]}
@@ -414,6 +431,62 @@ def run_refit(L, tr, dev_cl, rc_ptr, B, sp, out, out_tr, args):
                                   f"{REFIT_FLOPS_UPDATE} update) FP32 ops",
                          "peak_source": f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 "
                                         "lanes x 2 flops (FMA) x 2.07 GHz max SM clock (derived)"}}
+
+
+def run_time_frame(frame, tr0, args, device):
+    """A continuous-readout time frame (Sec. 3.3, Run 3 conditions): overlaid
+    min-bias collisions, each shifted by its unknown drift-time offset, tracked
+    as one event with the whole chain: tracking, refit, merging and the
+    per-collision offsets.  Inputs resident on the device; clusters/s of the
+    whole chain; the collisions found against the generator's offsets."""
+    import torch
+    from paper_1712_09430_gb300 import synth
+    from paper_1712_09430_gb300.tracker import Tracker
+    cl, rc, label, track_coll, coll_dz = frame
+    p = tr0.params
+    dev = torch.from_numpy(cl).to(device)
+    res = {}
+    for name, over in (("tracking", dict(refit=0, merge=0, t0=0)),
+                       ("chain", dict(refit=1, merge=1, t0=1))):
+        tr = Tracker(synth.row_x(), bz=0.5, use_graph=1, exact_fp32=p.exact_fp32,
+                     bin_target=p.bin_target, threads_per_row=p.threads_per_row,
+                     tracklets_per_warp=p.tracklets_per_warp, schedule=p.schedule, **over)
+        try:
+            for _ in range(3):
+                r = tr.track(dev, rc, 1)
+            torch.cuda.synchronize()
+            ms, st = [], np.zeros(7)
+            for _ in range(args.tf_steps):
+                r = tr.track(dev, rc, 1)
+                s7 = np.array(tr.stage_times())
+                ms.append(s7[5])
+                st += s7
+            st /= args.tf_steps
+        finally:
+            tr.close()
+        t = statistics.median(ms)
+        res[name] = {"ms": t, "clusters_per_s": len(cl) / (t * 1e-3), "after_selection_ms": float(st[6]),
+                     "tracks": int(len(r.tracks))}
+    # collisions found by the chain against the generator's offsets
+    coll = r.t0s["collision"]
+    maj = np.full(len(coll), -1)
+    for m in np.flatnonzero(coll >= 0):
+        v, c = np.unique(label[r.hits_of(m)], return_counts=True)
+        if v[np.argmax(c)] >= 0:
+            maj[m] = track_coll[v[np.argmax(c)]]
+    found = np.unique(coll[coll >= 0])
+    good = 0
+    for k in found:
+        sel = coll == k
+        if np.any(maj[sel] >= 0):
+            tc = np.bincount(maj[sel][maj[sel] >= 0]).argmax()
+            good += abs(float(r.t0s["dz"][sel][0]) - coll_dz[tc]) < 0.3
+    res.update({"clusters": int(len(cl)), "collisions": int(len(coll_dz)),
+                "collisions_found": int(len(found)), "found_within_0.3cm": int(good),
+                "tracks_assigned": float((coll >= 0).mean()),
+                "workload": f"time frame of {len(coll_dz)} min-bias collisions, each shifted by a drift "
+                            "offset ~ U[-250, 250] cm (continuous readout), 10% noise"})
+    return res
 
 
 def run_plain(L, tr, dev_cl, rc_ptr, B, N, world, sp, out, args, mode=1):
@@ -634,6 +707,9 @@ def main():
     ap.add_argument("--stream-seconds", type=float, default=2.0)
     ap.add_argument("--refit-steps", type=int, default=10,
                     help="steps of the final-refit leg (0: skip)")
+    ap.add_argument("--tf-collisions", type=int, default=50,
+                    help="collisions of the continuous-readout time-frame leg (0: skip)")
+    ap.add_argument("--tf-steps", type=int, default=5)
     ap.add_argument("--stream-batch", type=int, default=64, help="most events per serving batch")
     ap.add_argument("--stream-arena-gb", type=int, default=16)
     ap.add_argument("--pool", type=int, default=96, help="min-bias events in the serving pool")
