@@ -670,17 +670,18 @@ def algorithmic_bytes(tr, N, T):
     """Bytes the tracklet constructor moves by its own stage structure,
     counted exactly per tracklet by the kernel (TPC_DUMP_TRACKLET_WORK):
     per row step the row grid record (16 B), per bin-table row read two offsets
-    (8 B), per candidate cluster examined 8 B (its y, z), per seed-chain hit
-    16 B of cluster + 4 B of link, per Phase-2 cluster a 4 B write, and per
-    tracklet its 32 B seed record in and 68 B of state out."""
+    (8 B), per candidate cluster examined 8 B (its y, z), per Phase-2 cluster a
+    4 B write, and per tracklet its 80 B start record in (the state after the
+    seed chain, filtered by the seed kernel, and its row information) and 68 B
+    of state out."""
     from paper_1712_09430_gb300 import capi
     w = tr.dump(capi.TPC_DUMP_TRACKLET_WORK).astype(np.int64)
     n_hits = int(tr.dump(capi.TPC_DUMP_TRACKLET_N)[0].astype(np.int64).sum())
     steps, binrows, cand, chain = (int(v) for v in w.sum(axis=1))
-    b = 16 * steps + 8 * binrows + 8 * cand + 20 * chain + 4 * n_hits + T * (32 + 68)
+    b = 16 * steps + 8 * binrows + 8 * cand + 4 * n_hits + T * (80 + 68)
     return {"bytes": float(b), "row_steps": steps, "bin_rows": binrows, "candidates": cand,
             "chain_hits": chain, "tracklet_hits": n_hits,
-            "model": "16*row_steps + 8*bin_rows + 8*candidates + 20*chain_hits + 4*hits + 100*T"}
+            "model": "16*row_steps + 8*bin_rows + 8*candidates + 4*hits + 148*T"}
 
 
 def main():

@@ -8,6 +8,7 @@
 // division and square root, and no multiply-add is fused, so links, tracklet
 // clusters and selections are bit-identical to a CPU evaluation of the same
 // expressions.  The production build (tpc_fast) lets the compiler fuse.
+#include <algorithm>
 #include <cstdint>
 
 #include "tpc_dev.cuh"
@@ -441,10 +442,10 @@ __device__ __forceinline__ int search_row(const State& st, const RowGrid& g, flo
 
 // Tracklet construction (Sec. 2 step 2) as a per-lane state machine, so that
 // every iteration of the warp is one uniform row step: predict a copy of the
-// state to the row, take the chain cluster (phase 0) or search the window
-// (phases 1, 2), filter on a hit.  Phase 0/1: Phase 1 through the seed chain,
-// then outward; phase 2: fresh covariance, inward from the outermost cluster
-// to row 0, collecting the tracklet's clusters.
+// state to the row, search the window, filter on a hit.  Phase 1 through the
+// seed chain is done by k_seeds; here phase 1 continues outward, phase 2
+// (fresh covariance) goes inward from the outermost cluster to row 0,
+// collecting the tracklet's clusters.
 // The committed filter state of every lane lives in shared memory (16
 // floats, field-major so a warp's accesses hit distinct banks); registers
 // hold only the prediction of the current step.
@@ -452,9 +453,8 @@ constexpr int kTlThreads = 256;
 
 struct Lane {
     int t;        // tracklet, -1 idle
-    int phase;    // 0 chain, 1 outward search, 2 inward search
+    int phase;    // 1 outward search, 2 inward search
     int r;        // row of the next step
-    int h;        // next chain hit (phase 0)
     int ubase;    // row index of row 0 of the unit
     int r_out;    // row of the outermost filtered cluster
     int miss, n;
@@ -496,35 +496,67 @@ __device__ __forceinline__ void store_state(float* sp, const State& s, float chi
     sp[15 * kTlThreads] = chi2;
 }
 
+__device__ __forceinline__ void lane_finish(Lane& L, const KConst& k, const DevPtrs& p, bool writer);
+
+// End of Phase 1 (the search ran out, a step failed, or the rows ended):
+// Phase 2 starts from the outermost filtered cluster with a fresh covariance,
+// or the tracklet finishes without clusters.  Returns false when finished.
+__device__ __forceinline__ bool lane_end_phase1(Lane& L, const KConst& k, const DevPtrs& p, bool writer)
+{
+    if (L.have) {
+        L.phase = 2;
+        // fresh covariance and chi2 at the Phase-1 state
+        float* sp = L.sp;
+        sp[6 * kTlThreads] = k.sy2;
+        sp[7 * kTlThreads] = 0.0f;
+        sp[8 * kTlThreads] = k.var_s;
+        sp[9 * kTlThreads] = 0.0f;
+        sp[10 * kTlThreads] = 0.0f;
+        sp[11 * kTlThreads] = k.var_q;
+        sp[12 * kTlThreads] = k.sz2;
+        sp[13 * kTlThreads] = 0.0f;
+        sp[14 * kTlThreads] = k.var_t;
+        sp[15 * kTlThreads] = 0.0f;
+        L.r = L.r_out;
+        L.n = 0;
+        L.miss = 0;
+        return true;
+    }
+    lane_finish(L, k, p, writer);
+    return false;
+}
+
+// The seed chain was filtered by k_seeds (Phase 1 through the chain): start
+// at the first row after it, in Phase 1, or in Phase 2 when the chain ended
+// Phase 1 already.
 __device__ __forceinline__ void lane_init(Lane& L, int t, const KConst& k, const float* xs,
-                                          const DevPtrs& p)
+                                          const DevPtrs& p, bool writer)
 {
     const int NR = k.n_rows;
-    const float4 sd = __ldg(p.t_seed + t);  // one 32-byte record per tracklet
     const int4 info = __ldg(p.t_info + t);
+    const float4* src = p.t_state + (size_t)t * 4;
     const int rr0 = info.x;
     L.t = t;
     L.ubase = rr0 - rr0 % NR;
     L.z0 = (((rr0 / NR) % k.n_sectors) < k.n_sectors / 2) ? 0.0f : -k.z_max;
-    const int r0 = rr0 - L.ubase;
-    State st;
-    st.x = xs[r0];
-    st.y = sd.x;
-    st.z = sd.y;
-    st.s = sd.z;
-    st.t = sd.w;
-    st.q = 0.0f;
-    reset_cov(st, k);
-    store_state(L.sp, st, 0.0f);
-    L.phase = 0;
-    L.r = r0;
-    L.h = info.y;
-    L.have = false;
-    L.r_out = -1;
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        const float4 v = __ldg(src + i);
+        L.sp[(4 * i) * kTlThreads] = v.x;
+        L.sp[(4 * i + 1) * kTlThreads] = v.y;
+        L.sp[(4 * i + 2) * kTlThreads] = v.z;
+        L.sp[(4 * i + 3) * kTlThreads] = v.w;
+    }
+    L.phase = 1;
+    L.r = info.y;
+    L.r_out = (info.w & 0xffff) - 1;
+    L.have = L.r_out >= 0;
     L.miss = 0;
     L.n = 0;
     L.work = make_int4(0, 0, 0, info.z);
-    L.g = p.grid[rr0];  // not needed before the chain ends; the load overlaps it
+    const bool failed = (info.w >> 16) & 1;
+    if ((failed || L.r >= NR) && !lane_end_phase1(L, k, p, writer)) return;
+    L.g = p.grid[L.ubase + L.r];
 }
 
 __device__ __forceinline__ void lane_finish(Lane& L, const KConst& k, const DevPtrs& p, bool writer)
@@ -560,14 +592,7 @@ __device__ __forceinline__ void lane_step(Lane& L, const KConst& k, const float*
     const bool ok = propagate(pr, X, k.kB, k.s_max) && !outside(pr, X, k);
     int j = -1;
     float2 c = make_float2(0.0f, 0.0f);
-    if (ok) {
-        if (L.phase == 0) {
-            j = L.h;
-            c = __ldg(p.hyz + j);
-        } else {
-            j = search_row<G>(pr, L.g, -(X * k.tan_h + k.y_margin), L.z0, k, p, gl, gmask, L.work, c);
-        }
-    }
+    if (ok) j = search_row<G>(pr, L.g, -(X * k.tan_h + k.y_margin), L.z0, k, p, gl, gmask, L.work, c);
     bool end_phase = !ok;
     if (j >= 0) {
         float chi2 = L.sp[15 * kTlThreads];
@@ -585,41 +610,15 @@ __device__ __forceinline__ void lane_step(Lane& L, const KConst& k, const float*
         end_phase = ++L.miss > k.g_max;
     }
     if (!end_phase) {
-        if (L.phase == 0) {
-            L.h = p.up2[L.h];
-            L.r++;
-            if (L.h < 0) {
-                L.phase = 1;
-                end_phase = L.r >= NR;
-            }
-        } else if (L.phase == 1) {
-            end_phase = ++L.r >= NR;
-        } else {
-            end_phase = --L.r < 0;
-        }
+        if (L.phase == 1) end_phase = ++L.r >= NR;
+        else end_phase = --L.r < 0;
     }
     if (end_phase) {
-        if (L.phase < 2 && L.have) {
-            L.phase = 2;
-            // fresh covariance and chi2 at the Phase-1 state
-            float* sp = L.sp;
-            sp[6 * kTlThreads] = k.sy2;
-            sp[7 * kTlThreads] = 0.0f;
-            sp[8 * kTlThreads] = k.var_s;
-            sp[9 * kTlThreads] = 0.0f;
-            sp[10 * kTlThreads] = 0.0f;
-            sp[11 * kTlThreads] = k.var_q;
-            sp[12 * kTlThreads] = k.sz2;
-            sp[13 * kTlThreads] = 0.0f;
-            sp[14 * kTlThreads] = k.var_t;
-            sp[15 * kTlThreads] = 0.0f;
-            L.r = L.r_out;
-            L.n = 0;
-            L.miss = 0;
-        } else {
+        if (L.phase == 2) {
             lane_finish(L, k, p, gl == 0);
             return;
         }
+        if (!lane_end_phase1(L, k, p, gl == 0)) return;
     }
     L.g = p.grid[L.ubase + L.r];  // consumed by the next step; the load overlaps the loop
 }
@@ -657,7 +656,7 @@ __global__ void __launch_bounds__(kTlThreads, kTrackletCtasPerSm)
             int i = base + __popc(need & ((1u << gbase) - 1u));
             const bool mine = (need >> gbase) & 1u;
             if (mine) {
-                if (i < T) lane_init(L, by_row ? p.sched[i] : i, k, xs, p);
+                if (i < T) lane_init(L, by_row ? p.sched[i] : i, k, xs, p, gl == 0);
                 else done = true;
             }
         }
@@ -681,22 +680,32 @@ __global__ void __launch_bounds__(kTlThreads, 3) k_tracklets_plain(KConst k, con
     for (int t = t0 + blockIdx.x * blockDim.x + threadIdx.x; t < t1; t += gridDim.x * blockDim.x) {
         Lane L;
         L.sp = st_sh + threadIdx.x;
-        lane_init(L, t, k, xs, p);
+        lane_init(L, t, k, xs, p, true);
         while (L.t >= 0) lane_step<1>(L, k, xs, p, 0, self);
     }
 }
 
-// Seeds (T1): walk each seed chain to its last hit and compute the initial
-// state at the start hit from the chord to it: sin(phi) = dy / l,
-// tan(lambda) = dz / l, l = sqrt(dx^2 + dy^2).  One thread per tracklet.
+// Seeds (T1) and Phase 1 through the seed chain (T6): walk each chain to
+// its last hit, take the initial state at the start hit from the chord to it
+// (sin(phi) = dy / l, tan(lambda) = dz / l, l = sqrt(dx^2 + dy^2), q/pT = 0,
+// T1 covariance), then filter the chain's clusters in order: predict a copy
+// to the row (a failed step or a state outside the sector ends Phase 1),
+// update with the chain cluster, commit.  The constructor starts at the row
+// after the chain.  One thread per tracklet; these steps need no search, so
+// they run here rather than in the constructor's divergent loop.
 __global__ void k_seeds(KConst k, const float* __restrict__ row_x, DevPtrs p, int u0, int u1)
 {
     const int t0 = p.start_off[u0 * k.n_rows], t1 = p.start_off[u1 * k.n_rows];
     for (int t = t0 + blockIdx.x * blockDim.x + threadIdx.x; t < t1; t += gridDim.x * blockDim.x) {
         const int h0 = p.start[t];
+        // the first kChainCache chain clusters are kept for the filter loop
+        constexpr int kChainCache = 8;
+        int hc[kChainCache];
+        hc[0] = h0;
         int h = h0, len = 1;
         for (int j = p.up2[h]; j >= 0; j = p.up2[j]) {
             h = j;
+            if (len < kChainCache) hc[len] = j;
             len++;
         }
         const int rr0 = p.t_row[t];
@@ -704,8 +713,38 @@ __global__ void k_seeds(KConst k, const float* __restrict__ row_x, DevPtrs p, in
         const float2 c0 = p.hyz[h0], cL = p.hyz[h];
         const float dx = row_x[rL] - row_x[r0], dy = cL.x - c0.x, dz = cL.y - c0.y;
         const float l = sqrtf(dx * dx + dy * dy);
-        p.t_seed[t] = make_float4(c0.x, c0.y, dy / l, dz / l);
-        p.t_info[t] = make_int4(rr0, h0, len, 0);
+        State st;
+        st.x = row_x[r0];
+        st.y = c0.x;
+        st.z = c0.y;
+        st.s = dy / l;
+        st.t = dz / l;
+        st.q = 0.0f;
+        reset_cov(st, k);
+        float chi2 = 0.0f;
+        int r = r0, r_out = -1;
+        bool failed = false;
+        h = h0;
+        for (int i = 0; i < len; i++) {
+            if (i > 0) h = i < kChainCache ? hc[i] : p.up2[h];
+            State pr = st;
+            const float X = row_x[r];
+            if (!propagate(pr, X, k.kB, k.s_max) || outside(pr, X, k)) {
+                failed = true;
+                break;
+            }
+            const float2 c = p.hyz[h];
+            update(pr, c.x, c.y, k.sy2, k.sz2, chi2);
+            st = pr;
+            r_out = r;
+            r++;
+        }
+        float4* dst = p.t_state + (size_t)t * 4;
+        dst[0] = make_float4(st.x, st.y, st.z, st.s);
+        dst[1] = make_float4(st.t, st.q, st.cy[0], st.cy[1]);
+        dst[2] = make_float4(st.cy[2], st.cy[3], st.cy[4], st.cy[5]);
+        dst[3] = make_float4(st.cz[0], st.cz[1], st.cz[2], chi2);
+        p.t_info[t] = make_int4(rr0, r, len, (r_out + 1) | (failed ? 1 << 16 : 0));
         p.owned[t] = 0;  // counted by the selection
     }
 }
@@ -714,7 +753,9 @@ __global__ void k_seeds(KConst k, const float* __restrict__ row_x, DevPtrs p, in
 cudaError_t launch_seeds(const KConst& k, const float* row_x_dev, const DevPtrs& p, int n_sm, int u0,
                          int u1, cudaStream_t s)
 {
-    k_seeds<<<n_sm * 8, 256, 0, s>>>(k, row_x_dev, p, u0, u1);
+    // enough threads for every tracklet at once: the chain walks are latency-bound
+    const int blocks = std::max(1, std::min((p.t_cap + 255) / 256, n_sm * 64));
+    k_seeds<<<blocks, 256, 0, s>>>(k, row_x_dev, p, u0, u1);
     return cudaGetLastError();
 }
 

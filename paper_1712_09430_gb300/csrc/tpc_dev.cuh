@@ -86,8 +86,9 @@ struct DevPtrs {
     int* sched_off;            // [R + 1] schedule offsets (row-major order)
     int* start;                // [Tcap] binned index of the start hit of t
     int* t_row;                // [Tcap] row index rr of the start hit of t
-    float4* t_seed;            // [Tcap] seed state at the start hit: y, z, sin(phi), tan(lambda)
-    int4* t_info;              // [Tcap] row index rr of the start hit, start hit, chain length, 0
+    float4* t_state;           // [Tcap][4] filter state after the seed chain (16 floats)
+    int4* t_info;              // [Tcap] row index rr of the start hit, row after the chain,
+                               // chain length, (outermost filtered row + 1) | failed << 16
     int* sched;                // [Tcap] tracklets by expected length
     float* tl_f;               // [Tcap][16]
     int* tl_n;                 // [Tcap] Phase-2 cluster count

@@ -288,7 +288,7 @@ size_t tpc_layout(const tpc_tracker* tr, const BatchShape& sh, DevPtrs* p, char*
     q.sched_off = reinterpret_cast<int*>(take((R + 1) * 4));
     q.start = reinterpret_cast<int*>(take(Tc * 4));
     q.t_row = reinterpret_cast<int*>(take(Tc * 4));
-    q.t_seed = reinterpret_cast<float4*>(take(Tc * 16));
+    q.t_state = reinterpret_cast<float4*>(take(Tc * 64));
     q.t_info = reinterpret_cast<int4*>(take(Tc * 16));
     q.sched = reinterpret_cast<int*>(take(Tc * 4));
     q.tl_f = reinterpret_cast<float*>(take(Tc * kTlFloats * 4));
