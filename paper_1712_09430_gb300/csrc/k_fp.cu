@@ -446,9 +446,10 @@ __device__ __forceinline__ int search_row(const State& st, const RowGrid& g, flo
 // seed chain is done by k_seeds; here phase 1 continues outward, phase 2
 // (fresh covariance) goes inward from the outermost cluster to row 0,
 // collecting the tracklet's clusters.
-// The committed filter state of every lane lives in shared memory (16
-// floats, field-major so a warp's accesses hit distinct banks); registers
-// hold only the prediction of the current step.
+// The committed filter state of every lane is a 16-float array indexed only
+// by constants, so it stays in registers (3 CTAs per SM leave 85 per
+// thread); keeping it in shared memory to fit 4 CTAs per SM cost 7 % more in
+// loads and stores than the occupancy gained.
 constexpr int kTlThreads = 256;
 
 struct Lane {
@@ -461,39 +462,39 @@ struct Lane {
     bool have;
     float z0;     // grid z origin of the unit's side
     RowGrid g;    // grid record of row r, loaded one step ahead
-    float* sp;    // this lane's state column in shared memory (stride kTlThreads)
+    float* sp;    // this lane's committed state (16 floats, kept in registers)
     int4 work;
 };
 
 __device__ __forceinline__ State load_state(const float* sp)
 {
     State s;
-    s.x = sp[0 * kTlThreads];
-    s.y = sp[1 * kTlThreads];
-    s.z = sp[2 * kTlThreads];
-    s.s = sp[3 * kTlThreads];
-    s.t = sp[4 * kTlThreads];
-    s.q = sp[5 * kTlThreads];
+    s.x = sp[0];
+    s.y = sp[1];
+    s.z = sp[2];
+    s.s = sp[3];
+    s.t = sp[4];
+    s.q = sp[5];
 #pragma unroll
-    for (int i = 0; i < 6; i++) s.cy[i] = sp[(6 + i) * kTlThreads];
+    for (int i = 0; i < 6; i++) s.cy[i] = sp[6 + i];
 #pragma unroll
-    for (int i = 0; i < 3; i++) s.cz[i] = sp[(12 + i) * kTlThreads];
+    for (int i = 0; i < 3; i++) s.cz[i] = sp[12 + i];
     return s;
 }
 
 __device__ __forceinline__ void store_state(float* sp, const State& s, float chi2)
 {
-    sp[0 * kTlThreads] = s.x;
-    sp[1 * kTlThreads] = s.y;
-    sp[2 * kTlThreads] = s.z;
-    sp[3 * kTlThreads] = s.s;
-    sp[4 * kTlThreads] = s.t;
-    sp[5 * kTlThreads] = s.q;
+    sp[0] = s.x;
+    sp[1] = s.y;
+    sp[2] = s.z;
+    sp[3] = s.s;
+    sp[4] = s.t;
+    sp[5] = s.q;
 #pragma unroll
-    for (int i = 0; i < 6; i++) sp[(6 + i) * kTlThreads] = s.cy[i];
+    for (int i = 0; i < 6; i++) sp[6 + i] = s.cy[i];
 #pragma unroll
-    for (int i = 0; i < 3; i++) sp[(12 + i) * kTlThreads] = s.cz[i];
-    sp[15 * kTlThreads] = chi2;
+    for (int i = 0; i < 3; i++) sp[12 + i] = s.cz[i];
+    sp[15] = chi2;
 }
 
 __device__ __forceinline__ void lane_finish(Lane& L, const KConst& k, const DevPtrs& p, bool writer);
@@ -507,16 +508,16 @@ __device__ __forceinline__ bool lane_end_phase1(Lane& L, const KConst& k, const 
         L.phase = 2;
         // fresh covariance and chi2 at the Phase-1 state
         float* sp = L.sp;
-        sp[6 * kTlThreads] = k.sy2;
-        sp[7 * kTlThreads] = 0.0f;
-        sp[8 * kTlThreads] = k.var_s;
-        sp[9 * kTlThreads] = 0.0f;
-        sp[10 * kTlThreads] = 0.0f;
-        sp[11 * kTlThreads] = k.var_q;
-        sp[12 * kTlThreads] = k.sz2;
-        sp[13 * kTlThreads] = 0.0f;
-        sp[14 * kTlThreads] = k.var_t;
-        sp[15 * kTlThreads] = 0.0f;
+        sp[6] = k.sy2;
+        sp[7] = 0.0f;
+        sp[8] = k.var_s;
+        sp[9] = 0.0f;
+        sp[10] = 0.0f;
+        sp[11] = k.var_q;
+        sp[12] = k.sz2;
+        sp[13] = 0.0f;
+        sp[14] = k.var_t;
+        sp[15] = 0.0f;
         L.r = L.r_out;
         L.n = 0;
         L.miss = 0;
@@ -542,10 +543,10 @@ __device__ __forceinline__ void lane_init(Lane& L, int t, const KConst& k, const
 #pragma unroll
     for (int i = 0; i < 4; i++) {
         const float4 v = __ldg(src + i);
-        L.sp[(4 * i) * kTlThreads] = v.x;
-        L.sp[(4 * i + 1) * kTlThreads] = v.y;
-        L.sp[(4 * i + 2) * kTlThreads] = v.z;
-        L.sp[(4 * i + 3) * kTlThreads] = v.w;
+        L.sp[4 * i] = v.x;
+        L.sp[4 * i + 1] = v.y;
+        L.sp[4 * i + 2] = v.z;
+        L.sp[4 * i + 3] = v.w;
     }
     L.phase = 1;
     L.r = info.y;
@@ -572,8 +573,8 @@ __device__ __forceinline__ void lane_finish(Lane& L, const KConst& k, const DevP
             const float* sp = L.sp;
 #pragma unroll
             for (int i = 0; i < 4; i++)
-                __stcs(f4 + i, make_float4(sp[(4 * i) * kTlThreads], sp[(4 * i + 1) * kTlThreads],
-                                           sp[(4 * i + 2) * kTlThreads], sp[(4 * i + 3) * kTlThreads]));
+                __stcs(f4 + i, make_float4(sp[4 * i], sp[4 * i + 1],
+                                           sp[4 * i + 2], sp[4 * i + 3]));
         } else {
             const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
             __stcs(f4 + 0, z); __stcs(f4 + 1, z); __stcs(f4 + 2, z); __stcs(f4 + 3, z);
@@ -595,7 +596,7 @@ __device__ __forceinline__ void lane_step(Lane& L, const KConst& k, const float*
     if (ok) j = search_row<G>(pr, L.g, -(X * k.tan_h + k.y_margin), L.z0, k, p, gl, gmask, L.work, c);
     bool end_phase = !ok;
     if (j >= 0) {
-        float chi2 = L.sp[15 * kTlThreads];
+        float chi2 = L.sp[15];
         update(pr, c.x, c.y, k.sy2, k.sz2, chi2);
         store_state(L.sp, pr, chi2);
         if (L.phase == 2) {
@@ -626,14 +627,14 @@ __device__ __forceinline__ void lane_step(Lane& L, const KConst& k, const float*
 // Persistent, dynamically scheduled constructor: idle lane groups take the
 // next entries of the length-sorted schedule (long expected tracks first)
 // from a global counter, with one warp-aggregated atomic per refill.
-constexpr int kTrackletCtasPerSm = 4;  // 256 threads each: 32 warps per SM, <= 64 registers
+constexpr int kTrackletCtasPerSm = 3;  // 256 threads each: 24 warps per SM, <= 85 registers
 
 template <int G>
 __global__ void __launch_bounds__(kTlThreads, kTrackletCtasPerSm)
     k_tracklets_sched(KConst k, const float* __restrict__ row_x, DevPtrs p, int by_row)
 {
     __shared__ float xs[TPC_MAX_ROWS];
-    __shared__ float st_sh[16 * kTlThreads];
+    float st_sh[16];
     for (int r = threadIdx.x; r < k.n_rows; r += blockDim.x) xs[r] = row_x[r];
     __syncthreads();
     const unsigned FULL = 0xffffffffu;
@@ -644,7 +645,7 @@ __global__ void __launch_bounds__(kTlThreads, kTrackletCtasPerSm)
     const unsigned gmask = (G == 32) ? FULL : (((1u << G) - 1u) << gbase);
     Lane L;
     L.t = -1;
-    L.sp = st_sh + threadIdx.x;
+    L.sp = st_sh;
     bool done = false;
     while (true) {
         const unsigned need = __ballot_sync(FULL, L.t < 0 && !done && gl == 0);
@@ -672,14 +673,14 @@ __global__ void __launch_bounds__(kTlThreads, 3) k_tracklets_plain(KConst k, con
                                                                    DevPtrs p, int u0, int u1)
 {
     __shared__ float xs[TPC_MAX_ROWS];
-    __shared__ float st_sh[16 * kTlThreads];
+    float st_sh[16];
     for (int r = threadIdx.x; r < k.n_rows; r += blockDim.x) xs[r] = row_x[r];
     __syncthreads();
     const int t0 = p.start_off[u0 * k.n_rows], t1 = p.start_off[u1 * k.n_rows];
     const unsigned self = 1u << (threadIdx.x & 31);
     for (int t = t0 + blockIdx.x * blockDim.x + threadIdx.x; t < t1; t += gridDim.x * blockDim.x) {
         Lane L;
-        L.sp = st_sh + threadIdx.x;
+        L.sp = st_sh;
         lane_init(L, t, k, xs, p, true);
         while (L.t >= 0) lane_step<1>(L, k, xs, p, 0, self);
     }
