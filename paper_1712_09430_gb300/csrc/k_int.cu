@@ -443,7 +443,12 @@ __global__ void __launch_bounds__(1024) k_owner_units(KConst k, DevPtrs p, int c
         }
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < hi - lo; i += blockDim.x) p.owner[lo + i] = keys[i];
+    // keys out, and the clusters each tracklet owns (decoded from the key)
+    for (int i = threadIdx.x; i < hi - lo; i += blockDim.x) {
+        const unsigned key = keys[i];
+        p.owner[lo + i] = key;
+        if (key) atomicAdd(&p.owned[t0 + (int)(0x7FFFFFu - (key & 0x7FFFFFu))], 1);
+    }
 }
 
 // Clusters owned per tracklet: one pass over the clusters (a warp per row,
@@ -703,7 +708,7 @@ cudaError_t launch_start_write(const KConst& k, const DevPtrs& p, int threads, i
 }
 
 cudaError_t launch_select(const KConst& k, const DevPtrs& p, int n_sm, int u0, int u1, bool owner,
-                          cudaStream_t s)
+                          cudaStream_t s, bool counted)
 {
     if (owner) {  // the persistent constructor claims ownership itself
         k_owner<<<n_sm * 8, 256, 0, s>>>(k, p, u0, u1);
@@ -711,14 +716,16 @@ cudaError_t launch_select(const KConst& k, const DevPtrs& p, int n_sm, int u0, i
         if (e != cudaSuccess) return e;
     }
     const int rows = (u1 - u0) * k.n_rows;
-    if (rows > 0) k_owned_count<<<(rows + 7) / 8, 256, 0, s>>>(k, p, u0 * k.n_rows, rows);
+    if (rows > 0 && !counted) k_owned_count<<<(rows + 7) / 8, 256, 0, s>>>(k, p, u0 * k.n_rows, rows);
     k_accept<<<n_sm * 8, 256, 0, s>>>(k, p, u0, u1);
     return cudaGetLastError();
 }
 
+// Ownership with owned counts (the per-unit kernel counts them as well).
 cudaError_t launch_owner_units(const KConst& k, const DevPtrs& p, int n_units, int max_unit,
-                               cudaStream_t s)
+                               cudaStream_t s, bool* counted)
 {
+    *counted = true;
     if (n_units == 0 || max_unit == 0) return cudaSuccess;
     const int chunks = (max_unit + kOwnerChunk - 1) / kOwnerChunk;
     const size_t sm = (size_t)std::min(max_unit, kOwnerChunk) * 4;

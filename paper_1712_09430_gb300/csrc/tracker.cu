@@ -480,8 +480,9 @@ int tpc_enqueue(tpc_tracker* tr, const DevPtrs& p, const BatchShape& sh, cudaStr
         if (with_events) TPC_CUDA(cudaEventRecord(tr->ev[3], s));
         TPC_CUDA(tl(-1, -1));
         if (with_events) TPC_CUDA(cudaEventRecord(tr->ev[4], s));
-        TPC_CUDA(tpc_int::launch_owner_units(k, p, sh.n_units, sh.max_unit, s));
-        TPC_CUDA(tpc_int::launch_select(k, p, tr->n_sm, 0, sh.n_units, false, s));
+        bool counted = false;
+        TPC_CUDA(tpc_int::launch_owner_units(k, p, sh.n_units, sh.max_unit, s, &counted));
+        TPC_CUDA(tpc_int::launch_select(k, p, tr->n_sm, 0, sh.n_units, false, s, counted));
     } else if (P.plain_per_sector == 2) {
         // Multi-queue scheme (Sec. 3.1, Fig. 3): each unit's stages in order
         // on one of n_queues streams, units round-robin; the two global steps
