@@ -12,7 +12,9 @@ value      clusters/s, inputs resident in device memory when the timed region
            starts; the batch (B x 33 MB of clusters) exceeds the 129 MB L2
 e2e        the same metric through the C ABI with pinned HOST buffers: H2D of
            the clusters and row counts and D2H of the tracks inside the timed
-           region
+           region; through the serving API with two batches in flight, so one
+           batch's copies overlap the other's kernels (e2e_sync: the
+           synchronous call, copies and kernels in turn)
 roofline   the dominant kernel (tracklet constructor) against the measured HBM
            copy bandwidth
 cpu_baseline  the FP64 CPU oracle on the host cores, bounded sample
@@ -295,9 +297,11 @@ def run_ours(args):
     value = N * world / (ms * 1e-3)
 
     # ---- end to end through the C ABI with pinned host buffers
-    e2e = None
+    e2e = e2e_sync = None
     if not args.no_e2e:
-        e2e = run_e2e(L, tr, cl_np, rc_ptr, rc_np, B, N, world, sp, cap_t, cap_h, args)
+        e2e_sync = run_e2e(L, tr, cl_np, rc_ptr, rc_np, B, N, world, sp, cap_t, cap_h, args)
+        e2e_sync["api"] = "tpc_track_sectors with host buffers (synchronous: H2D, kernels, D2H in turn)"
+        e2e = run_e2e_stream(tr, cl_np, rc_np, B, N, world, args)
     plain = multi = None
     if args.plain_steps > 0:
         plain = run_plain(L, tr, dev_cl, rc_ptr, B, N, world, sp, out, args, mode=1)
@@ -356,7 +360,7 @@ def run_ours(args):
             "events_per_s": B * world / (ms * 1e-3),
             "stage_ms": stage_ms, "wall_s": wall,
             "gpu_launches": LAUNCHES_PER_STEP * args.steps,
-            "clocks": ck, "e2e": e2e, "roofline": rl, "cpu_baseline": cpu,
+            "clocks": ck, "e2e": e2e, "e2e_sync": e2e_sync, "roofline": rl, "cpu_baseline": cpu,
             "plain_per_sector": plain, "multi_queue_per_sector": multi, "stream": stream_res,
             "refit": refit, "time_frame": tframe}
     if stream_res:
@@ -642,6 +646,62 @@ def run_e2e(L, tr, cl_np, rc_ptr, rc_np, B, N, world, sp, cap_t, cap_h, args):
     d2h = hout.n_tracks * TRACK_DTYPE.itemsize + hout.n_hits * 4 + 64
     return {"value": N * world / e2e_s, "unit": "clusters/s", "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_s * 1e3, "steps": k2}
+
+
+def run_e2e_stream(tr0, cl_np, rc_np, B, N, world, args):
+    """Same metric end to end through the serving API: every step submits the
+    8-event batch from pinned host memory (tpc_stream_submit, no copy) and
+    takes its tracks from the library's pinned result buffers
+    (tpc_stream_poll_view); two batches are in flight, so one batch's H2D and
+    D2H overlap the other's kernels (the pipelining of Sec. 3.1)."""
+    import torch
+    from collections import deque
+    from paper_1712_09430_gb300 import synth
+    from paper_1712_09430_gb300.tracker import TRACK_DTYPE, Tracker
+    p = tr0.params
+    tr = Tracker(synth.row_x(), bz=0.5, exact_fp32=p.exact_fp32, bin_target=p.bin_target,
+                 threads_per_row=p.threads_per_row, tracklets_per_warp=p.tracklets_per_warp,
+                 schedule=p.schedule)
+    try:
+        pin = torch.from_numpy(cl_np).pin_memory()
+        tr.stream_configure(arena_bytes=args.stream_arena_gb << 30, max_batch_events=B, max_inflight=2,
+                            no_copy=True)
+        state = {"tracks": 0, "hits": 0}
+
+        def take(t):
+            r = None
+            while r is None:
+                r = tr.poll_view(t, timeout_us=1000)
+            state["tracks"] = len(r.tracks)
+            state["hits"] = len(r.hit_ids)
+            tr.release(t)
+
+        def run(k):
+            q = deque()
+            for _ in range(k):
+                t = tr.submit(pin, rc_np, B)
+                while t is None:          # not admitted now: finish the oldest first
+                    take(q.popleft())
+                    t = tr.submit(pin, rc_np, B)
+                q.append(t)
+                if len(q) > 2:
+                    take(q.popleft())
+            while q:
+                take(q.popleft())
+        run(3)
+        torch.cuda.synchronize()
+        k2 = max(3, args.steps // 2)
+        t1 = time.perf_counter()
+        run(k2)
+        e2e_s = (time.perf_counter() - t1) / k2
+    finally:
+        tr.close()
+    h2d = N * 16 + len(rc_np) * 4
+    d2h = state["tracks"] * TRACK_DTYPE.itemsize + state["hits"] * 4 + 64
+    return {"value": N * world / e2e_s, "unit": "clusters/s", "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_s * 1e3, "steps": k2,
+            "api": "tpc_stream_submit (no copy) + tpc_stream_poll_view/release, two batches in flight: "
+                   "H2D and D2H of one batch overlap the kernels of the other"}
 
 
 def measured_traffic(kernel_source, summary):
