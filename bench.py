@@ -311,7 +311,7 @@ def run_ours(args):
         stream_res = [run_stream(tr, mb_pool, args, rate) for rate in args.stream_rates]
     refit = None
     if args.refit_steps > 0:
-        refit = run_refit(L, tr, dev_cl, rc_ptr, B, sp, out, out_tr, args)
+        refit = run_refit(L, tr, dev_cl, rc_ptr, B, sp, out, out_tr, out_h, args)
     tframe = None
     if frame is not None:
         tframe = run_time_frame(frame, tr, args, dev_cl.device)
@@ -381,7 +381,7 @@ REFIT_FLOPS_UPDATE = 258
 FP32_LANES_PER_SM = 128  # Blackwell SM: 4 x 32 FP32 lanes, one FMA (2 flops) per lane per clock
 
 
-def run_refit(L, tr, dev_cl, rc_ptr, B, sp, out, out_tr, args):
+def run_refit(L, tr, dev_cl, rc_ptr, B, sp, out, out_tr, out_h, args):
     """The final full Kalman filter refit (Sec. 2 "Track fit") over the same
     batch: the batched step with params.refit = 1, the refit stage timed by
     its own CUDA events (stage 6).  Roofline: FP32 ALU (the refit does ~20
@@ -425,7 +425,11 @@ def run_refit(L, tr, dev_cl, rc_ptr, B, sp, out, out_tr, args):
     peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * 2.07e9 / 1e12
     achieved = flops / t / 1e12
     merge_ms = statistics.median(ms_merge) - t * 1e3
-    return {"ms": t * 1e3, "merge_ms": merge_ms, "tracks": int(M), "filter_steps": steps,
+    cpu = None
+    if not args.no_cpu_baseline:
+        hits = out_h[:out.n_hits].cpu().numpy()
+        cpu = oracle_phase2_baseline(tracks, hits, dev_cl.cpu().numpy())
+    return {"ms": t * 1e3, "merge_ms": merge_ms, "tracks": int(M), "filter_steps": steps, "cpu_baseline": cpu,
             "tracks_per_s": M / t, "clusters_per_s": float(n.sum()) / t,
             "mode": "exact" if args.exact else "production",
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
@@ -435,6 +439,34 @@ def run_refit(L, tr, dev_cl, rc_ptr, B, sp, out, out_tr, args):
                                   f"{REFIT_FLOPS_UPDATE} update) FP32 ops",
                          "peak_source": f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 "
                                         "lanes x 2 flops (FMA) x 2.07 GHz max SM clock (derived)"}}
+
+
+def oracle_phase2_baseline(tracks, hits, clusters, bz=0.5):
+    """The refit and merging oracles (FP64, as they stand, OpenMP for the
+    refit) on the host cores, on the tracks of the first event of the batch:
+    tracks/s of each.  tracks: host TRACK_DTYPE with hit_off into hits."""
+    import oracle
+    sel = np.flatnonzero(tracks["event"] == 0)
+    if len(sel) == 0:
+        return None
+    t = tracks[sel]
+    off = np.zeros(len(t) + 1, np.int64)
+    off[1:] = np.cumsum(t["nhits"])
+    h = np.concatenate([hits[a:a + n] for a, n in zip(t["hit_off"], t["nhits"])])
+    st6 = np.concatenate([t["x"][:, None], t["p"]], axis=1).astype(np.float64)
+    fp = oracle.fit_params(bz)
+    t0 = time.perf_counter()
+    fits = oracle.refit_lists(st6, off, h, clusters, fp, mode="f64")
+    t_refit = time.perf_counter() - t0
+    unit = t["event"].astype(np.int32) * 36 + t["sector"]
+    x_last = clusters[h[off[1:] - 1], 0].astype(np.float64)
+    t0 = time.perf_counter()
+    oracle.merge_tracks(unit, fits, x_last, fp, mode="f64")
+    t_merge = time.perf_counter() - t0
+    return {"kind": "oracle", "cores": oracle.max_threads(), "tracks": int(len(t)),
+            "refit_tracks_per_s": len(t) / t_refit, "merge_tracks_per_s": len(t) / t_merge,
+            "sample": f"the {len(t)} tracks of one central event; FP64 refit oracle (OpenMP over tracks) "
+                      "and merging oracle (one thread)"}
 
 
 def run_time_frame(frame, tr0, args, device):
@@ -451,6 +483,7 @@ def run_time_frame(frame, tr0, args, device):
     dev = torch.from_numpy(cl).to(device)
     res = {}
     for name, over in (("tracking", dict(refit=0, merge=0, t0=0)),
+                       ("refit_merge", dict(refit=1, merge=1, t0=0)),
                        ("chain", dict(refit=1, merge=1, t0=1))):
         tr = Tracker(synth.row_x(), bz=0.5, use_graph=1, exact_fp32=p.exact_fp32,
                      bin_target=p.bin_target, threads_per_row=p.threads_per_row,
@@ -471,6 +504,7 @@ def run_time_frame(frame, tr0, args, device):
         t = statistics.median(ms)
         res[name] = {"ms": t, "clusters_per_s": len(cl) / (t * 1e-3), "after_selection_ms": float(st[6]),
                      "tracks": int(len(r.tracks))}
+    res["collision_offsets_ms"] = res["chain"]["ms"] - res["refit_merge"]["ms"]
     # collisions found by the chain against the generator's offsets
     coll = r.t0s["collision"]
     maj = np.full(len(coll), -1)
@@ -485,6 +519,18 @@ def run_time_frame(frame, tr0, args, device):
         if np.any(maj[sel] >= 0):
             tc = np.bincount(maj[sel][maj[sel] >= 0]).argmax()
             good += abs(float(r.t0s["dz"][sel][0]) - coll_dz[tc]) < 0.3
+    if not args.no_cpu_baseline:
+        import oracle
+        f = r.fits
+        fits = np.concatenate([f["x"][:, None], f["p"], f["cov"], f["chi2"][:, None],
+                               f["ndf"][:, None], f["status"][:, None]], axis=1).astype(np.float64)
+        unit = r.tracks["event"].astype(np.int32) * 36 + r.tracks["sector"]
+        t0 = time.perf_counter()
+        oracle.t0_tracks(unit, fits, oracle.fit_params(0.5), mode="f64")
+        dt = time.perf_counter() - t0
+        res["cpu_baseline"] = {"kind": "oracle", "cores": 1, "tracks_per_s": len(unit) / dt,
+                               "sample": f"the collision offsets of this time frame's {len(unit)} refitted "
+                                         "tracks, FP64 oracle, one thread"}
     res.update({"clusters": int(len(cl)), "collisions": int(len(coll_dz)),
                 "collisions_found": int(len(found)), "found_within_0.3cm": int(good),
                 "tracks_assigned": float((coll >= 0).mean()),
