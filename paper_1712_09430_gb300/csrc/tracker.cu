@@ -303,24 +303,27 @@ size_t tpc_layout(const tpc_tracker* tr, const BatchShape& sh, DevPtrs* p, char*
     q.start_part = reinterpret_cast<int*>(take((R / kScanTile + 2) * 2 * 4));
     q.out_tracks = reinterpret_cast<tpc_track*>(take(Tc * sizeof(tpc_track)));
     q.out_hits = reinterpret_cast<int*>(take(N * 4));
-    q.out_fits = reinterpret_cast<tpc_fit*>(take(Tc * sizeof(tpc_fit)));
-    q.fit_bins = reinterpret_cast<int*>(take(2 * (TPC_MAX_ROWS + 1) * 4));
+    // the optional stages' buffers exist only when the stage is switched on
+    const tpc_params& P = tr->params;
+    auto opt = [&](bool on, size_t bytes) -> char* { return on ? take(bytes) : nullptr; };
+    q.out_fits = reinterpret_cast<tpc_fit*>(opt(P.refit, Tc * sizeof(tpc_fit)));
+    q.fit_bins = reinterpret_cast<int*>(opt(P.refit, 2 * (TPC_MAX_ROWS + 1) * 4));
     q.ev_first = reinterpret_cast<int2*>(take(((size_t)sh.n_events + 1) * 8));
     q.req_area = reinterpret_cast<int*>(take((size_t)sh.n_events * 4));
-    q.out_merges = reinterpret_cast<tpc_merge*>(take(Tc * sizeof(tpc_merge)));
-    q.mg_best = reinterpret_cast<unsigned long long*>(take(Tc * 16));
-    q.unit_first = reinterpret_cast<int*>(take(((size_t)sh.n_units + 1) * 4));
-    q.mg_keys = reinterpret_cast<float2*>(take(Tc * 8));
+    q.out_merges = reinterpret_cast<tpc_merge*>(opt(P.merge, Tc * sizeof(tpc_merge)));
+    q.mg_best = reinterpret_cast<unsigned long long*>(opt(P.merge, Tc * 16));
+    q.unit_first = reinterpret_cast<int*>(opt(P.merge, ((size_t)sh.n_units + 1) * 4));
+    q.mg_keys = reinterpret_cast<float2*>(opt(P.merge, Tc * 8));
     {
         const size_t E = (size_t)sh.n_events, nb = (size_t)std::max(tr->kc.t0_nb, 1);
-        q.out_t0s = reinterpret_cast<tpc_t0*>(take(Tc * sizeof(tpc_t0)));
-        q.t0_u = reinterpret_cast<float*>(take(Tc * 4));
-        q.t0_bin = reinterpret_cast<int*>(take(Tc * 4));
-        q.t0_hist = reinterpret_cast<int*>(take(E * nb * 4));
-        q.t0_peak = reinterpret_cast<int*>(take(E * nb * 4));
-        q.t0_npeak = reinterpret_cast<int*>(take(E * 4));
-        q.t0_sum = reinterpret_cast<unsigned long long*>(take(E * nb * 8));
-        q.t0_cnt = reinterpret_cast<int*>(take(E * nb * 4));
+        q.out_t0s = reinterpret_cast<tpc_t0*>(opt(P.t0, Tc * sizeof(tpc_t0)));
+        q.t0_u = reinterpret_cast<float*>(opt(P.t0, Tc * 4));
+        q.t0_bin = reinterpret_cast<int*>(opt(P.t0, Tc * 4));
+        q.t0_hist = reinterpret_cast<int*>(opt(P.t0, E * nb * 4));
+        q.t0_peak = reinterpret_cast<int*>(opt(P.t0, E * nb * 4));
+        q.t0_npeak = reinterpret_cast<int*>(opt(P.t0, E * 4));
+        q.t0_sum = reinterpret_cast<unsigned long long*>(opt(P.t0, E * nb * 8));
+        q.t0_cnt = reinterpret_cast<int*>(opt(P.t0, E * nb * 4));
     }
     // set by the serving loop for its batches; the synchronous call does not rebase
     q.req_first_event = nullptr;
