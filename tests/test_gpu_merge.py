@@ -139,3 +139,16 @@ def test_merge_needs_refit():
     from paper_1712_09430_gb300.tracker import TrackerError
     with pytest.raises(TrackerError):
         Tracker(XR, refit=0, merge=1)
+
+
+def test_merge_full_size_central_exact():
+    """Two full central events (4.1 M clusters), exact build: the merging
+    oracle on the GPU's refitted tracks gives the same links."""
+    evs = [S.central_event(seed=3), S.central_event(seed=4)]
+    cl, rc = S.concat_events(evs)
+    r = gpu_merge(cl, rc, 2, exact_fp32=1)
+    assert len(r.tracks) > 40000
+    nxt, chi = oracle_merge(r, cl, 0.5, "f32")
+    np.testing.assert_array_equal(r.merges["next"], nxt)
+    np.testing.assert_array_equal(r.merges["chi2"].view(np.uint32), chi.astype(np.float32).view(np.uint32))
+    assert (nxt >= 0).sum() > 100

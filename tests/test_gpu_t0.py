@@ -126,3 +126,15 @@ def test_t0_serving_equals_alone(frames):
 def test_t0_needs_refit():
     with pytest.raises(TrackerError):
         Tracker(XR, refit=0, t0=1)
+
+
+def test_t0_full_size_time_frame_exact():
+    """The full 50-collision time frame (5.5 M clusters) in the exact build:
+    the oracle's collision offsets on the GPU's refitted tracks agree bit for
+    bit."""
+    ev = S.time_frame(seed=4)
+    r = gpu_t0(ev.clusters, ev.row_counts, exact_fp32=1)
+    o = oracle_t0(r, "f32")
+    np.testing.assert_array_equal(r.t0s["collision"], o[:, 0].astype(np.int32))
+    np.testing.assert_array_equal(r.t0s["dz"].view(np.uint32), o[:, 2].astype(np.float32).view(np.uint32))
+    assert len(np.unique(r.t0s["collision"][r.t0s["collision"] >= 0])) >= 20
