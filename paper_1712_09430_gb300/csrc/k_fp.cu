@@ -646,7 +646,12 @@ __global__ void __launch_bounds__(kTlThreads, kTrackletCtasPerSm)
     Lane L;
     L.t = -1;
     L.sp = st_sh;
-    bool done = false;
+    // Fewer tracklets than lanes: spread them over every warp of the grid,
+    // so that each warp steps fewer divergent lanes (a shorter step).
+    const int n_warps = (int)gridDim.x * (kTlThreads / 32);
+    int lanes = ((T + n_warps - 1) / n_warps) * G;
+    lanes = lanes < G ? G : (lanes > 32 ? 32 : lanes);
+    bool done = lane >= lanes;
     while (true) {
         const unsigned need = __ballot_sync(FULL, L.t < 0 && !done && gl == 0);
         if (need) {

@@ -412,12 +412,20 @@ __global__ void k_owner(KConst k, DevPtrs p, int u0, int u1)
     }
 }
 
-// Ownership of one unit's clusters in shared memory: a CTA per (unit, chunk
-// of kOwnerChunk clusters) scans the cluster lists of the unit's live
-// tracklets (a warp per tracklet), applies atomicMax in shared memory to the
-// clusters of its chunk, then writes the chunk's keys out coalesced.
-// Ownership never crosses units, so no global atomics are needed.
-constexpr int kOwnerChunk = 48 * 1024;
+// Ownership of one unit's clusters in shared memory: a CTA per (unit, chunk)
+// applies atomicMax in shared memory to the clusters of its chunk, then
+// writes the chunk's keys out coalesced.  Ownership never crosses units, so
+// no global atomics are needed.  The chunks of a unit hold equal shares of
+// its clusters (one chunk whenever the unit fits).  A warp takes 32
+// tracklets at a time: their lengths (and, with several chunks, their
+// outermost and innermost clusters) are read one per lane, so that
+// tracklets without clusters in the chunk are skipped; the cluster lists of
+// the remaining ones are read kOwnerTracklets at a time, with all their loads
+// in flight together.
+constexpr int kOwnerChunk = 56 * 1024;  // 224 KB of keys
+constexpr int kListLoads = 5;           // loads per lane per pass: 160 list entries
+constexpr int kOwnerTracklets = 4;      // tracklets whose lists are read together
+constexpr int kEmitTracklets = 2;       // accepted tracklets written together
 
 __global__ void __launch_bounds__(1024) k_owner_units(KConst k, DevPtrs p, int chunks)
 {
@@ -425,21 +433,57 @@ __global__ void __launch_bounds__(1024) k_owner_units(KConst k, DevPtrs p, int c
     const int u = blockIdx.x / chunks, c = blockIdx.x % chunks;
     const int NR = k.n_rows;
     const int ub0 = p.row_off[u * NR], ub1 = p.row_off[(u + 1) * NR];
-    const int lo = ub0 + c * kOwnerChunk;
-    const int hi = min(ub1, lo + kOwnerChunk);
+    const int per = (ub1 - ub0 + chunks - 1) / chunks;
+    const int lo = ub0 + c * per;
+    const int hi = min(ub1, lo + per);
     if (lo >= hi) return;
     for (int i = threadIdx.x; i < hi - lo; i += blockDim.x) keys[i] = 0u;
     __syncthreads();
     const int t0 = p.start_off[u * NR], t1 = p.start_off[(u + 1) * NR];
+    const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    for (int t = t0 + (int)(threadIdx.x >> 5); t < t1; t += nw) {
-        const int n = p.tl_n[t];
-        if (n < k.n_min_tracklet) continue;
-        const unsigned key = ((unsigned)n << 23) | (0x7FFFFFu - (unsigned)(t - t0));
-        const int* h = p.tl_hits + (size_t)t * NR;
-        for (int j = lane; j < n; j += 32) {
-            const int b = h[j];
-            if (b >= lo && b < hi) atomicMax(&keys[b - lo], key);
+    for (int tb = t0 + 32 * (int)(threadIdx.x >> 5); tb < t1; tb += 32 * nw) {
+        const int tl = tb + lane;
+        const int n_l = tl < t1 ? __ldg(p.tl_n + tl) : 0;
+        bool live = n_l >= k.n_min_tracklet;
+        if (chunks > 1 && live) {
+            // rows descend along the list, and so do cluster positions
+            const int* h = p.tl_hits + (size_t)tl * NR;
+            live = __ldg(h) >= lo && __ldg(h + n_l - 1) < hi;
+        }
+        unsigned todo = __ballot_sync(FULL, live);
+        // kOwnerTracklets tracklets at a time, all their list loads in flight
+        while (todo) {
+            int b[kOwnerTracklets][kListLoads];
+            unsigned key[kOwnerTracklets];
+            int n[kOwnerTracklets], tv[kOwnerTracklets];
+#pragma unroll
+            for (int v = 0; v < kOwnerTracklets; v++) {
+                const int q = todo ? __ffs(todo) - 1 : 0;
+                const int nq = __shfl_sync(FULL, n_l, q);
+                n[v] = todo ? nq : 0;
+                tv[v] = tb + q;
+                key[v] = ((unsigned)nq << 23) | (0x7FFFFFu - (unsigned)(tv[v] - t0));
+                const int* h = p.tl_hits + (size_t)tv[v] * NR;
+#pragma unroll
+                for (int i = 0; i < kListLoads; i++) {
+                    const int j = 32 * i + lane;
+                    b[v][i] = j < n[v] ? __ldg(h + j) : -1;
+                }
+                todo &= todo - 1u;
+            }
+#pragma unroll
+            for (int v = 0; v < kOwnerTracklets; v++) {
+#pragma unroll
+                for (int i = 0; i < kListLoads; i++)
+                    if (b[v][i] >= lo && b[v][i] < hi) atomicMax(&keys[b[v][i] - lo], key[v]);
+                // lists longer than one pass (more than 32 x kListLoads rows)
+                const int* h = p.tl_hits + (size_t)tv[v] * NR;
+                for (int j = 32 * kListLoads + lane; j < n[v]; j += 32) {
+                    const int bj = __ldg(h + j);
+                    if (bj >= lo && bj < hi) atomicMax(&keys[bj - lo], key[v]);
+                }
+            }
         }
     }
     __syncthreads();
@@ -524,48 +568,101 @@ __global__ void __launch_bounds__(1024) k_scan_top(DevPtrs p)
 }
 
 // Write accepted tracks in canonical order with their owned clusters (input
-// positions, rows ascending).  One warp per tracklet: the record is written
-// word by word by 22 lanes, the owned clusters are compacted by ballot.
+// positions, rows ascending).  A warp takes 32 tracklets at a time and reads
+// their acceptance, lengths, rows and offsets one per lane; then, for the
+// accepted ones, kEmitTracklets at a time, the record is written word by
+// word by 22 lanes and the owned clusters are compacted by ballot.
 __global__ void k_emit(KConst k, DevPtrs p)
 {
     const int T = p.counters[C_T];
+    const unsigned FULL = 0xffffffffu;
+    const int NR = k.n_rows;
     const int lane = threadIdx.x & 31;
+    const unsigned below = (1u << lane) - 1u;
     const int w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
     constexpr int kWords = (int)(sizeof(tpc_track) / 4);
-    for (int t = w0; t < T; t += nw) {
-        const int2 a = p.acc[t];
-        if (!a.x) continue;
-        const int2 ex = p.acc_scan[t] + p.scan_part[t / kScanTile];
-        const int m = ex.x;
-        const int n = p.tl_n[t];
-        const int unit = p.t_row[t] / k.n_rows;
-        if (lane < kWords) {
-            // word layout of tpc_track: event sector tracklet x p[5] cov_y[6]
-            // cov_z[3] chi2 ndf nhits hit_off
-            int word;
-            if (lane == 0) word = unit / k.n_sectors;
-            else if (lane == 1) word = unit % k.n_sectors;
-            else if (lane == 2) word = t;
-            else if (lane < 19) word = __float_as_int(p.tl_f[(size_t)t * kTlFloats + (lane - 3)]);
-            else if (lane == 19) word = 2 * n - 5;
-            else if (lane == 20) word = a.y;
-            else word = ex.y;
-            reinterpret_cast<int*>(p.out_tracks + m)[lane] = word;
+    for (int tb = 32 * w0; tb < T; tb += 32 * nw) {
+        const int tl = tb + lane;
+        const int2 a = tl < T ? p.acc[tl] : make_int2(0, 0);
+        unsigned todo = __ballot_sync(FULL, a.x != 0);
+        if (!todo) continue;
+        int n_l = 0, rr_l = 0, first_l = 0;
+        int2 ex_l = make_int2(0, 0);
+        if (a.x) {
+            n_l = p.tl_n[tl];
+            rr_l = p.t_row[tl];
+            ex_l = p.acc_scan[tl] + p.scan_part[tl / kScanTile];
+            first_l = p.start_off[rr_l - rr_l % NR];  // the unit's first tracklet
         }
-        const unsigned key = tl_key(k, p, n, t);
-        const int* h = p.tl_hits + (size_t)t * k.n_rows;
-        int o = ex.y;
-        for (int j0 = 0; j0 < n; j0 += 32) {
-            const int j = j0 + lane;  // ascending rows: hits are stored descending
-            int b = -1;
-            bool own = false;
-            if (j < n) {
-                b = h[n - 1 - j];
-                own = p.owner[b] == key;
+        // kEmitTracklets accepted tracklets at a time: the loads of each pass
+        // over their cluster lists (list entries, then owner keys, then
+        // cluster ids) go out together
+        while (todo) {
+            int t[kEmitTracklets], n[kEmitTracklets], o[kEmitTracklets];
+            unsigned key[kEmitTracklets];
+#pragma unroll
+            for (int v = 0; v < kEmitTracklets; v++) {
+                const bool has = todo != 0u;
+                const int q = has ? __ffs(todo) - 1 : 0;
+                todo &= todo - 1u;
+                t[v] = tb + q;
+                const int nq = __shfl_sync(FULL, n_l, q);
+                const int unit = __shfl_sync(FULL, rr_l, q) / NR;
+                const int m = __shfl_sync(FULL, ex_l.x, q);
+                const int h0 = __shfl_sync(FULL, ex_l.y, q);
+                const int owned = __shfl_sync(FULL, a.y, q);
+                const int first = __shfl_sync(FULL, first_l, q);
+                n[v] = has ? nq : 0;
+                o[v] = h0;
+                key[v] = ((unsigned)nq << 23) | (0x7FFFFFu - (unsigned)(t[v] - first));
+                if (has && lane < kWords) {
+                    // word layout of tpc_track: event sector tracklet x p[5]
+                    // cov_y[6] cov_z[3] chi2 ndf nhits hit_off
+                    int word;
+                    if (lane == 0) word = unit / k.n_sectors;
+                    else if (lane == 1) word = unit % k.n_sectors;
+                    else if (lane == 2) word = t[v];
+                    else if (lane < 19) word = __float_as_int(p.tl_f[(size_t)t[v] * kTlFloats + (lane - 3)]);
+                    else if (lane == 19) word = 2 * nq - 5;
+                    else if (lane == 20) word = owned;
+                    else word = h0;
+                    reinterpret_cast<int*>(p.out_tracks + m)[lane] = word;
+                }
             }
-            const unsigned bal = __ballot_sync(0xffffffffu, own);
-            if (own) p.out_hits[o + __popc(bal & ((1u << lane) - 1u))] = __float_as_int(p.hits[b].w);
-            o += __popc(bal);
+            int nmax = 0;
+#pragma unroll
+            for (int v = 0; v < kEmitTracklets; v++) nmax = max(nmax, n[v]);
+            for (int j0 = 0; j0 < nmax; j0 += 32 * kListLoads) {
+                int b[kEmitTracklets][kListLoads];
+                bool own[kEmitTracklets][kListLoads];
+                int id[kEmitTracklets][kListLoads];
+#pragma unroll
+                for (int v = 0; v < kEmitTracklets; v++) {
+                    const int* h = p.tl_hits + (size_t)t[v] * NR;
+#pragma unroll
+                    for (int i = 0; i < kListLoads; i++) {
+                        const int j = j0 + 32 * i + lane;  // ascending rows: the list is descending
+                        b[v][i] = j < n[v] ? h[n[v] - 1 - j] : -1;
+                    }
+                }
+#pragma unroll
+                for (int v = 0; v < kEmitTracklets; v++)
+#pragma unroll
+                    for (int i = 0; i < kListLoads; i++) own[v][i] = b[v][i] >= 0 && p.owner[b[v][i]] == key[v];
+#pragma unroll
+                for (int v = 0; v < kEmitTracklets; v++)
+#pragma unroll
+                    for (int i = 0; i < kListLoads; i++)
+                        id[v][i] = own[v][i] ? __float_as_int(p.hits[b[v][i]].w) : 0;
+#pragma unroll
+                for (int v = 0; v < kEmitTracklets; v++)
+#pragma unroll
+                    for (int i = 0; i < kListLoads; i++) {
+                        const unsigned bal = __ballot_sync(FULL, own[v][i]);
+                        if (own[v][i]) p.out_hits[o[v] + __popc(bal & below)] = id[v][i];
+                        o[v] += __popc(bal);
+                    }
+            }
         }
     }
 }
