@@ -817,7 +817,9 @@ def main():
     ap.add_argument("--tf-collisions", type=int, default=50,
                     help="collisions of the continuous-readout time-frame leg (0: skip)")
     ap.add_argument("--tf-steps", type=int, default=5)
-    ap.add_argument("--stream-batch", type=int, default=64, help="most events per serving batch")
+    ap.add_argument("--stream-batch", type=int, default=16,
+                    help="most events per serving batch (a large batch formed after a burst "
+                         "holds all its requests until its last kernel)")
     ap.add_argument("--stream-arena-gb", type=int, default=16)
     ap.add_argument("--pool", type=int, default=96, help="min-bias events in the serving pool")
     args = ap.parse_args()
