@@ -56,25 +56,35 @@ def _gen_event(job):
     if kind == "timeframe":
         ev = synth.time_frame(seed=seed[0], n_coll=seed[1])
         return ev.clusters, ev.row_counts, ev.label, ev.track_coll, ev.coll_dz
+    if kind == "tfslice":
+        ev = synth.time_frame(seed=seed[0], n_coll=seed[1])
+        return ev.clusters, ev.row_counts
     ev = synth.central_event(seed=seed) if kind == "central" else synth.min_bias_event(seed)
     return ev.clusters, ev.row_counts
 
 
-def make_inputs(central_seeds, mb_seeds, tf=None):
-    """Central batch, min-bias pool and (tf = (seed, collisions)) a
-    continuous-readout time frame, generated in a spawned process pool (it
-    starts before any CUDA use in this process)."""
+def make_inputs(central_seeds, mb_seeds, tf=None, slices=()):
+    """Central batch, min-bias pool, (tf = (seed, collisions)) a
+    continuous-readout time frame and (slices = [(seed, collisions)]) time-frame
+    slices, generated in a spawned process pool (it starts before any CUDA use
+    in this process).  The frame and the slices come back only when asked for."""
     jobs = [("timeframe", tf)] if tf else []
+    jobs += [("tfslice", sl) for sl in slices]
     jobs += [("central", s) for s in central_seeds] + [("minbias", s) for s in mb_seeds]
+    # the longest jobs first, so that they overlap the many short ones
     with mp.get_context("spawn").Pool(min(len(jobs), max(1, os.cpu_count() or 1), 16)) as pool:
-        parts = pool.map(_gen_event, jobs)
+        parts = pool.map(_gen_event, jobs, chunksize=1)
     frame = parts.pop(0) if tf else None
+    sl = [parts.pop(0) for _ in slices]
     nc = len(central_seeds)
     cl = np.ascontiguousarray(np.concatenate([p[0] for p in parts[:nc]]))
     rc = np.ascontiguousarray(np.concatenate([p[1] for p in parts[:nc]]))
+    out = [cl, rc, parts[nc:]]
     if tf:
-        return cl, rc, parts[nc:], frame
-    return cl, rc, parts[nc:]
+        out.append(frame)
+    if slices:
+        out.append(sl)
+    return tuple(out)
 
 
 class ClockSampler:
@@ -229,8 +239,10 @@ def run_ours(args):
     seeds = rank_seeds(rank, args.batch)
     mb_seeds = [1000 + rank * args.pool + i for i in range(args.pool)] if args.stream_rates else []
     tf_job = (4 + rank, args.tf_collisions) if args.tf_collisions > 0 else None
-    cl_np, rc_np, mb_pool, *frame = make_inputs(seeds, mb_seeds, tf_job)   # before any CUDA use
-    frame = frame[0] if frame else None
+    sl_jobs = list(args.tf_slices)   # the same slices on every rank
+    cl_np, rc_np, mb_pool, *extra = make_inputs(seeds, mb_seeds, tf_job, sl_jobs)   # before any CUDA use
+    frame = extra.pop(0) if tf_job else None
+    slices = extra.pop(0) if sl_jobs else None
     import torch
     import ctypes as C
     dist = None
@@ -315,6 +327,9 @@ def run_ours(args):
     tframe = None
     if frame is not None:
         tframe = run_time_frame(frame, tr, args, dev_cl.device)
+    if slices:
+        tframe = tframe or {}
+        tframe["uneven_slices"] = run_slices(slices, tr, args, dev_cl.device)
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -536,6 +551,48 @@ def run_time_frame(frame, tr0, args, device):
                 "tracks_assigned": float((coll >= 0).mean()),
                 "workload": f"time frame of {len(coll_dz)} min-bias collisions, each shifted by a drift "
                             "offset ~ U[-250, 250] cm (continuous readout), 10% noise"})
+    return res
+
+
+def run_slices(slices, tr0, args, device):
+    """Continuous-readout time-frame slices of uneven size (about 1, 2, 3, 5
+    and 8 M clusters) tracked together in one launch, each slice one event:
+    tracking alone and the whole chain (refit, merging, collision offsets).
+    Inputs resident on the device; clusters/s of the batch."""
+    import torch
+    from paper_1712_09430_gb300 import synth
+    from paper_1712_09430_gb300.tracker import Tracker
+    cl = np.ascontiguousarray(np.concatenate([s[0] for s in slices]))
+    rc = np.ascontiguousarray(np.concatenate([s[1] for s in slices]))
+    E = len(slices)
+    p = tr0.params
+    dev = torch.from_numpy(cl).to(device)
+    res = {}
+    for name, over in (("tracking", dict(refit=0, merge=0, t0=0)), ("chain", dict(refit=1, merge=1, t0=1))):
+        tr = Tracker(synth.row_x(), bz=0.5, use_graph=1, exact_fp32=p.exact_fp32,
+                     bin_target=p.bin_target, threads_per_row=p.threads_per_row,
+                     tracklets_per_warp=p.tracklets_per_warp, schedule=p.schedule, **over)
+        try:
+            for _ in range(3):
+                r = tr.track(dev, rc, E)
+            ms, st = [], np.zeros(7)
+            for _ in range(args.tf_steps):
+                r = tr.track(dev, rc, E)
+                s7 = np.array(tr.stage_times())
+                ms.append(s7[5])
+                st += s7
+            st /= args.tf_steps
+        finally:
+            tr.close()
+        t = statistics.median(ms)
+        names = ["grid", "neighbours", "clean+starts", "tracklets", "select+emit"]
+        res[name] = {"ms": t, "clusters_per_s": len(cl) / (t * 1e-3), "tracks": int(len(r.tracks)),
+                     "stage_ms": {n: float(v) for n, v in zip(names, st[:5])},
+                     "after_selection_ms": float(st[6])}
+    res.update({"clusters": int(len(cl)), "slice_clusters": [int(len(s[0])) for s in slices],
+                "slice_collisions": [n for _, n in args.tf_slices], "launches": "one batch of all slices",
+                "workload": "continuous-readout time-frame slices of uneven size, min-bias collisions "
+                            "shifted by drift offsets ~ U[-250, 250] cm, 10% noise, one event each"})
     return res
 
 
@@ -817,6 +874,11 @@ def main():
     ap.add_argument("--tf-collisions", type=int, default=50,
                     help="collisions of the continuous-readout time-frame leg (0: skip)")
     ap.add_argument("--tf-steps", type=int, default=5)
+    ap.add_argument("--tf-slices",
+                    type=lambda v: [tuple(int(y) for y in x.split(":")) for x in v.split(",") if x.strip()],
+                    default=[(47, 8), (44, 16), (42, 24), (43, 40), (44, 64)],
+                    help="seed:collisions of each time-frame slice of the uneven-slice batch; the "
+                         "default gives 0.9, 2.0, 3.2, 4.9 and 8.5 M clusters; '' = off")
     ap.add_argument("--stream-batch", type=int, default=16,
                     help="most events per serving batch (a large batch formed after a burst "
                          "holds all its requests until its last kernel)")
