@@ -30,8 +30,9 @@ using namespace tpc;
 // --------------------------------------------------------- neighbour finder
 // One CTA per (event, sector, row r), r in [1, n_rows - 2].  Rows r - 1, r,
 // r + 1 are contiguous in the binned array, and so are their bin tables: two
-// bulk copies bring them into shared memory.  One thread per hit of row r
-// (one GPU thread per hit, Sec. 3).
+// bulk copies bring their (y, z) pairs and bin tables into shared memory.
+// One thread per hit of row r (one GPU thread per hit, Sec. 3).  Cluster ids
+// are read from global memory only to break an exact tie.
 //
 // For hit i (y_i, z_i) on row r and a target row rho = r +- 1:
 //   R = X_rho / X_r, W = k_win |X_rho - X_r|;
@@ -64,14 +65,19 @@ __global__ void k_neighbours(KConst k, const float* __restrict__ row_x, DevPtrs 
     const int n_bins3 = p.bin_cap_off[rr + 2] - bo_d;
     const int total3 = end_u - off_d;
 
+    // the pair copy starts at an even cluster (16-byte aligned) and covers an
+    // even count; it may read the pad entry after the last cluster
+    const int a0 = off_d & ~1;
+    const int n2 = (end_u - a0 + 1) & ~1;
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
-    float4* rec = reinterpret_cast<float4*>(smem + 16);
-    int* bins = reinterpret_cast<int*>(rec + total3);
+    float2* pairs = reinterpret_cast<float2*>(smem + 16);
+    const float2* rec = pairs + (off_d - a0);  // rec[j]: cluster off_d + j
+    int* bins = reinterpret_cast<int*>(pairs + n2);
     if (tid == 0) {
         mbar_init(bar, 1);
         fence_async_smem();
-        mbar_expect_tx(bar, (unsigned)total3 * 16u + (unsigned)n_bins3 * 4u);
-        bulk_g2s(rec, p.hits + off_d, (unsigned)total3 * 16u, bar);
+        mbar_expect_tx(bar, (unsigned)n2 * 8u + (unsigned)n_bins3 * 4u);
+        bulk_g2s(pairs, p.hyz + a0, (unsigned)n2 * 8u, bar);
         bulk_g2s(bins, p.bin_off + bo_d, (unsigned)n_bins3 * 4u, bar);
     }
     __syncthreads();
@@ -91,9 +97,10 @@ __global__ void k_neighbours(KConst k, const float* __restrict__ row_x, DevPtrs 
         if (tid == 0) atomicOr(&p.counters[C_ERR], E_TIMEOUT);
         return;
     }
-    const float4* recm = rec + cnt_d;
+    const float2* recm = rec + cnt_d;
+    auto id_of = [&](int j) { return __float_as_uint(__ldg(&p.hits[off_d + j].z)); };
     for (int i = tid; i < cnt_m; i += nt) {
-        const float4 ci = recm[i];
+        const float2 ci = recm[i];
         const float yi = ci.x, zi = ci.y;
         const float ycu = yi * Ru, ycd = yi * Rd;
         // bin windows (widened by kBinEps; the exact test below decides)
@@ -106,29 +113,28 @@ __global__ void k_neighbours(KConst k, const float* __restrict__ row_x, DevPtrs 
         const int dz0 = bin_index_fma(zi - Wd - kBinEps, czd, gd.inv_bz, nzd);
         const int dz1 = bin_index_fma(zi + Wd + kBinEps, czd, gd.inv_bz, nzd);
         int bu = -1, bd = -1;
-        unsigned bid_u = 0, bid_d = 0;
         float bD = 0.0f;
         // pair (u, d) -> keep the best by (D, id_u, id_d)
-        auto consider = [&](int ju, const float4& cu, int jd, const float4& cd) {
+        auto consider = [&](int ju, const float2& cu, int jd, const float2& cd) {
             const float yp = cd.x + (cu.x - cd.x) * tt;
             const float zp = cd.y + (cu.y - cd.y) * tt;
             const float ey = yi - yp;
             const float ez = zi - zp;
             const float D = ey * ey + ez * ez;
             if (!(D <= k.d_max2)) return;
-            const unsigned idu = __float_as_uint(cu.z), idd = __float_as_uint(cd.z);
             bool better;
-            if (bu < 0) better = true;
-            else if (D < bD) better = true;
-            else if (D > bD) better = false;
-            else if (idu != bid_u) better = idu < bid_u;
-            else better = idd < bid_d;
+            if (bu < 0 || D < bD) {
+                better = true;
+            } else if (D > bD) {
+                better = false;
+            } else {  // exact tie
+                const unsigned idu = id_of(ju), ibu = id_of(bu);
+                better = idu != ibu ? idu < ibu : id_of(jd) < id_of(bd);
+            }
             if (better) {
                 bu = ju;
                 bd = jd;
                 bD = D;
-                bid_u = idu;
-                bid_d = idd;
             }
         };
         // Candidates of a window: one flat loop over its first two z rows (so
@@ -153,9 +159,9 @@ __global__ void k_neighbours(KConst k, const float* __restrict__ row_x, DevPtrs 
         // down candidates once, into a register list of up to 4
         int nd = 0;
         int jd0 = -1, jd1 = -1, jd2 = -1, jd3 = -1;
-        float4 cd0 = make_float4(0.f, 0.f, 0.f, 0.f), cd1 = cd0, cd2 = cd0, cd3 = cd0;
+        float2 cd0 = make_float2(0.f, 0.f), cd1 = cd0, cd2 = cd0, cd3 = cd0;
         for_window(td, nyd, dy0, dy1, dz0, dz1, [&](int jd) {
-            const float4 cd = rec[jd];
+            const float2 cd = rec[jd];
             if (fabsf(cd.x - ycd) <= Wd && fabsf(cd.y - zi) <= Wd) {
                 jd3 = jd2; cd3 = cd2;
                 jd2 = jd1; cd2 = cd1;
@@ -166,7 +172,7 @@ __global__ void k_neighbours(KConst k, const float* __restrict__ row_x, DevPtrs 
         });
         if (nd > 0) {
             for_window(tu, nyu, uy0, uy1, uz0, uz1, [&](int ju) {
-                const float4 cu = rec[ju];
+                const float2 cu = rec[ju];
                 if (!(fabsf(cu.x - ycu) <= Wu && fabsf(cu.y - zi) <= Wu)) return;
                 if (nd <= 4) {
                     consider(ju, cu, jd0, cd0);
@@ -175,7 +181,7 @@ __global__ void k_neighbours(KConst k, const float* __restrict__ row_x, DevPtrs 
                     if (nd > 3) consider(ju, cu, jd3, cd3);
                 } else {  // a crowded window: scan the down row again
                     for_window(td, nyd, dy0, dy1, dz0, dz1, [&](int jd) {
-                        const float4 cd = rec[jd];
+                        const float2 cd = rec[jd];
                         if (fabsf(cd.x - ycd) <= Wd && fabsf(cd.y - zi) <= Wd) consider(ju, cu, jd, cd);
                     });
                 }
@@ -766,9 +772,11 @@ cudaError_t launch_seeds(const KConst& k, const float* row_x_dev, const DevPtrs&
 }
 
 cudaError_t launch_neighbours(const KConst& k, const float* row_x_dev, const DevPtrs& p, int max3,
-                              int threads, int unit0, int n_units, cudaStream_t s)
+                              int max_slots3, int threads, int unit0, int n_units, cudaStream_t s)
 {
-    size_t sm = 16 + (size_t)max3 * 16 + (size_t)3 * (kMaxBinsPerRow + 4) * 4;
+    // barrier, the (y, z) pairs of three rows (an even count, one more at
+    // most at each end) and their three bin tables
+    size_t sm = 16 + (size_t)(max3 + 2) * 8 + (size_t)max_slots3 * 4;
     cudaError_t e =
         cudaFuncSetAttribute(k_neighbours, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;

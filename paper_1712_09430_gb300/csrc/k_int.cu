@@ -321,13 +321,15 @@ __global__ void k_start_final(KConst k, DevPtrs p)
 }
 
 // One warp per row: number its start hits by cluster id (rank = number of
-// start hits of the row with a smaller id).
-constexpr int kStartWarpBuf = 128;  // start hits ranked in shared memory; more use global reads
+// start hits of the row with a smaller id).  Dense rows (time frames) hold
+// hundreds of start hits: they are ranked in shared memory too.
+constexpr int kStartWarps = 4;        // rows (warps) per CTA
+constexpr int kStartWarpBuf = 1024;   // start hits ranked in shared memory; more use global reads
 
-__global__ void k_start_write(KConst k, DevPtrs p, int rr0, int rows)
+__global__ void __launch_bounds__(32 * kStartWarps) k_start_write(KConst k, DevPtrs p, int rr0, int rows)
 {
-    __shared__ unsigned sid_sh[8][kStartWarpBuf];
-    __shared__ int sb_sh[8][kStartWarpBuf];
+    __shared__ unsigned sid_sh[kStartWarps][kStartWarpBuf];
+    __shared__ int sb_sh[kStartWarps][kStartWarpBuf];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (w >= rows) return;
@@ -427,13 +429,17 @@ constexpr int kListLoads = 5;           // loads per lane per pass: 160 list ent
 constexpr int kOwnerTracklets = 4;      // tracklets whose lists are read together
 constexpr int kEmitTracklets = 2;       // accepted tracklets written together
 
-__global__ void __launch_bounds__(1024) k_owner_units(KConst k, DevPtrs p, int chunks)
+__global__ void __launch_bounds__(1024) k_owner_units(KConst k, DevPtrs p, int chunks, int cap_keys)
 {
     extern __shared__ unsigned keys[];
     const int u = blockIdx.x / chunks, c = blockIdx.x % chunks;
     const int NR = k.n_rows;
     const int ub0 = p.row_off[u * NR], ub1 = p.row_off[(u + 1) * NR];
     const int per = (ub1 - ub0 + chunks - 1) / chunks;
+    if (per > cap_keys) {  // never with a matching launch: report, do not overrun
+        if (threadIdx.x == 0) atomicOr(&p.counters[C_ERR], E_SHAPE);
+        return;
+    }
     const int lo = ub0 + c * per;
     const int hi = min(ub1, lo + per);
     if (lo >= hi) return;
@@ -748,9 +754,11 @@ __global__ void k_dump_tl_work(DevPtrs p, int T, int* dst)
 }
 
 // ------------------------------------------------------------- launchers
-static size_t grid_smem(int max_row)
+// barrier, rows in and out (16 + 16 B per cluster), slot of each cluster in
+// its bin (4 B), bin counts (the row's table slots)
+static size_t grid_smem(int max_row, int max_slots)
 {
-    return 16 + (size_t)max_row * 36 + (size_t)(kMaxBinsPerRow + 4) * 4;
+    return 16 + (size_t)max_row * 36 + (size_t)max_slots * 4;
 }
 
 cudaError_t launch_plan(const KConst& k, const float* row_x_dev, const DevPtrs& p, int n_sm,
@@ -763,9 +771,9 @@ cudaError_t launch_plan(const KConst& k, const float* row_x_dev, const DevPtrs& 
 }
 
 cudaError_t launch_grid(const KConst& k, const float* row_x_dev, const DevPtrs& p, int max_row,
-                        int threads, int unit0, int n_units, cudaStream_t s)
+                        int max_slots, int threads, int unit0, int n_units, cudaStream_t s)
 {
-    size_t sm = grid_smem(max_row);
+    size_t sm = grid_smem(max_row, max_slots);
     cudaError_t e = cudaFuncSetAttribute(k_grid, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     int rows = n_units * k.n_rows;
@@ -800,7 +808,8 @@ cudaError_t launch_start_write(const KConst& k, const DevPtrs& p, int threads, i
     (void)threads;
     const int rows = n_units * k.n_rows;
     if (rows == 0) return cudaSuccess;
-    k_start_write<<<(rows + 7) / 8, 256, 0, s>>>(k, p, unit0 * k.n_rows, rows);  // a warp per row
+    k_start_write<<<(rows + kStartWarps - 1) / kStartWarps, 32 * kStartWarps, 0, s>>>(k, p, unit0 * k.n_rows,
+                                                                                      rows);  // a warp per row
     return cudaGetLastError();
 }
 
@@ -825,10 +834,11 @@ cudaError_t launch_owner_units(const KConst& k, const DevPtrs& p, int n_units, i
     *counted = true;
     if (n_units == 0 || max_unit == 0) return cudaSuccess;
     const int chunks = (max_unit + kOwnerChunk - 1) / kOwnerChunk;
-    const size_t sm = (size_t)std::min(max_unit, kOwnerChunk) * 4;
+    const int cap_keys = std::min(max_unit, kOwnerChunk);
+    const size_t sm = (size_t)cap_keys * 4;
     cudaError_t e = cudaFuncSetAttribute(k_owner_units, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    k_owner_units<<<n_units * chunks, 1024, sm, s>>>(k, p, chunks);
+    k_owner_units<<<n_units * chunks, 1024, sm, s>>>(k, p, chunks, cap_keys);
     return cudaGetLastError();
 }
 

@@ -83,19 +83,24 @@ extern "C" int tpc_links_noalloc(const tpc_geometry* g, const tpc_params* params
     int* plan_off = g_plan;
     int* plan_bins = g_plan + R + 1;
     int64_t N = 0, bins = 0;
-    int max_row = 1, max3 = 1;
+    int max_row = 1, max3 = 1, max_slots = 4, max_slots3 = 12;
     for (int r = 0; r < R; r++) {
         const int c = row_counts[r];
         if (c < 0 || c > TPC_MAX_ROW_CLUSTERS) return TPC_ERR_INVALID;
         plan_off[r] = (int)N;
         plan_bins[r] = (int)bins;
         N += c;
-        bins += row_bin_slots(c, P.bin_target);
+        const int slots = row_bin_slots(c, P.bin_target);
+        bins += slots;
         if (c > max_row) max_row = c;
+        if (slots > max_slots) max_slots = slots;
         const int rr = r % NR;
         if (rr >= 1 && rr + 1 < NR) {
             const int c3 = row_counts[r - 1] + c + row_counts[r + 1];
             if (c3 > max3) max3 = c3;
+            const int s3 = row_bin_slots(row_counts[r - 1], P.bin_target) + slots +
+                           row_bin_slots(row_counts[r + 1], P.bin_target);
+            if (s3 > max_slots3) max_slots3 = s3;
         }
     }
     if (N > kNoallocMaxClusters) return TPC_ERR_INVALID;  // beyond the fixed scratch
@@ -117,7 +122,7 @@ extern "C" int tpc_links_noalloc(const tpc_geometry* g, const tpc_params* params
     const size_t o_plan = take((size_t)(R + 1) * 8);
     const size_t o_grid = take((size_t)R * sizeof(RowGrid));
     const size_t o_hits = take(n * 16);
-    const size_t o_hyz = take(n * 8);
+    const size_t o_hyz = take((n + 2) * 8);  // + a pad entry read by whole-pair copies
     const size_t o_bins = take((size_t)bins * 4);
     const size_t o_up = take(n * 4), o_dn = take(n * 4), o_up2 = take(n * 4), o_dn2 = take(n * 4);
     const size_t o_start = take(n);
@@ -180,10 +185,10 @@ extern "C" int tpc_links_noalloc(const tpc_geometry* g, const tpc_params* params
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(base + o_plan, g_plan, (size_t)(R + 1) * 8, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = tpc_int::launch_plan(k, xd, p, nsm, s);
-    if (e == cudaSuccess) e = tpc_int::launch_grid(k, xd, p, max_row, P.threads_per_row, 0, S, s);
+    if (e == cudaSuccess) e = tpc_int::launch_grid(k, xd, p, max_row, max_slots, P.threads_per_row, 0, S, s);
     if (e == cudaSuccess)
-        e = P.exact_fp32 ? tpc_exact::launch_neighbours(k, xd, p, max3, P.threads_per_row, 0, S, s)
-                         : tpc_fast::launch_neighbours(k, xd, p, max3, P.threads_per_row, 0, S, s);
+        e = P.exact_fp32 ? tpc_exact::launch_neighbours(k, xd, p, max3, max_slots3, P.threads_per_row, 0, S, s)
+                         : tpc_fast::launch_neighbours(k, xd, p, max3, max_slots3, P.threads_per_row, 0, S, s);
     if (e == cudaSuccess) e = tpc_int::launch_clean(k, p, P.threads_per_row, 0, S, s);
     if (e == cudaSuccess) e = tpc_int::launch_dump_links(p, 1, d_links, s);
     if (e == cudaSuccess)

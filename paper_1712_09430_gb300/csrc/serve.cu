@@ -354,6 +354,7 @@ static void finish_batch(tpc_tracker* tr, Batch& b)
     const int M = b.sh.N ? c[C_M] : 0, MH = b.sh.N ? c[C_MH] : 0;
     if (b.sh.N && (c[C_ERR] & E_INPUT)) err = TPC_ERR_INVALID;
     if (b.sh.N && (c[C_ERR] & E_TIMEOUT)) err = TPC_ERR_TIMEOUT;
+    if (b.sh.N && (c[C_ERR] & E_SHAPE)) err = TPC_ERR_DEVICE;
     if (err == TPC_OK && (M > b.est_tracks || MH > b.est_hits)) {
         // the estimate was short: fetch the remainder now
         S->stats.refetches++;

@@ -33,7 +33,9 @@ enum {
     C_FIT = 6,      // persistent refit kernel work counter
     C_FIT_M = 7,    // tracks in the refit schedule
 };
-enum { E_INPUT = 1, E_TIMEOUT = 2, E_TOO_DENSE = 4 };
+// E_SHAPE: a launch configuration (shared memory sized on the host) does not
+// fit the batch the kernel finds in device memory; the kernel skips the work
+enum { E_INPUT = 1, E_TIMEOUT = 2, E_TOO_DENSE = 4, E_SHAPE = 8 };
 
 // Method constants in working precision (float), identical on every launch
 // of one call.
@@ -74,7 +76,7 @@ struct DevPtrs {
     const int* bin_cap_off;    // [R + 1] start of each row's bin table (x4 aligned)
     RowGrid* grid;             // [R]
     float4* hits;              // [N] binned: (y, z, id bits, input position bits)
-    float2* hyz;               // [N] binned (y, z): what the window scans read
+    float2* hyz;               // [N + 2] binned (y, z): what the window scans read (+ pad)
     int* bin_off;              // bin tables: absolute binned offsets
     int* up;                   // [N] binned space, before cleaning
     int* dn;
@@ -236,7 +238,7 @@ namespace tpc_int {
 cudaError_t launch_plan(const tpc::KConst& k, const float* row_x_dev, const tpc::DevPtrs& p,
                         int n_sm, cudaStream_t s);
 cudaError_t launch_grid(const tpc::KConst& k, const float* row_x_dev, const tpc::DevPtrs& p,
-                        int max_row, int threads, int unit0, int n_units, cudaStream_t s);
+                        int max_row, int max_slots, int threads, int unit0, int n_units, cudaStream_t s);
 cudaError_t launch_clean(const tpc::KConst& k, const tpc::DevPtrs& p, int threads, int unit0,
                          int n_units, cudaStream_t s);
 cudaError_t launch_start_scan(const tpc::KConst& k, const tpc::DevPtrs& p, cudaStream_t s);
@@ -257,7 +259,8 @@ cudaError_t launch_dump_tl_work(const tpc::DevPtrs& p, int T, int* dst, cudaStre
 
 #define TPC_FP_DECLS                                                                              \
     cudaError_t launch_neighbours(const tpc::KConst& k, const float* row_x_dev,                   \
-                                  const tpc::DevPtrs& p, int max3, int threads, int unit0,        \
+                                  const tpc::DevPtrs& p, int max3, int max_slots3, int threads,   \
+                                  int unit0,                                                      \
                                   int n_units, cudaStream_t s);                                   \
     cudaError_t launch_tracklets(const tpc::KConst& k, const float* row_x_dev,                    \
                                  const tpc::DevPtrs& p, int n_sm, int lanes_per_tracklet,         \

@@ -276,7 +276,7 @@ size_t tpc_layout(const tpc_tracker* tr, const BatchShape& sh, DevPtrs* p, char*
     q.bin_cap_off = q.row_off ? q.row_off + (R + 1) : nullptr;
     q.grid = reinterpret_cast<RowGrid*>(take(R * sizeof(RowGrid)));
     q.hits = reinterpret_cast<float4*>(take(N * 16));
-    q.hyz = reinterpret_cast<float2*>(take(N * 8));
+    q.hyz = reinterpret_cast<float2*>(take((N + 2) * 8));  // + a pad entry read by whole-pair copies
     q.bin_off = reinterpret_cast<int*>(take((size_t)sh.bin_slots * 4));
     q.up = reinterpret_cast<int*>(take(N * 4));
     q.dn = reinterpret_cast<int*>(take(N * 4));
@@ -345,7 +345,7 @@ int tpc_shape(tpc_tracker* tr, const int32_t* row_counts, int n_events, BatchSha
     const int64_t R = (int64_t)n_events * S * NR;
     if (R > (1 << 28)) return tr->fail(TPC_ERR_INVALID, "too many rows in one call");
     int64_t N = 0, bins = 0, max_unit = 0;
-    int max_row = 0, max3 = 0;
+    int max_row = 0, max3 = 0, max_slots = 0, max_slots3 = 0;
     if ((size_t)(2 * (R + 1)) > tr->plan_cap) {
         cudaFreeHost(tr->plan_host);
         tr->plan_host = nullptr;
@@ -389,9 +389,13 @@ int tpc_shape(tpc_tracker* tr, const int32_t* row_counts, int n_events, BatchSha
             N += c;
             bins += lut[c];
             max_row = std::max(max_row, c);
+            max_slots = std::max(max_slots, lut[c]);
         }
         max_unit = std::max<int64_t>(max_unit, N - n_before);
-        for (int r = 1; r + 1 < NR; r++) max3 = std::max(max3, cnt[r - 1] + cnt[r] + cnt[r + 1]);
+        for (int r = 1; r + 1 < NR; r++) {
+            max3 = std::max(max3, cnt[r - 1] + cnt[r] + cnt[r + 1]);
+            max_slots3 = std::max(max_slots3, lut[cnt[r - 1]] + lut[cnt[r]] + lut[cnt[r + 1]]);
+        }
     }
     if (N >= (int64_t)1 << 30) return tr->fail(TPC_ERR_INVALID, "more than 2^30 clusters in one call");
     if (bins >= (int64_t)1 << 31) return tr->fail(TPC_ERR_INVALID, "search grid too large for one call");
@@ -407,6 +411,8 @@ int tpc_shape(tpc_tracker* tr, const int32_t* row_counts, int n_events, BatchSha
     sh->max_row = std::max(max_row, 1);
     sh->max3 = std::max(max3, 1);
     sh->max_unit = (int)max_unit;
+    sh->max_slots = std::max(max_slots, 4);
+    sh->max_slots3 = std::max(max_slots3, 12);
     return TPC_OK;
 }
 
@@ -454,10 +460,10 @@ int tpc_enqueue(tpc_tracker* tr, const DevPtrs& p, const BatchShape& sh, cudaStr
     const tpc_params& P = tr->params;
     const float* xd = tr->row_x_dev;
     const bool exact = P.exact_fp32 != 0;
-    auto nb = [&](const tpc::KConst& kk, const float* x, const DevPtrs& pp, int max3, int th, int u0,
-                  int nu, cudaStream_t ss) {
-        return exact ? tpc_exact::launch_neighbours(kk, x, pp, max3, th, u0, nu, ss)
-                     : tpc_fast::launch_neighbours(kk, x, pp, max3, th, u0, nu, ss);
+    auto nb = [&](const tpc::KConst& kk, const float* x, const DevPtrs& pp, int max3, int slots3, int th,
+                  int u0, int nu, cudaStream_t ss) {
+        return exact ? tpc_exact::launch_neighbours(kk, x, pp, max3, slots3, th, u0, nu, ss)
+                     : tpc_fast::launch_neighbours(kk, x, pp, max3, slots3, th, u0, nu, ss);
     };
     auto seeds = [&](int u0, int u1, cudaStream_t ss) {
         return exact ? tpc_exact::launch_seeds(k, xd, p, tr->n_sm, u0, u1, ss)
@@ -472,9 +478,9 @@ int tpc_enqueue(tpc_tracker* tr, const DevPtrs& p, const BatchShape& sh, cudaStr
     if (with_events) TPC_CUDA(cudaEventRecord(tr->ev[0], s));
     TPC_CUDA(tpc_int::launch_plan(k, xd, p, tr->n_sm, s));
     if (!P.plain_per_sector) {
-        TPC_CUDA(tpc_int::launch_grid(k, xd, p, sh.max_row, th, 0, sh.n_units, s));
+        TPC_CUDA(tpc_int::launch_grid(k, xd, p, sh.max_row, sh.max_slots, th, 0, sh.n_units, s));
         if (with_events) TPC_CUDA(cudaEventRecord(tr->ev[1], s));
-        TPC_CUDA(nb(k, xd, p, sh.max3, th, 0, sh.n_units, s));
+        TPC_CUDA(nb(k, xd, p, sh.max3, sh.max_slots3, th, 0, sh.n_units, s));
         if (with_events) TPC_CUDA(cudaEventRecord(tr->ev[2], s));
         TPC_CUDA(tpc_int::launch_clean(k, p, th, 0, sh.n_units, s));
         TPC_CUDA(tpc_int::launch_start_scan(k, p, s));
@@ -516,8 +522,8 @@ int tpc_enqueue(tpc_tracker* tr, const DevPtrs& p, const BatchShape& sh, cudaStr
         if (rc != TPC_OK) return rc;
         for (int u = 0; u < sh.n_units; u++) {
             cudaStream_t q = tr->queues[(size_t)(u % nq)];
-            TPC_CUDA(tpc_int::launch_grid(k, xd, p, sh.max_row, th, u, 1, q));
-            TPC_CUDA(nb(k, xd, p, sh.max3, th, u, 1, q));
+            TPC_CUDA(tpc_int::launch_grid(k, xd, p, sh.max_row, sh.max_slots, th, u, 1, q));
+            TPC_CUDA(nb(k, xd, p, sh.max3, sh.max_slots3, th, u, 1, q));
             TPC_CUDA(tpc_int::launch_clean(k, p, th, u, 1, q));
         }
         rc = join();
@@ -543,9 +549,9 @@ int tpc_enqueue(tpc_tracker* tr, const DevPtrs& p, const BatchShape& sh, cudaStr
     } else {
         // The Run 1/2 scheduling (Sec. 3): every stage launched per sector.
         for (int u = 0; u < sh.n_units; u++)
-            TPC_CUDA(tpc_int::launch_grid(k, xd, p, sh.max_row, th, u, 1, s));
+            TPC_CUDA(tpc_int::launch_grid(k, xd, p, sh.max_row, sh.max_slots, th, u, 1, s));
         if (with_events) TPC_CUDA(cudaEventRecord(tr->ev[1], s));
-        for (int u = 0; u < sh.n_units; u++) TPC_CUDA(nb(k, xd, p, sh.max3, th, u, 1, s));
+        for (int u = 0; u < sh.n_units; u++) TPC_CUDA(nb(k, xd, p, sh.max3, sh.max_slots3, th, u, 1, s));
         if (with_events) TPC_CUDA(cudaEventRecord(tr->ev[2], s));
         for (int u = 0; u < sh.n_units; u++) TPC_CUDA(tpc_int::launch_clean(k, p, th, u, 1, s));
         TPC_CUDA(tpc_int::launch_start_scan(k, p, s));
@@ -576,9 +582,12 @@ int tpc_enqueue(tpc_tracker* tr, const DevPtrs& p, const BatchShape& sh, cudaStr
 
 static std::string graph_key_of(const tpc_tracker* tr, const BatchShape& sh, const DevPtrs& p)
 {
-    char b[256];
-    std::snprintf(b, sizeof b, "%d/%d/%d/%d/%d/%p/%p/%d/%d/%d/%d/%d/%g/%d", sh.N, sh.R, sh.n_units,
-                  sh.max_row, sh.max3, (const void*)p.clusters, (const void*)p.counters,
+    // every quantity a launch configuration (grid, shared memory, chunks) is
+    // derived from
+    char b[320];
+    std::snprintf(b, sizeof b, "%d/%d/%d/%d/%d/%d/%d/%d/%p/%p/%d/%d/%d/%d/%d/%g/%d", sh.N, sh.R, sh.n_units,
+                  sh.max_row, sh.max3, sh.max_unit, sh.max_slots, sh.max_slots3,
+                  (const void*)p.clusters, (const void*)p.counters,
                   tr->params.exact_fp32, tr->params.threads_per_row, tr->params.tracklets_per_warp,
                   tr->params.plain_per_sector, tr->params.schedule, (double)tr->params.bin_target,
                   tr->params.n_queues);
@@ -633,6 +642,7 @@ static int finish_counters(tpc_tracker* tr, cudaStream_t s)
         return tr->fail(TPC_ERR_INVALID, m);
     }
     if (c[C_ERR] & E_TIMEOUT) return tr->fail(TPC_ERR_TIMEOUT, "bulk copy wait ran out in a kernel");
+    if (c[C_ERR] & E_SHAPE) return tr->fail(TPC_ERR_DEVICE, "a launch configuration did not fit the batch");
     tr->last_T = c[C_T];
     tr->last_M = c[C_M];
     tr->last_MH = c[C_MH];

@@ -171,6 +171,55 @@ def test_dense_row_at_limit():
     assert_exact_equal(g, o)
 
 
+def _uniform_rows(unit_rows, per_row, seed, n_tracks=40):
+    """per_row clusters on each of the first n rows of each unit: n_tracks
+    straight tracks through those rows, the rest uniform noise."""
+    rng = np.random.default_rng(seed)
+    rc = np.zeros(36 * 159, np.int32)
+    for u, n_rows in unit_rows.items():
+        rc[u * 159:u * 159 + n_rows] = per_row
+    n = int(rc.sum())
+    rr = np.repeat(np.arange(36 * 159), rc)
+    rows, secs = rr % 159, rr // 159
+    cl = np.zeros((n, 4), np.float32)
+    cl[:, 0] = XR[rows]
+    half = XR[rows] * np.tan(np.radians(10.0))
+    cl[:, 1] = rng.uniform(-1, 1, n) * half
+    cl[:, 2] = np.where(secs < 18, 1, -1) * rng.uniform(0, 250, n)
+    # the first n_tracks clusters of every row lie on straight tracks
+    first = np.r_[0, np.cumsum(rc)[:-1]]
+    for u in unit_rows:
+        sgn = 1.0 if u < 18 else -1.0
+        y0 = rng.uniform(-10, 10, n_tracks)
+        ty = rng.uniform(-0.05, 0.05, n_tracks)
+        z0 = rng.uniform(20, 230, n_tracks)
+        tz = rng.uniform(-0.1, 0.1, n_tracks)
+        for r in range(unit_rows[u]):
+            i0 = first[u * 159 + r]
+            dx = XR[r] - XR[0]
+            cl[i0:i0 + n_tracks, 1] = y0 + ty * dx
+            cl[i0:i0 + n_tracks, 2] = sgn * (z0 + tz * dx)
+    cl.view(np.uint32)[:, 3] = rng.permutation(n)
+    return cl, rc
+
+
+def test_graph_not_replayed_for_a_larger_unit():
+    """Two batches alike in cluster count, rows and row maxima whose largest
+    (event, sector) unit differs: the second must not replay the first's
+    graph, whose ownership launch is sized for the smaller unit."""
+    a = _uniform_rows({0: 10, 1: 10}, 1000, 11)
+    b = _uniform_rows({0: 20}, 1000, 12)
+    assert len(a[0]) == len(b[0])
+    with Tracker(XR, use_graph=1, exact_fp32=1) as tr:
+        tr.track(*a, 1)
+        got = tr.track(*b, 1)
+    with Tracker(XR, use_graph=0, exact_fp32=1) as tr:
+        want = tr.track(*b, 1)
+    assert len(want.tracks) > 0
+    np.testing.assert_array_equal(got.tracks.view(np.uint8), want.tracks.view(np.uint8))
+    np.testing.assert_array_equal(got.hit_ids, want.hit_ids)
+
+
 def test_invalid_inputs_are_rejected(events):
     ev = events["c2"]
     with Tracker(XR, bz=ev.bz) as tr:
