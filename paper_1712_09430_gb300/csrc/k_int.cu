@@ -427,7 +427,7 @@ __global__ void k_owner(KConst k, DevPtrs p, int u0, int u1)
 constexpr int kOwnerChunk = 56 * 1024;  // 224 KB of keys
 constexpr int kListLoads = 5;           // loads per lane per pass: 160 list entries
 constexpr int kOwnerTracklets = 4;      // tracklets whose lists are read together
-constexpr int kEmitTracklets = 2;       // accepted tracklets written together
+constexpr int kEmitTracklets = 4;       // accepted tracklets written together
 
 __global__ void __launch_bounds__(1024) k_owner_units(KConst k, DevPtrs p, int chunks, int cap_keys)
 {
