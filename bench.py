@@ -858,7 +858,8 @@ def main():
     ap.add_argument("--bin-target", type=float, default=0.25)
     ap.add_argument("--threads-per-row", type=int, default=128)
     ap.add_argument("--tracklets-per-warp", type=int, default=32)
-    ap.add_argument("--schedule", type=int, default=0, help="0 unit by unit, 1 by start row")
+    ap.add_argument("--schedule", type=int, default=2,
+                    help="0 unit by unit, 1 by start row, 2 by start row inside blocks of ~2 M clusters")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="use the given execution parameters instead of tuning them first")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)

@@ -118,7 +118,11 @@ typedef struct {
     int schedule;            /* tracklet order of the persistent constructor:
                                 0 unit by unit (canonical order; keeps the
                                 working set of a few sectors in L2), 1 by start
-                                row across all units (longest expected first)  */
+                                row across all units (longest expected first),
+                                2 by start row inside blocks of units holding
+                                about 2 M clusters (both: a working set that
+                                fits L2, long tracklets first in every block;
+                                the default)                                   */
     /* final track fit (Sec. 2 "Track fit", Table 1 row 4) */
     int refit;               /* 1: refit every selected track with the full
                                 Kalman filter after selection (tpc_fit output);

@@ -252,10 +252,27 @@ __global__ void k_clean(KConst k, DevPtrs p, int rr0, int rows)
 }
 
 // Tracklet offsets per row in canonical (unit, row) order and in the
-// schedule order (row, unit): long expected tracks (low start rows) first.
-// Multi-CTA: each CTA scans kScanTile rows of both orders; a one-CTA pass
-// scans the tile sums; k_start_write adds the tile prefix.
-__device__ __forceinline__ int sched_row(int j, int U, int NR) { return (j % U) * NR + j / U; }
+// schedule order: units in blocks of Bk (all units when Bk is 0), and inside
+// a block (row, unit), so long expected tracks (low start rows) come first
+// in each block.  Multi-CTA: each CTA scans kScanTile rows of both orders; a
+// one-CTA pass scans the tile sums; k_start_write adds the tile prefix.
+// sched_row: the row (unit * NR + row) at schedule position j;
+// sched_pos: its inverse.
+__device__ __forceinline__ int sched_row(int j, int U, int NR, int Bk)
+{
+    if (Bk <= 0 || Bk >= U) return (j % U) * NR + j / U;
+    const int b = j / (Bk * NR), w = j - b * Bk * NR;
+    const int nb = min(Bk, U - b * Bk);
+    return (b * Bk + w % nb) * NR + w / nb;
+}
+
+__device__ __forceinline__ int sched_pos(int rr, int U, int NR, int Bk)
+{
+    const int u = rr / NR, r = rr % NR;
+    if (Bk <= 0 || Bk >= U) return r * U + u;
+    const int b = u / Bk, nb = min(Bk, U - b * Bk);
+    return b * Bk * NR + r * nb + (u - b * Bk);
+}
 
 __global__ void k_start_tiles(KConst k, DevPtrs p)
 {
@@ -267,14 +284,14 @@ __global__ void k_start_tiles(KConst k, DevPtrs p)
     int2 sv = make_int2(0, 0);
     for (int i = i0; i < i0 + per && i < R; i++) {
         sv.x += p.row_nstart[i];
-        sv.y += p.row_nstart[sched_row(i, U, NR)];
+        sv.y += p.row_nstart[sched_row(i, U, NR, p.sched_block)];
     }
     int2 total;
     int2 ex = block_excl_sum<int2>(sv, &total);
     for (int i = i0; i < i0 + per && i < R; i++) {
         p.start_off[i] = ex.x;
         ex.x += p.row_nstart[i];
-        const int rr = sched_row(i, U, NR);
+        const int rr = sched_row(i, U, NR, p.sched_block);
         p.sched_off[rr] = ex.y;
         ex.y += p.row_nstart[rr];
     }
@@ -314,7 +331,7 @@ __global__ void k_start_final(KConst k, DevPtrs p)
 {
     const int ntiles = (p.R + kScanTile - 1) / kScanTile;
     for (int rr = blockIdx.x * blockDim.x + threadIdx.x; rr < p.R; rr += gridDim.x * blockDim.x) {
-        const int j = (rr % k.n_rows) * p.n_units + rr / k.n_rows;
+        const int j = sched_pos(rr, p.n_units, k.n_rows, p.sched_block);
         p.start_off[rr] += p.start_part[rr / kScanTile];
         p.sched_off[rr] += p.start_part[ntiles + 1 + j / kScanTile];
     }

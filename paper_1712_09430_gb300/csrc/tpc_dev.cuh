@@ -57,6 +57,10 @@ struct KConst {
     int n_rows, n_sectors;
 };
 
+// schedule 2: by start row inside blocks of units that hold about this many
+// clusters together (their rows stay in L2 while the block is built)
+constexpr int kSchedBlockClusters = 1 << 21;
+
 // Search grid of one row: nbins = ny * nz, bin = iz * ny + iy.  The grid
 // covers y in [y0, -y0] with y0 = -(X tan_h + y_margin) and z in the drift
 // half of the unit's side (z0 = 0 on side A, -z_max on side C).
@@ -125,6 +129,7 @@ struct DevPtrs {
     int* t0_cnt;                 // [E * nb] member counts
     int* counters;             // [kNumCounters]
     int N, R, n_units, t_cap, m_cap, mh_cap;
+    int sched_block;  // units per block of the by-row schedule (0: all units)
 };
 
 constexpr int kScanTile = 2048;  // elements per CTA in the multi-CTA scan

@@ -101,7 +101,7 @@ static const char* check_params(const tpc_params& P)
     if (t != 32 && t != 64 && t != 128 && t != 256) return "threads_per_row must be 32, 64, 128 or 256";
     int w = P.tracklets_per_warp;
     if (w != 1 && w != 2 && w != 4 && w != 8 && w != 16 && w != 32) return "tracklets_per_warp";
-    if (P.schedule != 0 && P.schedule != 1) return "schedule must be 0 or 1";
+    if (P.schedule < 0 || P.schedule > 2) return "schedule must be 0, 1 or 2";
     if (P.plain_per_sector < 0 || P.plain_per_sector > 2) return "plain_per_sector must be 0, 1 or 2";
     if (P.n_queues < 1 || P.n_queues > 64) return "n_queues must be in [1, 64]";
     if (P.refit != 0 && P.refit != 1) return "refit must be 0 or 1";
@@ -147,7 +147,7 @@ extern "C" void tpc_params_default(tpc_params* p)
     p->plain_per_sector = 0;
     p->use_graph = 0;
     p->n_queues = 8;
-    p->schedule = 0;
+    p->schedule = 2;
     p->refit = 0;
     p->merge = 0;
     p->merge_chi2 = 30.0f;
@@ -331,6 +331,11 @@ size_t tpc_layout(const tpc_tracker* tr, const BatchShape& sh, DevPtrs* p, char*
     q.N = sh.N;
     q.R = sh.R;
     q.n_units = sh.n_units;
+    q.sched_block = 0;
+    if (tr->params.schedule == 2 && sh.n_units > 0) {
+        const double per_unit = std::max(1.0, (double)sh.N / sh.n_units);
+        q.sched_block = (int)std::min<double>(sh.n_units, std::max(1.0, std::round(kSchedBlockClusters / per_unit)));
+    }
     q.t_cap = sh.t_cap;
     q.m_cap = sh.t_cap;
     q.mh_cap = sh.N;
@@ -843,7 +848,7 @@ extern "C" int tpc_autotune(tpc_tracker* tr, const tpc_cluster* clusters, const 
         int kind;  // 0 schedule, 1 bin_target, 2 tracklets_per_warp, 3 threads_per_row
         std::vector<float> values;
     };
-    const std::vector<Axis> axes = {{0, {0, 1}},
+    const std::vector<Axis> axes = {{0, {0, 1, 2}},
                                     {1, {0.25f, 0.5f, 1.0f, 2.0f}},
                                     {2, {32, 16, 8}},
                                     {3, {64, 128, 256}}};

@@ -67,7 +67,8 @@ def test_exact_parity_multi_event_batch(events):
                                   dict(plain_per_sector=2, n_queues=8),
                                   dict(plain_per_sector=2, n_queues=3, use_graph=1),
                                   dict(tracklets_per_warp=4), dict(schedule=1),
-                                  dict(tracklets_per_warp=16, schedule=1)])
+                                  dict(tracklets_per_warp=16, schedule=1), dict(schedule=2),
+                                  dict(tracklets_per_warp=8, schedule=2)])
 def test_execution_params_do_not_change_results(events, over):
     ev = events["c3s"]
     base = gpu_run(ev.clusters, ev.row_counts, 1, exact_fp32=1)
@@ -278,6 +279,21 @@ def test_full_size_central_batch_exact():
     g = gpu_run(cl, rc, len(evs), exact_fp32=1, use_graph=1)
     o = oracle_run(cl, rc, len(evs), mode="f32")
     assert_exact_equal(g, o)
+
+
+def test_block_schedule_full_size():
+    """Schedule 2 on two full central events: blocks of about 2 M clusters
+    (37 and 35 of the 72 units, the last one ragged) give the same tracks as
+    the canonical order."""
+    evs = [S.central_event(seed=3 + i) for i in range(2)]
+    cl, rc = S.concat_events(evs)
+    with Tracker(XR, exact_fp32=1, use_graph=1, schedule=0) as tr:
+        a = tr.track(cl, rc, 2)
+    with Tracker(XR, exact_fp32=1, use_graph=1, schedule=2) as tr:
+        b = tr.track(cl, rc, 2)
+    assert len(a.tracks) > 40000
+    np.testing.assert_array_equal(a.tracks.view(np.uint8), b.tracks.view(np.uint8))
+    np.testing.assert_array_equal(a.hit_ids, b.hit_ids)
 
 
 def test_autotune_keeps_results_and_caches(events, tmp_path):
