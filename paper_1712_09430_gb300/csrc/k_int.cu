@@ -172,22 +172,25 @@ __global__ void k_grid(KConst k, const float* __restrict__ row_x, DevPtrs p, int
             p.dn[off + i] = -1;
         }
     }
+    // slot[i] = bin << 12 | place of cluster i in its bin (a row holds at
+    // most 2^12 clusters)
+    static_assert(kMaxBinsPerRow <= (1 << 19) && TPC_MAX_ROW_CLUSTERS <= (1 << 12), "slot packing");
     for (int i = tid; i < cnt; i += nt) {
         float4 c = in[i];
         bool ok = fabsf(c.x - X) <= kCoordTol && isfinite(c.y) && isfinite(c.z);
         if (!ok) flag_error(p.counters, E_INPUT, rr);
         int by = bin_index(c.y, y0, g.inv_by, ny);
         int bz = bin_index(c.z, z0, g.inv_bz, nz);
-        slot[i] = atomicAdd(&hist[bz * ny + by], 1);
+        const int b = bz * ny + by;
+        slot[i] = (b << 12) | atomicAdd(&hist[b], 1);
     }
     __syncthreads();
     block_scan_smem(hist, nb + 1);
     for (int b = tid; b <= nb; b += nt) p.bin_off[g.bin_base + b] = off + hist[b];
     for (int i = tid; i < cnt; i += nt) {
-        float4 c = in[i];
-        int by = bin_index(c.y, y0, g.inv_by, ny);
-        int bz = bin_index(c.z, z0, g.inv_bz, nz);
-        out[hist[bz * ny + by] + slot[i]] = make_float4(c.y, c.z, c.w, __int_as_float(off + i));
+        const float4 c = in[i];
+        const int v = slot[i];
+        out[hist[v >> 12] + (v & 4095)] = make_float4(c.y, c.z, c.w, __int_as_float(off + i));
     }
     __syncthreads();
     // order inside each bin by id (insertion sort; bins hold a few clusters)
