@@ -240,7 +240,7 @@ static int launch_batch_impl(tpc_tracker* tr)
     BatchShape sh;
     int rc = tpc_shape(tr, counts, ev, &sh);  // fills tr->plan_host
     if (rc != TPC_OK) return rc;
-    std::memcpy(counts + R, tr->plan_host, (R + 1) * 2 * sizeof(int));
+    std::memcpy(counts + R, tr->plan_host + R, (R + 1) * 2 * sizeof(int));
     const size_t bytes = align256(tpc_layout(tr, sh, nullptr, nullptr));
     size_t off = 0;
     if (!S->arena.alloc(bytes, &off)) return TPC_BUSY;  // wait for a running batch
@@ -277,10 +277,8 @@ static int launch_batch_impl(tpc_tracker* tr)
     }
     S->pending.erase(S->pending.begin(), S->pending.begin() + (long)take.size());
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(const_cast<int*>(p.row_cnt), counts, R * sizeof(int), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(const_cast<int*>(p.row_off), counts + R, (R + 1) * 2 * sizeof(int),
-                            cudaMemcpyHostToDevice, s);
+        e = cudaMemcpyAsync(const_cast<int*>(p.row_cnt), counts, (3 * R + 2) * sizeof(int),
+                            cudaMemcpyHostToDevice, s);  // counts and plan, adjacent on both sides
     if (e == cudaSuccess && ev > 0)
         e = cudaMemcpyAsync(p.req_area, req_first, (size_t)ev * sizeof(int), cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return tr->fail(TPC_ERR_DEVICE, cudaGetErrorString(e));

@@ -41,7 +41,7 @@ struct tpc_tracker {
     int last_T = 0, last_M = 0, last_MH = 0;
     cudaStream_t last_stream = nullptr;
     int* counters_host = nullptr;  // pinned
-    int* plan_host = nullptr;      // pinned: row CSR offsets + bin-table offsets of a call
+    int* plan_host = nullptr;      // pinned: row counts, row CSR offsets, bin-table offsets of a call
     size_t plan_cap = 0;           // ints
     std::vector<int> slots_lut;    // bin-table slots per row count (current bin_target)
     float slots_lut_bt = 0.0f;

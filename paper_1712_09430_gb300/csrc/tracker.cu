@@ -270,9 +270,10 @@ size_t tpc_layout(const tpc_tracker* tr, const BatchShape& sh, DevPtrs* p, char*
     const size_t NR = (size_t)tr->geom.n_rows;
     DevPtrs q{};
     q.clusters = reinterpret_cast<const float4*>(take(N * 16));
-    q.row_cnt = reinterpret_cast<const int*>(take(R * 4));
-    // row_off and bin_cap_off are adjacent: one H2D of the host plan fills both
-    q.row_off = reinterpret_cast<const int*>(take((R + 1) * 4 * 2));
+    // row_cnt, row_off and bin_cap_off are adjacent: one H2D of the host plan
+    // fills all three
+    q.row_cnt = reinterpret_cast<const int*>(take((3 * R + 2) * 4));
+    q.row_off = q.row_cnt ? q.row_cnt + R : nullptr;
     q.bin_cap_off = q.row_off ? q.row_off + (R + 1) : nullptr;
     q.grid = reinterpret_cast<RowGrid*>(take(R * sizeof(RowGrid)));
     q.hits = reinterpret_cast<float4*>(take(N * 16));
@@ -351,19 +352,23 @@ int tpc_shape(tpc_tracker* tr, const int32_t* row_counts, int n_events, BatchSha
     if (R > (1 << 28)) return tr->fail(TPC_ERR_INVALID, "too many rows in one call");
     int64_t N = 0, bins = 0, max_unit = 0;
     int max_row = 0, max3 = 0, max_slots = 0, max_slots3 = 0;
-    if ((size_t)(2 * (R + 1)) > tr->plan_cap) {
+    if ((size_t)(3 * R + 2) > tr->plan_cap) {
         cudaFreeHost(tr->plan_host);
         tr->plan_host = nullptr;
         tr->plan_cap = 0;
-        size_t want = (size_t)(2 * (R + 1)) + (size_t)(R / 4) + 64;
+        size_t want = (size_t)(3 * R + 2) + (size_t)(R / 4) + 64;
         if (cudaMallocHost(&tr->plan_host, want * sizeof(int)) != cudaSuccess) {
             cudaGetLastError();
             return tr->fail(TPC_ERR_NOMEM, "cannot allocate pinned plan buffer");
         }
         tr->plan_cap = want;
     }
-    int* plan_off = tr->plan_host;           // [R + 1] CSR offsets of rows
-    int* plan_bins = tr->plan_host + R + 1;  // [R + 1] bin-table offsets
+    // the pinned plan: row counts [R], CSR offsets of rows [R + 1], bin-table
+    // offsets [R + 1], laid out as on the device so that one copy uploads all
+    int* plan_cnt = tr->plan_host;
+    int* plan_off = tr->plan_host + R;
+    int* plan_bins = tr->plan_host + 2 * R + 1;
+    if (plan_cnt != row_counts) std::memcpy(plan_cnt, row_counts, (size_t)R * sizeof(int));
     // bin-table slots per row count, for the current bin_target
     if (tr->slots_lut.size() != TPC_MAX_ROW_CLUSTERS + 1 || tr->slots_lut_bt != tr->params.bin_target) {
         tr->slots_lut.resize(TPC_MAX_ROW_CLUSTERS + 1);
@@ -716,9 +721,8 @@ extern "C" int tpc_track_sectors(tpc_tracker* tr, const tpc_cluster* clusters, c
     } else {
         p.clusters = reinterpret_cast<const float4*>(clusters);
     }
-    TPC_CUDA(cudaMemcpyAsync(const_cast<int*>(p.row_cnt), row_counts, (size_t)sh.R * 4,
-                             cudaMemcpyHostToDevice, s));
-    TPC_CUDA(cudaMemcpyAsync(const_cast<int*>(p.row_off), tr->plan_host, (size_t)(sh.R + 1) * 8,
+    // row counts and the plan, from pinned memory in one copy
+    TPC_CUDA(cudaMemcpyAsync(const_cast<int*>(p.row_cnt), tr->plan_host, (size_t)(3 * sh.R + 2) * 4,
                              cudaMemcpyHostToDevice, s));
     tr->cur = p;
     tr->cur_shape = sh;
