@@ -172,11 +172,16 @@ def cpu_baseline(seconds_target=15.0, ev=None):
         oracle.run(cl6, rc6, 1, ev.bz, synth.row_x(), mode="f64", threads=th)
         per_threads[str(th)] = ncl / (time.perf_counter() - t1)
     per_threads[str(cores)] = done / dt
+    # the FP32_EXACT mode (binary32 expressions without fused multiply-add)
+    # on all cores, one event
+    t1 = time.perf_counter()
+    oracle.run(ev.clusters, ev.row_counts, 1, ev.bz, synth.row_x(), mode="f32", threads=cores)
+    f32 = ev.n / (time.perf_counter() - t1)
     return {"value": done / dt, "unit": "clusters/s", "cores": cores, "kind": "oracle",
             "sample": f"{n_ev} x one central Pb-Pb event ({ev.n} clusters), FP64 oracle, "
                       f"OpenMP over the 36 sectors, {dt:.1f} s wall; 1 and 4 threads on sectors "
-                      f"0-5 of the same event ({ncl} clusters)",
-            "by_threads": per_threads}
+                      f"0-5 of the same event ({ncl} clusters); FP32_EXACT mode on one event, all cores",
+            "by_threads": per_threads, "f32_exact_all_cores": f32}
 
 
 def run_reference(args):
@@ -236,13 +241,17 @@ def run_ours(args):
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    seeds = rank_seeds(rank, args.batch)
+    n_central = max([args.batch] + list(args.batch_sizes))
+    seeds = rank_seeds(rank, n_central)   # the step's batch is the first args.batch of them
     mb_seeds = [1000 + rank * args.pool + i for i in range(args.pool)] if args.stream_rates else []
     tf_job = (4 + rank, args.tf_collisions) if args.tf_collisions > 0 else None
     sl_jobs = list(args.tf_slices)   # the same slices on every rank
-    cl_np, rc_np, mb_pool, *extra = make_inputs(seeds, mb_seeds, tf_job, sl_jobs)   # before any CUDA use
+    cl_all, rc_all, mb_pool, *extra = make_inputs(seeds, mb_seeds, tf_job, sl_jobs)   # before any CUDA use
     frame = extra.pop(0) if tf_job else None
     slices = extra.pop(0) if sl_jobs else None
+    units_per_event = 36 * 159
+    cl_np = np.ascontiguousarray(cl_all[:int(rc_all[:args.batch * units_per_event].sum())])
+    rc_np = np.ascontiguousarray(rc_all[:args.batch * units_per_event])
     import torch
     import ctypes as C
     dist = None
@@ -306,6 +315,9 @@ def run_ours(args):
     ms = reduce_step_ms(ms, dist, dev_cl.device)
     M, MH = out.n_tracks, out.n_hits
     T = len(tr.dump(capi.TPC_DUMP_STARTS)) if rank == 0 else 0
+    # the tracklet kernel's own work counts of this batch, taken before other
+    # legs run other batches through the same tracker
+    algo_step = algorithmic_bytes(tr, N, T) if rank == 0 else None
     value = N * world / (ms * 1e-3)
 
     # ---- end to end through the C ABI with pinned host buffers
@@ -321,6 +333,9 @@ def run_ours(args):
     stream_res = None
     if args.stream_rates:
         stream_res = [run_stream(tr, mb_pool, args, rate) for rate in args.stream_rates]
+    batch_sizes = None
+    if args.batch_sizes:
+        batch_sizes = run_batch_sizes(L, tr, cl_all, rc_all, args, dev_cl.device, sp)
     refit = None
     if args.refit_steps > 0:
         refit = run_refit(L, tr, dev_cl, rc_ptr, B, sp, out, out_tr, out_h, args)
@@ -344,7 +359,7 @@ def run_ours(args):
     names = ["grid", "neighbours", "clean+starts", "tracklets", "select+emit"]
     stage_ms = {n: float(v) for n, v in zip(names, stage[:5])}
     dom = max(stage_ms, key=stage_ms.get)
-    algo = algorithmic_bytes(tr, N, T) if dom == "tracklets" else None
+    algo = algo_step if dom == "tracklets" else None
     rl = None
     if algo is not None:
         achieved = algo["bytes"] / (stage_ms[dom] * 1e-3) / 1e9
@@ -377,7 +392,7 @@ def run_ours(args):
             "gpu_launches": LAUNCHES_PER_STEP * args.steps,
             "clocks": ck, "e2e": e2e, "e2e_sync": e2e_sync, "roofline": rl, "cpu_baseline": cpu,
             "plain_per_sector": plain, "multi_queue_per_sector": multi, "stream": stream_res,
-            "refit": refit, "time_frame": tframe}
+            "refit": refit, "time_frame": tframe, "batch_sizes": batch_sizes}
     if stream_res:
         line["latency_ms"] = {"p50": stream_res[0]["p50_ms"], "p99": stream_res[0]["p99_ms"],
                               "rate_hz": stream_res[0]["rate_hz"]}
@@ -551,6 +566,50 @@ def run_time_frame(frame, tr0, args, device):
                 "tracks_assigned": float((coll >= 0).mean()),
                 "workload": f"time frame of {len(coll_dz)} min-bias collisions, each shifted by a drift "
                             "offset ~ U[-250, 250] cm (continuous readout), 10% noise"})
+    return res
+
+
+def run_batch_sizes(L, tr, cl_all, rc_all, args, device, sp):
+    """The batched step over other numbers of central events per call (the
+    survey's x1 and x32 beside the x8 of the headline): graph replay, inputs
+    resident, CUDA events around each call, median over the steps."""
+    import ctypes as C
+    import torch
+    from paper_1712_09430_gb300 import capi
+    from paper_1712_09430_gb300.tracker import TRACK_DTYPE
+    upe = 36 * 159
+    res = []
+    for B in args.batch_sizes:
+        rc = np.ascontiguousarray(rc_all[:B * upe])
+        n = int(rc.sum())
+        dev = torch.from_numpy(np.ascontiguousarray(cl_all[:n])).to(device)
+        cap_t, cap_h = n // 10 + 1024, n
+        out_tr = torch.empty(cap_t * TRACK_DTYPE.itemsize, dtype=torch.uint8, device=device)
+        out_h = torch.empty(cap_h, dtype=torch.int32, device=device)
+        out = capi.tpc_output(out_tr.data_ptr(), out_h.data_ptr(), cap_t, cap_h, capi.TPC_MEM_DEVICE, 0, 0)
+        rc_ptr = rc.ctypes.data_as(C.c_void_p)
+        stream = torch.cuda.Stream(device)
+
+        def step():
+            r = L.tpc_track_sectors(tr.h, C.c_void_p(dev.data_ptr()), rc_ptr, B, capi.TPC_MEM_DEVICE,
+                                    C.byref(out), C.c_void_p(stream.cuda_stream))
+            if r != capi.TPC_OK:
+                raise RuntimeError(f"tpc_track_sectors: {capi.STATUS_NAMES.get(r)}: {tr.error()}")
+        for _ in range(max(3, args.warmup)):
+            step()
+        steps = max(5, min(args.steps, int(2000 / max(B, 1))))
+        ms = []
+        for _ in range(steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        t = statistics.median(ms)
+        res.append({"events": B, "clusters": n, "ms": t, "clusters_per_s": n / (t * 1e-3),
+                    "events_per_s": B / (t * 1e-3), "steps": steps, "tracks": int(out.n_tracks)})
+        del dev, out_tr, out_h
     return res
 
 
@@ -875,6 +934,8 @@ def main():
     ap.add_argument("--tf-collisions", type=int, default=50,
                     help="collisions of the continuous-readout time-frame leg (0: skip)")
     ap.add_argument("--tf-steps", type=int, default=5)
+    ap.add_argument("--batch-sizes", type=lambda v: [int(x) for x in v.split(",") if x.strip()],
+                    default=[1, 32], help="other central events per call to time beside --batch; '' = off")
     ap.add_argument("--tf-slices",
                     type=lambda v: [tuple(int(y) for y in x.split(":")) for x in v.split(",") if x.strip()],
                     default=[(47, 8), (44, 16), (42, 24), (43, 40), (44, 64)],
