@@ -333,6 +333,17 @@ def run_ours(args):
     stream_res = None
     if args.stream_rates:
         stream_res = [run_stream(tr, mb_pool, args, rate) for rate in args.stream_rates]
+    stream_central = None
+    if args.stream_central_rates:
+        upe = 36 * 159
+        offs = np.r_[0, np.cumsum([int(rc_np[e * upe:(e + 1) * upe].sum()) for e in range(B)])]
+        central_pool = [(np.ascontiguousarray(cl_np[offs[e]:offs[e + 1]]),
+                         np.ascontiguousarray(rc_np[e * upe:(e + 1) * upe])) for e in range(B)]
+        stream_central = [run_stream(tr, central_pool, args, rate, batch=args.batch,
+                                     workload=f"central Pb-Pb-like events (the step's {B} events, "
+                                              "sampled with replacement), Poisson arrivals, one event "
+                                              "per request")
+                          for rate in args.stream_central_rates]
     batch_sizes = None
     if args.batch_sizes:
         batch_sizes = run_batch_sizes(L, tr, cl_all, rc_all, args, dev_cl.device, sp)
@@ -392,7 +403,8 @@ def run_ours(args):
             "gpu_launches": LAUNCHES_PER_STEP * args.steps,
             "clocks": ck, "e2e": e2e, "e2e_sync": e2e_sync, "roofline": rl, "cpu_baseline": cpu,
             "plain_per_sector": plain, "multi_queue_per_sector": multi, "stream": stream_res,
-            "refit": refit, "time_frame": tframe, "batch_sizes": batch_sizes}
+            "refit": refit, "time_frame": tframe, "batch_sizes": batch_sizes,
+            "stream_central": stream_central}
     if stream_res:
         line["latency_ms"] = {"p50": stream_res[0]["p50_ms"], "p99": stream_res[0]["p99_ms"],
                               "rate_hz": stream_res[0]["rate_hz"]}
@@ -685,11 +697,16 @@ def run_plain(L, tr, dev_cl, rc_ptr, B, N, world, sp, out, args, mode=1):
                     ("on one stream" if mode == 1 else "round-robin over 8 streams")}
 
 
-def run_stream(tr0, pool, args, rate):
-    """Serving: Poisson arrivals of min-bias events (sampled with replacement
-    from the pool) at `rate` Hz for args.stream_seconds, through
-    tpc_stream_submit/poll.  Latency = result in hand - arrival (includes
-    queueing, H2D, the batched stages and D2H)."""
+MINBIAS_STREAM = ("min-bias events (b ~ U[0,15] fm, 10-10,000 primaries + 30% secondaries, "
+                  "10% noise), Poisson arrivals, one event per request")
+
+
+def run_stream(tr0, pool, args, rate, batch=None, workload=MINBIAS_STREAM):
+    """Serving: Poisson arrivals of events (sampled with replacement from the
+    pool) at `rate` Hz for args.stream_seconds, through tpc_stream_submit/poll,
+    at most `batch` events per batch.  Latency = result in hand - arrival
+    (includes queueing, H2D, the batched stages and D2H)."""
+    batch = batch or args.stream_batch
     from paper_1712_09430_gb300 import synth
     from paper_1712_09430_gb300.tracker import Tracker
     p = tr0.params
@@ -701,7 +718,7 @@ def run_stream(tr0, pool, args, rate):
         # events arrive in pinned host memory (as from a readout link) and are
         # submitted without a copy; each stays untouched until its result is in
         pool = [(torch.from_numpy(cl).pin_memory(), rc) for cl, rc in pool]
-        tr.stream_configure(arena_bytes=args.stream_arena_gb << 30, max_batch_events=args.stream_batch,
+        tr.stream_configure(arena_bytes=args.stream_arena_gb << 30, max_batch_events=batch,
                             max_inflight=2, no_copy=True)
         rng = np.random.default_rng(5)
         n_req = int(rate * args.stream_seconds)
@@ -709,7 +726,7 @@ def run_stream(tr0, pool, args, rate):
         picks = rng.integers(0, len(pool), n_req)
         # warm-up: one burst of a full batch (the result buffers reach their
         # working size), then a few single requests, drained
-        for burst in (min(args.stream_batch, len(pool)), 1, 1, 1, 1):
+        for burst in (min(batch, len(pool)), 1, 1, 1, 1):
             warm = [tr.submit(pool[i][0], pool[i][1], 1) for i in range(burst)]
             for t in warm:
                 while t is not None and tr.poll(t, 1000) is None:
@@ -771,8 +788,7 @@ def run_stream(tr0, pool, args, rate):
             "clusters_per_s": clusters / wall, "events_per_s": n_req / wall, "wall_s": wall,
             "tracks": n_tracks, "client": "tpc_stream_poll_view + tpc_stream_release (results read in place)",
             "pool_events": len(pool), "mean_clusters_per_event": float(np.mean([len(p[0]) for p in pool])),
-            "workload": "min-bias events (b ~ U[0,15] fm, 10-10,000 primaries + 30% secondaries, "
-                        "10% noise), Poisson arrivals, one event per request"}
+            "max_batch_events": batch, "workload": workload}
 
 
 def run_e2e(L, tr, cl_np, rc_ptr, rc_np, B, N, world, sp, cap_t, cap_h, args):
@@ -929,6 +945,9 @@ def main():
                     default=[1000.0, 3000.0, 5000.0],
                     help="Poisson arrival rates (Hz) of the serving leg, comma separated; '' = off")
     ap.add_argument("--stream-seconds", type=float, default=2.0)
+    ap.add_argument("--stream-central-rates", type=lambda v: [float(x) for x in v.split(",") if x.strip()],
+                    default=[250.0, 500.0, 1000.0],
+                    help="Poisson arrival rates (Hz) of central events through the serving API; '' = off")
     ap.add_argument("--refit-steps", type=int, default=10,
                     help="steps of the final-refit leg (0: skip)")
     ap.add_argument("--tf-collisions", type=int, default=50,
