@@ -631,8 +631,9 @@ __device__ __forceinline__ void lane_step(Lane& L, const KConst& k, const float*
 }
 
 // Persistent, dynamically scheduled constructor: idle lane groups take the
-// next entries of the length-sorted schedule (long expected tracks first)
-// from a global counter, with one warp-aggregated atomic per refill.
+// next entries of the schedule (canonical order, or by start row -- long
+// expected tracks first -- across all units or inside blocks of units) from
+// a global counter, with one warp-aggregated atomic per refill.
 constexpr int kTrackletCtasPerSm = 3;  // 256 threads each: 24 warps per SM, <= 85 registers
 
 template <int G>
