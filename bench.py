@@ -704,8 +704,9 @@ MINBIAS_STREAM = ("min-bias events (b ~ U[0,15] fm, 10-10,000 primaries + 30% se
 def run_stream(tr0, pool, args, rate, batch=None, workload=MINBIAS_STREAM):
     """Serving: Poisson arrivals of events (sampled with replacement from the
     pool) at `rate` Hz for args.stream_seconds, through tpc_stream_submit/poll,
-    at most `batch` events per batch.  Latency = result in hand - arrival
-    (includes queueing, H2D, the batched stages and D2H)."""
+    at most `batch` events and the library's default cluster limit (about 4 M)
+    per batch.  Latency = result in hand - arrival (includes queueing, H2D,
+    the batched stages and D2H)."""
     batch = batch or args.stream_batch
     from paper_1712_09430_gb300 import synth
     from paper_1712_09430_gb300.tracker import Tracker
@@ -944,7 +945,7 @@ def main():
     ap.add_argument("--stream-rates", type=lambda v: [float(x) for x in v.split(",") if x.strip()],
                     default=[1000.0, 3000.0, 5000.0],
                     help="Poisson arrival rates (Hz) of the serving leg, comma separated; '' = off")
-    ap.add_argument("--stream-seconds", type=float, default=2.0)
+    ap.add_argument("--stream-seconds", type=float, default=3.0)
     ap.add_argument("--stream-central-rates", type=lambda v: [float(x) for x in v.split(",") if x.strip()],
                     default=[250.0, 500.0, 1000.0],
                     help="Poisson arrival rates (Hz) of central events through the serving API; '' = off")

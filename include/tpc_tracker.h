@@ -311,15 +311,20 @@ int tpc_stream_submit(tpc_tracker* tr, const tpc_cluster* clusters, const int32_
 /* Serving configuration, before the first submit: the device arena that
  * admission draws on (0: half of the free device memory, at most 24 GiB),
  * the most events one batch may hold, how many batches may run at once
- * (1..8; each on its own stream), and flags:
+ * (1..8; each on its own stream), flags, and the most clusters one batch may
+ * hold (0: no limit; a request larger than that forms a batch of its own).
+ * A batch formed after a burst of arrivals holds all its requests until its
+ * last kernel, so the cluster limit bounds the latency a burst adds (the
+ * default 2^22 is about two central or sixteen min-bias events).  Flags:
  *   TPC_STREAM_NO_COPY  tpc_stream_submit does not copy the clusters; the
  *                       caller keeps the buffer valid and unchanged until the
  *                       ticket's result has been polled (pinned host memory
  *                       makes the copy to the device asynchronous).
  * TPC_BUSY once serving has started. */
 #define TPC_STREAM_NO_COPY 1
+#define TPC_STREAM_BATCH_CLUSTERS (1 << 22)
 int tpc_stream_configure(tpc_tracker* tr, size_t arena_bytes, int max_batch_events, int max_inflight,
-                         int flags);
+                         int flags, int64_t max_batch_clusters);
 
 /* Poll a ticket, waiting at most timeout_us (0: do not wait).  Returns
  * TPC_PENDING, TPC_OK (out filled; the ticket is released) or an error

@@ -34,6 +34,7 @@ TPC_DUMP_TRACKLET_HITS = 5
 TPC_DUMP_TRACKLET_WORK = 6
 TPC_NOALLOC_MAX_CLUSTERS = 65536
 TPC_STREAM_NO_COPY = 1
+TPC_STREAM_BATCH_CLUSTERS = 1 << 22  # default cluster limit of one serving batch
 
 STATUS_NAMES = {0: "TPC_OK", 1: "TPC_PENDING", 2: "TPC_BUSY", -1: "TPC_ERR_INVALID",
                 -2: "TPC_ERR_NOMEM", -3: "TPC_ERR_OUTPUT_TRUNCATED", -4: "TPC_ERR_TIMEOUT",
@@ -128,7 +129,7 @@ def lib() -> C.CDLL:
         L.tpc_autotune.argtypes = [V, V, V, C.c_int, C.c_int, C.c_int, P(tpc_params), P(C.c_float)]
         L.tpc_stream_submit.argtypes = [V, V, V, C.c_int, C.c_uint64, P(C.c_uint64)]
         L.tpc_stream_poll.argtypes = [V, C.c_uint64, P(tpc_output), C.c_int]
-        L.tpc_stream_configure.argtypes = [V, C.c_size_t, C.c_int, C.c_int, C.c_int]
+        L.tpc_stream_configure.argtypes = [V, C.c_size_t, C.c_int, C.c_int, C.c_int, C.c_int64]
         L.tpc_stream_get_stats.argtypes = [V, P(tpc_stream_stats)]
         L.tpc_stream_poll_view.argtypes = [V, C.c_uint64, P(tpc_stream_view), C.c_int]
         L.tpc_stream_release.argtypes = [V, C.c_uint64]

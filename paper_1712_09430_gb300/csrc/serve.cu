@@ -117,6 +117,7 @@ bool fault(const char* name)
 struct ServeState {
     size_t arena_bytes = 0;        // 0: choose at first submit
     int max_batch_events = 64;
+    int64_t max_batch_clusters = TPC_STREAM_BATCH_CLUSTERS;  // 0: no limit
     int max_inflight = 2;
     int max_requests = 4096;
     int flags = 0;                 // TPC_STREAM_NO_COPY
@@ -216,11 +217,15 @@ static int launch_batch_impl(tpc_tracker* tr)
     // take requests in arrival order
     std::vector<uint64_t> take;
     int ev = 0;
+    int64_t ncl = 0;
     for (uint64_t t : S->pending) {
         const Request& r = S->req[t];
-        if (!take.empty() && ev + r.n_events > S->max_batch_events) break;
+        if (!take.empty() && (ev + r.n_events > S->max_batch_events ||
+                              (S->max_batch_clusters > 0 && ncl + r.N > S->max_batch_clusters)))
+            break;
         take.push_back(t);
         ev += r.n_events;
+        ncl += r.N;
     }
     const int NR = tr->geom.n_rows, NS = tr->geom.n_sectors;
     const size_t R = (size_t)ev * NS * NR;
@@ -490,18 +495,19 @@ void tpc_serve_shutdown(tpc_tracker* tr)
 bool tpc_serve_busy(const tpc_tracker* tr) { return tr->serve && !tr->serve->req.empty(); }
 
 extern "C" int tpc_stream_configure(tpc_tracker* tr, size_t arena_bytes, int max_batch_events,
-                                    int max_inflight, int flags)
+                                    int max_inflight, int flags, int64_t max_batch_clusters)
 {
     if (!tr) return TPC_ERR_INVALID;
     if (tr->serve && (tr->serve->arena_base || !tr->serve->req.empty()))
         return tr->fail(TPC_BUSY, "serving already started");
-    if (max_batch_events < 1 || max_inflight < 1 || max_inflight > 8)
-        return tr->fail(TPC_ERR_INVALID, "max_batch_events >= 1, max_inflight in [1, 8]");
+    if (max_batch_events < 1 || max_inflight < 1 || max_inflight > 8 || max_batch_clusters < 0)
+        return tr->fail(TPC_ERR_INVALID, "max_batch_events >= 1, max_inflight in [1, 8], max_batch_clusters >= 0");
     if (!tr->serve) tr->serve = new ServeState();
     tr->serve->arena_bytes = arena_bytes;
     tr->serve->max_batch_events = max_batch_events;
     tr->serve->max_inflight = max_inflight;
     tr->serve->flags = flags;
+    tr->serve->max_batch_clusters = max_batch_clusters;
     return TPC_OK;
 }
 

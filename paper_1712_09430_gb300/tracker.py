@@ -179,10 +179,12 @@ class Tracker:
         return [a.ctypes.data if a is not None else None for a in opt]
 
     # ---- serving (continuous batching) -----------------------------------
-    def stream_configure(self, arena_bytes=0, max_batch_events=64, max_inflight=2, no_copy=False):
+    def stream_configure(self, arena_bytes=0, max_batch_events=64, max_inflight=2, no_copy=False,
+                         max_batch_clusters=capi.TPC_STREAM_BATCH_CLUSTERS):
         self.check(lib().tpc_stream_configure(self.h, int(arena_bytes), int(max_batch_events),
                                               int(max_inflight),
-                                              capi.TPC_STREAM_NO_COPY if no_copy else 0))
+                                              capi.TPC_STREAM_NO_COPY if no_copy else 0,
+                                              int(max_batch_clusters)))
 
     def stream_stats(self):
         """Counters of the request loop (batches, events, device and host ms)."""

@@ -296,6 +296,18 @@ def test_block_schedule_full_size():
     np.testing.assert_array_equal(a.hit_ids, b.hit_ids)
 
 
+def test_full_size_time_frame_exact():
+    """The full 50-collision continuous-readout time frame (5.5 M clusters as
+    one event; rows of up to ~1,500 clusters, hundreds of start hits in a
+    row) against the FP32 oracle, every stage, batched launch with graph
+    replay."""
+    ev = S.time_frame(seed=4)
+    assert int(ev.row_counts.max()) > 1000
+    g = gpu_run(ev.clusters, ev.row_counts, 1, exact_fp32=1, use_graph=1)
+    o = oracle_run(ev.clusters, ev.row_counts, 1, mode="f32")
+    assert_exact_equal(g, o)
+
+
 def test_autotune_keeps_results_and_caches(events, tmp_path):
     from paper_1712_09430_gb300 import autotune
     ev = events["c3s"]

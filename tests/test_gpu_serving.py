@@ -194,3 +194,35 @@ def test_stream_release_of_pending_ticket_is_refused(pool):
             tr.release(t)
         assert e.value.code == capi.TPC_ERR_INVALID
         assert _drain(tr, [t])[t] is not None
+
+
+@pytest.mark.parametrize("cap", [0, 1])
+def test_batches_respect_the_cluster_limit(cap):
+    """Requests queued behind a running batch join the next one up to the
+    event and cluster limits: with room for one event's clusters every
+    later request runs alone; without a cluster limit they run together.
+    Results are unchanged either way."""
+    evs = [S.central_event(seed=70 + i, scale=0.5) for i in range(4)]
+    limit = int(max(e.n for e in evs) * 1.5) if cap else 0
+    with Tracker(XR) as alone:
+        ref = [alone.track(e.clusters, e.row_counts, 1) for e in evs]
+    pinned = [torch.from_numpy(e.clusters).pin_memory() for e in evs]  # fast submits: no copy
+    with Tracker(XR) as tr:
+        tr.stream_configure(arena_bytes=4 << 30, max_batch_events=8, max_inflight=1,
+                            max_batch_clusters=limit, no_copy=True)
+        tickets = [tr.submit(c, e.row_counts, 1) for c, e in zip(pinned, evs)]
+        assert all(t is not None for t in tickets)
+        got = _drain(tr, tickets)
+        st = tr.stream_stats()
+    for t, r in zip(tickets, ref):
+        _same(got[t], r)
+    if cap:
+        assert st["batches"] == 4 and st["max_batch_events"] == 1
+    else:  # the three queued behind the first run together (unless it ended first)
+        assert st["batches"] < 4 and st["max_batch_events"] >= 2
+
+
+def test_cluster_limit_is_validated():
+    with Tracker(XR) as tr:
+        with pytest.raises(TrackerError):
+            tr.stream_configure(max_batch_clusters=-1)
