@@ -150,6 +150,12 @@ typedef struct {
     float t0_radius;         /* a track joins a collision within this (1 cm)    */
     int t0_window;           /* peak suppression half-width in bins (8)         */
     int t0_n_min;            /* candidates within +-2 bins of a peak (8)        */
+    /* measurement */
+    int count_work;          /* 1: the batched tracklet constructor also counts
+                                its row steps, bin-table rows and candidate
+                                clusters per tracklet (TPC_DUMP_TRACKLET_WORK);
+                                0 (default): it does not spend the
+                                instructions                                   */
 } tpc_params;
 
 /* A selected track: the best tracklet instance (Sec. 2 step 2), with the
@@ -394,7 +400,8 @@ int tpc_stream_get_stats(const tpc_tracker* tr, tpc_stream_stats* stats);
 #define TPC_DUMP_TRACKLETS 3
 #define TPC_DUMP_TRACKLET_N 4
 #define TPC_DUMP_TRACKLET_HITS 5
-#define TPC_DUMP_TRACKLET_WORK 6
+#define TPC_DUMP_TRACKLET_WORK 6  /* needs params.count_work = 1 in the batched
+                                     form (the plain per-sector form always counts) */
 int tpc_debug_dump(tpc_tracker* tr, int what, void* dst, int64_t cap, int64_t* n_items);
 
 /* Device time of each stage of the last call, in milliseconds, measured

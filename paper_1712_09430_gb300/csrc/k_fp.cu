@@ -341,7 +341,7 @@ __device__ __forceinline__ bool outside(const State& st, float X, const KConst& 
 // a group share the candidate scan (lane gl takes every G-th candidate) and
 // reduce the best (d2, id) with warp shuffles; every lane of the group
 // returns the same binned index (or -1).
-template <int G>
+template <int G, bool CW>
 __device__ __forceinline__ int search_row(const State& st, const RowGrid& g, float y0, float z0,
                                           const KConst& k, const DevPtrs& p, int gl, unsigned gmask,
                                           int4& work, float2& found)
@@ -365,8 +365,10 @@ __device__ __forceinline__ int search_row(const State& st, const RowGrid& g, flo
     unsigned bid = 0;
     bool have_bid = false;  // the best id is read only when a tie needs it
     float bd2 = __int_as_float(0x7f800000);  // +inf: the first candidate in the window wins
-    work.x += 1;
-    work.y += bz1 - bz0 + 1;
+    if (CW) {  // work counts of the byte model (params.count_work only)
+        work.x += 1;
+        work.y += bz1 - bz0 + 1;
+    }
     // One flat loop over the candidates of the first two z rows of the window
     // (their bin-table reads go out together), so that lanes with different
     // numbers of z rows and candidates diverge as little as possible; a
@@ -379,7 +381,7 @@ __device__ __forceinline__ int search_row(const State& st, const RowGrid& g, flo
         jb1 = __ldg(rb + (bz0 + 1) * ny + (by1 - by0) + 1);
     }
     const int na = ja1 - ja0, ntot = na + (jb1 - jb0);
-    work.z += ntot;
+    if (CW) work.z += ntot;
     // one candidate: the window test and the distance, then a branch taken
     // only for an improvement or a tie inside the window
     auto consider = [&](int j, const float2 c) {
@@ -423,7 +425,7 @@ __device__ __forceinline__ int search_row(const State& st, const RowGrid& g, flo
     }
     for (int bz = bz0 + 2; bz <= bz1; bz++) {
         const int j0 = __ldg(rb + bz * ny), j1 = __ldg(rb + bz * ny + (by1 - by0) + 1);
-        work.z += j1 - j0;
+        if (CW) work.z += j1 - j0;
         for (int j = j0 + gl; j < j1; j += G) consider(j, __ldg(p.hyz + j));
     }
     if (G > 1) {
@@ -503,11 +505,13 @@ __device__ __forceinline__ void store_state(float* sp, const State& s, float chi
     sp[15] = chi2;
 }
 
+template <bool CW>
 __device__ __forceinline__ void lane_finish(Lane& L, const KConst& k, const DevPtrs& p, bool writer);
 
 // End of Phase 1 (the search ran out, a step failed, or the rows ended):
 // Phase 2 starts from the outermost filtered cluster with a fresh covariance,
 // or the tracklet finishes without clusters.  Returns false when finished.
+template <bool CW>
 __device__ __forceinline__ bool lane_end_phase1(Lane& L, const KConst& k, const DevPtrs& p, bool writer)
 {
     if (L.have) {
@@ -529,13 +533,14 @@ __device__ __forceinline__ bool lane_end_phase1(Lane& L, const KConst& k, const 
         L.miss = 0;
         return true;
     }
-    lane_finish(L, k, p, writer);
+    lane_finish<CW>(L, k, p, writer);
     return false;
 }
 
 // The seed chain was filtered by k_seeds (Phase 1 through the chain): start
 // at the first row after it, in Phase 1, or in Phase 2 when the chain ended
 // Phase 1 already.
+template <bool CW>
 __device__ __forceinline__ void lane_init(Lane& L, int t, const KConst& k, const float* xs,
                                           const DevPtrs& p, bool writer)
 {
@@ -560,12 +565,13 @@ __device__ __forceinline__ void lane_init(Lane& L, int t, const KConst& k, const
     L.have = L.r_out >= 0;
     L.miss = 0;
     L.n = 0;
-    L.work = make_int4(0, 0, 0, info.z);
+    if (CW) L.work = make_int4(0, 0, 0, info.z);
     const bool failed = (info.w >> 16) & 1;
-    if ((failed || L.r >= NR) && !lane_end_phase1(L, k, p, writer)) return;
+    if ((failed || L.r >= NR) && !lane_end_phase1<CW>(L, k, p, writer)) return;
     L.g = p.grid[L.ubase + L.r];
 }
 
+template <bool CW>
 __device__ __forceinline__ void lane_finish(Lane& L, const KConst& k, const DevPtrs& p, bool writer)
 {
     if (writer) {
@@ -573,7 +579,7 @@ __device__ __forceinline__ void lane_finish(Lane& L, const KConst& k, const DevP
         // keep the row data of the units in flight in L2
         const int t = L.t;
         __stcs(p.tl_n + t, L.n);
-        __stcs(p.tl_work + t, L.work);
+        if (CW) __stcs(p.tl_work + t, L.work);
         float4* f4 = reinterpret_cast<float4*>(p.tl_f + (size_t)t * kTlFloats);
         if (L.n > 0) {
             const float* sp = L.sp;
@@ -589,7 +595,7 @@ __device__ __forceinline__ void lane_finish(Lane& L, const KConst& k, const DevP
     L.t = -1;
 }
 
-template <int G>
+template <int G, bool CW>
 __device__ __forceinline__ void lane_step(Lane& L, const KConst& k, const float* xs,
                                           const DevPtrs& p, int gl, unsigned gmask)
 {
@@ -599,7 +605,7 @@ __device__ __forceinline__ void lane_step(Lane& L, const KConst& k, const float*
     const bool ok = propagate(pr, X, k.kB, k.s_max) && !outside(pr, X, k);
     int j = -1;
     float2 c = make_float2(0.0f, 0.0f);
-    if (ok) j = search_row<G>(pr, L.g, -(X * k.tan_h + k.y_margin), L.z0, k, p, gl, gmask, L.work, c);
+    if (ok) j = search_row<G, CW>(pr, L.g, -(X * k.tan_h + k.y_margin), L.z0, k, p, gl, gmask, L.work, c);
     bool end_phase = !ok;
     if (j >= 0) {
         float chi2 = L.sp[15];
@@ -622,10 +628,10 @@ __device__ __forceinline__ void lane_step(Lane& L, const KConst& k, const float*
     }
     if (end_phase) {
         if (L.phase == 2) {
-            lane_finish(L, k, p, gl == 0);
+            lane_finish<CW>(L, k, p, gl == 0);
             return;
         }
-        if (!lane_end_phase1(L, k, p, gl == 0)) return;
+        if (!lane_end_phase1<CW>(L, k, p, gl == 0)) return;
     }
     L.g = p.grid[L.ubase + L.r];  // consumed by the next step; the load overlaps the loop
 }
@@ -636,7 +642,7 @@ __device__ __forceinline__ void lane_step(Lane& L, const KConst& k, const float*
 // a global counter, with one warp-aggregated atomic per refill.
 constexpr int kTrackletCtasPerSm = 3;  // 256 threads each: 24 warps per SM, <= 85 registers
 
-template <int G>
+template <int G, bool CW>
 __global__ void __launch_bounds__(kTlThreads, kTrackletCtasPerSm)
     k_tracklets_sched(KConst k, const float* __restrict__ row_x, DevPtrs p, int by_row)
 {
@@ -669,12 +675,12 @@ __global__ void __launch_bounds__(kTlThreads, kTrackletCtasPerSm)
             int i = base + __popc(need & ((1u << gbase) - 1u));
             const bool mine = (need >> gbase) & 1u;
             if (mine) {
-                if (i < T) lane_init(L, by_row ? p.sched[i] : i, k, xs, p, gl == 0);
+                if (i < T) lane_init<CW>(L, by_row ? p.sched[i] : i, k, xs, p, gl == 0);
                 else done = true;
             }
         }
         if (__all_sync(FULL, done)) break;
-        if (L.t >= 0) lane_step<G>(L, k, xs, p, gl, gmask);
+        if (L.t >= 0) lane_step<G, CW>(L, k, xs, p, gl, gmask);
     }
 }
 
@@ -693,8 +699,8 @@ __global__ void __launch_bounds__(kTlThreads, 3) k_tracklets_plain(KConst k, con
     for (int t = t0 + blockIdx.x * blockDim.x + threadIdx.x; t < t1; t += gridDim.x * blockDim.x) {
         Lane L;
         L.sp = st_sh;
-        lane_init(L, t, k, xs, p, true);
-        while (L.t >= 0) lane_step<1>(L, k, xs, p, 0, self);
+        lane_init<true>(L, t, k, xs, p, true);
+        while (L.t >= 0) lane_step<1, true>(L, k, xs, p, 0, self);
     }
 }
 
@@ -788,21 +794,27 @@ cudaError_t launch_neighbours(const KConst& k, const float* row_x_dev, const Dev
 }
 
 cudaError_t launch_tracklets(const KConst& k, const float* row_x_dev, const DevPtrs& p, int n_sm,
-                             int lanes_per_tracklet, int schedule, int u0, int u1, cudaStream_t s)
+                             int lanes_per_tracklet, int schedule, int u0, int u1, bool count_work,
+                             cudaStream_t s)
 {
     if (u0 >= 0) {
         k_tracklets_plain<<<n_sm * 2, kTlThreads, 0, s>>>(k, row_x_dev, p, u0, u1);
         return cudaGetLastError();
     }
     const int grid = n_sm * kTrackletCtasPerSm;  // one wave of resident CTAs
+    // the work counts of the byte model are compiled in only when asked for
+#define TPC_TL_LAUNCH(G)                                                                         \
+    (count_work ? (k_tracklets_sched<G, true><<<grid, kTlThreads, 0, s>>>(k, row_x_dev, p, schedule)) \
+                : (k_tracklets_sched<G, false><<<grid, kTlThreads, 0, s>>>(k, row_x_dev, p, schedule)))
     switch (lanes_per_tracklet) {
-        case 1: k_tracklets_sched<1><<<grid, kTlThreads, 0, s>>>(k, row_x_dev, p, schedule); break;
-        case 2: k_tracklets_sched<2><<<grid, kTlThreads, 0, s>>>(k, row_x_dev, p, schedule); break;
-        case 4: k_tracklets_sched<4><<<grid, kTlThreads, 0, s>>>(k, row_x_dev, p, schedule); break;
-        case 8: k_tracklets_sched<8><<<grid, kTlThreads, 0, s>>>(k, row_x_dev, p, schedule); break;
-        case 16: k_tracklets_sched<16><<<grid, kTlThreads, 0, s>>>(k, row_x_dev, p, schedule); break;
-        default: k_tracklets_sched<32><<<grid, kTlThreads, 0, s>>>(k, row_x_dev, p, schedule); break;
+        case 1: TPC_TL_LAUNCH(1); break;
+        case 2: TPC_TL_LAUNCH(2); break;
+        case 4: TPC_TL_LAUNCH(4); break;
+        case 8: TPC_TL_LAUNCH(8); break;
+        case 16: TPC_TL_LAUNCH(16); break;
+        default: TPC_TL_LAUNCH(32); break;
     }
+#undef TPC_TL_LAUNCH
     return cudaGetLastError();
 }
 

@@ -269,7 +269,8 @@ cudaError_t launch_dump_tl_work(const tpc::DevPtrs& p, int T, int* dst, cudaStre
                                   int n_units, cudaStream_t s);                                   \
     cudaError_t launch_tracklets(const tpc::KConst& k, const float* row_x_dev,                    \
                                  const tpc::DevPtrs& p, int n_sm, int lanes_per_tracklet,         \
-                                 int schedule, int t_first_unit, int t_last_unit, cudaStream_t s); \
+                                 int schedule, int t_first_unit, int t_last_unit, bool count_work, \
+                                 cudaStream_t s);                                                 \
     cudaError_t launch_seeds(const tpc::KConst& k, const float* row_x_dev, const tpc::DevPtrs& p,   \
                              int n_sm, int u0, int u1, cudaStream_t s);                             \
     cudaError_t launch_refit(const tpc::KConst& k, const tpc::DevPtrs& p, int n_sm, cudaStream_t s); \

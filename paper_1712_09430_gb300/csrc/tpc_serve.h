@@ -38,6 +38,7 @@ struct tpc_tracker {
     tpc::DevPtrs cur{};
     BatchShape cur_shape{};
     bool has_result = false;
+    bool last_counted = false;     // the last call's constructor counted its work
     int last_T = 0, last_M = 0, last_MH = 0;
     cudaStream_t last_stream = nullptr;
     int* counters_host = nullptr;  // pinned

@@ -110,6 +110,7 @@ static const char* check_params(const tpc_params& P)
     if (!(P.merge_chi2 > 0) || !(P.merge_gap > 0) || !(P.merge_overlap >= 0) || !(P.merge_window > 0))
         return "merge cuts must be positive";
     if (P.t0 != 0 && P.t0 != 1) return "t0 must be 0 or 1";
+    if (P.count_work != 0 && P.count_work != 1) return "count_work must be 0 or 1";
     if (P.t0 && !P.refit) return "t0 needs refit = 1 (it extrapolates refitted states)";
     if (!(P.t0_y_cut > 0) || !(P.t0_bin >= 0.01f) || !(P.t0_radius > 0) || P.t0_window < 0 || P.t0_n_min < 1)
         return "t0 parameters";
@@ -160,6 +161,7 @@ extern "C" void tpc_params_default(tpc_params* p)
     p->t0_radius = 1.0f;
     p->t0_window = 8;
     p->t0_n_min = 8;
+    p->count_work = 0;
 }
 
 extern "C" int tpc_tracker_create(const tpc_geometry* g, double bz, const tpc_params* params,
@@ -481,8 +483,9 @@ int tpc_enqueue(tpc_tracker* tr, const DevPtrs& p, const BatchShape& sh, cudaStr
     };
     auto tl = [&](int u0, int u1) {
         const int lpt = 32 / P.tracklets_per_warp;
-        return exact ? tpc_exact::launch_tracklets(k, xd, p, tr->n_sm, lpt, P.schedule, u0, u1, s)
-                     : tpc_fast::launch_tracklets(k, xd, p, tr->n_sm, lpt, P.schedule, u0, u1, s);
+        const bool cw = P.count_work != 0;
+        return exact ? tpc_exact::launch_tracklets(k, xd, p, tr->n_sm, lpt, P.schedule, u0, u1, cw, s)
+                     : tpc_fast::launch_tracklets(k, xd, p, tr->n_sm, lpt, P.schedule, u0, u1, cw, s);
     };
     const int th = P.threads_per_row;
     if (with_events) TPC_CUDA(cudaEventRecord(tr->ev[0], s));
@@ -549,8 +552,8 @@ int tpc_enqueue(tpc_tracker* tr, const DevPtrs& p, const BatchShape& sh, cudaStr
             TPC_CUDA(tpc_int::launch_start_write(k, p, th, u, 1, q));
             TPC_CUDA(seeds(u, u + 1, q));
             const int lpt = 32 / P.tracklets_per_warp;
-            TPC_CUDA(exact ? tpc_exact::launch_tracklets(k, xd, p, tr->n_sm, lpt, P.schedule, u, u + 1, q)
-                           : tpc_fast::launch_tracklets(k, xd, p, tr->n_sm, lpt, P.schedule, u, u + 1, q));
+            TPC_CUDA(exact ? tpc_exact::launch_tracklets(k, xd, p, tr->n_sm, lpt, P.schedule, u, u + 1, true, q)
+                           : tpc_fast::launch_tracklets(k, xd, p, tr->n_sm, lpt, P.schedule, u, u + 1, true, q));
             TPC_CUDA(tpc_int::launch_select(k, p, tr->n_sm, u, u + 1, true, q));
         }
         rc = join();
@@ -592,15 +595,15 @@ int tpc_enqueue(tpc_tracker* tr, const DevPtrs& p, const BatchShape& sh, cudaStr
 
 static std::string graph_key_of(const tpc_tracker* tr, const BatchShape& sh, const DevPtrs& p)
 {
-    // every quantity a launch configuration (grid, shared memory, chunks) is
-    // derived from
+    // every quantity a launch configuration (grid, shared memory, chunks,
+    // kernel variant) is derived from
     char b[320];
-    std::snprintf(b, sizeof b, "%d/%d/%d/%d/%d/%d/%d/%d/%p/%p/%d/%d/%d/%d/%d/%g/%d", sh.N, sh.R, sh.n_units,
-                  sh.max_row, sh.max3, sh.max_unit, sh.max_slots, sh.max_slots3,
+    std::snprintf(b, sizeof b, "%d/%d/%d/%d/%d/%d/%d/%d/%p/%p/%d/%d/%d/%d/%d/%g/%d/%d", sh.N, sh.R,
+                  sh.n_units, sh.max_row, sh.max3, sh.max_unit, sh.max_slots, sh.max_slots3,
                   (const void*)p.clusters, (const void*)p.counters,
                   tr->params.exact_fp32, tr->params.threads_per_row, tr->params.tracklets_per_warp,
                   tr->params.plain_per_sector, tr->params.schedule, (double)tr->params.bin_target,
-                  tr->params.n_queues);
+                  tr->params.n_queues, tr->params.count_work);
     return std::string(b);
 }
 
@@ -727,6 +730,7 @@ extern "C" int tpc_track_sectors(tpc_tracker* tr, const tpc_cluster* clusters, c
     tr->cur = p;
     tr->cur_shape = sh;
     tr->has_result = false;
+    tr->last_counted = tr->params.count_work != 0 || tr->params.plain_per_sector != 0;
     rc = tpc_run_stages(tr, p, sh, s);
     if (rc != TPC_OK) return rc;
     rc = finish_counters(tr, s);
@@ -775,7 +779,12 @@ extern "C" int tpc_debug_dump(tpc_tracker* tr, int what, void* dst, int64_t cap,
         case TPC_DUMP_TRACKLETS: *n_items = T; bytes = (size_t)T * kTlFloats * 4; break;
         case TPC_DUMP_TRACKLET_N: *n_items = T; bytes = (size_t)T * 8; break;
         case TPC_DUMP_TRACKLET_HITS: *n_items = T; bytes = (size_t)T * NR * 4; break;
-        case TPC_DUMP_TRACKLET_WORK: *n_items = T; bytes = (size_t)T * 16; break;
+        case TPC_DUMP_TRACKLET_WORK:
+            if (!tr->last_counted)
+                return tr->fail(TPC_ERR_INVALID, "work counts need params.count_work = 1 in the call");
+            *n_items = T;
+            bytes = (size_t)T * 16;
+            break;
         default: return tr->fail(TPC_ERR_INVALID, "unknown dump");
     }
     if ((int64_t)bytes > cap) return tr->fail(TPC_ERR_OUTPUT_TRUNCATED, "dump buffer too small");

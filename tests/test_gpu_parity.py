@@ -308,6 +308,27 @@ def test_full_size_time_frame_exact():
     assert_exact_equal(g, o)
 
 
+def test_work_counts_only_on_request(events):
+    """The constructor's work counts (the byte model of the roofline) are
+    compiled in only with params.count_work = 1; counting does not change
+    the results, and the counts are consistent with the tracklets."""
+    ev = events["c3s"]
+    with Tracker(XR, exact_fp32=1, use_graph=1) as tr:
+        a = tr.track(ev.clusters, ev.row_counts, 1)
+        with pytest.raises(TrackerError):
+            tr.dump(capi.TPC_DUMP_TRACKLET_WORK)
+        tr.set_params(count_work=1)
+        b = tr.track(ev.clusters, ev.row_counts, 1)
+        w = tr.dump(capi.TPC_DUMP_TRACKLET_WORK)
+        n = tr.dump(capi.TPC_DUMP_TRACKLET_N)[0]
+    np.testing.assert_array_equal(a.tracks.view(np.uint8), b.tracks.view(np.uint8))
+    np.testing.assert_array_equal(a.hit_ids, b.hit_ids)
+    steps, bin_rows, cand, chain = w
+    assert len(steps) == len(n) > 0
+    assert np.all(steps >= n) and np.all(bin_rows >= steps) and np.all(chain >= 3)
+    assert cand.sum() >= n.sum()
+
+
 def test_autotune_keeps_results_and_caches(events, tmp_path):
     from paper_1712_09430_gb300 import autotune
     ev = events["c3s"]
