@@ -126,6 +126,68 @@ def test_production_vs_fp64(events):
     assert n_cmp >= 0.9 * len(g["tracks"])
 
 
+def test_full_size_bench_configuration_sampled_vs_fp64():
+    """The configuration the benchmark times: eight full central events in one
+    call (16.4 M clusters), production build, graph replay, the default
+    (block) schedule.  The FP64 oracle tracks a sample of 24 of the 288
+    (event, sector) units, each unit as an event of its own (units are
+    independent); the GPU batch's tracks of those units reach the oracle's
+    QA rates within 0.2 pp, and tracks with identical cluster lists agree in
+    their parameters within 1e-4 relative + 1e-3 absolute."""
+    evs = [S.central_event(seed=3 + i) for i in range(8)]
+    cl, rc = S.concat_events(evs)
+    lab = _labels_batch(evs)
+    with Tracker(XR, use_graph=1, exact_fp32=0) as tr:
+        tr.track(cl, rc, 8)
+        r = tr.track(cl, rc, 8)   # a graph replay
+        gstart = tr.dump(capi.TPC_DUMP_STARTS)
+    units = np.sort(np.random.default_rng(11).choice(8 * 36, 24, replace=False))
+    ucnt = rc.reshape(-1, 159)
+    uoff = np.r_[0, np.cumsum(ucnt.sum(1))]
+    # the sample as a batch of one-unit events
+    parts, rcs, labs, base = [], [], [], {}
+    pos = 0
+    for k, u in enumerate(units):
+        parts.append(cl[uoff[u]:uoff[u + 1]])
+        labs.append(np.where(lab[uoff[u]:uoff[u + 1]] >= 0, lab[uoff[u]:uoff[u + 1]] + k * 10_000_000, -1))
+        r1 = np.zeros(36 * 159, np.int32)
+        r1[(u % 36) * 159:(u % 36 + 1) * 159] = ucnt[u]
+        rcs.append(r1)
+        base[int(u)] = (k, pos - uoff[u])   # sample event, position shift
+        pos += len(parts[-1])
+    cl_s, rc_s, lab_s = np.concatenate(parts), np.concatenate(rcs), np.concatenate(labs)
+    o = oracle_run(cl_s, rc_s, len(units), mode="f64")
+    # the GPU tracks of the sampled units, in the sample's numbering
+    sel = [m for m, t in enumerate(r.tracks) if int(t["event"]) * 36 + int(t["sector"]) in base]
+    g_off, g_hits, g_keys = [0], [], []
+    for m in sel:
+        t = r.tracks[m]
+        _, shift = base[int(t["event"]) * 36 + int(t["sector"])]
+        h = r.hits_of(m) + shift
+        g_hits.append(h)
+        g_off.append(g_off[-1] + len(h))
+        g_keys.append((int(gstart[t["tracklet"]]) + shift, tuple(h.tolist())))
+    g_hits = np.concatenate(g_hits)
+    assert len(sel) > 2000
+    qg = qa.qa(lab_s, rc_s, np.array(g_off), g_hits)
+    qo = qa.qa(lab_s, rc_s, o["trk_hit_off"], o["trk_hits"])
+    for key in ("eff", "clone", "fake"):
+        assert abs(qg[key] - qo[key]) <= 0.002, (key, qg[key], qo[key])
+    want = {}
+    for m, t in enumerate(o["trk_t"]):
+        h = o["trk_hits"][o["trk_hit_off"][m]:o["trk_hit_off"][m + 1]]
+        want[(int(o["start"][t]), tuple(h.tolist()))] = o["tl_f"][t][0:6]
+    n_cmp = 0
+    for m, key in zip(sel, g_keys):
+        if key not in want:
+            continue
+        t = r.tracks[m]
+        got = np.array([t["x"], *t["p"]], np.float64)
+        assert np.all(np.abs(got - want[key]) <= 1e-3 + 1e-4 * np.abs(want[key])), (got, want[key])
+        n_cmp += 1
+    assert n_cmp >= 0.9 * len(sel)
+
+
 # ------------------------------------------------------------------ edges
 
 def test_empty_inputs():
