@@ -16,12 +16,22 @@ e2e        the same metric through the C ABI with pinned HOST buffers: H2D of
            batch's copies overlap the other's kernels (e2e_sync: the
            synchronous call, copies and kernels in turn)
 roofline   the dominant kernel (tracklet constructor) against the measured HBM
-           copy bandwidth
-cpu_baseline  the FP64 CPU oracle on the host cores, bounded sample
+           copy bandwidth; its algorithmic bytes are counted by the kernel in
+           one extra untimed call (params.count_work)
+cpu_baseline  the FP64 CPU oracle on the host cores, bounded sample (and the
+           FP32_EXACT mode on all cores)
+plain_per_sector, multi_queue_per_sector
+           the same batch with one launch per (event, sector) per stage, on one
+           stream and round-robin over 8 streams (Sec. 3, Sec. 3.1)
+batch_sizes  the batched step at 1 and 32 central events per call
+stream     min-bias events (Poisson arrivals at 1, 3, 5 kHz) through the
+           serving API: p50/p99 latency from arrival to the result in hand
+stream_central  central events through the serving API at 250, 500, 1000 Hz
 refit      the final refit and the track merging on the same batch (Sec. 2
            Phase II): device time, tracks/s, FP32 ALU roofline of the refit
 time_frame a continuous-readout time frame (Sec. 3.3): overlaid shifted
-           collisions, the whole chain with the per-collision offsets
+           collisions, the whole chain with the per-collision offsets; and
+           five uneven time-frame slices (0.9-8.5 M clusters) in one launch
 --impl reference  times the CPU oracle as the reference arm (same metric)
 
 Multi-GPU: events shard across ranks with no collective (weak scaling), one
