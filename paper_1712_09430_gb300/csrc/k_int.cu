@@ -258,7 +258,7 @@ __global__ void k_clean(KConst k, DevPtrs p, int rr0, int rows)
 // schedule order: units in blocks of Bk (all units when Bk is 0), and inside
 // a block (row, unit), so long expected tracks (low start rows) come first
 // in each block.  Multi-CTA: each CTA scans kScanTile rows of both orders; a
-// one-CTA pass scans the tile sums; k_start_write adds the tile prefix.
+// one-CTA pass scans the tile sums; k_start_final adds the tile prefixes.
 // sched_row: the row (unit * NR + row) at schedule position j;
 // sched_pos: its inverse.
 __device__ __forceinline__ int sched_row(int j, int U, int NR, int Bk)
@@ -437,7 +437,8 @@ __global__ void k_owner(KConst k, DevPtrs p, int u0, int u1)
 // Ownership of one unit's clusters in shared memory: a CTA per (unit, chunk)
 // applies atomicMax in shared memory to the clusters of its chunk, then
 // writes the chunk's keys out coalesced.  Ownership never crosses units, so
-// no global atomics are needed.  The chunks of a unit hold equal shares of
+// the keys need no global atomics (the owned counts use one global add per
+// owned cluster).  The chunks of a unit hold equal shares of
 // its clusters (one chunk whenever the unit fits).  A warp takes 32
 // tracklets at a time: their lengths (and, with several chunks, their
 // outermost and innermost clusters) are read one per lane, so that
