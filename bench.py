@@ -392,7 +392,8 @@ def run_ours(args):
         achieved = algo["bytes"] / (stage_ms[dom] * 1e-3) / 1e9
         traffic = None
         if B == 8 and not args.exact:
-            traffic = measured_traffic(os.path.join(ROOT, "paper_1712_09430_gb300", "csrc", "k_fp.cu"),
+            csrc = os.path.join(ROOT, "paper_1712_09430_gb300", "csrc")
+            traffic = measured_traffic([os.path.join(csrc, "k_fp.cu"), os.path.join(csrc, "tpc_dev.cuh")],
                                        os.path.join(ROOT, "profiles", "k_tracklets_sched_traffic_central8.md"))
         rl = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
               "frac": achieved / hbm, "traffic": traffic, "kernel": "k_tracklets_sched",
@@ -899,13 +900,17 @@ def run_e2e_stream(tr0, cl_np, rc_np, B, N, world, args):
                    "H2D and D2H of one batch overlap the kernels of the other"}
 
 
-def measured_traffic(kernel_source, summary):
+def measured_traffic(kernel_sources, summary):
     """DRAM bytes per launch of the tracklet kernel from a committed ncu
-    summary, valid only while the kernel source is the one it was taken on
-    (its SHA-1 is recorded in the summary); None otherwise."""
+    summary, valid only while the kernel's sources are the ones it was taken
+    on (the SHA-1 of their concatenation is recorded in the summary); None
+    otherwise."""
     import hashlib
     try:
-        src = hashlib.sha1(open(kernel_source, "rb").read()).hexdigest()
+        h = hashlib.sha1()
+        for path in kernel_sources:
+            h.update(open(path, "rb").read())
+        src = h.hexdigest()
         fields = {}
         for line in open(summary):
             if ":" in line and not line.startswith("#"):

@@ -15,7 +15,7 @@
 
 namespace tpc {
 
-constexpr int kMaxBinsPerRow = 1024;   // search-grid bins in one row
+constexpr int kMaxBinsPerRow = 2048;   // search-grid bins in one row
 constexpr int kTlFloats = 16;          // x y z s t q cy[6] cz[3] chi2
 constexpr int kNumCounters = 16;
 constexpr float kCoordTol = 1e-3f;     // |x - row_x| accepted on input
