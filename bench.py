@@ -242,7 +242,7 @@ def reduce_step_ms(ms, dist, device=None):
 
 
 # Launches of our kernels per batched step: plan, grid, neighbours, clean,
-# start tiles, start top, start final, start write, chain end, tracklets,
+# start tiles, start top, start final, start write, seeds, tracklets,
 # owner, accept, scan tiles, scan top, emit.
 LAUNCHES_PER_STEP = 15
 
