@@ -29,16 +29,30 @@ def events():
         "c3s": S.central_event(seed=3, scale=0.1),
         "tf": S.time_frame(seed=4, n_coll=4, scale=0.3),
         "lowB": S.make_event(21, 300, 60, pt_mean=0.3, noise_frac=0.2, bz=0.2),
+        "negB": S.make_event(23, 300, 60, pt_mean=0.4, noise_frac=0.1, bz=-0.5),  # reversed field
     }
 
 
-@pytest.mark.parametrize("name", ["c1", "c2", "c3s", "tf", "lowB"])
+@pytest.mark.parametrize("name", ["c1", "c2", "c3s", "tf", "lowB", "negB"])
 def test_exact_parity_every_stage(events, name):
     ev = events[name]
     g = gpu_run(ev.clusters, ev.row_counts, 1, bz=ev.bz, exact_fp32=1)
     o = oracle_run(ev.clusters, ev.row_counts, 1, bz=ev.bz, mode="f32")
     assert len(o["trk_t"]) > 0
     assert_exact_equal(g, o)
+
+
+def test_exact_parity_batch_with_an_empty_event(events):
+    """An event without clusters between two others: its 36 units are empty
+    in every stage, the schedule blocks and the selection skip them."""
+    empty = np.zeros(36 * 159, np.int32)
+    evs = [events["c2"], events["c3s"]]
+    cl = np.concatenate([evs[0].clusters, evs[1].clusters])
+    rc = np.concatenate([evs[0].row_counts, empty, evs[1].row_counts])
+    g = gpu_run(cl, rc, 3, exact_fp32=1, use_graph=1)
+    o = oracle_run(cl, rc, 3, mode="f32")
+    assert_exact_equal(g, o)
+    assert not np.any(g["tracks"]["event"] == 1)
 
 
 def test_exact_parity_multi_event_batch(events):
