@@ -83,20 +83,21 @@ def test_generator_sizes():
 
 # -------------------------------------------------------------- propagation
 
-@pytest.mark.parametrize("inward", [False, True])
-def test_propagate_follows_exact_helix(inward):
+@pytest.mark.parametrize("inward,bz", [(False, BZ), (True, BZ), (False, -BZ), (True, -BZ)])
+def test_propagate_follows_exact_helix(inward, bz):
     """orc_prop: one pad-row step from the exact state at row r lands on the
-    exact crossing at the next row, outward and inward.  y and sin(phi) are
-    exact; z is exact up to the first neglected term of the arc series,
-    |t L| (5/112) u^6.  A dropped u^2 or u^4 term, or an unsigned chord,
-    exceeds that bound."""
+    exact crossing at the next row, outward and inward, in either field
+    direction.  y and sin(phi) are exact; z is exact up to the first
+    neglected term of the arc series, |t L| (5/112) u^6.  A dropped u^2 or
+    u^4 term, an unsigned chord or a wrong curvature sign exceeds that
+    bound."""
     rng = np.random.default_rng(5)
     tr = _tracks(rng, 200, vtx=20.0)
-    cr = S.crossings(tr, BZ)
+    cr = S.crossings(tr, bz)
     n_steps = 0
     u4_power = 0
     for m in range(len(tr)):
-        k = -0.00299792458 * BZ * tr.q[m] / tr.pt[m]
+        k = -0.00299792458 * bz * tr.q[m] / tr.pt[m]
         for sec in np.unique(cr["sector"][cr["track"] == m]):
             c = _rows_of_track(cr, m, sec)
             for j in range(len(c["row"]) - 1):
@@ -106,7 +107,7 @@ def test_propagate_follows_exact_helix(inward):
                 qpt = tr.q[m] / tr.pt[m]
                 v = oracle.state_vec(XR[c["row"][a]], c["y"][a], c["z"][a], c["sphi"][a],
                                      tr.tanl[m], qpt)
-                ok, w = oracle.propagate(v, XR[c["row"][b]], BZ)
+                ok, w = oracle.propagate(v, XR[c["row"][b]], bz)
                 if not ok:
                     continue
                 d = XR[c["row"][b]] - XR[c["row"][a]]

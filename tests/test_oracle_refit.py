@@ -92,17 +92,18 @@ def refit_double(st6, x, y, z, fp, mode="f64"):
 
 # ------------------------------------------------------------- propagation
 
-@pytest.mark.parametrize("inward", [False, True])
-def test_refit_propagate_follows_exact_helix(inward):
-    """orc_refit_propagate (uniform field): one pad-row step from the exact
-    state at row r lands on the generator's closed-form crossing at the next
-    row; z within the first neglected term of the arc series."""
+@pytest.mark.parametrize("inward,bz", [(False, BZ), (True, BZ), (False, -BZ), (True, -BZ)])
+def test_refit_propagate_follows_exact_helix(inward, bz):
+    """orc_refit_propagate (uniform field, either direction): one pad-row step
+    from the exact state at row r lands on the generator's closed-form
+    crossing at the next row; z within the first neglected term of the arc
+    series."""
     rng = np.random.default_rng(21)
     tr = _tracks(rng, 150, pt_lo=0.1, vtx=20.0)
-    fp = oracle.fit_params(BZ)
+    fp = oracle.fit_params(bz)
     n_steps = 0
-    for m, c in _long_segments(tr, BZ, min_rows=5):
-        k = -KAPPA * BZ * tr.q[m] / tr.pt[m]
+    for m, c in _long_segments(tr, bz, min_rows=5):
+        k = -KAPPA * bz * tr.q[m] / tr.pt[m]
         for j in range(len(c["row"]) - 1):
             a, b = (j + 1, j) if inward else (j, j + 1)
             v = oracle.fit_vec(XR[c["row"][a]], [c["y"][a], c["z"][a], c["sphi"][a], tr.tanl[m],
@@ -123,7 +124,7 @@ def test_refit_propagate_follows_exact_helix(inward):
     assert n_steps > 3000
 
 
-@pytest.mark.parametrize("bz", [0.0, 0.5])
+@pytest.mark.parametrize("bz", [0.0, 0.5, -0.5])
 def test_refit_jacobian_matches_finite_differences(bz):
     """Every entry of the transport Jacobian: with the factor S = e_k e_k^T
     (C = e_k e_k^T) the transported covariance's column k is J[:, k]; compare
