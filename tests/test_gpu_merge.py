@@ -30,6 +30,7 @@ def events():
         "lowB": S.make_event(21, 300, 60, pt_mean=0.3, noise_frac=0.2, bz=0.2),
         "lowpt": S.make_event(22, 400, 0, pt_mean=0.25, noise_frac=0.05),
         "negB": S.make_event(24, 400, 0, pt_mean=0.25, noise_frac=0.05, bz=-0.5),  # reversed field
+        "zeroB": S.make_event(25, 300, 60, pt_mean=0.5, noise_frac=0.1, bz=0.0),  # straight tracks
     }
 
 
@@ -51,7 +52,7 @@ def oracle_merge(r, clusters, bz, mode):
     return oracle.merge_tracks(unit, fit_matrix(r.fits), x_last, oracle.fit_params(bz), mode=mode)
 
 
-@pytest.mark.parametrize("name", ["c2", "c3s", "tf", "lowB", "lowpt", "negB"])
+@pytest.mark.parametrize("name", ["c2", "c3s", "tf", "lowB", "lowpt", "negB", "zeroB"])
 def test_merge_exact_parity(events, name):
     ev = events[name]
     r = gpu_merge(ev.clusters, ev.row_counts, bz=ev.bz, exact_fp32=1)
@@ -59,7 +60,7 @@ def test_merge_exact_parity(events, name):
     np.testing.assert_array_equal(r.merges["next"], nxt)
     np.testing.assert_array_equal(r.merges["chi2"].view(np.uint32),
                                   chi.astype(np.float32).view(np.uint32))
-    if name in ("c3s", "lowpt", "tf", "negB"):
+    if name in ("c3s", "lowpt", "tf", "negB", "zeroB"):
         assert (nxt >= 0).sum() > 0
 
 

@@ -30,10 +30,11 @@ def events():
         "tf": S.time_frame(seed=4, n_coll=4, scale=0.3),
         "lowB": S.make_event(21, 300, 60, pt_mean=0.3, noise_frac=0.2, bz=0.2),
         "negB": S.make_event(23, 300, 60, pt_mean=0.4, noise_frac=0.1, bz=-0.5),  # reversed field
+        "zeroB": S.make_event(25, 300, 60, pt_mean=0.5, noise_frac=0.1, bz=0.0),  # straight tracks
     }
 
 
-@pytest.mark.parametrize("name", ["c1", "c2", "c3s", "tf", "lowB", "negB"])
+@pytest.mark.parametrize("name", ["c1", "c2", "c3s", "tf", "lowB", "negB", "zeroB"])
 def test_exact_parity_every_stage(events, name):
     ev = events[name]
     g = gpu_run(ev.clusters, ev.row_counts, 1, bz=ev.bz, exact_fp32=1)

@@ -34,6 +34,7 @@ def events():
         "tf": S.time_frame(seed=4, n_coll=4, scale=0.3),
         "lowB": S.make_event(21, 300, 60, pt_mean=0.3, noise_frac=0.2, bz=0.2),
         "negB": S.make_event(23, 300, 60, pt_mean=0.4, noise_frac=0.1, bz=-0.5),
+        "zeroB": S.make_event(25, 300, 60, pt_mean=0.5, noise_frac=0.1, bz=0.0),  # straight tracks
     }
 
 
@@ -72,7 +73,7 @@ def assert_bits_equal(g, o):
     np.testing.assert_array_equal(g[:, 22:], o[:, 22:])
 
 
-@pytest.mark.parametrize("name", ["c1", "c2", "c3s", "tf", "lowB", "negB"])
+@pytest.mark.parametrize("name", ["c1", "c2", "c3s", "tf", "lowB", "negB", "zeroB"])
 def test_refit_exact_parity(events, name):
     ev = events[name]
     r, ms = gpu_fits(ev.clusters, ev.row_counts, bz=ev.bz, exact_fp32=1)

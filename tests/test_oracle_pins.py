@@ -125,6 +125,35 @@ def test_propagate_follows_exact_helix(inward, bz):
     assert u4_power > 500
 
 
+@pytest.mark.parametrize("inward", [False, True])
+def test_propagate_straight_line_at_zero_field(inward):
+    """Bz = 0 (the degenerate field of the method): a track is a straight
+    line, so one pad-row step from the exact crossing keeps sin(phi) and q/pT,
+    moves y by d tan(phi) and z by t times the chord, all exactly (up to
+    rounding) on the generator's straight-line crossings."""
+    rng = np.random.default_rng(8)
+    tr = _tracks(rng, 100, vtx=20.0)
+    cr = S.crossings(tr, 0.0)
+    n_steps = 0
+    for m in range(len(tr)):
+        for sec in np.unique(cr["sector"][cr["track"] == m]):
+            c = _rows_of_track(cr, m, sec)
+            for j in range(len(c["row"]) - 1):
+                a, b = (j + 1, j) if inward else (j, j + 1)
+                if abs(c["row"][a] - c["row"][b]) != 1:
+                    continue
+                v = oracle.state_vec(XR[c["row"][a]], c["y"][a], c["z"][a], c["sphi"][a],
+                                     tr.tanl[m], tr.q[m] / tr.pt[m])
+                ok, w = oracle.propagate(v, XR[c["row"][b]], 0.0)
+                if not ok:
+                    continue
+                assert c["sphi"][a] == c["sphi"][b] and w[3] == v[3] and w[5] == v[5]
+                assert abs(w[1] - c["y"][b]) < 1e-10
+                assert abs(w[2] - c["z"][b]) < 1e-10
+                n_steps += 1
+    assert n_steps > 2000
+
+
 def test_propagate_multi_row_and_stop():
     rng = np.random.default_rng(6)
     tr = _tracks(rng, 50, pt_lo=0.5, pt_hi=5.0)
