@@ -63,7 +63,6 @@ __global__ void k_neighbours(KConst k, const float* __restrict__ row_x, DevPtrs 
     }
     const int bo_d = p.bin_cap_off[rr - 1];
     const int n_bins3 = p.bin_cap_off[rr + 2] - bo_d;
-    const int total3 = end_u - off_d;
 
     // the pair copy starts at an even cluster (16-byte aligned) and covers an
     // even count; it may read the pad entry after the last cluster
@@ -95,6 +94,7 @@ __global__ void k_neighbours(KConst k, const float* __restrict__ row_x, DevPtrs 
     const float tt = (Xr - Xd) / (Xu - Xd);
     if (!mbar_wait_bounded(bar, 0)) {
         if (tid == 0) atomicOr(&p.counters[C_ERR], E_TIMEOUT);
+        mbar_wait_bounded(bar, 0);  // the copies in flight, before the CTA returns
         return;
     }
     const float2* recm = rec + cnt_d;

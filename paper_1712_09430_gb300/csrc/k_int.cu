@@ -161,6 +161,7 @@ __global__ void k_grid(KConst k, const float* __restrict__ row_x, DevPtrs p, int
     __syncthreads();
     if (!mbar_wait_bounded(bar, 0)) {
         if (tid == 0) flag_error(p.counters, E_TIMEOUT, rr);
+        mbar_wait_bounded(bar, 0);  // the copy in flight, before the CTA returns
         return;
     }
     const int row = rr % k.n_rows;

@@ -195,7 +195,9 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity)
     return ok != 0;
 }
 
-// Bounded wait: false after kSpinLimit polls (the caller records E_TIMEOUT).
+// Bounded wait: false after kSpinLimit polls.  The caller then records
+// E_TIMEOUT and waits once more (again bounded), so that bulk copies still in
+// flight land before the CTA returns and its shared memory is reused.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity)
 {
     for (unsigned i = 0; i < kSpinLimit; i++)
