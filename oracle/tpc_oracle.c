@@ -26,7 +26,9 @@
  *   transport      finite differences of propagate (Bz = 0: exact derivative)
  *   update         Bayesian posterior in information form (numpy.linalg)
  *   fit (P2 pass)  noise-free helices: fixed point = truth within 1e-9;
- *                  Bz = 0 z-block equals weighted least squares; chi2/ndf ~ 1
+ *                  Bz = 0: z-block equals weighted least squares, the
+ *                  y-block's fixed point is the least-squares line;
+ *                  chi2/ndf ~ 1
  *   neighbours     hand-built cases (collinear triple, exact tie, cuts) and
  *                  links == generator truth on isolated tracks
  *   cleaner        symmetry invariant + a hand-built asymmetric case
