@@ -599,9 +599,9 @@ def run_time_frame(frame, tr0, args, device):
 
 
 def run_batch_sizes(L, tr, cl_all, rc_all, args, device, sp):
-    """The batched step over other numbers of central events per call (the
-    survey's x1 and x32 beside the x8 of the headline): graph replay, inputs
-    resident, CUDA events around each call, median over the steps."""
+    """The batched step over other numbers of central events per call (one
+    and 32 events beside the eight of the headline step): graph replay,
+    inputs resident, CUDA events around each call, median over the steps."""
     import ctypes as C
     import torch
     from paper_1712_09430_gb300 import capi
