@@ -390,3 +390,41 @@ def concat_events(events):
     cl = np.concatenate([e.clusters for e in events]) if events else np.zeros((0, 4), np.float32)
     rc = np.concatenate([e.row_counts for e in events]) if events else np.zeros(0, np.int32)
     return np.ascontiguousarray(cl), np.ascontiguousarray(rc)
+
+
+def tiny_lattice_events(n_events, seed):
+    """Many tiny events for exhaustive parity: in each, one random sector gets
+    a patch of 3-30 consecutive pad rows with up to 50 clusters a row whose y
+    and z lie on a 0.05 cm lattice (|y| <= 1.5 cm, |z| in [10, 13] cm), so
+    that clusters at identical positions and exact distance ties are common,
+    plus up to three lines of one cluster per row (so that chains and
+    tracklets form).  Cluster ids are a random permutation.  Returns the batch
+    layout (clusters, row_counts [n_events * 36 * 159])."""
+    rng = np.random.default_rng(seed)
+    xr = row_x()
+    rcs, cls = [], []
+    for _ in range(n_events):
+        rc = np.zeros(N_SECTORS * N_ROWS, np.int32)
+        sec = int(rng.integers(0, N_SECTORS))
+        nr = int(rng.integers(3, 31))
+        r0 = int(rng.integers(0, N_ROWS - nr + 1))
+        n_lines = int(rng.integers(0, 4))
+        ly = rng.integers(-20, 21, n_lines) * 0.05
+        lsl = rng.integers(-2, 3, n_lines) * 0.05
+        lz = rng.integers(200, 261, n_lines) * 0.05
+        side = 1.0 if sec < N_SECTORS // 2 else -1.0
+        for j in range(nr):
+            r = r0 + j
+            k = int(rng.integers(0, 51 - 2 * n_lines)) if j % 7 else int(rng.integers(0, 6))
+            y = np.concatenate([rng.integers(-30, 31, k) * 0.05, ly + lsl * j])
+            z = np.concatenate([rng.integers(200, 261, k) * 0.05, lz])
+            rc[sec * N_ROWS + r] = len(y)
+            c = np.zeros((len(y), 4), np.float32)
+            c[:, 0] = xr[r]
+            c[:, 1] = y
+            c[:, 2] = side * z
+            cls.append(c)
+        rcs.append(rc)
+    cl = np.concatenate(cls) if cls else np.zeros((0, 4), np.float32)
+    cl.view(np.uint32)[:, 3] = rng.permutation(len(cl)).astype(np.uint32)
+    return np.ascontiguousarray(cl), np.concatenate(rcs)

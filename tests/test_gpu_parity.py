@@ -205,6 +205,20 @@ def test_full_size_bench_configuration_sampled_vs_fp64():
 
 # ------------------------------------------------------------------ edges
 
+def test_tiny_lattice_events_exact():
+    """1000 tiny seeded events in one call (a patch of 3-30 rows in a random
+    sector, up to 50 clusters a row on a 0.05 cm lattice: duplicate positions
+    and exact distance ties are common): every stage equals the brute-force
+    oracle bit for bit, through the search grid at a fine and a coarse bin
+    size."""
+    cl, rc = S.tiny_lattice_events(1000, seed=12)
+    o = oracle_run(cl, rc, 1000, mode="f32")
+    assert len(o["trk_t"]) > 0
+    for bt in (0.25, 4.0):
+        g = gpu_run(cl, rc, 1000, exact_fp32=1, bin_target=bt)
+        assert_exact_equal(g, o)
+
+
 def test_empty_inputs():
     rc = np.zeros(36 * 159, np.int32)
     g = gpu_run(np.zeros((0, 4), np.float32), rc, 1, dumps=False)

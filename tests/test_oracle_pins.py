@@ -81,6 +81,25 @@ def test_generator_sizes():
     assert np.all(e.clusters[:, 0] == XR[rows].astype(np.float32))
 
 
+def test_tiny_lattice_events_carry_ties():
+    """The exhaustive parity inputs: valid layout, and rows with clusters at
+    identical positions (so that the tie rules decide links) in most events."""
+    cl, rc = S.tiny_lattice_events(200, seed=12)
+    assert rc.size == 200 * 36 * 159 and int(rc.sum()) == len(cl)
+    rows = np.repeat(np.arange(rc.size), rc)
+    assert np.all(cl[:, 0] == XR[rows % 159].astype(np.float32))
+    sec = (rows // 159) % 36
+    assert np.all((cl[:, 2] > 0) == (sec < 18))
+    assert len(np.unique(cl.view(np.uint32)[:, 3])) == len(cl)
+    dup_events = set()
+    off = np.concatenate([[0], np.cumsum(rc)])
+    for rr in np.nonzero(rc > 1)[0]:
+        yz = cl[off[rr]:off[rr + 1], 1:3]
+        if len(np.unique(yz, axis=0)) < len(yz):
+            dup_events.add(rr // (36 * 159))
+    assert len(dup_events) > 100
+
+
 # -------------------------------------------------------------- propagation
 
 @pytest.mark.parametrize("inward,bz", [(False, BZ), (True, BZ), (False, -BZ), (True, -BZ)])
