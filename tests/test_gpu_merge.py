@@ -64,6 +64,17 @@ def test_merge_exact_parity(events, name):
         assert (nxt >= 0).sum() > 0
 
 
+def test_merge_exact_parity_tiny_lattice_events():
+    """1000 tiny one-sector events in one call: links (none expected across
+    these short patches) and their chi2 equal the oracle's."""
+    cl, rc = S.tiny_lattice_events(1000, seed=13)
+    r = gpu_merge(cl, rc, n_events=1000, exact_fp32=1)
+    nxt, chi = oracle_merge(r, cl, 0.5, "f32")
+    np.testing.assert_array_equal(r.merges["next"], nxt)
+    np.testing.assert_array_equal(r.merges["chi2"].view(np.uint32),
+                                  chi.astype(np.float32).view(np.uint32))
+
+
 def test_merge_links_mostly_join_one_mc_track(events):
     """Quality (not parity): the segments a link joins mostly come from the
     same generated track, and a good share of tracks crossing a sector

@@ -84,6 +84,15 @@ def test_refit_exact_parity(events, name):
     assert ms[6] > 0.0
 
 
+def test_refit_exact_parity_tiny_lattice_events():
+    """1000 tiny events in one call (short tracks of 10-30 clusters on a
+    0.05 cm lattice): every fit equals the oracle's bit for bit."""
+    cl, rc = S.tiny_lattice_events(1000, seed=13)
+    r, _ = gpu_fits(cl, rc, n_events=1000, exact_fp32=1)
+    assert len(r.tracks) > 0
+    assert_bits_equal(fit_matrix(r.fits), oracle_fits(r, cl, 0.5, mode="f32"))
+
+
 def test_refit_exact_parity_polynomial_field(events):
     ev = events["c3s"]
     r, _ = gpu_fits(ev.clusters, ev.row_counts, bz=ev.bz, exact_fp32=1, field=FIELD32)
