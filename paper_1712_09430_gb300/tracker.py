@@ -102,6 +102,7 @@ class Tracker:
         self._est_hits = 65536
 
     def close(self):
+        """Destroy the tracker (device memory, streams, graphs); idempotent."""
         if getattr(self, "h", None):
             lib().tpc_tracker_destroy(self.h)
             self.h = None
@@ -119,14 +120,18 @@ class Tracker:
         self.close()
 
     def error(self):
+        """Message of the last failed call (tpc_last_error)."""
         return lib().tpc_last_error(self.h).decode()
 
     def check(self, rc, ok=(capi.TPC_OK,)):
+        """Raise TrackerError(rc, message) unless rc is one of `ok`."""
         if rc not in ok:
             raise TrackerError(rc, self.error())
         return rc
 
     def set_params(self, **over):
+        """Change parameters by name (tpc_tracker_set_params); the others keep
+        their current values.  Invalid values raise and change nothing."""
         p = capi.tpc_params()
         C.memmove(C.byref(p), C.byref(self.params), C.sizeof(p))
         for k, v in over.items():
@@ -181,6 +186,11 @@ class Tracker:
     # ---- serving (continuous batching) -----------------------------------
     def stream_configure(self, arena_bytes=0, max_batch_events=64, max_inflight=2, no_copy=False,
                          max_batch_clusters=capi.TPC_STREAM_BATCH_CLUSTERS):
+        """Set up the request loop (tpc_stream_configure): device arena bytes
+        (0: half of the free device memory, at most 24 GiB), events and
+        clusters per batch (max_batch_clusters 0: no limit), batches in
+        flight (1..8); no_copy: submitted host buffers are read in place
+        (pinned memory the caller keeps alive until the result is polled)."""
         self.check(lib().tpc_stream_configure(self.h, int(arena_bytes), int(max_batch_events),
                                               int(max_inflight),
                                               capi.TPC_STREAM_NO_COPY if no_copy else 0,
@@ -248,9 +258,14 @@ class Tracker:
                       fits, merges, t0s)
 
     def release(self, ticket):
+        """Return a ticket's result buffers (after poll_view) to the library."""
         self.check(lib().tpc_stream_release(self.h, int(ticket)))
 
     def dump(self, what):
+        """Per-stage results of the last call (tpc_debug_dump, capi.TPC_DUMP_*)
+        as numpy arrays: links [2, N], start hits [T], tracklet states [T, 16],
+        tracklet counts and survival [2, T], work counts [4, T], tracklet
+        clusters [T, n_rows]."""
         n = C.c_int64()
         # probe the size
         rc = lib().tpc_debug_dump(self.h, what, _ptr(np.zeros(1, np.int32)), 0, C.byref(n))
