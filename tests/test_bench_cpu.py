@@ -1,6 +1,7 @@
 """Host-side rules of bench.py (no GPU): the DRAM traffic of the committed
 ncu summary is reported only for the kernel sources it was taken on, and
-ranks track disjoint events (weak scaling without a data-path collective)."""
+ranks track disjoint events (weak scaling without a data-path collective),
+and the reference arm prints the contract's line."""
 import os
 import shutil
 
@@ -36,3 +37,25 @@ def test_ranks_track_disjoint_events():
         seen |= set(s)
     assert bench.rank_seeds(0, 8) == list(range(3, 11))   # the single-GPU batch
     assert bench.reduce_step_ms(4.2, None) == 4.2
+
+
+def test_reference_arm_line(capsys, monkeypatch):
+    """--impl reference: the oracle on the GPU step's own events, one JSON
+    line with the GPU arm's metric and workload, its own cpu_baseline and an
+    e2e without host-device bytes; ranks other than 0 print nothing."""
+    import argparse
+    import json
+    args = argparse.Namespace(gpus=1, steps=1, warmup=0, batch=1)
+    monkeypatch.setenv("RANK", "1")
+    bench.run_reference(args)
+    assert capsys.readouterr().out == ""
+    monkeypatch.setenv("RANK", "0")
+    bench.run_reference(args)
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC
+    assert line["config"]["workload"] == bench.WORKLOAD
+    assert line["unit"] == "clusters/s" and line["higher_is_better"] is True and line["value"] > 0
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == line["value"] and cb["cores"] >= 1
+    assert line["e2e"] == {"value": line["value"], "unit": "clusters/s", "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
