@@ -33,12 +33,17 @@ class TrackerError(RuntimeError):
 
 
 def _set(p, k, v):
+    """Set field k of a tpc_params; a name that is not a field is an error
+    (a ctypes structure would otherwise keep it as a plain attribute)."""
+    if k not in {f for f, _ in type(p)._fields_}:
+        raise TypeError(f"unknown tracker parameter {k!r}")
     if k == "field":
         v = (C.c_float * 5)(*[float(x) for x in v])
     setattr(p, k, v)
 
 
 def default_params(**over) -> capi.tpc_params:
+    """tpc_params_default() with the named fields replaced."""
     p = capi.tpc_params()
     lib().tpc_params_default(C.byref(p))
     for k, v in over.items():

@@ -31,3 +31,11 @@ def test_failed_build_raises(monkeypatch, tmp_path):
 def test_no_device_is_an_error_not_a_cpu_run():
     with pytest.raises(TrackerError, match="TPC_ERR_DEVICE"):
         Tracker(synth.row_x(), bz=0.5)
+
+
+def test_unknown_parameter_name_is_an_error():
+    from paper_1712_09430_gb300.tracker import default_params
+    p = default_params(bin_target=0.5, field=(1e-5, 0, 0, 0, 0))
+    assert p.bin_target == 0.5 and abs(p.field[0] - 1e-5) < 1e-12
+    with pytest.raises(TypeError, match="unknown tracker parameter"):
+        default_params(bin_targt=0.5)
