@@ -106,11 +106,19 @@ def lib(mode="f64"):
     return _LIBS[mode]
 
 
+def _set_field(st, k, v):
+    """Set field k of a ctypes structure; a name that is not a field raises
+    (setattr alone would keep it as a plain attribute and change nothing)."""
+    if k not in {f for f, _ in type(st)._fields_}:
+        raise TypeError(f"unknown oracle parameter {k!r}")
+    setattr(st, k, v)
+
+
 def default_params(**over) -> Params:
     p = Params()
     lib("f64").orc_params_default(C.byref(p))
     for k, v in over.items():
-        setattr(p, k, v)
+        _set_field(p, k, v)
     return p
 
 
@@ -229,7 +237,7 @@ def fit_params(bz, field=None, params=None, **over) -> FitParams:
     for j, v in enumerate(field if field is not None else (0.0,) * 5):
         f.b[j] = v
     for k, v in over.items():
-        setattr(f, k, v)
+        _set_field(f, k, v)
     return f
 
 
