@@ -555,7 +555,22 @@ def test_start_hits_one_per_chain(central_small):
 
 
 def test_selection_single_owner_and_best_instance(central_small):
-    ev, o = central_small
+    _check_selection(*central_small)
+
+
+def test_selection_rules_on_a_denser_event():
+    """The same invariants where overlaps are common enough that some live
+    tracklets own between half and 70 % of their clusters."""
+    ev = S.central_event(seed=3, scale=0.5)
+    _check_selection(ev, oracle.run(ev.clusters, ev.row_counts, 1, ev.bz, XR))
+
+
+def _check_selection(ev, o):
+    """Sel1/Sel2 (readings): each cluster in at most one track; a track keeps
+    only clusters its tracklet owns, owns >= 10 and >= 70 % of them; every
+    cluster of a live tracklet is owned by the live tracklet with the largest
+    key (more clusters, then smaller id); every rejected live tracklet fails
+    a rule."""
     hits = o["trk_hits"]
     assert len(np.unique(hits)) == len(hits)      # each cluster in <= 1 track
     key = lambda t: (int(o["tl_n"][t]) << 32) | (0xFFFFFFFF - int(t))
@@ -586,6 +601,92 @@ def test_selection_single_owner_and_best_instance(central_small):
         th = o["tl_hits"][o["tl_hit_off"][t]:o["tl_hit_off"][t + 1]]
         owned = sum(1 for x in th if max(by_hit[int(x)], key=key) == t)
         assert owned < 10 or 10 * owned < 7 * o["tl_n"][t]
+
+
+# ------------------------------------------- hand-built straight tracks
+
+def _line_clusters(rows, sector=3, y0=2.0, b=0.05, z0=40.0, t=0.3):
+    """Exact clusters of one straight track (zero field) on the given pad
+    rows of one sector: y = y0 + b (x - X_0), z = z0 + t * path, ids 0.."""
+    rows = np.asarray(rows)
+    x = XR[rows].astype(np.float64)
+    y = y0 + b * (x - XR[0])
+    z = z0 + t * (x - XR[0]) * math.sqrt(1 + b * b)
+    rc = np.zeros(36 * 159, np.int32)
+    rc[sector * 159 + rows] = 1
+    cl = np.zeros((len(rows), 4), np.float32)
+    cl[:, 0] = x
+    cl[:, 1] = y
+    cl[:, 2] = z
+    cl.view(np.uint32)[:, 3] = np.arange(len(rows))
+    return cl, rc
+
+
+def test_gap_of_g_max_empty_rows_is_bridged():
+    """T6/T7: the search stops after more than g_max = 8 consecutive misses.
+    A straight track with 8 empty rows in its middle is one track of all its
+    clusters (both seed chains' tracklets cross the gap; the one with the
+    smaller id wins); with 9 empty rows it is two tracks, split at the gap."""
+    g_max = oracle.default_params().g_max
+    assert g_max == 8
+    for gap in (g_max, g_max + 1):
+        inner, outer = np.arange(20, 50), np.arange(50 + gap, 81)
+        cl, rc = _line_clusters(np.concatenate([inner, outer]))
+        o = oracle.run(cl, rc, 1, 0.0, XR)
+        tracks = sorted(sorted(o["trk_hits"][o["trk_hit_off"][m]:o["trk_hit_off"][m + 1]].tolist())
+                        for m in range(len(o["trk_t"])))
+        if gap == g_max:
+            assert tracks == [list(range(len(cl)))]
+        else:
+            assert tracks == [list(range(len(inner))), list(range(len(inner), len(cl)))]
+
+
+def test_shortest_kept_track_has_ten_clusters():
+    """T8/Sel2: a straight track on exactly 10 rows is kept with all 10
+    clusters; on 9 rows it is not."""
+    for n, kept in ((10, True), (9, False)):
+        cl, rc = _line_clusters(np.arange(30, 30 + n))
+        o = oracle.run(cl, rc, 1, 0.0, XR)
+        assert len(o["trk_t"]) == (1 if kept else 0)
+        if kept:
+            assert sorted(o["trk_hits"].tolist()) == list(range(n))
+
+
+def test_phase2_covariance_is_a_fresh_fit_of_its_clusters():
+    """T7: Phase 2 restarts from the reset covariance.  At Bz = 0 the (z, t)
+    block is linear, so its covariance at the innermost cluster is the
+    inverse information of the Phase-2 clusters alone (each sigma_z^2, the
+    reset prior on z counting as one more measurement at the outermost
+    cluster, and var_t on t); carrying Phase 1's information over would make
+    it smaller."""
+    p = oracle.default_params()
+    b = 0.05
+    rows = np.concatenate([np.arange(20, 50), np.arange(58, 81)])
+    cl, rc = _line_clusters(rows, b=b)
+    o = oracle.run(cl, rc, 1, 0.0, XR)
+    assert len(o["trk_t"]) == 1 and o["trk_n"][0] == len(rows)
+    x = XR[rows].astype(np.float64)
+    path = (x - x[0]) * math.sqrt(1 + b * b)      # signed, from the innermost cluster
+    H = np.stack([np.ones_like(path), path], axis=1)
+    info = H.T @ H / p.sigma_z ** 2
+    info += np.outer(H[-1], H[-1]) / p.sigma_z ** 2
+    info[1, 1] += 1.0 / p.var_t
+    C = np.linalg.inv(info)
+    f = o["tl_f"][o["trk_t"][0]]
+    assert f[0] == np.float32(XR[20])
+    got = np.array([f[12], f[13], f[14]])
+    want = np.array([C[0, 0], C[1, 0], C[1, 1]])
+    assert np.allclose(got, want, rtol=1e-9, atol=0), (got, want)
+
+
+def test_tracklet_clusters_ascend_by_row(central_small):
+    """T7: a tracklet's clusters are stored in ascending row order, one per
+    row."""
+    ev, o = central_small
+    rows = np.repeat(np.arange(36 * 159), ev.row_counts) % 159
+    for t in range(len(o["tl_n"])):
+        h = o["tl_hits"][o["tl_hit_off"][t]:o["tl_hit_off"][t + 1]]
+        assert np.all(np.diff(rows[h]) > 0)
 
 
 def test_isolated_tracks_links_follow_truth():
