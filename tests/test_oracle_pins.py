@@ -679,6 +679,96 @@ def test_phase2_covariance_is_a_fresh_fit_of_its_clusters():
     assert np.allclose(got, want, rtol=1e-9, atol=0), (got, want)
 
 
+def _tracklet_hits(o):
+    return [o["tl_hits"][o["tl_hit_off"][t]:o["tl_hit_off"][t + 1]].tolist() for t in range(len(o["tl_n"]))]
+
+
+@pytest.mark.parametrize("coord", [1, 2])
+def test_search_window_floor(coord):
+    """T5: the window half-width is at least w_min = 0.3 cm.  With n_sigma = 2
+    the sigma window of Phase 2 after many clusters is ~0.21 cm, so a cluster
+    0.25 cm off the line (in y, or in z) is taken only through the floor."""
+    P = oracle.default_params(n_sigma=2.0)
+    cl, rc = _line_clusters(np.arange(20, 81))
+    k = 5                                            # row 25
+    cl[k, coord] += np.float32(0.25)
+    o = oracle.run(cl, rc, 1, 0.0, XR, params=P)
+    assert len(o["trk_t"]) == 1 and k in o["trk_hits"].tolist()
+
+
+@pytest.mark.parametrize("coord", [1, 2])
+def test_search_window_ceiling(coord):
+    """T5: the window half-width is at most w_max = 3 cm.  Phase 2 restarts
+    from the reset covariance at the outermost cluster (row 80); three empty
+    rows later its sigma window is ~7 cm in y and ~14 cm in z, so a lone
+    cluster 3.5 cm off the line on row 76 is skipped only through the
+    ceiling."""
+    rows = np.concatenate([np.arange(20, 77), [80]])
+    cl, rc = _line_clusters(rows)
+    k = int(np.nonzero(rows == 76)[0][0])
+    cl[k, coord] += np.float32(3.5)
+    o = oracle.run(cl, rc, 1, 0.0, XR)
+    assert len(o["trk_t"]) == 1
+    assert sorted(o["trk_hits"].tolist()) == [i for i in range(len(rows)) if i != k]
+    assert all(k not in h for h in _tracklet_hits(o))
+
+
+def test_search_tie_goes_to_the_smaller_id():
+    """T5: of two clusters at the same distance (the same position) the one
+    with the smaller id is taken."""
+    rows = np.arange(20, 81)
+    cl, rc = _line_clusters(rows)
+    k = int(np.nonzero(rows == 50)[0][0])
+    dup = cl[k].copy()
+    dup.view(np.uint32)[3] = len(cl)                 # a larger id than every other cluster
+    cl = np.insert(cl, k + 1, dup, axis=0)
+    rc[3 * 159 + 50] += 1
+    o = oracle.run(cl, rc, 1, 0.0, XR)
+    assert len(o["trk_t"]) == 1
+    h = o["trk_hits"].tolist()
+    assert k in h and k + 1 not in h
+
+
+def test_search_distance_is_normalised_per_coordinate():
+    """T5: candidates are ranked by dy^2 / S_y + dz^2 / S_z.  After Phase 2's
+    reset and three empty rows S_z is ~4 S_y (var_t = 1, var_s = 0.25), so of
+    two lone candidates on row 76, 0.4 cm off in y and 0.5 cm off in z, the
+    z one is nearer (0.25 / 16 < 0.16 / 4); in cm it is the other way round."""
+    rows = np.concatenate([np.arange(20, 76), [76, 76], [80]])
+    cl, rc = _line_clusters(rows)
+    rc[3 * 159 + 76] = 2
+    a, b = int(np.nonzero(rows == 76)[0][0]), int(np.nonzero(rows == 76)[0][1])
+    cl[a, 1] += np.float32(0.4)
+    cl[b, 2] += np.float32(0.5)
+    o = oracle.run(cl, rc, 1, 0.0, XR)
+    took = [h for h in _tracklet_hits(o) if a in h or b in h]
+    assert took and all(b in h and a not in h for h in took)
+
+
+@pytest.mark.parametrize("beyond,kept", [(1.0, True), (3.0, False)])
+def test_sector_edge_margin(beyond, kept):
+    """T6: a prediction may lie up to y_margin = 2 cm beyond the sector edge
+    |y| = X tan 10 deg before the search stops: a straight track running 1 cm
+    beyond the edge is kept, one running 3 cm beyond it is not."""
+    rows = np.arange(20, 81)
+    cl, rc = _line_clusters(rows)
+    cl[:, 1] = (XR[rows].astype(np.float64) * math.tan(math.radians(10.0)) + beyond).astype(np.float32)
+    o = oracle.run(cl, rc, 1, 0.0, XR)
+    assert len(o["trk_t"]) == (1 if kept else 0)
+
+
+def test_phase1_misses_count_consecutive_rows():
+    """T6: the miss count restarts at every cluster found.  A straight track
+    with two gaps of 5 empty rows: the tracklet seeded on its inner part
+    (the first in canonical order) crosses both in Phase 1 (10 misses in all,
+    never more than 8 in a row) and keeps every cluster."""
+    rows = np.concatenate([np.arange(20, 51), np.arange(56, 61), np.arange(66, 81)])
+    cl, rc = _line_clusters(rows)
+    o = oracle.run(cl, rc, 1, 0.0, XR)
+    assert o["start"][0] == 1                        # the inner chain starts at row 21
+    assert o["tl_n"][0] == len(rows)
+
+
 def test_tracklet_clusters_ascend_by_row(central_small):
     """T7: a tracklet's clusters are stored in ascending row order, one per
     row."""
