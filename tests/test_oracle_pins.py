@@ -482,6 +482,43 @@ def test_neighbours_cuts():
     assert o["up_raw"][1] == 2 and o["dn_raw"][1] == 0
 
 
+def test_neighbours_where_the_row_pitch_changes():
+    """N2/N3 across the pitch change at rows 62/63/64 (X = 131.5, 135, 136):
+    the collinearity residual interpolates at tt = (X_r - X_d) / (X_u - X_d)
+    = 7/9, and each window scales with its own row distance (W_d = 5.25,
+    W_u = 1.5 cm)."""
+    # a straight line in z (dz/dx = 0.5) links with D = 0; the midpoint
+    # (tt = 1/2) would be 0.625 cm off the middle cluster
+    z = lambda x: 10.0 + 0.5 * (x - XR[62])
+    cl, rc = _hand_event([(62, 0.0, z(XR[62]), 1), (63, 0.0, z(XR[63]), 2), (64, 0.0, z(XR[64]), 3)])
+    o = oracle.run(cl, rc, 1, BZ, XR)
+    assert o["up_raw"][1] == 2 and o["dn_raw"][1] == 0
+    # an up cluster 1.6 cm away in z is outside W_u = 1.5 although the pair
+    # (D = 0.127 with a down cluster 4 cm away, inside W_d) would pass the cut
+    cl, rc = _hand_event([(62, 0.0, 6.0, 1), (63, 0.0, 10.0, 2), (64, 0.0, 11.6, 3)])
+    o = oracle.run(cl, rc, 1, BZ, XR)
+    assert o["up_raw"][1] == -1 and o["dn_raw"][1] == -1
+    cl, rc = _hand_event([(62, 0.0, 6.0, 1), (63, 0.0, 10.0, 2), (64, 0.0, 11.4, 3)])
+    o = oracle.run(cl, rc, 1, BZ, XR)
+    assert o["up_raw"][1] == 2 and o["dn_raw"][1] == 0
+
+
+def test_neighbour_window_scales_with_row_distance():
+    """N2: at the 1.5 cm pitch of the outer rows the window is 1.5 * 1.5 =
+    2.25 cm: a collinear triple with 1.8 cm steps in y links."""
+    cl, rc = _hand_event([(130, -1.8, 10.0, 1), (131, 0.0, 10.0, 2), (132, 1.8, 10.0, 3)])
+    o = oracle.run(cl, rc, 1, BZ, XR)
+    assert o["up_raw"][1] == 2 and o["dn_raw"][1] == 0
+
+
+def test_neighbour_cut_is_inclusive():
+    """N3: a pair with D exactly equal to D_max^2 = 0.25 (the middle cluster
+    0.5 cm off the line in z) is kept."""
+    cl, rc = _hand_event([(0, 0.0, 10.0, 1), (1, 0.0, 10.5, 2), (2, 0.0, 10.0, 3)])
+    o = oracle.run(cl, rc, 1, BZ, XR)
+    assert o["up_raw"][1] == 2 and o["dn_raw"][1] == 0
+
+
 def test_cleaner_asymmetric_case():
     # A (row 2, y = 0) links up to B (row 3, y = 0.3) with D = 0.15^2, but B's
     # best pair is (E above, C below) on the line y = 0.3 with D = 0, so B
