@@ -250,7 +250,9 @@ typedef struct {
 
 typedef struct tpc_tracker tpc_tracker;
 
-/* Fill p with the default readings (see tpc_params). */
+/* Fill p with the default readings of the constants the paper leaves open
+ * (Sec. 2 steps 1-2; see tpc_params) and the default execution fields.
+ * p: caller-owned, not NULL. */
 void tpc_params_default(tpc_params* p);
 
 /* Create a tracker on the current CUDA device for geometry g and field
@@ -260,13 +262,16 @@ void tpc_params_default(tpc_params* p);
 int tpc_tracker_create(const tpc_geometry* g, double bz_tesla, const tpc_params* params,
                        tpc_tracker** out);
 
-/* Destroy; in-flight stream tickets are cancelled.  NULL is a no-op. */
+/* Destroy (library bookkeeping, no passage of the paper): frees every device
+ * and pinned buffer of tr; in-flight stream tickets are cancelled.  NULL is a
+ * no-op. */
 void tpc_tracker_destroy(tpc_tracker* tr);
 
 /* Change the execution fields of the parameters (exact_fp32, bin_target,
  * threads_per_row, tracklets_per_warp, plain_per_sector, use_graph) and,
- * if given, the method constants.  Not allowed while stream tickets are in
- * flight (TPC_BUSY). */
+ * if given, the method constants (Sec. 2 readings).  params is copied.
+ * TPC_ERR_INVALID for out-of-range values (nothing changes); not allowed
+ * while stream tickets are in flight (TPC_BUSY). */
 int tpc_tracker_set_params(tpc_tracker* tr, const tpc_params* params);
 
 /* Track n_events events (Sec. 2 Phase I), synchronously.
@@ -288,7 +293,10 @@ int tpc_track_sectors(tpc_tracker* tr, const tpc_cluster* clusters, const int32_
                       int n_events, int mem_kind, tpc_output* out, void* cuda_stream);
 
 /* Copy the result of the last tpc_track_sectors call again into out (for
- * example into larger buffers after TPC_ERR_OUTPUT_TRUNCATED). */
+ * example into larger buffers after TPC_ERR_OUTPUT_TRUNCATED): the second
+ * half of the estimate-then-fetch-the-rest scheme of Sec. 3.1, without
+ * tracking again.  Same truncation rule as tpc_track_sectors;
+ * TPC_ERR_INVALID if there is no result to fetch. */
 int tpc_fetch_output(tpc_tracker* tr, tpc_output* out);
 
 /* Autotuner of the execution fields (the batched launch of Sec. 3 has no
@@ -354,12 +362,13 @@ typedef struct {
     int32_t n_hits;
 } tpc_stream_view;
 
-/* TPC_PENDING, TPC_OK (view filled; the ticket stays valid) or an error (the
- * ticket is released). */
+/* Serving (Sec. 3.2).  TPC_PENDING, TPC_OK (view filled; the ticket stays
+ * valid) or an error (the ticket is released).  view: caller-owned. */
 int tpc_stream_poll_view(tpc_tracker* tr, uint64_t ticket, tpc_stream_view* view, int timeout_us);
 
-/* Release a finished ticket (after tpc_stream_poll_view).  TPC_ERR_INVALID
- * while it is still pending, TPC_ERR_UNKNOWN_TICKET if unknown. */
+/* Serving (Sec. 3.2): release a finished ticket (after tpc_stream_poll_view),
+ * ending the validity of its view.  TPC_ERR_INVALID while it is still
+ * pending, TPC_ERR_UNKNOWN_TICKET if unknown. */
 int tpc_stream_release(tpc_tracker* tr, uint64_t ticket);
 
 /* Counters of the request loop since tpc_stream_configure (observability
@@ -377,6 +386,7 @@ typedef struct {
     double host_copy_ms;     /* host time spent copying results in polls        */
 } tpc_stream_stats;
 
+/* Fill *stats (caller-owned); zeros before tpc_stream_configure. */
 int tpc_stream_get_stats(const tpc_tracker* tr, tpc_stream_stats* stats);
 
 /* Per-stage results of the last tpc_track_sectors call, for the step-by-step
@@ -404,15 +414,18 @@ int tpc_stream_get_stats(const tpc_tracker* tr, tpc_stream_stats* stats);
                                      form (the plain per-sector form always counts) */
 int tpc_debug_dump(tpc_tracker* tr, int what, void* dst, int64_t cap, int64_t* n_items);
 
-/* Device time of each stage of the last call, in milliseconds, measured
- * with CUDA events on the launching stream: [0] grid build, [1] neighbours,
+/* Device time of each stage of the last call (the per-kernel timeline the
+ * paper shows for its own tracker, Sec. 3), in milliseconds, measured with
+ * CUDA events on the launching stream: [0] grid build, [1] neighbours,
  * [2] clean + start hits, [3] tracklet construction, [4] selection + output,
  * [5] whole call, [6] final refit and merging (0 when params.refit = 0).
  * n = entries wanted (<= 7). */
 int tpc_stage_times(tpc_tracker* tr, float* ms, int n);
 
 /* One-line description of the last error on tr (or of the last failed
- * tpc_tracker_create when tr is NULL). */
+ * tpc_tracker_create when tr is NULL); library bookkeeping, no passage of
+ * the paper.  The string belongs to the library and stays valid until the
+ * next call on tr. */
 const char* tpc_last_error(const tpc_tracker* tr);
 
 /* ---- allocation-free link finding -------------------------------------- *
