@@ -276,6 +276,15 @@ def test_candidate_geometry():
     nxt, _ = oracle.merge_tracks(np.zeros(2, np.int32), fw, np.array([120.0, 190.0]), fp,
                                  mp=oracle.merge_params(window=6.0))
     assert nxt[0] == 1
+    # the same in z
+    far_z = pb.copy()
+    far_z[1] += 5.5
+    fz = np.array([_fit_row(100.0, pa), _fit_row(xb, far_z, var=100.0)])
+    nxt, _ = oracle.merge_tracks(np.zeros(2, np.int32), fz, np.array([120.0, 190.0]), fp)
+    assert nxt[0] == -1
+    nxt, _ = oracle.merge_tracks(np.zeros(2, np.int32), fz, np.array([120.0, 190.0]), fp,
+                                 mp=oracle.merge_params(window=6.0))
+    assert nxt[0] == 1
     # a failed fit never merges
     f2 = fits.copy()
     f2[1, 23] = 1
