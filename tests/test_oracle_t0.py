@@ -137,3 +137,39 @@ def test_time_frame_collisions_recovered():
     # every collision with many primaries reconstructed is found
     big = [c for c in range(len(ev.coll_dz)) if np.sum(truth == c) > 300]
     assert found >= len(big) >= 3
+
+
+def test_assignment_tie_centre_and_range_edge():
+    """T03/T04: bin centres are -z_max + (b + 1/2) w; a candidate exactly r
+    from two collisions' centres joins the lower one; the histogram covers
+    [-z_max, z_max), so candidates at u = z_max form no collision."""
+    fp = oracle.fit_params(BZ)
+    tp = oracle.t0_params(n_min=3, window=2, radius=1.0)
+    a = [10.125] * 4                 # bin 1040, centre 10.125
+    b = [12.125] * 4                 # bin 1048, centre 12.125: a second peak (8 bins > W = 2)
+    units, fits, us = _beam_fits(a + b + [11.125])
+    out = oracle.t0_tracks(units, fits, fp, tp)
+    got = {float(u): int(k) for u, (k, _, _) in zip(us, out)}
+    assert got[10.125] == 0 and got[12.125] == 1
+    assert got[11.125] == 0          # 1.0 cm from both centres: the lower collision
+    # the range is half-open
+    units, fits, us = _beam_fits([250.0] * 4)
+    out = oracle.t0_tracks(units, fits, fp, oracle.t0_params(n_min=3))
+    assert np.all(out[:, 0] == -1)
+    units, fits, us = _beam_fits([-250.0] * 4)
+    out = oracle.t0_tracks(units, fits, fp, oracle.t0_params(n_min=3))
+    assert np.all(out[:, 0] == 0)
+
+
+def test_smoothing_spans_five_bins():
+    """T03: counts and scores are taken over b-2..b+2 with weights 1 2 3 2 1.
+    Three candidates in bin 1040 and two in bin 1042 (n_min = 5): only the
+    five-bin sum reaches n_min at bin 1040, which is the peak (score 11 against
+    10 at bin 1041), so with r = 0.3 cm the two candidates 0.5 cm above its
+    centre join no collision."""
+    fp = oracle.fit_params(BZ)
+    tp = oracle.t0_params(n_min=5, radius=0.3)
+    units, fits, us = _beam_fits([10.125] * 3 + [10.625] * 2)
+    out = oracle.t0_tracks(units, fits, fp, tp)
+    got = [(float(u), int(k)) for u, (k, _, _) in zip(us, out)]
+    assert sorted(got) == [(10.125, 0)] * 3 + [(10.625, -1)] * 2
