@@ -156,6 +156,15 @@ typedef struct {
                                 clusters per tracklet (TPC_DUMP_TRACKLET_WORK);
                                 0 (default): it does not spend the
                                 instructions                                   */
+    /* testing */
+    int debug_wait_polls;    /* 0 (default): every wait on a bulk copy gives
+                                up after a fixed bound of 2^22 polls; n > 0:
+                                the first wait of the grid and neighbour
+                                kernels gives up after n non-blocking polls,
+                                so that a test can drive a call into
+                                TPC_ERR_TIMEOUT (the copies still land before
+                                the kernel returns; the next call with 0 is
+                                unaffected).  Not for production use.          */
 } tpc_params;
 
 /* A selected track: the best tracklet instance (Sec. 2 step 2), with the
@@ -448,20 +457,31 @@ const char* tpc_last_error(const tpc_tracker* tr);
  *   d_links     DEVICE output, int32 [2][N]: up links then down links, as
  *               positions in d_clusters (-1: none)
  *   cuda_stream stream to run on (NULL: the default stream); the call waits
- *               for its own work before returning
+ *               for its own work before returning, so it must not be
+ *               called on a stream that is being captured into a graph
+ *               (TPC_ERR_INVALID, nothing enqueued)
  * Limits and errors: at most TPC_NOALLOC_MAX_CLUSTERS clusters and
  * n_sectors * n_rows <= 16384 rows; larger events return TPC_ERR_INVALID
  * before any GPU work (use tpc_track_sectors for them).  TPC_ERR_NOMEM if the
- * bin tables for this bin_target do not fit the fixed scratch,
- * TPC_ERR_INVALID for bad arguments or input (NaN, x off its row),
- * TPC_ERR_DEVICE for CUDA errors.
- * Set-up: the first call on a device looks up the device address of the
- * scratch with cudaGetSymbolAddress (that device current); make that first
- * call before any stream capture.
+ * bin tables for this bin_target do not fit the fixed scratch, or if the
+ * first call on a device finds no device memory to load the library's code
+ * and scratch there (below); TPC_ERR_INVALID for bad arguments or input
+ * (NaN, x off its row); TPC_ERR_TIMEOUT if a bounded wait ran out;
+ * TPC_ERR_DEVICE for other CUDA errors.  After an error the next call starts
+ * afresh.
+ * Set-up: every call looks up the scratch's device address on the current
+ * device with cudaGetSymbolAddress.  CUDA loads device code lazily, so the
+ * FIRST call on each device loads this library's code there, and with it
+ * the scratch array; that loading does take device memory (once, held until
+ * the process exits) and may synchronize.  Make that first call at start-up,
+ * before any stream capture: a call with an empty event (all row_counts 0,
+ * d_clusters and d_links may be NULL) loads the scratch and the kernels and
+ * does nothing else.  Later calls allocate nothing.
  * Sharing: all calls in the process use the same scratch, and each call
- * overwrites what the previous one left there.  Two calls whose GPU work
- * overlapped would race on it, so the function takes a process-wide lock
- * and holds it until its GPU work has finished. */
+ * overwrites what the previous one left there (the counters it reads are
+ * cleared by the call itself).  Two calls whose GPU work overlapped would
+ * race on it, so the function takes a process-wide lock and holds it until
+ * its GPU work has finished. */
 #define TPC_NOALLOC_MAX_CLUSTERS 65536
 #define TPC_NOALLOC_SCRATCH_BYTES (8u << 20)
 int tpc_links_noalloc(const tpc_geometry* g, const tpc_params* params,

@@ -43,6 +43,7 @@ using namespace tpc;
 // the pair with the smallest D wins, ties by smaller id_u, then id_d.
 __global__ void k_neighbours(KConst k, const float* __restrict__ row_x, DevPtrs p, int unit0)
 {
+    if (stage_aborted(p.counters)) return;  // a stage before this one failed
     extern __shared__ __align__(16) unsigned char smem[];
     const int NR = k.n_rows;
     const int u = unit0 + blockIdx.x / (NR - 2);
@@ -92,7 +93,7 @@ __global__ void k_neighbours(KConst k, const float* __restrict__ row_x, DevPtrs 
     const float Wu = k.k_win * fabsf(Xu - Xr);
     const float Wd = k.k_win * fabsf(Xd - Xr);
     const float tt = (Xr - Xd) / (Xu - Xd);
-    if (!mbar_wait_bounded(bar, 0)) {
+    if (!mbar_wait_first(bar, 0, k.wait_polls)) {
         if (tid == 0) atomicOr(&p.counters[C_ERR], E_TIMEOUT);
         mbar_wait_bounded(bar, 0);  // the copies in flight, before the CTA returns
         return;
@@ -646,6 +647,7 @@ template <int G, bool CW>
 __global__ void __launch_bounds__(kTlThreads, kTrackletCtasPerSm)
     k_tracklets_sched(KConst k, const float* __restrict__ row_x, DevPtrs p, int by_row)
 {
+    if (stage_aborted(p.counters)) return;  // a stage before this one failed
     __shared__ float xs[TPC_MAX_ROWS];
     float st_sh[16];
     for (int r = threadIdx.x; r < k.n_rows; r += blockDim.x) xs[r] = row_x[r];
@@ -690,6 +692,7 @@ __global__ void __launch_bounds__(kTlThreads, kTrackletCtasPerSm)
 __global__ void __launch_bounds__(kTlThreads, 3) k_tracklets_plain(KConst k, const float* __restrict__ row_x,
                                                                    DevPtrs p, int u0, int u1)
 {
+    if (stage_aborted(p.counters)) return;  // a stage before this one failed
     __shared__ float xs[TPC_MAX_ROWS];
     float st_sh[16];
     for (int r = threadIdx.x; r < k.n_rows; r += blockDim.x) xs[r] = row_x[r];
@@ -714,6 +717,7 @@ __global__ void __launch_bounds__(kTlThreads, 3) k_tracklets_plain(KConst k, con
 // they run here rather than in the constructor's divergent loop.
 __global__ void k_seeds(KConst k, const float* __restrict__ row_x, DevPtrs p, int u0, int u1)
 {
+    if (stage_aborted(p.counters)) return;  // a stage before this one failed
     const int t0 = p.start_off[u0 * k.n_rows], t1 = p.start_off[u1 * k.n_rows];
     for (int t = t0 + blockIdx.x * blockDim.x + threadIdx.x; t < t1; t += gridDim.x * blockDim.x) {
         const int h0 = p.start[t];
@@ -816,6 +820,12 @@ cudaError_t launch_tracklets(const KConst& k, const float* row_x_dev, const DevP
     }
 #undef TPC_TL_LAUNCH
     return cudaGetLastError();
+}
+
+cudaError_t preload_neighbours()
+{
+    cudaFuncAttributes a;
+    return cudaFuncGetAttributes(&a, k_neighbours);
 }
 
 }  // namespace TPC_FP_NS

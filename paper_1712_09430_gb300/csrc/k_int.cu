@@ -159,7 +159,7 @@ __global__ void k_grid(KConst k, const float* __restrict__ row_x, DevPtrs p, int
     }
     for (int b = tid; b <= nb; b += nt) hist[b] = 0;
     __syncthreads();
-    if (!mbar_wait_bounded(bar, 0)) {
+    if (!mbar_wait_first(bar, 0, k.wait_polls)) {
         if (tid == 0) flag_error(p.counters, E_TIMEOUT, rr);
         mbar_wait_bounded(bar, 0);  // the copy in flight, before the CTA returns
         return;
@@ -223,6 +223,7 @@ __global__ void k_grid(KConst k, const float* __restrict__ row_x, DevPtrs p, int
 // arrays; start(i) = up'[i] >= 0, dn'[i] < 0 and a chain of >= l_seed hits.
 __global__ void k_clean(KConst k, DevPtrs p, int rr0, int rows)
 {
+    if (stage_aborted(p.counters)) return;  // a stage before this one failed
     // one warp per row
     const int lane = threadIdx.x & 31;
     const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -280,6 +281,7 @@ __device__ __forceinline__ int sched_pos(int rr, int U, int NR, int Bk)
 
 __global__ void k_start_tiles(KConst k, DevPtrs p)
 {
+    if (stage_aborted(p.counters)) return;  // a stage before this one failed
     const int R = p.R, U = p.n_units, NR = k.n_rows;
     const int ntiles = (R + kScanTile - 1) / kScanTile;
     const int base = blockIdx.x * kScanTile;
@@ -307,6 +309,7 @@ __global__ void k_start_tiles(KConst k, DevPtrs p)
 
 __global__ void __launch_bounds__(1024) k_start_top(KConst k, DevPtrs p)
 {
+    if (stage_aborted(p.counters)) return;  // a stage before this one failed
     const int R = p.R;
     const int ntiles = (R + kScanTile - 1) / kScanTile;
     const int tid = threadIdx.x, nt = blockDim.x;
@@ -333,6 +336,7 @@ __global__ void __launch_bounds__(1024) k_start_top(KConst k, DevPtrs p)
 // prefixes (one thread per row).
 __global__ void k_start_final(KConst k, DevPtrs p)
 {
+    if (stage_aborted(p.counters)) return;  // a stage before this one failed
     const int ntiles = (p.R + kScanTile - 1) / kScanTile;
     for (int rr = blockIdx.x * blockDim.x + threadIdx.x; rr < p.R; rr += gridDim.x * blockDim.x) {
         const int j = sched_pos(rr, p.n_units, k.n_rows, p.sched_block);
@@ -349,6 +353,7 @@ constexpr int kStartWarpBuf = 1024;   // start hits ranked in shared memory; mor
 
 __global__ void __launch_bounds__(32 * kStartWarps) k_start_write(KConst k, DevPtrs p, int rr0, int rows)
 {
+    if (stage_aborted(p.counters)) return;  // a stage before this one failed
     __shared__ unsigned sid_sh[kStartWarps][kStartWarpBuf];
     __shared__ int sb_sh[kStartWarps][kStartWarpBuf];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -423,6 +428,7 @@ __device__ __forceinline__ unsigned tl_key(const KConst& k, const DevPtrs& p, in
 // warp per tracklet (coalesced reads of its cluster list).
 __global__ void k_owner(KConst k, DevPtrs p, int u0, int u1)
 {
+    if (stage_aborted(p.counters)) return;  // a stage before this one failed
     const int t0 = p.start_off[u0 * k.n_rows], t1 = p.start_off[u1 * k.n_rows];
     const int lane = threadIdx.x & 31;
     const int w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
@@ -453,6 +459,7 @@ constexpr int kEmitTracklets = 4;       // accepted tracklets written together
 
 __global__ void __launch_bounds__(1024) k_owner_units(KConst k, DevPtrs p, int chunks, int cap_keys)
 {
+    if (stage_aborted(p.counters)) return;  // a stage before this one failed
     extern __shared__ unsigned keys[];
     const int u = blockIdx.x / chunks, c = blockIdx.x % chunks;
     const int NR = k.n_rows;
@@ -527,6 +534,7 @@ __global__ void __launch_bounds__(1024) k_owner_units(KConst k, DevPtrs p, int c
 // coalesced reads of the owner keys); the winner is decoded from its key.
 __global__ void k_owned_count(KConst k, DevPtrs p, int rr0, int rows)
 {
+    if (stage_aborted(p.counters)) return;  // a stage before this one failed
     const int lane = threadIdx.x & 31;
     const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (w >= rows) return;
@@ -543,6 +551,7 @@ __global__ void k_owned_count(KConst k, DevPtrs p, int rr0, int rows)
 // A tracklet keeps the clusters it owns; accepted if enough remain.
 __global__ void k_accept(KConst k, DevPtrs p, int u0, int u1)
 {
+    if (stage_aborted(p.counters)) return;  // a stage before this one failed
     const int t0 = p.start_off[u0 * k.n_rows], t1 = p.start_off[u1 * k.n_rows];
     for (int t = t0 + blockIdx.x * blockDim.x + threadIdx.x; t < t1; t += gridDim.x * blockDim.x) {
         const int n = p.tl_n[t];
@@ -556,6 +565,7 @@ __global__ void k_accept(KConst k, DevPtrs p, int u0, int u1)
 // Multi-CTA exclusive scan of acc[0..T): tile sums, top scan, apply in emit.
 __global__ void k_scan_tiles(DevPtrs p)
 {
+    if (stage_aborted(p.counters)) return;  // a stage before this one failed
     const int T = p.counters[C_T];
     const int base = blockIdx.x * kScanTile;
     if (base >= T) return;
@@ -575,6 +585,7 @@ __global__ void k_scan_tiles(DevPtrs p)
 
 __global__ void __launch_bounds__(1024) k_scan_top(DevPtrs p)
 {
+    if (stage_aborted(p.counters)) return;  // a stage before this one failed
     const int T = p.counters[C_T];
     const int nblk = (T + kScanTile - 1) / kScanTile;
     const int nt = blockDim.x, tid = threadIdx.x;
@@ -602,6 +613,7 @@ __global__ void __launch_bounds__(1024) k_scan_top(DevPtrs p)
 // word by 22 lanes and the owned clusters are compacted by ballot.
 __global__ void k_emit(KConst k, DevPtrs p)
 {
+    if (stage_aborted(p.counters)) return;  // a stage before this one failed
     const int T = p.counters[C_T];
     const unsigned FULL = 0xffffffffu;
     const int NR = k.n_rows;
@@ -700,6 +712,7 @@ __global__ void k_emit(KConst k, DevPtrs p)
 // event, canonical tracklet, hit and cluster).  A warp per track.
 __global__ void k_rebase(KConst k, DevPtrs p)
 {
+    if (stage_aborted(p.counters)) return;  // a stage before this one failed
     const int M = p.counters[C_M];
     const int lane = threadIdx.x & 31;
     const int w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
@@ -726,6 +739,7 @@ __global__ void k_rebase(KConst k, DevPtrs p)
 // exclusive scan at the event's first canonical tracklet; entry E is (M, MH).
 __global__ void k_ev_first(KConst k, DevPtrs p, int E)
 {
+    if (stage_aborted(p.counters)) return;  // a stage before this one failed
     const int T = p.counters[C_T];
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e <= E; e += gridDim.x * blockDim.x) {
         const int t = p.start_off[e * k.n_sectors * k.n_rows];
@@ -737,6 +751,7 @@ __global__ void k_ev_first(KConst k, DevPtrs p, int E)
 // ------------------------------------------------------------------ dumps
 __global__ void k_dump_links(DevPtrs p, int cleaned, int* dst)
 {
+    if (stage_aborted(p.counters)) return;  // a stage before this one failed
     const int* U = cleaned ? p.up2 : p.up;
     const int* D = cleaned ? p.dn2 : p.dn;
     for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < p.N; b += gridDim.x * blockDim.x) {
@@ -749,12 +764,14 @@ __global__ void k_dump_links(DevPtrs p, int cleaned, int* dst)
 
 __global__ void k_dump_starts(DevPtrs p, int T, int* dst)
 {
+    if (stage_aborted(p.counters)) return;  // a stage before this one failed
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < T; t += gridDim.x * blockDim.x)
         dst[t] = __float_as_int(p.hits[p.start[t]].w);
 }
 
 __global__ void k_dump_tl_hits(KConst k, DevPtrs p, int T, int* dst)
 {
+    if (stage_aborted(p.counters)) return;  // a stage before this one failed
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < T; t += gridDim.x * blockDim.x) {
         int n = p.tl_n[t];
         const int* h = p.tl_hits + (size_t)t * k.n_rows;
@@ -766,6 +783,7 @@ __global__ void k_dump_tl_hits(KConst k, DevPtrs p, int T, int* dst)
 
 __global__ void k_dump_tl_work(DevPtrs p, int T, int* dst)
 {
+    if (stage_aborted(p.counters)) return;  // a stage before this one failed
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < T; t += gridDim.x * blockDim.x) {
         int4 w = p.tl_work[t];
         dst[t] = w.x;
@@ -904,6 +922,16 @@ cudaError_t launch_dump_tl_work(const DevPtrs& p, int T, int* dst, cudaStream_t 
 {
     k_dump_tl_work<<<256, 256, 0, s>>>(p, T, dst);
     return cudaGetLastError();
+}
+
+cudaError_t preload_link_kernels()
+{
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, k_plan);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_grid);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_clean);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_dump_links);
+    return e;
 }
 
 }  // namespace tpc_int

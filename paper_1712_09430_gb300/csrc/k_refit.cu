@@ -245,6 +245,7 @@ __device__ __forceinline__ int fit_idx(int g, int n) { return g < n ? g : 2 * n 
 
 __global__ void __launch_bounds__(kRefitThreads, kRefitCtasPerSm) k_refit(KConst k, DevPtrs p)
 {
+    if (stage_aborted(p.counters)) return;  // a stage before this one failed
     const unsigned FULL = 0xffffffffu;
     const int M = p.counters[C_FIT_M];
     const int lane = threadIdx.x & 31;
@@ -323,6 +324,7 @@ constexpr int kFitBins = TPC_MAX_ROWS + 1;
 
 __global__ void k_fit_hist(DevPtrs p, int* bins)
 {
+    if (stage_aborted(p.counters)) return;  // a stage before this one failed
     __shared__ int h[kFitBins];
     for (int i = threadIdx.x; i < kFitBins; i += blockDim.x) h[i] = 0;
     __syncthreads();
@@ -338,6 +340,7 @@ __global__ void k_fit_hist(DevPtrs p, int* bins)
 
 __global__ void k_fit_offsets(DevPtrs p, int* bins)
 {
+    if (stage_aborted(p.counters)) return;  // a stage before this one failed
     if (threadIdx.x == 0) {
         int acc = 0;
         for (int n = kFitBins - 1; n >= 0; n--) {
@@ -350,6 +353,7 @@ __global__ void k_fit_offsets(DevPtrs p, int* bins)
 
 __global__ void k_fit_scatter(DevPtrs p, int* bins)
 {
+    if (stage_aborted(p.counters)) return;  // a stage before this one failed
     const int M = p.counters[C_M];
     for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < M; m += gridDim.x * blockDim.x) {
         const int n = min(max(p.out_tracks[m].nhits, 0), kFitBins - 1);
@@ -534,6 +538,7 @@ __device__ __forceinline__ bool mg_chi2(const float* pa, const Cov& Ca, const fl
 // tracklets at the unit's first canonical tracklet.
 __global__ void k_unit_first(KConst k, DevPtrs p)
 {
+    if (stage_aborted(p.counters)) return;  // a stage before this one failed
     const int T = p.counters[C_T], M = p.counters[C_M];
     for (int u = blockIdx.x * blockDim.x + threadIdx.x; u <= p.n_units; u += gridDim.x * blockDim.x) {
         const int t = p.start_off[u * k.n_rows];
@@ -545,6 +550,7 @@ __global__ void k_unit_first(KConst k, DevPtrs p)
 // the candidate scan reads 8 bytes per track, coalesced.
 __global__ void k_merge_init(DevPtrs p)
 {
+    if (stage_aborted(p.counters)) return;  // a stage before this one failed
     const int M = p.counters[C_M];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 2 * M; i += gridDim.x * blockDim.x) {
         p.mg_best[i] = ~0ull;
@@ -556,6 +562,7 @@ __global__ void k_merge_init(DevPtrs p)
 // of the two adjacent units of the same side.
 __global__ void __launch_bounds__(256) k_merge_pairs(KConst k, DevPtrs p)
 {
+    if (stage_aborted(p.counters)) return;  // a stage before this one failed
     const int M = p.counters[C_M];
     const int lane = threadIdx.x & 31;
     const int S = k.n_sectors, half = S / 2;
@@ -640,6 +647,7 @@ __global__ void __launch_bounds__(256) k_merge_pairs(KConst k, DevPtrs p)
 // Mutual best candidates are linked.
 __global__ void k_merge_link(DevPtrs p)
 {
+    if (stage_aborted(p.counters)) return;  // a stage before this one failed
     const int M = p.counters[C_M];
     for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < M; a += gridDim.x * blockDim.x) {
         const unsigned long long ka = p.mg_best[a];
@@ -680,6 +688,7 @@ cudaError_t launch_merge(const KConst& k, const DevPtrs& p, int n_sm, cudaStream
 
 __global__ void k_t0_clear(KConst k, DevPtrs p, int E)
 {
+    if (stage_aborted(p.counters)) return;  // a stage before this one failed
     const int n = E * k.t0_nb;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         p.t0_hist[i] = 0;
@@ -691,6 +700,7 @@ __global__ void k_t0_clear(KConst k, DevPtrs p, int E)
 // A thread per track: offset estimate, bin, histogram.
 __global__ void k_t0_track(KConst k, DevPtrs p)
 {
+    if (stage_aborted(p.counters)) return;  // a stage before this one failed
     const int M = p.counters[C_M];
     const int half = k.n_sectors / 2, nb = k.t0_nb;
     for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < M; m += gridDim.x * blockDim.x) {
@@ -726,6 +736,7 @@ __global__ void k_t0_track(KConst k, DevPtrs p)
 // compaction keeps the order).
 __global__ void k_t0_peaks(KConst k, DevPtrs p, int E)
 {
+    if (stage_aborted(p.counters)) return;  // a stage before this one failed
     const int lane = threadIdx.x & 31;
     const int nb = k.t0_nb, W = k.t0_window;
     for (int e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; e < E; e += (gridDim.x * blockDim.x) >> 5) {
@@ -764,6 +775,7 @@ __global__ void k_t0_peaks(KConst k, DevPtrs p, int E)
 // A thread per track: nearest peak centre within r (ties: the lower), sums.
 __global__ void k_t0_assign(KConst k, DevPtrs p)
 {
+    if (stage_aborted(p.counters)) return;  // a stage before this one failed
     const int M = p.counters[C_M];
     const int nb = k.t0_nb;
     for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < M; m += gridDim.x * blockDim.x) {
@@ -792,6 +804,7 @@ __global__ void k_t0_assign(KConst k, DevPtrs p)
 
 __global__ void k_t0_out(KConst k, DevPtrs p)
 {
+    if (stage_aborted(p.counters)) return;  // a stage before this one failed
     const int M = p.counters[C_M];
     const int nb = k.t0_nb;
     for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < M; m += gridDim.x * blockDim.x) {

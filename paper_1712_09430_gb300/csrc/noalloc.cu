@@ -22,34 +22,34 @@ namespace {
 constexpr int kNoallocMaxClusters = TPC_NOALLOC_MAX_CLUSTERS;
 constexpr size_t kScratchBytes = TPC_NOALLOC_SCRATCH_BYTES;
 constexpr int kNoallocMaxRows = 16384;  // n_sectors * n_rows of one event
-constexpr int kMaxDevices = 64;
 
-// The scratch: one copy per device that loads this library, held until the
-// process exits.  Host code must not use this name as an address; it takes
-// the device address from cudaGetSymbolAddress (see scratch_on_device).
+// The scratch: one copy per device that loads this library's device code,
+// held until the process exits.  Host code must not use this name as an
+// address; it takes the device address from cudaGetSymbolAddress (see
+// scratch_address).
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 std::mutex g_mu;                       // one call at a time, see the header
-void* g_scratch_addr[kMaxDevices];     // device address per device, set once
 int g_plan[2 * (kNoallocMaxRows + 1)]; // host plan (row and bin-table offsets)
 int g_counters[kNumCounters];
 
 size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 
-// First call on a device: look up the scratch's device address with that
-// device current.
-int scratch_on_device(int dev, void** out)
+// Device address of the scratch on the current device, looked up on every
+// call (a table lookup once the module is loaded; a stored address would
+// dangle after the device's context is torn down and recreated).  CUDA
+// loads device code lazily: the first lookup on a device loads this
+// library's module there, and with it the scratch array, which can fail for
+// lack of device memory.
+int scratch_address(void** out)
 {
-    if (dev < 0 || dev >= kMaxDevices) return TPC_ERR_DEVICE;
-    if (!g_scratch_addr[dev]) {
-        void* ptr = nullptr;
-        if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) {
-            cudaGetLastError();
-            return TPC_ERR_DEVICE;
-        }
-        g_scratch_addr[dev] = ptr;
+    void* ptr = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess || !ptr) {
+        cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? TPC_ERR_NOMEM : TPC_ERR_DEVICE;
     }
-    *out = g_scratch_addr[dev];
+    *out = ptr;
     return TPC_OK;
 }
 
@@ -76,6 +76,15 @@ extern "C" int tpc_links_noalloc(const tpc_geometry* g, const tpc_params* params
     if (params) P = *params;
     if (!params_ok(P)) return TPC_ERR_INVALID;
     if (reinterpret_cast<uintptr_t>(d_clusters) & 15) return TPC_ERR_INVALID;
+
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    // every call synchronizes with its own work, which a capturing stream
+    // does not allow: refuse before enqueuing anything
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) {
+        cudaGetLastError();
+        return TPC_ERR_INVALID;
+    }
 
     std::lock_guard<std::mutex> lock(g_mu);
     // plan on the host: row CSR offsets and bin-table offsets
@@ -106,7 +115,24 @@ extern "C" int tpc_links_noalloc(const tpc_geometry* g, const tpc_params* params
     if (N > kNoallocMaxClusters) return TPC_ERR_INVALID;  // beyond the fixed scratch
     plan_off[R] = (int)N;
     plan_bins[R] = (int)bins;
-    if (N == 0) return TPC_OK;
+    // the scratch on this device, also for an empty event: an empty call at
+    // start-up loads it
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return TPC_ERR_DEVICE;
+    void* base_v = nullptr;
+    int rc = scratch_address(&base_v);
+    if (rc != TPC_OK) return rc;
+    char* base = static_cast<char*>(base_v);
+    if (N == 0) {
+        // the kernels too: an empty call leaves nothing to load later
+        cudaError_t e = tpc_int::preload_link_kernels();
+        if (e == cudaSuccess) e = P.exact_fp32 ? tpc_exact::preload_neighbours() : tpc_fast::preload_neighbours();
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return e == cudaErrorMemoryAllocation ? TPC_ERR_NOMEM : TPC_ERR_DEVICE;
+        }
+        return TPC_OK;
+    }
     if (!d_clusters || !d_links) return TPC_ERR_INVALID;
 
     // lay out the scratch
@@ -130,13 +156,6 @@ extern "C" int tpc_links_noalloc(const tpc_geometry* g, const tpc_params* params
     const size_t o_owner = take(n * 4);
     const size_t o_count = take(kNumCounters * 4);
     if (off > kScratchBytes) return TPC_ERR_NOMEM;  // bin tables too large at this bin_target
-
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return TPC_ERR_DEVICE;
-    void* base_v = nullptr;
-    int rc = scratch_on_device(dev, &base_v);
-    if (rc != TPC_OK) return rc;
-    char* base = static_cast<char*>(base_v);
 
     KConst k;
     std::memset(&k, 0, sizeof k);
@@ -172,7 +191,6 @@ extern "C" int tpc_links_noalloc(const tpc_geometry* g, const tpc_params* params
     p.R = R;
     p.n_units = S;
 
-    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     const float* xd = reinterpret_cast<const float*>(base + o_rowx);
     int nsm = 0;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);

@@ -55,6 +55,7 @@ struct KConst {
     float bin_target;
     int l_seed, g_max, n_min_tracklet, n_min_track, own_num, own_den;
     int n_rows, n_sectors;
+    unsigned wait_polls;  // params.debug_wait_polls: 0 = the built-in bound
 };
 
 // schedule 2: by start row inside blocks of units that hold about this many
@@ -205,6 +206,47 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity
     return false;
 }
 
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, "
+        "0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// The first wait on a row's bulk copies in the grid and neighbour kernels.
+// polls = 0: the bounded wait above.  polls > 0 (the debug_wait_polls test
+// field): that many non-blocking tests of the phase, so that a test can make
+// the wait run out on purpose; the drain wait after a time-out keeps the
+// full bound either way.
+__device__ __forceinline__ bool mbar_wait_first(uint64_t* bar, unsigned parity, unsigned polls)
+{
+    if (polls == 0) return mbar_wait_bounded(bar, parity);
+    for (unsigned i = 0; i < polls; i++)
+        if (mbar_test_wait(bar, parity)) return true;
+    return false;
+}
+
+// Stages after a failed one do nothing.  A bulk-copy wait that ran out
+// (E_TIMEOUT) or a launch shape that did not fit its batch (E_SHAPE) leaves
+// buffers unwritten that later stages would index; every later kernel
+// checks the flag on entry and returns, the counters keep the zeros this
+// call started from, and the host reports the failure.  Thread 0 reads the
+// flag once and shares it, so that every thread of the CTA takes the same
+// branch (a stage of another unit, on another stream, may set it
+// meanwhile).  Called by all threads, before any other barrier or return.
+__device__ __forceinline__ bool stage_aborted(const int* counters)
+{
+    __shared__ int s_abort;
+    if (threadIdx.x == 0) s_abort = *reinterpret_cast<const volatile int*>(counters + C_ERR) & (E_TIMEOUT | E_SHAPE);
+    __syncthreads();
+    return s_abort != 0;
+}
+
 // shared -> global bulk copy (bulk-group completion)
 __device__ __forceinline__ void bulk_s2g(void* dst, const void* src, unsigned bytes)
 {
@@ -262,6 +304,10 @@ cudaError_t launch_dump_starts(const tpc::DevPtrs& p, int T, int* dst, cudaStrea
 cudaError_t launch_dump_tl_hits(const tpc::KConst& k, const tpc::DevPtrs& p, int T, int* dst,
                                 cudaStream_t s);
 cudaError_t launch_dump_tl_work(const tpc::DevPtrs& p, int T, int* dst, cudaStream_t s);
+// Load the link-finding kernels (plan, grid, cleaner, link dump) on the
+// current device now rather than at their first launch (CUDA loads device
+// code lazily, and loading needs device memory of its own).
+cudaError_t preload_link_kernels();
 }  // namespace tpc_int
 
 #define TPC_FP_DECLS                                                                              \
@@ -277,7 +323,8 @@ cudaError_t launch_dump_tl_work(const tpc::DevPtrs& p, int T, int* dst, cudaStre
                              int n_sm, int u0, int u1, cudaStream_t s);                             \
     cudaError_t launch_refit(const tpc::KConst& k, const tpc::DevPtrs& p, int n_sm, cudaStream_t s); \
     cudaError_t launch_merge(const tpc::KConst& k, const tpc::DevPtrs& p, int n_sm, cudaStream_t s);   \
-    cudaError_t launch_t0(const tpc::KConst& k, const tpc::DevPtrs& p, int n_sm, int n_events, cudaStream_t s);
+    cudaError_t launch_t0(const tpc::KConst& k, const tpc::DevPtrs& p, int n_sm, int n_events, cudaStream_t s); \
+    cudaError_t preload_neighbours();
 
 namespace tpc_exact { TPC_FP_DECLS }
 namespace tpc_fast { TPC_FP_DECLS }

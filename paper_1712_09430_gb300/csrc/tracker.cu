@@ -84,6 +84,7 @@ static KConst make_kconst(const tpc_params& P, const tpc_geometry& G, double bz)
     k.own_den = P.own_den;
     k.n_rows = G.n_rows;
     k.n_sectors = G.n_sectors;
+    k.wait_polls = (unsigned)P.debug_wait_polls;
     return k;
 }
 
@@ -111,6 +112,7 @@ static const char* check_params(const tpc_params& P)
         return "merge cuts must be positive";
     if (P.t0 != 0 && P.t0 != 1) return "t0 must be 0 or 1";
     if (P.count_work != 0 && P.count_work != 1) return "count_work must be 0 or 1";
+    if (P.debug_wait_polls < 0) return "debug_wait_polls must be >= 0";
     if (P.t0 && !P.refit) return "t0 needs refit = 1 (it extrapolates refitted states)";
     if (!(P.t0_y_cut > 0) || !(P.t0_bin >= 0.01f) || !(P.t0_radius > 0) || P.t0_window < 0 || P.t0_n_min < 1)
         return "t0 parameters";
