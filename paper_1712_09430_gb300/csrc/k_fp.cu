@@ -93,7 +93,8 @@ __global__ void k_neighbours(KConst k, const float* __restrict__ row_x, DevPtrs 
     const float Wu = k.k_win * fabsf(Xu - Xr);
     const float Wd = k.k_win * fabsf(Xd - Xr);
     const float tt = (Xr - Xd) / (Xu - Xd);
-    if (!mbar_wait_first(bar, 0, k.wait_polls)) {
+    const bool landed = mbar_wait_first(bar, 0, k.wait_polls);
+    if (__syncthreads_or(!landed)) {  // one decision for the whole CTA
         if (tid == 0) atomicOr(&p.counters[C_ERR], E_TIMEOUT);
         mbar_wait_bounded(bar, 0);  // the copies in flight, before the CTA returns
         return;

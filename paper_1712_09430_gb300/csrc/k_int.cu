@@ -159,7 +159,10 @@ __global__ void k_grid(KConst k, const float* __restrict__ row_x, DevPtrs p, int
     }
     for (int b = tid; b <= nb; b += nt) hist[b] = 0;
     __syncthreads();
-    if (!mbar_wait_first(bar, 0, k.wait_polls)) {
+    // one decision for the whole CTA: a thread whose wait ran out must not
+    // leave the others to bin with its clusters missing
+    const bool landed = mbar_wait_first(bar, 0, k.wait_polls);
+    if (__syncthreads_or(!landed)) {
         if (tid == 0) flag_error(p.counters, E_TIMEOUT, rr);
         mbar_wait_bounded(bar, 0);  // the copy in flight, before the CTA returns
         return;
