@@ -33,6 +33,7 @@ TPC_DUMP_TRACKLET_N = 4
 TPC_DUMP_TRACKLET_HITS = 5
 TPC_DUMP_TRACKLET_WORK = 6
 TPC_NOALLOC_MAX_CLUSTERS = 65536
+TPC_NOALLOC_SCRATCH_BYTES = 8 << 20
 TPC_STREAM_NO_COPY = 1
 TPC_STREAM_BATCH_CLUSTERS = 1 << 22  # default cluster limit of one serving batch
 

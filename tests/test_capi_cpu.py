@@ -51,6 +51,8 @@ int main(void)
            sizeof(tpc_output), sizeof(tpc_stream_view), sizeof(tpc_stream_stats), sizeof(fns) / sizeof(fns[0]));
     printf("%d %d %d %g %g %d\n", p.n_min_tracklet, p.tracklets_per_warp, p.schedule, (double)p.bin_target,
            (double)p.k_win, p.count_work);
+    printf("%d %u %d %d\n", TPC_NOALLOC_MAX_CLUSTERS, (unsigned)TPC_NOALLOC_SCRATCH_BYTES,
+           (int)TPC_STREAM_BATCH_CLUSTERS, p.debug_wait_polls);
     return 0;
 }
 """
@@ -80,7 +82,7 @@ def test_header_is_plain_c_and_matches_the_binding(tmp_path):
     assert r.returncode == 0, r.stderr
     r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
     assert r.returncode == 0, r.stderr
-    sizes, defaults = r.stdout.split("\n")[:2]
+    sizes, defaults, consts = r.stdout.split("\n")[:3]
     got = [int(v) for v in sizes.split()]
     want = [16, C.sizeof(capi.tpc_geometry), C.sizeof(capi.tpc_params), C.sizeof(capi.tpc_track),
             C.sizeof(capi.tpc_fit), C.sizeof(capi.tpc_merge), C.sizeof(capi.tpc_t0),
@@ -91,3 +93,5 @@ def test_header_is_plain_c_and_matches_the_binding(tmp_path):
     assert [int(d[0]), int(d[1]), int(d[2]), int(d[5])] == [p.n_min_tracklet, p.tracklets_per_warp,
                                                              p.schedule, p.count_work]
     assert float(d[3]) == p.bin_target and abs(float(d[4]) - p.k_win) < 1e-6
+    assert [int(v) for v in consts.split()] == [capi.TPC_NOALLOC_MAX_CLUSTERS, capi.TPC_NOALLOC_SCRATCH_BYTES,
+                                                 capi.TPC_STREAM_BATCH_CLUSTERS, 0]
