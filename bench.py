@@ -758,9 +758,10 @@ def run_stream(tr0, pool, args, rate, batch=None, workload=MINBIAS_STREAM):
         # submitted without a copy; each stays untouched until its result is in
         pool = [(torch.from_numpy(cl).pin_memory(), rc) for cl, rc in pool]
         tr.stream_configure(arena_bytes=args.stream_arena_gb << 30, max_batch_events=batch,
-                            max_inflight=2, no_copy=True)
+                            max_inflight=args.stream_inflight, no_copy=True,
+                            max_batch_clusters=args.stream_batch_clusters)
         rng = np.random.default_rng(5)
-        n_req = int(rate * args.stream_seconds)
+        n_req = args.stream_requests or int(rate * args.stream_seconds)
         arrivals = np.cumsum(rng.exponential(1.0 / rate, n_req))
         picks = rng.integers(0, len(pool), n_req)
         # warm-up: one burst of a full batch (the result buffers reach their
@@ -793,22 +794,23 @@ def run_stream(tr0, pool, args, rate, batch=None, workload=MINBIAS_STREAM):
                     break               # not admitted now (memory/slots): retry later
                 outstanding[t] = i
                 backlog.pop(0)
-            # the oldest requests finish first: poll from the oldest and stop
-            # after a few pending ones (each poll of a pending ticket costs a
-            # pass of the request loop)
-            misses = 0
-            for t in list(outstanding)[:64]:
+            # take every result that is ready, in the order the batches
+            # finished (one call per result, no scan over pending tickets);
+            # with nothing to submit, wait in the library until the next
+            # arrival is due
+            wait_us = 0
+            if not backlog and nxt < n_req:
+                wait_us = int(max(0.0, min(1e-4, arrivals[nxt] - (time.perf_counter() - t0))) * 1e6)
+            while True:
                 ts = time.perf_counter()
-                r = tr.poll_view(t, 0)   # no copy: the tracks are read in place
-                if r is not None:
-                    n_tracks += len(r.tracks)
-                    tr.release(t)
+                got = tr.poll_any(wait_us)
                 t_poll += time.perf_counter() - ts
-                if r is None:
-                    misses += 1
-                    if misses >= 4:
-                        break
-                    continue
+                if got is None:
+                    break
+                wait_us = 0
+                t, r = got
+                n_tracks += len(r.tracks)   # the tracks are read in place
+                tr.release(t)
                 i = outstanding.pop(t)
                 lat[i] = time.perf_counter() - t0 - arrivals[i]
                 clusters += len(pool[picks[i]][0])
@@ -824,8 +826,10 @@ def run_stream(tr0, pool, args, rate, batch=None, workload=MINBIAS_STREAM):
     return {"rate_hz": rate, "requests": n_req, "p50_ms": float(np.percentile(lat, 50) * 1e3),
             "loop": st,
             "p99_ms": float(np.percentile(lat, 99) * 1e3), "max_ms": float(lat.max() * 1e3),
+            "max_arrival_s": float(arrivals[int(np.argmax(lat))]),
             "clusters_per_s": clusters / wall, "events_per_s": n_req / wall, "wall_s": wall,
-            "tracks": n_tracks, "client": "tpc_stream_poll_view + tpc_stream_release (results read in place)",
+            "tracks": n_tracks, "client": "tpc_stream_poll_any + tpc_stream_release (results read in place)",
+            "batches_in_flight": args.stream_inflight,
             "pool_events": len(pool), "mean_clusters_per_event": float(np.mean([len(p[0]) for p in pool])),
             "max_batch_events": batch, "workload": workload}
 
@@ -1018,6 +1022,11 @@ def main():
                     help="most events per serving batch (a large batch formed after a burst "
                          "holds all its requests until its last kernel)")
     ap.add_argument("--stream-arena-gb", type=int, default=16)
+    ap.add_argument("--stream-inflight", type=int, default=2, help="serving batches in flight")
+    ap.add_argument("--stream-batch-clusters", type=int, default=1 << 22,
+                    help="most clusters in one serving batch (the library's default: 2^22)")
+    ap.add_argument("--stream-requests", type=int, default=0,
+                    help="requests per serving rate (0: rate x --stream-seconds)")
     ap.add_argument("--pool", type=int, default=96, help="min-bias events in the serving pool")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -375,6 +375,18 @@ typedef struct {
  * valid) or an error (the ticket is released).  view: caller-owned. */
 int tpc_stream_poll_view(tpc_tracker* tr, uint64_t ticket, tpc_stream_view* view, int timeout_us);
 
+/* Serving (Sec. 3.2): the result of whichever ticket finished first and has
+ * not been taken yet, without a copy, waiting at most timeout_us (0: do not
+ * wait).  A client that keeps many requests in flight takes results as they
+ * come instead of polling each ticket in turn.  Returns TPC_PENDING (nothing
+ * finished), TPC_OK (*ticket and view filled; the ticket stays valid until
+ * tpc_stream_release, as after tpc_stream_poll_view) or the error of a
+ * failed request (*ticket names it; it is released).  Tickets already taken
+ * by tpc_stream_poll or tpc_stream_poll_view are skipped.  Drives the
+ * request loop like tpc_stream_poll.  Library bookkeeping; no passage of
+ * the paper. */
+int tpc_stream_poll_any(tpc_tracker* tr, uint64_t* ticket, tpc_stream_view* view, int timeout_us);
+
 /* Serving (Sec. 3.2): release a finished ticket (after tpc_stream_poll_view),
  * ending the validity of its view.  TPC_ERR_INVALID while it is still
  * pending, TPC_ERR_UNKNOWN_TICKET if unknown. */

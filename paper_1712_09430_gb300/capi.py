@@ -135,6 +135,7 @@ def lib() -> C.CDLL:
         L.tpc_stream_get_stats.argtypes = [V, P(tpc_stream_stats)]
         L.tpc_stream_poll_view.argtypes = [V, C.c_uint64, P(tpc_stream_view), C.c_int]
         L.tpc_stream_release.argtypes = [V, C.c_uint64]
+        L.tpc_stream_poll_any.argtypes = [V, P(C.c_uint64), P(tpc_stream_view), C.c_int]
         L.tpc_debug_dump.argtypes = [V, C.c_int, V, C.c_int64, P(C.c_int64)]
         L.tpc_stage_times.argtypes = [V, P(C.c_float), C.c_int]
         L.tpc_last_error.argtypes = [V]

@@ -127,6 +127,7 @@ struct ServeState {
     char* pin = nullptr;           // pinned input staging
     Arena pin_arena;
     std::deque<uint64_t> pending;
+    std::deque<uint64_t> finished;  // tickets in the order their batches finished (tpc_stream_poll_any)
     std::map<uint64_t, Request> req;
     std::vector<Batch> batches;    // slots
     uint64_t next_ticket = 1;
@@ -142,6 +143,8 @@ double ms_since(std::chrono::steady_clock::time_point t0)
     return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
 }
 }  // namespace
+
+static int grow_pinned(tpc_tracker* tr, void** ptr, size_t* cap, size_t want);
 
 static int serve_init(tpc_tracker* tr)
 {
@@ -173,6 +176,30 @@ static int serve_init(tpc_tracker* tr)
             cudaEventCreate(&b.done) != cudaSuccess || cudaEventCreate(&b.start) != cudaSuccess ||
             cudaMallocHost(&b.counters, sizeof(int) * kNumCounters) != cudaSuccess)
             return tr->fail(TPC_ERR_DEVICE, "cannot create serving streams");
+    }
+    // With a cluster limit per batch, every slot's pinned buffers are sized
+    // for a full batch now: growing them while serving would mean
+    // cudaFreeHost / cudaMallocHost, which synchronize the device and stall
+    // every batch in flight.  Hits of a batch never exceed its clusters;
+    // tracks are sized for 2 % of them (central and min-bias events make
+    // about 1.1 %), beyond which the estimate-then-fetch path still works.
+    if (S->max_batch_clusters > 0) {
+        const size_t cap = (size_t)S->max_batch_clusters;
+        const size_t nt = cap / 50 + 1024, nh = cap + 4096;
+        const size_t R = (size_t)S->max_batch_events * tr->geom.n_sectors * tr->geom.n_rows;
+        const size_t plan = (3 * R + 2 + 3 * (size_t)S->max_batch_events + 2) * sizeof(int);
+        for (auto& b : S->batches) {
+            if (grow_pinned(tr, reinterpret_cast<void**>(&b.plan), &b.plan_cap, plan) != TPC_OK ||
+                grow_pinned(tr, reinterpret_cast<void**>(&b.tracks), &b.tracks_cap, sizeof(tpc_track) * nt) != TPC_OK ||
+                grow_pinned(tr, reinterpret_cast<void**>(&b.hits), &b.hits_cap, sizeof(int) * nh) != TPC_OK ||
+                (tr->params.refit &&
+                 grow_pinned(tr, reinterpret_cast<void**>(&b.fits), &b.fits_cap, sizeof(tpc_fit) * nt) != TPC_OK) ||
+                (tr->params.merge &&
+                 grow_pinned(tr, reinterpret_cast<void**>(&b.merges), &b.merges_cap, sizeof(tpc_merge) * nt) != TPC_OK) ||
+                (tr->params.t0 &&
+                 grow_pinned(tr, reinterpret_cast<void**>(&b.t0s), &b.t0s_cap, sizeof(tpc_t0) * nt) != TPC_OK))
+                return TPC_ERR_NOMEM;
+        }
     }
     return TPC_OK;
 }
@@ -440,6 +467,15 @@ static void finish_batch(tpc_tracker* tr, Batch& b)
         if (r.pin_bytes) S->pin_arena.release(r.pin_off, r.pin_bytes);
         r.pin_bytes = 0;
         b.open_results++;
+        S->finished.push_back(t);
+    }
+    if (S->finished.size() > 4 * (size_t)S->max_requests) {  // drop tickets taken by per-ticket polls
+        std::deque<uint64_t> keep;
+        for (uint64_t t : S->finished) {
+            auto it = S->req.find(t);
+            if (it != S->req.end() && !it->second.viewed) keep.push_back(t);
+        }
+        S->finished.swap(keep);
     }
     S->arena.release(b.arena_off, b.arena_bytes);
     S->inflight--;
@@ -651,6 +687,45 @@ extern "C" int tpc_stream_poll_view(tpc_tracker* tr, uint64_t ticket, tpc_stream
     view->n_hits = r->h1 - r->h0;
     r->viewed = true;
     return TPC_OK;
+}
+
+extern "C" int tpc_stream_poll_any(tpc_tracker* tr, uint64_t* ticket, tpc_stream_view* view, int timeout_us)
+{
+    if (!tr) return TPC_ERR_INVALID;
+    if (!ticket || !view) return tr->fail(TPC_ERR_INVALID, "NULL ticket or view");
+    if (!tr->serve) return TPC_PENDING;
+    if (cudaSetDevice(tr->dev) != cudaSuccess) return tr->fail(TPC_ERR_DEVICE, "cudaSetDevice");
+    ServeState* S = tr->serve;
+    const auto t_end = std::chrono::steady_clock::now() + std::chrono::microseconds(std::max(0, timeout_us));
+    while (true) {
+        int rc = progress(tr);
+        if (rc != TPC_OK) return rc;
+        while (!S->finished.empty()) {
+            const uint64_t t = S->finished.front();
+            S->finished.pop_front();
+            auto it = S->req.find(t);
+            if (it == S->req.end() || it->second.viewed) continue;  // taken by a per-ticket poll
+            Request& r = it->second;
+            *ticket = t;
+            if (r.err != TPC_OK) {
+                const int result = r.err;
+                release_ticket(tr, t);
+                return tr->fail(result, "batch failed");
+            }
+            const Batch& b = S->batches[(size_t)r.batch];
+            view->tracks = b.tracks + r.m0;
+            view->hit_ids = b.hits + r.h0;
+            view->fits = tr->params.refit ? b.fits + r.m0 : nullptr;
+            view->merges = tr->params.merge ? b.merges + r.m0 : nullptr;
+            view->t0s = tr->params.t0 ? b.t0s + r.m0 : nullptr;
+            view->n_tracks = r.m1 - r.m0;
+            view->n_hits = r.h1 - r.h0;
+            r.viewed = true;
+            return TPC_OK;
+        }
+        if (std::chrono::steady_clock::now() >= t_end) return TPC_PENDING;
+        std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
 }
 
 extern "C" int tpc_stream_release(tpc_tracker* tr, uint64_t ticket)

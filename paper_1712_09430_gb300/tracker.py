@@ -251,7 +251,10 @@ class Tracker:
         if rc == capi.TPC_PENDING:
             return None
         self.check(rc)
+        return self._view_result(v)
 
+    def _view_result(self, v):
+        """Numpy views of a tpc_stream_view."""
         def arr(ptr, n, dt):
             if n == 0 or not ptr:
                 return np.zeros(0, dt)
@@ -261,6 +264,19 @@ class Tracker:
         t0s = arr(v.t0s, v.n_tracks, T0_DTYPE) if self.params.t0 else None
         return Result(arr(v.tracks, v.n_tracks, TRACK_DTYPE), arr(v.hit_ids, v.n_hits, np.dtype(np.int32)),
                       fits, merges, t0s)
+
+    def poll_any(self, timeout_us=0):
+        """(ticket, Result as numpy views) of whichever ticket finished first
+        and has not been taken yet, or None; the views stay valid until
+        release(ticket).  A failed request raises TrackerError (its ticket
+        is released)."""
+        v = capi.tpc_stream_view()
+        t = C.c_uint64()
+        rc = lib().tpc_stream_poll_any(self.h, C.byref(t), C.byref(v), int(timeout_us))
+        if rc == capi.TPC_PENDING:
+            return None
+        self.check(rc)
+        return int(t.value), self._view_result(v)
 
     def release(self, ticket):
         """Return a ticket's result buffers (after poll_view) to the library."""

@@ -196,6 +196,33 @@ def test_stream_release_of_pending_ticket_is_refused(pool):
         assert _drain(tr, [t])[t] is not None
 
 
+def test_poll_any_returns_each_result_once(pool):
+    """tpc_stream_poll_any hands out finished tickets in the order their
+    batches finished, each once, with the same results as tracked alone;
+    a ticket already taken by a per-ticket poll is skipped."""
+    evs = pool[:6]
+    with Tracker(XR, exact_fp32=1) as alone:
+        ref = [alone.track(e.clusters, e.row_counts, 1) for e in evs]
+    with Tracker(XR, exact_fp32=1) as tr:
+        tr.stream_configure(arena_bytes=2 << 30, max_batch_events=3, max_inflight=2)
+        tickets = {tr.submit(e.clusters, e.row_counts, 1): i for i, e in enumerate(evs)}
+        first = next(iter(tickets))
+        _same(_drain(tr, [first])[first], ref[tickets[first]])
+        seen = set()
+        t_end = time.time() + 60
+        while len(seen) < len(tickets) - 1:
+            got = tr.poll_any(200)
+            if got is None:
+                assert time.time() < t_end, "poll_any timed out"
+                continue
+            t, r = got
+            assert t in tickets and t != first and t not in seen
+            _same(r, ref[tickets[t]])
+            tr.release(t)
+            seen.add(t)
+        assert tr.poll_any(0) is None
+
+
 @pytest.mark.parametrize("cap", [0, 1])
 def test_batches_respect_the_cluster_limit(cap):
     """Requests queued behind a running batch join the next one up to the
