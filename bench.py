@@ -779,8 +779,13 @@ def run_stream(tr0, pool, args, rate, batch=None, workload=MINBIAS_STREAM):
         t_submit = t_poll = 0.0
         n_tracks = 0
         t0 = time.perf_counter()
+        last = 0.0
+        max_gap, max_gap_at = 0.0, 0.0   # the longest pass of the client loop (a host-side stall)
         while done < n_req:
             now = time.perf_counter() - t0
+            if now - last > max_gap:
+                max_gap, max_gap_at = now - last, last
+            last = now
             while nxt < n_req and arrivals[nxt] <= now:
                 backlog.append(nxt)
                 nxt += 1
@@ -827,6 +832,7 @@ def run_stream(tr0, pool, args, rate, batch=None, workload=MINBIAS_STREAM):
             "loop": st,
             "p99_ms": float(np.percentile(lat, 99) * 1e3), "max_ms": float(lat.max() * 1e3),
             "max_arrival_s": float(arrivals[int(np.argmax(lat))]),
+            "client_max_gap_ms": max_gap * 1e3, "client_max_gap_at_s": max_gap_at,
             "clusters_per_s": clusters / wall, "events_per_s": n_req / wall, "wall_s": wall,
             "tracks": n_tracks, "client": "tpc_stream_poll_any + tpc_stream_release (results read in place)",
             "batches_in_flight": args.stream_inflight,

@@ -714,27 +714,79 @@ __global__ void __launch_bounds__(kTlThreads, 3) k_tracklets_plain(KConst k, con
 // T1 covariance), then filter the chain's clusters in order: predict a copy
 // to the row (a failed step or a state outside the sector ends Phase 1),
 // update with the chain cluster, commit.  The constructor starts at the row
-// after the chain.  One thread per tracklet; these steps need no search, so
-// they run here rather than in the constructor's divergent loop.
-__global__ void k_seeds(KConst k, const float* __restrict__ row_x, DevPtrs p, int u0, int u1)
+// after the chain.  These steps need no search, so they run here rather than
+// in the constructor's divergent loop.
+// A CTA takes 256 tracklets at a time: each thread first walks its chain to
+// learn its length and last hit, the CTA orders the 256 chains by length in
+// shared memory, and each thread then filters the chain of its rank, so that
+// the threads of a warp filter chains of (nearly) the same length instead of
+// idling while the longest chain of a random warp is filtered.
+constexpr int kSeedThreads = 256;
+
+__global__ void __launch_bounds__(kSeedThreads) k_seeds(KConst k, const float* __restrict__ row_x, DevPtrs p,
+                                                        int u0, int u1)
 {
     if (stage_aborted(p.counters)) return;  // a stage before this one failed
+    __shared__ int hist[TPC_MAX_ROWS + 1];
+    __shared__ int s_t[kSeedThreads], s_len[kSeedThreads], s_last[kSeedThreads];
+    const int tid = threadIdx.x;
     const int t0 = p.start_off[u0 * k.n_rows], t1 = p.start_off[u1 * k.n_rows];
-    for (int t = t0 + blockIdx.x * blockDim.x + threadIdx.x; t < t1; t += gridDim.x * blockDim.x) {
-        const int h0 = p.start[t];
-        // the first kChainCache chain clusters are kept for the filter loop
-        constexpr int kChainCache = 8;
-        int hc[kChainCache];
-        hc[0] = h0;
-        int h = h0, len = 1;
-        for (int j = p.up2[h]; j >= 0; j = p.up2[j]) {
-            h = j;
-            if (len < kChainCache) hc[len] = j;
-            len++;
+    for (int base = t0 + blockIdx.x * kSeedThreads; base < t1; base += gridDim.x * kSeedThreads) {
+        // the chain of tracklet base + tid: its length and last hit
+        const int tw = base + tid;
+        int len = 0, last = -1;
+        if (tw < t1) {
+            int h = p.start[tw];
+            len = 1;
+            for (int j = p.up2[h]; j >= 0; j = p.up2[j]) {
+                h = j;
+                len++;
+            }
+            last = h;
         }
+        // order the CTA's chains by length (counting sort; len <= n_rows)
+        for (int b = tid; b <= TPC_MAX_ROWS; b += kSeedThreads) hist[b] = 0;
+        __syncthreads();
+        atomicAdd(&hist[len], 1);
+        __syncthreads();
+        if (tid < 32) {  // exclusive scan of the 257 counts, one warp, 9 a lane
+            int v[9], sum = 0;
+#pragma unroll
+            for (int q = 0; q < 9; q++) {
+                const int b = tid * 9 + q;
+                v[q] = b <= TPC_MAX_ROWS ? hist[b] : 0;
+                sum += v[q];
+            }
+            int inc = sum;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, inc, o);
+                if (tid >= o) inc += y;
+            }
+            int run = inc - sum;
+#pragma unroll
+            for (int q = 0; q < 9; q++) {
+                const int b = tid * 9 + q;
+                if (b <= TPC_MAX_ROWS) hist[b] = run;
+                run += v[q];
+            }
+        }
+        __syncthreads();
+        const int pos = atomicAdd(&hist[len], 1);
+        s_t[pos] = tw;
+        s_len[pos] = len;
+        s_last[pos] = last;
+        __syncthreads();
+        // filter the chain of rank tid
+        const int t = s_t[tid];
+        const int n = s_len[tid];
+        const int hL = s_last[tid];
+        __syncthreads();  // the next round reuses hist and the rank arrays
+        if (n == 0) continue;
+        const int h0 = p.start[t];
         const int rr0 = p.t_row[t];
-        const int r0 = rr0 % k.n_rows, rL = r0 + len - 1;
-        const float2 c0 = p.hyz[h0], cL = p.hyz[h];
+        const int r0 = rr0 % k.n_rows, rL = r0 + n - 1;
+        const float2 c0 = p.hyz[h0], cL = p.hyz[hL];
         const float dx = row_x[rL] - row_x[r0], dy = cL.x - c0.x, dz = cL.y - c0.y;
         const float l = sqrtf(dx * dx + dy * dy);
         State st;
@@ -748,9 +800,9 @@ __global__ void k_seeds(KConst k, const float* __restrict__ row_x, DevPtrs p, in
         float chi2 = 0.0f;
         int r = r0, r_out = -1;
         bool failed = false;
-        h = h0;
-        for (int i = 0; i < len; i++) {
-            if (i > 0) h = i < kChainCache ? hc[i] : p.up2[h];
+        int h = h0;
+        for (int i = 0; i < n; i++) {
+            if (i > 0) h = p.up2[h];
             State pr = st;
             const float X = row_x[r];
             if (!propagate(pr, X, k.kB, k.s_max) || outside(pr, X, k)) {
@@ -768,7 +820,7 @@ __global__ void k_seeds(KConst k, const float* __restrict__ row_x, DevPtrs p, in
         dst[1] = make_float4(st.t, st.q, st.cy[0], st.cy[1]);
         dst[2] = make_float4(st.cy[2], st.cy[3], st.cy[4], st.cy[5]);
         dst[3] = make_float4(st.cz[0], st.cz[1], st.cz[2], chi2);
-        p.t_info[t] = make_int4(rr0, r, len, (r_out + 1) | (failed ? 1 << 16 : 0));
+        p.t_info[t] = make_int4(rr0, r, n, (r_out + 1) | (failed ? 1 << 16 : 0));
         p.owned[t] = 0;  // counted by the selection
     }
 }
@@ -778,8 +830,8 @@ cudaError_t launch_seeds(const KConst& k, const float* row_x_dev, const DevPtrs&
                          int u1, cudaStream_t s)
 {
     // enough threads for every tracklet at once: the chain walks are latency-bound
-    const int blocks = std::max(1, std::min((p.t_cap + 255) / 256, n_sm * 64));
-    k_seeds<<<blocks, 256, 0, s>>>(k, row_x_dev, p, u0, u1);
+    const int blocks = std::max(1, std::min((p.t_cap + kSeedThreads - 1) / kSeedThreads, n_sm * 64));
+    k_seeds<<<blocks, kSeedThreads, 0, s>>>(k, row_x_dev, p, u0, u1);
     return cudaGetLastError();
 }
 
