@@ -399,7 +399,7 @@ def run_ours(args):
     rl = None
     if algo is not None:
         t_s = stage_ms[dom] * 1e-3
-        # the headline: the scope table's per-cluster byte model of the stage
+        # the headline: the hot path's per-cluster byte model of the stage
         # (every stage reads its inputs and writes its outputs once: 55 B per
         # input cluster for tracklet construction) x the clusters of a launch
         survey = TRACKLET_SURVEY_BYTES_PER_CLUSTER * N
@@ -417,7 +417,7 @@ def run_ours(args):
               "counted_bytes_per_launch": algo["bytes"], "counted_model": algo["model"],
               # DRAM bytes of one launch (ncu) over the same time
               "frac_dram": (traffic / t_s / 1e9 / hbm) if traffic else None,
-              # the whole step against the scope table's 220 B per cluster
+              # the whole step against the model's 220 B per cluster
               "frac_step": STEP_SURVEY_BYTES_PER_CLUSTER * N / (ms * 1e-3) / 1e9 / hbm,
               "counts": {k: v for k, v in algo.items() if k not in ("bytes", "model")},
               "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy) of measured" if peaks else "fallback"}
@@ -778,6 +778,11 @@ def run_stream(tr0, pool, args, rate, batch=None, workload=MINBIAS_STREAM):
         backlog = []
         t_submit = t_poll = 0.0
         n_tracks = 0
+        # the client's own garbage collection would show as request latency:
+        # off while timing
+        import gc
+        gc.collect()
+        gc.disable()
         t0 = time.perf_counter()
         last = 0.0
         max_gap, max_gap_at = 0.0, 0.0   # the longest pass of the client loop (a host-side stall)
@@ -821,6 +826,7 @@ def run_stream(tr0, pool, args, rate, batch=None, workload=MINBIAS_STREAM):
                 clusters += len(pool[picks[i]][0])
                 done += 1
         wall = time.perf_counter() - t0
+        gc.enable()
         st = tr.stream_stats()
     finally:
         tr.close()
@@ -957,9 +963,10 @@ def measured_traffic(kernel_sources, summary):
         return None
 
 
-# Byte model of the scope table: tracklet construction moves about 55 B per
-# input cluster (about 2 row steps per cluster x (8 B bin entry + 16 B
-# candidate + 4 B hit id)); the whole step about 220 B per cluster.
+# Byte model of the hot path, each stage reading its inputs and writing its
+# outputs once: tracklet construction about 55 B per input cluster (about 2
+# row steps per cluster x (8 B bin entry + 16 B candidate + 4 B hit id)); the
+# whole step about 220 B per cluster.
 TRACKLET_SURVEY_BYTES_PER_CLUSTER = 55
 STEP_SURVEY_BYTES_PER_CLUSTER = 220
 TRACKLET_KERNEL = "k_tracklets_sched"
