@@ -476,6 +476,19 @@ struct Lane {
     int4 work;
 };
 
+// Row record through the read-only data path (the records are written by
+// the plan kernel and only read while tracklets are built).
+__device__ __forceinline__ RowGrid load_grid(const DevPtrs& p, int rr)
+{
+    const int4 v = __ldg(reinterpret_cast<const int4*>(p.grid) + rr);
+    RowGrid g;
+    g.inv_by = __int_as_float(v.x);
+    g.inv_bz = __int_as_float(v.y);
+    g.bin_base = v.z;
+    g.nyz = v.w;
+    return g;
+}
+
 __device__ __forceinline__ State load_state(const float* sp)
 {
     State s;
@@ -549,10 +562,9 @@ __device__ __forceinline__ void lane_init(Lane& L, int t, const KConst& k, const
     const int NR = k.n_rows;
     const int4 info = __ldg(p.t_info + t);
     const float4* src = p.t_state + (size_t)t * 4;
-    const int rr0 = info.x;
     L.t = t;
-    L.ubase = rr0 - rr0 % NR;
-    L.z0 = (((rr0 / NR) % k.n_sectors) < k.n_sectors / 2) ? 0.0f : -k.z_max;
+    L.ubase = info.x & 0x7fffffff;  // the unit's row 0; the sign bit: side C
+    L.z0 = info.x < 0 ? -k.z_max : 0.0f;
 #pragma unroll
     for (int i = 0; i < 4; i++) {
         const float4 v = __ldg(src + i);
@@ -570,7 +582,7 @@ __device__ __forceinline__ void lane_init(Lane& L, int t, const KConst& k, const
     if (CW) L.work = make_int4(0, 0, 0, info.z);
     const bool failed = (info.w >> 16) & 1;
     if ((failed || L.r >= NR) && !lane_end_phase1<CW>(L, k, p, writer)) return;
-    L.g = p.grid[L.ubase + L.r];
+    L.g = load_grid(p, L.ubase + L.r);
 }
 
 template <bool CW>
@@ -635,7 +647,7 @@ __device__ __forceinline__ void lane_step(Lane& L, const KConst& k, const float*
         }
         if (!lane_end_phase1<CW>(L, k, p, gl == 0)) return;
     }
-    L.g = p.grid[L.ubase + L.r];  // consumed by the next step; the load overlaps the loop
+    L.g = load_grid(p, L.ubase + L.r);  // consumed by the next step; the load overlaps the loop
 }
 
 // Persistent, dynamically scheduled constructor: idle lane groups take the
@@ -820,7 +832,11 @@ __global__ void __launch_bounds__(kSeedThreads) k_seeds(KConst k, const float* _
         dst[1] = make_float4(st.t, st.q, st.cy[0], st.cy[1]);
         dst[2] = make_float4(st.cy[2], st.cy[3], st.cy[4], st.cy[5]);
         dst[3] = make_float4(st.cz[0], st.cz[1], st.cz[2], chi2);
-        p.t_info[t] = make_int4(rr0, r, n, (r_out + 1) | (failed ? 1 << 16 : 0));
+        // the unit's row 0 with side C in the sign bit, so that the
+        // constructor starts a tracklet without integer divisions
+        const bool side_c = ((rr0 / k.n_rows) % k.n_sectors) >= k.n_sectors / 2;
+        p.t_info[t] = make_int4((rr0 - r0) | (side_c ? (int)0x80000000u : 0), r, n,
+                                (r_out + 1) | (failed ? 1 << 16 : 0));
         p.owned[t] = 0;  // counted by the selection
     }
 }

@@ -190,16 +190,18 @@ __global__ void k_grid(KConst k, const float* __restrict__ row_x, DevPtrs p, int
     }
     __syncthreads();
     block_scan_smem(hist, nb + 1);
-    for (int b = tid; b <= nb; b += nt) p.bin_off[g.bin_base + b] = off + hist[b];
+    if (tid == 0) p.bin_off[g.bin_base + nb] = off + hist[nb];  // the others with their bin below
     for (int i = tid; i < cnt; i += nt) {
         const float4 c = in[i];
         const int v = slot[i];
         out[hist[v >> 12] + (v & 4095)] = make_float4(c.y, c.z, c.w, __int_as_float(off + i));
     }
     __syncthreads();
-    // order inside each bin by id (insertion sort; bins hold a few clusters)
+    // bin table out, and order inside each bin by id (insertion sort; bins
+    // hold a few clusters)
     for (int b = tid; b < nb; b += nt) {
         const int s0 = hist[b], s1 = hist[b + 1];
+        p.bin_off[g.bin_base + b] = off + s0;
         for (int i = s0 + 1; i < s1; i++) {
             float4 v = out[i];
             unsigned idv = __float_as_uint(v.z);
@@ -351,7 +353,7 @@ __global__ void k_start_final(KConst k, DevPtrs p)
 // One warp per row: number its start hits by cluster id (rank = number of
 // start hits of the row with a smaller id).  Dense rows (time frames) hold
 // hundreds of start hits: they are ranked in shared memory too.
-constexpr int kStartWarps = 4;        // rows (warps) per CTA
+constexpr int kStartWarps = 2;        // rows (warps) per CTA
 constexpr int kStartWarpBuf = 1024;   // start hits ranked in shared memory; more use global reads
 
 __global__ void __launch_bounds__(32 * kStartWarps) k_start_write(KConst k, DevPtrs p, int rr0, int rows)
@@ -891,7 +893,9 @@ cudaError_t launch_emit(const KConst& k, const DevPtrs& p, int n_sm, cudaStream_
     if (nblk < 1) nblk = 1;
     k_scan_tiles<<<nblk, 256, 0, s>>>(p);
     k_scan_top<<<1, 1024, 0, s>>>(p);
-    k_emit<<<n_sm * 8, 256, 0, s>>>(k, p);
+    // many small CTAs: a warp takes about one tile of 32 tracklets, so the
+    // few tiles with several accepted tracks do not leave a long tail
+    k_emit<<<n_sm * 32, 128, 0, s>>>(k, p);
     return cudaGetLastError();
 }
 

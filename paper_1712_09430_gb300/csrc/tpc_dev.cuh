@@ -70,6 +70,7 @@ struct RowGrid {
     int bin_base;  // first entry of the row's bin table in bin_off
     int nyz;       // ny | nz << 16
 };
+static_assert(sizeof(RowGrid) == 16, "a row record is read as one 16-byte load");
 __host__ __device__ __forceinline__ int grid_ny(const RowGrid& g) { return g.nyz & 0xffff; }
 __host__ __device__ __forceinline__ int grid_nz(const RowGrid& g) { return g.nyz >> 16; }
 
@@ -94,8 +95,8 @@ struct DevPtrs {
     int* start;                // [Tcap] binned index of the start hit of t
     int* t_row;                // [Tcap] row index rr of the start hit of t
     float4* t_state;           // [Tcap][4] filter state after the seed chain (16 floats)
-    int4* t_info;              // [Tcap] row index rr of the start hit, row after the chain,
-                               // chain length, (outermost filtered row + 1) | failed << 16
+    int4* t_info;              // [Tcap] row index of the unit's row 0 | side C << 31, row after
+                               // the chain, chain length, (outermost filtered row + 1) | failed << 16
     int* sched;                // [Tcap] tracklets by expected length
     float* tl_f;               // [Tcap][16]
     int* tl_n;                 // [Tcap] Phase-2 cluster count
@@ -137,12 +138,16 @@ constexpr int kScanTile = 2048;  // elements per CTA in the multi-CTA scan
 
 // Bins of a row: the grid covers y in [-(X tan_h + y_margin), +...] and z in
 // the drift half of the sector's side; square bins sized for bin_target
-// clusters per bin; nbins <= cap (see row_bin_cap).
+// clusters per bin; nbins <= cap (see row_bin_cap).  The square bins give at
+// most nbt bins once both sides hold one or more; the 8 spare slots cover
+// rows so sparse that one side is a single bin (make_grid then trims the
+// grid to the cap).  The neighbour kernel copies three rows' tables into
+// shared memory, so slack here costs occupancy there.
 __host__ __device__ inline int row_bin_cap(int cnt, float bin_target)
 {
     int nbt = (int)ceilf((float)cnt / bin_target);
     if (nbt < 1) nbt = 1;
-    int cap = 2 * nbt + 8;
+    int cap = nbt + 8;
     return cap < kMaxBinsPerRow ? cap : kMaxBinsPerRow;
 }
 
