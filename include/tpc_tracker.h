@@ -295,6 +295,9 @@ int tpc_tracker_set_params(tpc_tracker* tr, const tpc_params* params);
  *               TPC_ERR_OUTPUT_TRUNCATED is returned with the required sizes
  *               in n_tracks / n_hits: the estimate-then-fetch-the-rest scheme
  *               of Sec. 3.1 (re-fetch with tpc_fetch_output, no recompute).
+ *               The part of the result the previous call's size predicts is
+ *               copied together with the counters, so entries past n_tracks
+ *               and n_hits, within the capacities, may be overwritten.
  *   cuda_stream a cudaStream_t to run on, or NULL for the tracker's own.
  * Errors: TPC_ERR_INVALID (NULL pointers, negative or oversize counts, NaN
  * coordinates, x off its row), TPC_ERR_NOMEM, TPC_ERR_DEVICE. */

@@ -226,7 +226,9 @@ __global__ void k_grid(KConst k, const float* __restrict__ row_x, DevPtrs p, int
 // ------------------------------------------------------ clean + start hits
 // up'[i] = up[i] if dn[up[i]] == i (and symmetric), from the pre-clean
 // arrays; start(i) = up'[i] >= 0, dn'[i] < 0 and a chain of >= l_seed hits.
-__global__ void k_clean(KConst k, DevPtrs p, int rr0, int rows)
+// The row's start hits are also listed, in row order, from the row's first
+// position of start_list on (ballot compaction), for the start-hit writer.
+__global__ void k_clean(KConst k, DevPtrs p, int rr0, int rows, int zero_owner)
 {
     if (stage_aborted(p.counters)) return;  // a stage before this one failed
     // one warp per row
@@ -236,28 +238,31 @@ __global__ void k_clean(KConst k, DevPtrs p, int rr0, int rows)
     const int rr = rr0 + w;
     const int b0 = p.row_off[rr], b1 = p.row_off[rr + 1];
     int nstart = 0;
-    for (int b = b0 + lane; b < b1; b += 32) {
-        int u = p.up[b], d = p.dn[b];
-        int u2 = (u >= 0 && p.dn[u] == b) ? u : -1;
-        int d2 = (d >= 0 && p.up[d] == b) ? d : -1;
-        p.up2[b] = u2;
-        p.dn2[b] = d2;
-        p.owner[b] = 0u;  // selection starts from no owner
+    for (int c0 = b0; c0 < b1; c0 += 32) {
+        const int b = c0 + lane;
         int st = 0;
-        if (u2 >= 0 && d2 < 0) {
-            int len = 2, j = u2;
-            while (len < k.l_seed) {
-                int nx = p.up[j];
-                if (nx < 0 || p.dn[nx] != j) break;
-                j = nx;
-                len++;
+        if (b < b1) {
+            int u = p.up[b], d = p.dn[b];
+            int u2 = (u >= 0 && p.dn[u] == b) ? u : -1;
+            int d2 = (d >= 0 && p.up[d] == b) ? d : -1;
+            p.up2[b] = u2;
+            p.dn2[b] = d2;
+            if (zero_owner) p.owner[b] = 0u;  // global-atomic selection starts from no owner
+            if (u2 >= 0 && d2 < 0) {
+                int len = 2, j = u2;
+                while (len < k.l_seed) {
+                    int nx = p.up[j];
+                    if (nx < 0 || p.dn[nx] != j) break;
+                    j = nx;
+                    len++;
+                }
+                st = len >= k.l_seed;
             }
-            st = len >= k.l_seed;
         }
-        p.is_start[b] = (unsigned char)st;
-        nstart += st;
+        const unsigned bal = __ballot_sync(0xffffffffu, st);
+        if (st) p.start_list[b0 + nstart + __popc(bal & ((1u << lane) - 1u))] = b;
+        nstart += __popc(bal);
     }
-    nstart = __reduce_add_sync(0xffffffffu, nstart);
     if (lane == 0) p.row_nstart[rr] = nstart;
 }
 
@@ -376,22 +381,14 @@ __global__ void __launch_bounds__(32 * kStartWarps) k_start_write(KConst k, DevP
     s0 = __shfl_sync(0xffffffffu, s0, 0);
     unsigned* sid = sid_sh[wib];
     int* sb = sb_sh[wib];
-    const int b0 = p.row_off[rr], b1 = p.row_off[rr + 1];
-    // compact the row's start hits (ballot prefix), in row order
-    int n = 0;
-    for (int c0 = b0; c0 < b1; c0 += 32) {
-        const int b = c0 + lane;
-        const bool st = b < b1 && p.is_start[b];
-        const unsigned bal = __ballot_sync(0xffffffffu, st);
-        const int pos = n + __popc(bal & ((1u << lane) - 1u));
-        if (st && pos < kStartWarpBuf) {
-            sid[pos] = __float_as_uint(p.hits[b].z);
-            sb[pos] = b;
-        }
-        n += __popc(bal);
-    }
-    __syncwarp();
+    const int* list = p.start_list + p.row_off[rr];  // the row's start hits, in row order
     if (m <= kStartWarpBuf) {
+        for (int i = lane; i < m; i += 32) {
+            const int b = list[i];
+            sb[i] = b;
+            sid[i] = __float_as_uint(p.hits[b].z);
+        }
+        __syncwarp();
         for (int i = lane; i < m; i += 32) {
             const unsigned v = sid[i];
             int rank = 0;
@@ -403,11 +400,11 @@ __global__ void __launch_bounds__(32 * kStartWarps) k_start_write(KConst k, DevP
         }
     } else {
         // many start hits in one row: rank straight from global memory
-        for (int b = b0 + lane; b < b1; b += 32) {
-            if (!p.is_start[b]) continue;
+        for (int i = lane; i < m; i += 32) {
+            const int b = list[i];
             const unsigned v = __float_as_uint(p.hits[b].z);
             int rank = 0;
-            for (int j = b0; j < b1; j++) rank += p.is_start[j] && __float_as_uint(p.hits[j].z) < v;
+            for (int j = 0; j < m; j++) rank += __float_as_uint(p.hits[list[j]].z) < v;
             const int t = t0 + rank;
             p.start[t] = b;
             p.t_row[t] = rr;
@@ -828,12 +825,12 @@ cudaError_t launch_grid(const KConst& k, const float* row_x_dev, const DevPtrs& 
 }
 
 cudaError_t launch_clean(const KConst& k, const DevPtrs& p, int threads, int unit0, int n_units,
-                         cudaStream_t s)
+                         bool zero_owner, cudaStream_t s)
 {
     (void)threads;
     const int rows = n_units * k.n_rows;
     if (rows == 0) return cudaSuccess;
-    k_clean<<<(rows + 7) / 8, 256, 0, s>>>(k, p, unit0 * k.n_rows, rows);  // a warp per row
+    k_clean<<<(rows + 7) / 8, 256, 0, s>>>(k, p, unit0 * k.n_rows, rows, zero_owner ? 1 : 0);  // a warp per row
     return cudaGetLastError();
 }
 

@@ -151,7 +151,7 @@ extern "C" int tpc_links_noalloc(const tpc_geometry* g, const tpc_params* params
     const size_t o_hyz = take((n + 2) * 8);  // + a pad entry read by whole-pair copies
     const size_t o_bins = take((size_t)bins * 4);
     const size_t o_up = take(n * 4), o_dn = take(n * 4), o_up2 = take(n * 4), o_dn2 = take(n * 4);
-    const size_t o_start = take(n);
+    const size_t o_start = take(n * 4);
     const size_t o_nstart = take((size_t)R * 4);
     const size_t o_owner = take(n * 4);
     const size_t o_count = take(kNumCounters * 4);
@@ -183,7 +183,7 @@ extern "C" int tpc_links_noalloc(const tpc_geometry* g, const tpc_params* params
     p.dn = reinterpret_cast<int*>(base + o_dn);
     p.up2 = reinterpret_cast<int*>(base + o_up2);
     p.dn2 = reinterpret_cast<int*>(base + o_dn2);
-    p.is_start = reinterpret_cast<unsigned char*>(base + o_start);
+    p.start_list = reinterpret_cast<int*>(base + o_start);
     p.row_nstart = reinterpret_cast<int*>(base + o_nstart);
     p.owner = reinterpret_cast<unsigned*>(base + o_owner);
     p.counters = reinterpret_cast<int*>(base + o_count);
@@ -207,7 +207,7 @@ extern "C" int tpc_links_noalloc(const tpc_geometry* g, const tpc_params* params
     if (e == cudaSuccess)
         e = P.exact_fp32 ? tpc_exact::launch_neighbours(k, xd, p, max3, max_slots3, P.threads_per_row, 0, S, s)
                          : tpc_fast::launch_neighbours(k, xd, p, max3, max_slots3, P.threads_per_row, 0, S, s);
-    if (e == cudaSuccess) e = tpc_int::launch_clean(k, p, P.threads_per_row, 0, S, s);
+    if (e == cudaSuccess) e = tpc_int::launch_clean(k, p, P.threads_per_row, 0, S, true, s);
     if (e == cudaSuccess) e = tpc_int::launch_dump_links(p, 1, d_links, s);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(g_counters, p.counters, sizeof g_counters, cudaMemcpyDeviceToHost, s);

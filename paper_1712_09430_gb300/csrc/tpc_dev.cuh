@@ -88,7 +88,7 @@ struct DevPtrs {
     int* dn;
     int* up2;                  // [N] after cleaning
     int* dn2;
-    unsigned char* is_start;   // [N]
+    int* start_list;           // [N] each row's start hits in row order, from the row's first position
     int* row_nstart;           // [R]
     int* start_off;            // [R + 1] canonical tracklet offsets per row
     int* sched_off;            // [R + 1] schedule offsets (row-major order)
@@ -294,7 +294,7 @@ cudaError_t launch_plan(const tpc::KConst& k, const float* row_x_dev, const tpc:
 cudaError_t launch_grid(const tpc::KConst& k, const float* row_x_dev, const tpc::DevPtrs& p,
                         int max_row, int max_slots, int threads, int unit0, int n_units, cudaStream_t s);
 cudaError_t launch_clean(const tpc::KConst& k, const tpc::DevPtrs& p, int threads, int unit0,
-                         int n_units, cudaStream_t s);
+                         int n_units, bool zero_owner, cudaStream_t s);
 cudaError_t launch_start_scan(const tpc::KConst& k, const tpc::DevPtrs& p, cudaStream_t s);
 cudaError_t launch_start_write(const tpc::KConst& k, const tpc::DevPtrs& p, int threads, int unit0,
                                int n_units, cudaStream_t s);

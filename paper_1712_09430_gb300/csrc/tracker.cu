@@ -287,7 +287,7 @@ size_t tpc_layout(const tpc_tracker* tr, const BatchShape& sh, DevPtrs* p, char*
     q.dn = reinterpret_cast<int*>(take(N * 4));
     q.up2 = reinterpret_cast<int*>(take(N * 4));
     q.dn2 = reinterpret_cast<int*>(take(N * 4));
-    q.is_start = reinterpret_cast<unsigned char*>(take(N));
+    q.start_list = reinterpret_cast<int*>(take(N * 4));
     q.row_nstart = reinterpret_cast<int*>(take(R * 4));
     q.start_off = reinterpret_cast<int*>(take((R + 1) * 4));
     q.sched_off = reinterpret_cast<int*>(take((R + 1) * 4));
@@ -497,7 +497,8 @@ int tpc_enqueue(tpc_tracker* tr, const DevPtrs& p, const BatchShape& sh, cudaStr
         if (with_events) TPC_CUDA(cudaEventRecord(tr->ev[1], s));
         TPC_CUDA(nb(k, xd, p, sh.max3, sh.max_slots3, th, 0, sh.n_units, s));
         if (with_events) TPC_CUDA(cudaEventRecord(tr->ev[2], s));
-        TPC_CUDA(tpc_int::launch_clean(k, p, th, 0, sh.n_units, s));
+        // the per-unit ownership kernel writes every owner key itself
+        TPC_CUDA(tpc_int::launch_clean(k, p, th, 0, sh.n_units, false, s));
         TPC_CUDA(tpc_int::launch_start_scan(k, p, s));
         TPC_CUDA(tpc_int::launch_start_write(k, p, th, 0, sh.n_units, s));
         TPC_CUDA(seeds(0, sh.n_units, s));
@@ -539,7 +540,7 @@ int tpc_enqueue(tpc_tracker* tr, const DevPtrs& p, const BatchShape& sh, cudaStr
             cudaStream_t q = tr->queues[(size_t)(u % nq)];
             TPC_CUDA(tpc_int::launch_grid(k, xd, p, sh.max_row, sh.max_slots, th, u, 1, q));
             TPC_CUDA(nb(k, xd, p, sh.max3, sh.max_slots3, th, u, 1, q));
-            TPC_CUDA(tpc_int::launch_clean(k, p, th, u, 1, q));
+            TPC_CUDA(tpc_int::launch_clean(k, p, th, u, 1, true, q));
         }
         rc = join();
         if (rc != TPC_OK) return rc;
@@ -568,7 +569,7 @@ int tpc_enqueue(tpc_tracker* tr, const DevPtrs& p, const BatchShape& sh, cudaStr
         if (with_events) TPC_CUDA(cudaEventRecord(tr->ev[1], s));
         for (int u = 0; u < sh.n_units; u++) TPC_CUDA(nb(k, xd, p, sh.max3, sh.max_slots3, th, u, 1, s));
         if (with_events) TPC_CUDA(cudaEventRecord(tr->ev[2], s));
-        for (int u = 0; u < sh.n_units; u++) TPC_CUDA(tpc_int::launch_clean(k, p, th, u, 1, s));
+        for (int u = 0; u < sh.n_units; u++) TPC_CUDA(tpc_int::launch_clean(k, p, th, u, 1, true, s));
         TPC_CUDA(tpc_int::launch_start_scan(k, p, s));
         for (int u = 0; u < sh.n_units; u++) {
             TPC_CUDA(tpc_int::launch_start_write(k, p, th, u, 1, s));
@@ -640,12 +641,10 @@ int tpc_run_stages(tpc_tracker* tr, const DevPtrs& p, const BatchShape& sh, cuda
     return TPC_OK;
 }
 
-// Read counters after the stages; checks the device error bits.
-static int finish_counters(tpc_tracker* tr, cudaStream_t s)
+// The counters of the last call, read back to the host: checks the device
+// error bits and keeps the result sizes.
+static int check_counters(tpc_tracker* tr)
 {
-    TPC_CUDA(cudaMemcpyAsync(tr->counters_host, tr->cur.counters, sizeof(int) * kNumCounters,
-                             cudaMemcpyDeviceToHost, s));
-    TPC_CUDA(cudaStreamSynchronize(s));
     const int* c = tr->counters_host;
     if (c[C_ERR] & E_INPUT) {
         int rr = c[C_BADROW] - 1;
@@ -664,34 +663,58 @@ static int finish_counters(tpc_tracker* tr, cudaStream_t s)
     return TPC_OK;
 }
 
-// Copy the device result into out.  Estimate first (the previous result size
-// with margin), fetch the rest if the estimate was short (Sec. 3.1).
-int tpc_copy_out(tpc_tracker* tr, const DevPtrs& p, int M, int MH, tpc_output* out, cudaStream_t s)
+// Enqueue the copies of tracks [t0, t1) and hits [h0, h1) of the device
+// result into out (with the refit, merge and collision records of the same
+// tracks when they are on and asked for).
+static int enqueue_out(tpc_tracker* tr, const DevPtrs& p, tpc_output* out, int t0, int t1, int h0, int h1,
+                       cudaStream_t s)
+{
+    const cudaMemcpyKind kind = out->mem_kind == TPC_MEM_DEVICE ? cudaMemcpyDeviceToDevice
+                                                                : cudaMemcpyDeviceToHost;
+    if (t1 > t0) {
+        if (!out->tracks) return tr->fail(TPC_ERR_INVALID, "NULL tracks buffer");
+        const size_t n = (size_t)(t1 - t0);
+        TPC_CUDA(cudaMemcpyAsync(static_cast<tpc_track*>(out->tracks) + t0, p.out_tracks + t0,
+                                 sizeof(tpc_track) * n, kind, s));
+        if (out->fits && tr->params.refit)
+            TPC_CUDA(cudaMemcpyAsync(static_cast<tpc_fit*>(out->fits) + t0, p.out_fits + t0,
+                                     sizeof(tpc_fit) * n, kind, s));
+        if (out->merges && tr->params.merge)
+            TPC_CUDA(cudaMemcpyAsync(static_cast<tpc_merge*>(out->merges) + t0, p.out_merges + t0,
+                                     sizeof(tpc_merge) * n, kind, s));
+        if (out->t0s && tr->params.t0)
+            TPC_CUDA(cudaMemcpyAsync(static_cast<tpc_t0*>(out->t0s) + t0, p.out_t0s + t0,
+                                     sizeof(tpc_t0) * n, kind, s));
+    }
+    if (h1 > h0) {
+        if (!out->hit_ids) return tr->fail(TPC_ERR_INVALID, "NULL hit_ids buffer");
+        TPC_CUDA(cudaMemcpyAsync(static_cast<int*>(out->hit_ids) + h0, p.out_hits + h0,
+                                 sizeof(int) * (size_t)(h1 - h0), kind, s));
+    }
+    return TPC_OK;
+}
+
+// Copy the device result into out, the part from track t_done and hit
+// h_done on (the part before is there already), and wait for it.
+static int copy_out_rest(tpc_tracker* tr, const DevPtrs& p, int M, int MH, tpc_output* out, cudaStream_t s,
+                         int t_done, int h_done)
 {
     if (!out) return tr->fail(TPC_ERR_INVALID, "NULL output");
     out->n_tracks = M;
     out->n_hits = MH;
-    const cudaMemcpyKind kind = out->mem_kind == TPC_MEM_DEVICE ? cudaMemcpyDeviceToDevice
-                                                                : cudaMemcpyDeviceToHost;
     const int mt = std::min(M, std::max(out->cap_tracks, 0));
     const int mh = std::min(MH, std::max(out->cap_hits, 0));
-    if (mt > 0) {
-        if (!out->tracks) return tr->fail(TPC_ERR_INVALID, "NULL tracks buffer");
-        TPC_CUDA(cudaMemcpyAsync(out->tracks, p.out_tracks, sizeof(tpc_track) * mt, kind, s));
-    }
-    if (mh > 0) {
-        if (!out->hit_ids) return tr->fail(TPC_ERR_INVALID, "NULL hit_ids buffer");
-        TPC_CUDA(cudaMemcpyAsync(out->hit_ids, p.out_hits, sizeof(int) * mh, kind, s));
-    }
-    if (mt > 0 && out->fits && tr->params.refit)
-        TPC_CUDA(cudaMemcpyAsync(out->fits, p.out_fits, sizeof(tpc_fit) * mt, kind, s));
-    if (mt > 0 && out->merges && tr->params.merge)
-        TPC_CUDA(cudaMemcpyAsync(out->merges, p.out_merges, sizeof(tpc_merge) * mt, kind, s));
-    if (mt > 0 && out->t0s && tr->params.t0)
-        TPC_CUDA(cudaMemcpyAsync(out->t0s, p.out_t0s, sizeof(tpc_t0) * mt, kind, s));
+    int rc = enqueue_out(tr, p, out, std::min(t_done, mt), mt, std::min(h_done, mh), mh, s);
+    if (rc != TPC_OK) return rc;
     TPC_CUDA(cudaStreamSynchronize(s));
     if (mt < M || mh < MH) return tr->fail(TPC_ERR_OUTPUT_TRUNCATED, "output capacity too small");
     return TPC_OK;
+}
+
+// Copy the device result into out (the whole of it).
+int tpc_copy_out(tpc_tracker* tr, const DevPtrs& p, int M, int MH, tpc_output* out, cudaStream_t s)
+{
+    return copy_out_rest(tr, p, M, MH, out, s, 0, 0);
 }
 
 extern "C" int tpc_track_sectors(tpc_tracker* tr, const tpc_cluster* clusters, const int32_t* row_counts,
@@ -735,11 +758,22 @@ extern "C" int tpc_track_sectors(tpc_tracker* tr, const tpc_cluster* clusters, c
     tr->last_counted = tr->params.count_work != 0 || tr->params.plain_per_sector != 0;
     rc = tpc_run_stages(tr, p, sh, s);
     if (rc != TPC_OK) return rc;
-    rc = finish_counters(tr, s);
+    // Estimate first, fetch the rest if the estimate was short (Sec. 3.1):
+    // the counters and the expected part of the output (the previous
+    // result's size with a margin, within the capacities) go out together,
+    // so that a result of the expected size takes one round trip to the
+    // host.  Output entries past n_tracks / n_hits may be overwritten.
+    const int est_t = std::min(std::max(out->cap_tracks, 0), tr->last_M + tr->last_M / 16 + 64);
+    const int est_h = std::min(std::max(out->cap_hits, 0), tr->last_MH + tr->last_MH / 16 + 1024);
+    TPC_CUDA(cudaMemcpyAsync(tr->counters_host, p.counters, sizeof(int) * kNumCounters, cudaMemcpyDeviceToHost, s));
+    rc = enqueue_out(tr, p, out, 0, est_t, 0, est_h, s);
+    if (rc != TPC_OK) return rc;
+    TPC_CUDA(cudaStreamSynchronize(s));
+    rc = check_counters(tr);
     if (rc != TPC_OK) return rc;
     tr->has_result = true;
     tr->last_stream = s;
-    return tpc_copy_out(tr, p, tr->last_M, tr->last_MH, out, s);
+    return copy_out_rest(tr, p, tr->last_M, tr->last_MH, out, s, est_t, est_h);
 }
 
 extern "C" int tpc_fetch_output(tpc_tracker* tr, tpc_output* out)
