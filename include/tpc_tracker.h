@@ -165,6 +165,12 @@ typedef struct {
                                 TPC_ERR_TIMEOUT (the copies still land before
                                 the kernel returns; the next call with 0 is
                                 unaffected).  Not for production use.          */
+    /* execution (continued) */
+    int lanes_per_hit;       /* 1, 2, 4 or 8: lanes of a warp that share one
+                                hit in the neighbour finder (1: one thread per
+                                hit; more: the lanes split the hit's window
+                                candidates, compact them by warp ballot and
+                                reduce the best pair by warp shuffles)         */
 } tpc_params;
 
 /* A selected track: the best tracklet instance (Sec. 2 step 2), with the
@@ -277,8 +283,9 @@ int tpc_tracker_create(const tpc_geometry* g, double bz_tesla, const tpc_params*
 void tpc_tracker_destroy(tpc_tracker* tr);
 
 /* Change the execution fields of the parameters (exact_fp32, bin_target,
- * threads_per_row, tracklets_per_warp, plain_per_sector, use_graph) and,
- * if given, the method constants (Sec. 2 readings).  params is copied.
+ * threads_per_row, tracklets_per_warp, lanes_per_hit, plain_per_sector,
+ * use_graph) and, if given, the method constants (Sec. 2 readings).  params
+ * is copied.
  * TPC_ERR_INVALID for out-of-range values (nothing changes); not allowed
  * while stream tickets are in flight (TPC_BUSY). */
 int tpc_tracker_set_params(tpc_tracker* tr, const tpc_params* params);
@@ -315,7 +322,8 @@ int tpc_fetch_output(tpc_tracker* tr, tpc_output* out);
  * fixed best shape on a new GPU; the paper tunes its number of command
  * queues the same way, Fig. 3).  Runs the batch given exactly as
  * tpc_track_sectors would, for candidate values of schedule, bin_target,
- * tracklets_per_warp and threads_per_row (coordinate descent, two passes,
+ * tracklets_per_warp, threads_per_row and lanes_per_hit (coordinate
+ * descent, two passes,
  * each candidate scored by the median device time of `reps` runs), keeps
  * the fastest in the tracker and writes it to *best (may be NULL).
  * Results do not depend on these fields, so tuning never changes output.

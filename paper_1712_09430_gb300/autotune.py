@@ -1,6 +1,6 @@
 """Autotuner front end: tpc_autotune (native, in libtpcca.so) picks the
 execution fields -- schedule, grid bin size, tracklets per warp, threads per
-row -- for a workload by timing it on the device; this module keeps the
+row, lanes per hit of the neighbour finder -- for a workload by timing it on the device; this module keeps the
 winners in a JSON cache keyed by GPU and workload shape, so a serving
 process tunes once per workload class.
 
@@ -18,7 +18,7 @@ import numpy as np
 from . import capi
 from .capi import lib
 
-FIELDS = ("schedule", "bin_target", "tracklets_per_warp", "threads_per_row")
+FIELDS = ("schedule", "bin_target", "tracklets_per_warp", "threads_per_row", "lanes_per_hit")
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "tpc_gb300_autotune.json")
 
 
@@ -53,7 +53,7 @@ def tune(tracker, clusters, row_counts, n_events, reps=3, cache_path=None, devic
     without timing, and new choices are stored.  Returns (fields, ms)."""
     key = workload_key(row_counts, n_events, device_name)
     cache = load_cache(cache_path) if cache_path else {}
-    if key in cache:
+    if key in cache and all(f in cache[key] for f in FIELDS):
         tracker.set_params(**{f: cache[key][f] for f in FIELDS})
         return {f: cache[key][f] for f in FIELDS}, cache[key].get("ms")
     rc_arr = np.ascontiguousarray(row_counts, dtype=np.int32)

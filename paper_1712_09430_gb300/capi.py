@@ -63,7 +63,8 @@ class tpc_params(C.Structure):
                 ("merge_overlap", C.c_float), ("merge_window", C.c_float),
                 ("t0", C.c_int), ("t0_y_cut", C.c_float), ("t0_bin", C.c_float),
                 ("t0_radius", C.c_float), ("t0_window", C.c_int), ("t0_n_min", C.c_int),
-                ("count_work", C.c_int), ("debug_wait_polls", C.c_int)]
+                ("count_work", C.c_int), ("debug_wait_polls", C.c_int),
+                ("lanes_per_hit", C.c_int)]
 
 
 class tpc_track(C.Structure):

@@ -41,6 +41,18 @@ using namespace tpc;
 //   y_p = y_d + (y_u - y_d) tt, z_p = z_d + (z_u - z_d) tt,
 //   D = (y_i - y_p)^2 + (z_i - z_p)^2, kept if D <= d_max2;
 // the pair with the smallest D wins, ties by smaller id_u, then id_d.
+//
+// G > 1 (warp-cooperative form): G lanes of a warp share one hit of row r.
+// The lanes of a group take every G-th candidate of the hit's down window,
+// compact the ones inside it into a per-group list in shared memory (ballot,
+// then popc of the lanes below), take every G-th candidate of the up window,
+// pair each one inside it with the whole list, and reduce the group's best
+// (D, id_u, id_d) with shuffles.  Every pair is considered once and the
+// order is a strict total order (ids are unique in a row), so the links are
+// the ones of the one-thread-per-hit form (G = 1), bit for bit.
+constexpr int kNbList = 8;  // down candidates listed per group; more: rescan
+
+template <int G>
 __global__ void k_neighbours(KConst k, const float* __restrict__ row_x, DevPtrs p, int unit0)
 {
     if (stage_aborted(p.counters)) return;  // a stage before this one failed
@@ -101,7 +113,16 @@ __global__ void k_neighbours(KConst k, const float* __restrict__ row_x, DevPtrs 
     }
     const float2* recm = rec + cnt_d;
     auto id_of = [&](int j) { return __float_as_uint(__ldg(&p.hits[off_d + j].z)); };
-    for (int i = tid; i < cnt_m; i += nt) {
+    // G = 1: thread tid takes hits tid, tid + nt, ...; G > 1: lane group
+    // tid / G takes hits tid / G, tid / G + nt / G, ... (a bound uniform in
+    // the group, so its ballots and shuffles see every lane of the group)
+    const int gl = tid & (G - 1);
+    const unsigned gmask = G == 1 ? 0u : (((1u << G) - 1u) << ((tid & 31) - gl));
+    // the groups' lists follow the bin tables (16-byte aligned; one pad
+    // entry per list so that the groups of a warp use different banks)
+    float4* list = reinterpret_cast<float4*>(smem + ((16u + (unsigned)n2 * 8u + (unsigned)n_bins3 * 4u + 15u) & ~15u)) +
+                   (tid / G) * (kNbList + 1);
+    for (int i = tid / G; i < cnt_m; i += nt / G) {
         const float2 ci = recm[i];
         const float yi = ci.x, zi = ci.y;
         const float ycu = yi * Ru, ycd = yi * Rd;
@@ -118,11 +139,19 @@ __global__ void k_neighbours(KConst k, const float* __restrict__ row_x, DevPtrs 
         float bD = 0.0f;
         // pair (u, d) -> keep the best by (D, id_u, id_d)
         auto consider = [&](int ju, const float2& cu, int jd, const float2& cd) {
+#if TPC_FAST_MATH  // the multiply-adds spelled out, so every form rounds alike
+            const float yp = __fmaf_rn(cu.x - cd.x, tt, cd.x);
+            const float zp = __fmaf_rn(cu.y - cd.y, tt, cd.y);
+            const float ey = yi - yp;
+            const float ez = zi - zp;
+            const float D = __fmaf_rn(ey, ey, ez * ez);
+#else
             const float yp = cd.x + (cu.x - cd.x) * tt;
             const float zp = cd.y + (cu.y - cd.y) * tt;
             const float ey = yi - yp;
             const float ez = zi - zp;
             const float D = ey * ey + ez * ez;
+#endif
             if (!(D <= k.d_max2)) return;
             bool better;
             if (bu < 0 || D < bD) {
@@ -158,39 +187,125 @@ __global__ void k_neighbours(KConst k, const float* __restrict__ row_x, DevPtrs 
                 for (int j = j0; j < j1; j++) f(j);
             }
         };
-        // down candidates once, into a register list of up to 4
-        int nd = 0;
-        int jd0 = -1, jd1 = -1, jd2 = -1, jd3 = -1;
-        float2 cd0 = make_float2(0.f, 0.f), cd1 = cd0, cd2 = cd0, cd3 = cd0;
-        for_window(td, nyd, dy0, dy1, dz0, dz1, [&](int jd) {
-            const float2 cd = rec[jd];
-            if (fabsf(cd.x - ycd) <= Wd && fabsf(cd.y - zi) <= Wd) {
-                jd3 = jd2; cd3 = cd2;
-                jd2 = jd1; cd2 = cd1;
-                jd1 = jd0; cd1 = cd0;
-                jd0 = jd; cd0 = cd;
-                nd++;
-            }
-        });
-        if (nd > 0) {
-            for_window(tu, nyu, uy0, uy1, uz0, uz1, [&](int ju) {
-                const float2 cu = rec[ju];
-                if (!(fabsf(cu.x - ycu) <= Wu && fabsf(cu.y - zi) <= Wu)) return;
-                if (nd <= 4) {
-                    consider(ju, cu, jd0, cd0);
-                    if (nd > 1) consider(ju, cu, jd1, cd1);
-                    if (nd > 2) consider(ju, cu, jd2, cd2);
-                    if (nd > 3) consider(ju, cu, jd3, cd3);
-                } else {  // a crowded window: scan the down row again
-                    for_window(td, nyd, dy0, dy1, dz0, dz1, [&](int jd) {
-                        const float2 cd = rec[jd];
-                        if (fabsf(cd.x - ycd) <= Wd && fabsf(cd.y - zi) <= Wd) consider(ju, cu, jd, cd);
-                    });
+        if constexpr (G == 1) {
+            // down candidates once, into a register list of up to 4
+            int nd = 0;
+            int jd0 = -1, jd1 = -1, jd2 = -1, jd3 = -1;
+            float2 cd0 = make_float2(0.f, 0.f), cd1 = cd0, cd2 = cd0, cd3 = cd0;
+            for_window(td, nyd, dy0, dy1, dz0, dz1, [&](int jd) {
+                const float2 cd = rec[jd];
+                if (fabsf(cd.x - ycd) <= Wd && fabsf(cd.y - zi) <= Wd) {
+                    jd3 = jd2; cd3 = cd2;
+                    jd2 = jd1; cd2 = cd1;
+                    jd1 = jd0; cd1 = cd0;
+                    jd0 = jd; cd0 = cd;
+                    nd++;
                 }
             });
+            if (nd > 0) {
+                for_window(tu, nyu, uy0, uy1, uz0, uz1, [&](int ju) {
+                    const float2 cu = rec[ju];
+                    if (!(fabsf(cu.x - ycu) <= Wu && fabsf(cu.y - zi) <= Wu)) return;
+                    if (nd <= 4) {
+                        consider(ju, cu, jd0, cd0);
+                        if (nd > 1) consider(ju, cu, jd1, cd1);
+                        if (nd > 2) consider(ju, cu, jd2, cd2);
+                        if (nd > 3) consider(ju, cu, jd3, cd3);
+                    } else {  // a crowded window: scan the down row again
+                        for_window(td, nyd, dy0, dy1, dz0, dz1, [&](int jd) {
+                            const float2 cd = rec[jd];
+                            if (fabsf(cd.x - ycd) <= Wd && fabsf(cd.y - zi) <= Wd) consider(ju, cu, jd, cd);
+                        });
+                    }
+                });
+            }
+        } else {
+            // Down window: lane gl tests candidates gl, gl + G, ...; the ones
+            // inside the window go to the group's list in the order found.
+            auto group_window = [&](int tab, int ny, int y0b, int y1b, int z0b, int z1b, auto&& f) {
+                const int* rb = bins + tab + y0b;
+                const int span = y1b - y0b + 1;
+                const int a0 = rb[z0b * ny] - off_d, a1 = rb[z0b * ny + span] - off_d;
+                int b0 = 0, b1 = 0;
+                if (z1b > z0b) {
+                    b0 = rb[(z0b + 1) * ny] - off_d;
+                    b1 = rb[(z0b + 1) * ny + span] - off_d;
+                }
+                const int na = a1 - a0, ntot = na + (b1 - b0);
+                for (int c0 = 0; c0 < ntot; c0 += G) {
+                    const int c = c0 + gl;
+                    f(c < na ? a0 + c : b0 + (c - na), c < ntot);
+                }
+                for (int bz = z0b + 2; bz <= z1b; bz++) {
+                    const int j0 = rb[bz * ny] - off_d, j1 = rb[bz * ny + span] - off_d;
+                    for (int c0 = j0; c0 < j1; c0 += G) f(c0 + gl, c0 + gl < j1);
+                }
+            };
+            int nd = 0;  // the same in every lane of the group
+            group_window(td, nyd, dy0, dy1, dz0, dz1, [&](int jd, bool valid) {
+                float2 cd = make_float2(0.f, 0.f);
+                bool in = false;
+                if (valid) {
+                    cd = rec[jd];
+                    in = fabsf(cd.x - ycd) <= Wd && fabsf(cd.y - zi) <= Wd;
+                }
+                const unsigned bal = __ballot_sync(gmask, in) & gmask;
+                if (in) {
+                    const int slot = nd + __popc(bal & ((1u << (tid & 31)) - 1u));
+                    if (slot < kNbList) list[slot] = make_float4(cd.x, cd.y, __int_as_float(jd), 0.f);
+                }
+                nd += __popc(bal);
+            });
+            if (nd > 0) {
+                __syncwarp(gmask);  // the list is written
+                // Up window: lane gl takes candidates gl, gl + G, ... and
+                // pairs each one inside the window with the whole list.
+                group_window(tu, nyu, uy0, uy1, uz0, uz1, [&](int ju, bool valid) {
+                    if (!valid) return;
+                    const float2 cu = rec[ju];
+                    if (!(fabsf(cu.x - ycu) <= Wu && fabsf(cu.y - zi) <= Wu)) return;
+                    if (nd <= kNbList) {
+                        for (int d = 0; d < nd; d++) {
+                            const float4 e = list[d];
+                            consider(ju, cu, __float_as_int(e.z), make_float2(e.x, e.y));
+                        }
+                    } else {  // a crowded window: scan the down row again
+                        for_window(td, nyd, dy0, dy1, dz0, dz1, [&](int jd) {
+                            const float2 cd = rec[jd];
+                            if (fabsf(cd.x - ycd) <= Wd && fabsf(cd.y - zi) <= Wd) consider(ju, cu, jd, cd);
+                        });
+                    }
+                });
+                // the group's best by (D, id_u, id_d)
+#pragma unroll
+                for (int o = G / 2; o > 0; o >>= 1) {
+                    const int ou = __shfl_xor_sync(gmask, bu, o);
+                    const int od = __shfl_xor_sync(gmask, bd, o);
+                    const float oD = __shfl_xor_sync(gmask, bD, o);
+                    if (ou >= 0) {
+                        bool better;
+                        if (bu < 0 || oD < bD) {
+                            better = true;
+                        } else if (oD > bD) {
+                            better = false;
+                        } else {  // exact tie between two lanes' pairs
+                            const unsigned iou = id_of(ou), ibu = id_of(bu);
+                            better = iou != ibu ? iou < ibu : id_of(od) < id_of(bd);
+                        }
+                        if (better) {
+                            bu = ou;
+                            bd = od;
+                            bD = oD;
+                        }
+                    }
+                }
+            }
+            __syncwarp(gmask);  // the list is read before the group's next hit rewrites it
         }
-        p.up[off_m + i] = bu >= 0 ? off_d + bu : -1;
-        p.dn[off_m + i] = bd >= 0 ? off_d + bd : -1;
+        if (G == 1 || gl == 0) {
+            p.up[off_m + i] = bu >= 0 ? off_d + bu : -1;
+            p.dn[off_m + i] = bd >= 0 ? off_d + bd : -1;
+        }
     }
 }
 
@@ -851,19 +966,33 @@ cudaError_t launch_seeds(const KConst& k, const float* row_x_dev, const DevPtrs&
     return cudaGetLastError();
 }
 
+template <int G>
+static cudaError_t launch_nb(const KConst& k, const float* row_x_dev, const DevPtrs& p, size_t sm, int blocks,
+                             int threads, int unit0, cudaStream_t s)
+{
+    if (G > 1) sm += 16 + (size_t)(threads / G) * (kNbList + 1) * sizeof(float4);  // the groups' down lists
+    cudaError_t e = cudaFuncSetAttribute(k_neighbours<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k_neighbours<G><<<blocks, threads, sm, s>>>(k, row_x_dev, p, unit0);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_neighbours(const KConst& k, const float* row_x_dev, const DevPtrs& p, int max3,
-                              int max_slots3, int threads, int unit0, int n_units, cudaStream_t s)
+                              int max_slots3, int threads, int lanes_per_hit, int unit0, int n_units,
+                              cudaStream_t s)
 {
     // barrier, the (y, z) pairs of three rows (an even count, one more at
     // most at each end) and their three bin tables
-    size_t sm = 16 + (size_t)(max3 + 2) * 8 + (size_t)max_slots3 * 4;
-    cudaError_t e =
-        cudaFuncSetAttribute(k_neighbours, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    int blocks = n_units * (k.n_rows - 2);
+    const size_t sm = 16 + (size_t)(max3 + 2) * 8 + (size_t)max_slots3 * 4;
+    const int blocks = n_units * (k.n_rows - 2);
     if (blocks == 0) return cudaSuccess;
-    k_neighbours<<<blocks, threads, sm, s>>>(k, row_x_dev, p, unit0);
-    return cudaGetLastError();
+    switch (lanes_per_hit) {
+        case 1: return launch_nb<1>(k, row_x_dev, p, sm, blocks, threads, unit0, s);
+        case 2: return launch_nb<2>(k, row_x_dev, p, sm, blocks, threads, unit0, s);
+        case 4: return launch_nb<4>(k, row_x_dev, p, sm, blocks, threads, unit0, s);
+        case 8: return launch_nb<8>(k, row_x_dev, p, sm, blocks, threads, unit0, s);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_tracklets(const KConst& k, const float* row_x_dev, const DevPtrs& p, int n_sm,
@@ -894,7 +1023,7 @@ cudaError_t launch_tracklets(const KConst& k, const float* row_x_dev, const DevP
 cudaError_t preload_neighbours()
 {
     cudaFuncAttributes a;
-    return cudaFuncGetAttributes(&a, k_neighbours);
+    return cudaFuncGetAttributes(&a, k_neighbours<1>);
 }
 
 }  // namespace TPC_FP_NS

@@ -205,8 +205,8 @@ extern "C" int tpc_links_noalloc(const tpc_geometry* g, const tpc_params* params
     if (e == cudaSuccess) e = tpc_int::launch_plan(k, xd, p, nsm, s);
     if (e == cudaSuccess) e = tpc_int::launch_grid(k, xd, p, max_row, max_slots, P.threads_per_row, 0, S, s);
     if (e == cudaSuccess)
-        e = P.exact_fp32 ? tpc_exact::launch_neighbours(k, xd, p, max3, max_slots3, P.threads_per_row, 0, S, s)
-                         : tpc_fast::launch_neighbours(k, xd, p, max3, max_slots3, P.threads_per_row, 0, S, s);
+        e = P.exact_fp32 ? tpc_exact::launch_neighbours(k, xd, p, max3, max_slots3, P.threads_per_row, 1, 0, S, s)
+                         : tpc_fast::launch_neighbours(k, xd, p, max3, max_slots3, P.threads_per_row, 1, 0, S, s);
     if (e == cudaSuccess) e = tpc_int::launch_clean(k, p, P.threads_per_row, 0, S, true, s);
     if (e == cudaSuccess) e = tpc_int::launch_dump_links(p, 1, d_links, s);
     if (e == cudaSuccess)

@@ -102,6 +102,8 @@ static const char* check_params(const tpc_params& P)
     if (t != 32 && t != 64 && t != 128 && t != 256) return "threads_per_row must be 32, 64, 128 or 256";
     int w = P.tracklets_per_warp;
     if (w != 1 && w != 2 && w != 4 && w != 8 && w != 16 && w != 32) return "tracklets_per_warp";
+    const int lh = P.lanes_per_hit;
+    if (lh != 1 && lh != 2 && lh != 4 && lh != 8) return "lanes_per_hit must be 1, 2, 4 or 8";
     if (P.schedule < 0 || P.schedule > 2) return "schedule must be 0, 1 or 2";
     if (P.plain_per_sector < 0 || P.plain_per_sector > 2) return "plain_per_sector must be 0, 1 or 2";
     if (P.n_queues < 1 || P.n_queues > 64) return "n_queues must be in [1, 64]";
@@ -147,6 +149,7 @@ extern "C" void tpc_params_default(tpc_params* p)
     p->bin_target = 1.0f;
     p->threads_per_row = 128;
     p->tracklets_per_warp = 32;
+    p->lanes_per_hit = 1;
     p->plain_per_sector = 0;
     p->use_graph = 0;
     p->n_queues = 8;
@@ -476,8 +479,9 @@ int tpc_enqueue(tpc_tracker* tr, const DevPtrs& p, const BatchShape& sh, cudaStr
     const bool exact = P.exact_fp32 != 0;
     auto nb = [&](const tpc::KConst& kk, const float* x, const DevPtrs& pp, int max3, int slots3, int th,
                   int u0, int nu, cudaStream_t ss) {
-        return exact ? tpc_exact::launch_neighbours(kk, x, pp, max3, slots3, th, u0, nu, ss)
-                     : tpc_fast::launch_neighbours(kk, x, pp, max3, slots3, th, u0, nu, ss);
+        const int lh = P.lanes_per_hit;
+        return exact ? tpc_exact::launch_neighbours(kk, x, pp, max3, slots3, th, lh, u0, nu, ss)
+                     : tpc_fast::launch_neighbours(kk, x, pp, max3, slots3, th, lh, u0, nu, ss);
     };
     auto seeds = [&](int u0, int u1, cudaStream_t ss) {
         return exact ? tpc_exact::launch_seeds(k, xd, p, tr->n_sm, u0, u1, ss)
@@ -894,13 +898,15 @@ extern "C" int tpc_autotune(tpc_tracker* tr, const tpc_cluster* clusters, const 
     int rc = run_ms(&cur_ms);
     if (rc != TPC_OK) return rc;
     struct Axis {
-        int kind;  // 0 schedule, 1 bin_target, 2 tracklets_per_warp, 3 threads_per_row
+        int kind;  // 0 schedule, 1 bin_target, 2 tracklets_per_warp, 3 threads_per_row,
+                   // 4 lanes_per_hit
         std::vector<float> values;
     };
     const std::vector<Axis> axes = {{0, {0, 1, 2}},
                                     {1, {0.25f, 0.5f, 1.0f, 2.0f}},
                                     {2, {32, 16, 8}},
-                                    {3, {64, 128, 256}}};
+                                    {3, {64, 128, 256}},
+                                    {4, {1, 2, 4, 8}}};
     for (int pass = 0; pass < 2; pass++) {
         bool changed = false;
         for (const Axis& ax : axes) {
@@ -910,6 +916,7 @@ extern "C" int tpc_autotune(tpc_tracker* tr, const tpc_cluster* clusters, const 
                 if (ax.kind == 1) cand.bin_target = v;
                 if (ax.kind == 2) cand.tracklets_per_warp = (int)v;
                 if (ax.kind == 3) cand.threads_per_row = (int)v;
+                if (ax.kind == 4) cand.lanes_per_hit = (int)v;
                 if (std::memcmp(&cand, &cur, sizeof cand) == 0) continue;
                 rc = tpc_tracker_set_params(tr, &cand);
                 if (rc != TPC_OK) return rc;

@@ -41,7 +41,8 @@ def test_cached_choice_is_applied_without_timing(tmp_path):
     rc = np.zeros(36 * 159, np.int32)
     rc[:4] = 50
     key = autotune.workload_key(rc, 1, "dev")
-    choice = {"schedule": 1, "bin_target": 2.0, "tracklets_per_warp": 4, "threads_per_row": 64}
+    choice = {"schedule": 1, "bin_target": 2.0, "tracklets_per_warp": 4, "threads_per_row": 64,
+              "lanes_per_hit": 4}
     path = tmp_path / "c.json"
     path.write_text(json.dumps({key: dict(choice, ms=1.5)}))
     tr = FakeTracker()

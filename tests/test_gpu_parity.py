@@ -83,7 +83,10 @@ def test_exact_parity_multi_event_batch(events):
                                   dict(plain_per_sector=2, n_queues=3, use_graph=1),
                                   dict(tracklets_per_warp=4), dict(schedule=1),
                                   dict(tracklets_per_warp=16, schedule=1), dict(schedule=2),
-                                  dict(tracklets_per_warp=8, schedule=2)])
+                                  dict(tracklets_per_warp=8, schedule=2),
+                                  dict(lanes_per_hit=2), dict(lanes_per_hit=4, threads_per_row=256),
+                                  dict(lanes_per_hit=8, threads_per_row=32, bin_target=8.0),
+                                  dict(lanes_per_hit=4, plain_per_sector=2, n_queues=4)])
 def test_execution_params_do_not_change_results(events, over):
     ev = events["c3s"]
     base = gpu_run(ev.clusters, ev.row_counts, 1, exact_fp32=1)
@@ -92,6 +95,19 @@ def test_execution_params_do_not_change_results(events, over):
         np.testing.assert_array_equal(g[k], base[k], err_msg=k)
     np.testing.assert_array_equal(g["tl_f"].view(np.uint32), base["tl_f"].view(np.uint32))
     np.testing.assert_array_equal(g["hit_ids"], base["hit_ids"])
+
+
+def test_neighbour_forms_agree_in_production_build(events):
+    """The production build too gives the same links and tracks whichever
+    number of lanes shares a hit in the neighbour finder (the pair residual
+    rounds alike in every form)."""
+    ev = events["c3s"]
+    base = gpu_run(ev.clusters, ev.row_counts, 1, exact_fp32=0)
+    for lh in (2, 4, 8):
+        g = gpu_run(ev.clusters, ev.row_counts, 1, exact_fp32=0, lanes_per_hit=lh)
+        for k in ("up_raw", "dn_raw", "up", "dn", "start"):
+            np.testing.assert_array_equal(g[k], base[k], err_msg=f"{k} lanes_per_hit={lh}")
+        np.testing.assert_array_equal(g["hit_ids"], base["hit_ids"])
 
 
 def test_graph_replay_repeats(events):
@@ -214,8 +230,10 @@ def test_tiny_lattice_events_exact():
     cl, rc = S.tiny_lattice_events(1000, seed=12)
     o = oracle_run(cl, rc, 1000, mode="f32")
     assert len(o["trk_t"]) > 0
-    for bt in (0.25, 4.0):
-        g = gpu_run(cl, rc, 1000, exact_fp32=1, bin_target=bt)
+    # lanes_per_hit > 1: the warp-cooperative neighbour search, whose windows
+    # here often hold more down candidates than its per-group list (rescan)
+    for bt, lh in ((0.25, 1), (4.0, 1), (0.25, 4), (4.0, 8), (0.25, 2)):
+        g = gpu_run(cl, rc, 1000, exact_fp32=1, bin_target=bt, lanes_per_hit=lh)
         assert_exact_equal(g, o)
 
 
@@ -367,9 +385,10 @@ def test_full_size_central_batch_exact():
     graph replay) against the FP32 oracle, every stage."""
     evs = [S.central_event(seed=3 + i) for i in range(2)]
     cl, rc = S.concat_events(evs)
-    g = gpu_run(cl, rc, len(evs), exact_fp32=1, use_graph=1)
     o = oracle_run(cl, rc, len(evs), mode="f32")
-    assert_exact_equal(g, o)
+    for lh in (1, 4):  # one thread per hit, and four lanes sharing a hit
+        g = gpu_run(cl, rc, len(evs), exact_fp32=1, use_graph=1, lanes_per_hit=lh)
+        assert_exact_equal(g, o)
 
 
 def test_block_schedule_full_size():
@@ -394,9 +413,10 @@ def test_full_size_time_frame_exact():
     replay."""
     ev = S.time_frame(seed=4)
     assert int(ev.row_counts.max()) > 1000
-    g = gpu_run(ev.clusters, ev.row_counts, 1, exact_fp32=1, use_graph=1)
     o = oracle_run(ev.clusters, ev.row_counts, 1, mode="f32")
-    assert_exact_equal(g, o)
+    for lh in (1, 8):
+        g = gpu_run(ev.clusters, ev.row_counts, 1, exact_fp32=1, use_graph=1, lanes_per_hit=lh)
+        assert_exact_equal(g, o)
 
 
 def test_work_counts_only_on_request(events):
