@@ -760,6 +760,7 @@ def run_stream(tr0, pool, args, rate, batch=None, workload=MINBIAS_STREAM):
         tr.stream_configure(arena_bytes=args.stream_arena_gb << 30, max_batch_events=batch,
                             max_inflight=args.stream_inflight, no_copy=True,
                             max_batch_clusters=args.stream_batch_clusters)
+        tr.stream_set_batching(args.stream_min_batch_clusters, args.stream_max_wait_us)
         rng = np.random.default_rng(5)
         n_req = args.stream_requests or int(rate * args.stream_seconds)
         arrivals = np.cumsum(rng.exponential(1.0 / rate, n_req))
@@ -842,6 +843,9 @@ def run_stream(tr0, pool, args, rate, batch=None, workload=MINBIAS_STREAM):
             "clusters_per_s": clusters / wall, "events_per_s": n_req / wall, "wall_s": wall,
             "tracks": n_tracks, "client": "tpc_stream_poll_any + tpc_stream_release (results read in place)",
             "batches_in_flight": args.stream_inflight,
+            "batch_clusters_max": args.stream_batch_clusters,
+            "batching": {"min_batch_clusters": args.stream_min_batch_clusters,
+                         "max_wait_us": args.stream_max_wait_us},
             "pool_events": len(pool), "mean_clusters_per_event": float(np.mean([len(p[0]) for p in pool])),
             "max_batch_events": batch, "workload": workload}
 
@@ -1038,6 +1042,11 @@ def main():
     ap.add_argument("--stream-inflight", type=int, default=2, help="serving batches in flight")
     ap.add_argument("--stream-batch-clusters", type=int, default=1 << 22,
                     help="most clusters in one serving batch (the library's default: 2^22)")
+    ap.add_argument("--stream-min-batch-clusters", type=int, default=1 << 20,
+                    help="serving: while a batch runs, form the next once this many clusters are "
+                         "pending (0: whenever a slot is free)")
+    ap.add_argument("--stream-max-wait-us", type=int, default=1000,
+                    help="serving: ... or once the oldest pending request has waited this long")
     ap.add_argument("--stream-requests", type=int, default=0,
                     help="requests per serving rate (0: rate x --stream-seconds)")
     ap.add_argument("--pool", type=int, default=96, help="min-bias events in the serving pool")

@@ -360,6 +360,20 @@ int tpc_stream_submit(tpc_tracker* tr, const tpc_cluster* clusters, const int32_
 int tpc_stream_configure(tpc_tracker* tr, size_t arena_bytes, int max_batch_events, int max_inflight,
                          int flags, int64_t max_batch_clusters);
 
+/* Batching policy of the request loop (scheduling of this library; the
+ * paper only says that independent events share the GPU, Sec. 3.2).  While
+ * another batch is in flight, a new batch forms only once the pending
+ * requests hold at least min_batch_clusters clusters, fill a batch, or the
+ * oldest of them has waited max_wait_us; with no batch in flight, pending
+ * requests go at once.  Small events then share fewer, larger batches under
+ * load instead of queueing behind many small ones.  min_batch_clusters = 0
+ * (the default) forms a batch whenever a slot is free.  May be called at
+ * any time; it applies to batches formed afterwards.  The loop checks the
+ * policy whenever the caller submits or polls, so a caller waiting in
+ * tpc_stream_poll(_any) with a timeout keeps it driven.
+ * TPC_ERR_INVALID for negative values. */
+int tpc_stream_set_batching(tpc_tracker* tr, int64_t min_batch_clusters, int max_wait_us);
+
 /* Poll a ticket, waiting at most timeout_us (0: do not wait).  Returns
  * TPC_PENDING, TPC_OK (out filled; the ticket is released) or an error
  * (TPC_ERR_OUTPUT_TRUNCATED keeps the ticket so the caller can poll again

@@ -133,6 +133,7 @@ def lib() -> C.CDLL:
         L.tpc_stream_submit.argtypes = [V, V, V, C.c_int, C.c_uint64, P(C.c_uint64)]
         L.tpc_stream_poll.argtypes = [V, C.c_uint64, P(tpc_output), C.c_int]
         L.tpc_stream_configure.argtypes = [V, C.c_size_t, C.c_int, C.c_int, C.c_int, C.c_int64]
+        L.tpc_stream_set_batching.argtypes = [V, C.c_int64, C.c_int]
         L.tpc_stream_get_stats.argtypes = [V, P(tpc_stream_stats)]
         L.tpc_stream_poll_view.argtypes = [V, C.c_uint64, P(tpc_stream_view), C.c_int]
         L.tpc_stream_release.argtypes = [V, C.c_uint64]

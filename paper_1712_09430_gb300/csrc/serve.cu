@@ -5,7 +5,8 @@
 // covers its reservation and a slot is free; the input is copied to pinned
 // host memory before the call returns.  Admitted requests wait in a FIFO.
 // Whenever fewer than max_inflight batches run, all pending requests (up to
-// max_batch_events events) form the next batch: one H2D per request, the
+// max_batch_events events) form the next batch (with a batching policy set,
+// only once enough work is pending while another batch runs): one H2D per request, the
 // batched stages of tpc_track_sectors on the batch's own stream, and a D2H
 // of the counters and of an estimated output (fetch the rest if the estimate
 // was short, Sec. 3.1).  Requests that arrive while batches run join the
@@ -41,6 +42,7 @@ struct Request {
     int m0 = 0, m1 = 0;                 // track range
     int h0 = 0, h1 = 0;                 // hit range
     bool viewed = false;                // handed out by tpc_stream_poll_view
+    std::chrono::steady_clock::time_point t_submit;  // admission time (batching policy)
 };
 
 struct Batch {
@@ -119,6 +121,11 @@ struct ServeState {
     int max_batch_events = 64;
     int64_t max_batch_clusters = TPC_STREAM_BATCH_CLUSTERS;  // 0: no limit
     int max_inflight = 2;
+    // batching policy: while a batch runs, the next one forms only once the
+    // pending requests hold min_batch_clusters clusters or the oldest has
+    // waited max_wait_us (0: whenever a slot is free)
+    int64_t min_batch_clusters = 0;
+    int max_wait_us = 0;
     int max_requests = 4096;
     int flags = 0;                 // TPC_STREAM_NO_COPY
     void* arena_base = nullptr;
@@ -482,6 +489,26 @@ static void finish_batch(tpc_tracker* tr, Batch& b)
     S->stats.host_finish_ms += ms_since(t_host);
 }
 
+// With a batch already running: is the pending work worth a batch of its
+// own now (enough clusters, a full batch, or the oldest request waited long
+// enough)?  Otherwise it waits and joins a larger batch.
+static bool batch_ready(const ServeState* S)
+{
+    int64_t ncl = 0;
+    int ev = 0;
+    for (uint64_t t : S->pending) {
+        const Request& r = S->req.at(t);
+        ncl += r.N;
+        ev += r.n_events;
+    }
+    if (ncl >= S->min_batch_clusters || ev >= S->max_batch_events) return true;
+    if (S->max_batch_clusters > 0 && ncl >= S->max_batch_clusters) return true;
+    const Request& oldest = S->req.at(S->pending.front());
+    const auto waited = std::chrono::duration_cast<std::chrono::microseconds>(
+        std::chrono::steady_clock::now() - oldest.t_submit);
+    return waited.count() >= S->max_wait_us;
+}
+
 static int progress(tpc_tracker* tr)
 {
     ServeState* S = tr->serve;
@@ -498,6 +525,7 @@ static int progress(tpc_tracker* tr)
         }
     }
     while (!S->pending.empty() && S->inflight < S->max_inflight) {
+        if (S->inflight > 0 && S->min_batch_clusters > 0 && !batch_ready(S)) break;
         int rc = launch_batch(tr);
         if (rc == TPC_BUSY) break;  // arena fragmented: wait for a running batch
         if (rc != TPC_OK) return rc;
@@ -547,6 +575,17 @@ extern "C" int tpc_stream_configure(tpc_tracker* tr, size_t arena_bytes, int max
     return TPC_OK;
 }
 
+extern "C" int tpc_stream_set_batching(tpc_tracker* tr, int64_t min_batch_clusters, int max_wait_us)
+{
+    if (!tr) return TPC_ERR_INVALID;
+    if (min_batch_clusters < 0 || max_wait_us < 0)
+        return tr->fail(TPC_ERR_INVALID, "min_batch_clusters and max_wait_us must be >= 0");
+    if (!tr->serve) tr->serve = new ServeState();
+    tr->serve->min_batch_clusters = min_batch_clusters;
+    tr->serve->max_wait_us = max_wait_us;
+    return TPC_OK;
+}
+
 extern "C" int tpc_stream_submit(tpc_tracker* tr, const tpc_cluster* clusters, const int32_t* row_counts,
                                  int n_events, uint64_t tag, uint64_t* ticket)
 {
@@ -586,6 +625,7 @@ extern "C" int tpc_stream_submit(tpc_tracker* tr, const tpc_cluster* clusters, c
     r.pin_bytes = pin_bytes;
     r.src = no_copy ? clusters : nullptr;
     r.reserve = reserve;
+    r.t_submit = std::chrono::steady_clock::now();
     S->reserved += reserve;
     S->req[r.ticket] = std::move(r);
     S->pending.push_back(S->next_ticket - 1);

@@ -201,6 +201,12 @@ class Tracker:
                                               capi.TPC_STREAM_NO_COPY if no_copy else 0,
                                               int(max_batch_clusters)))
 
+    def stream_set_batching(self, min_batch_clusters=0, max_wait_us=0):
+        """Batching policy (tpc_stream_set_batching): while a batch runs, form
+        the next one only once min_batch_clusters clusters are pending, a
+        batch is full, or the oldest request has waited max_wait_us."""
+        self.check(lib().tpc_stream_set_batching(self.h, int(min_batch_clusters), int(max_wait_us)))
+
     def stream_stats(self):
         """Counters of the request loop (batches, events, device and host ms)."""
         st = capi.tpc_stream_stats()

@@ -43,7 +43,8 @@ int main(void)
                    (void*)tpc_autotune, (void*)tpc_stream_configure, (void*)tpc_stream_submit,
                    (void*)tpc_stream_poll, (void*)tpc_stream_poll_view, (void*)tpc_stream_release,
                    (void*)tpc_stream_get_stats, (void*)tpc_debug_dump, (void*)tpc_stage_times,
-                   (void*)tpc_last_error, (void*)tpc_links_noalloc, (void*)tpc_stream_poll_any};
+                   (void*)tpc_last_error, (void*)tpc_links_noalloc, (void*)tpc_stream_poll_any,
+                   (void*)tpc_stream_set_batching};
     tpc_params p;
     tpc_params_default(&p);  /* host only: no device needed */
     printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(tpc_cluster), sizeof(tpc_geometry),

@@ -50,12 +50,18 @@ def _drain(tr, tickets, timeout_s=60):
     return out
 
 
-@pytest.mark.parametrize("exact,no_copy", [(1, False), (0, False), (0, True)])
-def test_stream_results_equal_alone(pool, exact, no_copy):
+@pytest.mark.parametrize("exact,no_copy,policy", [(1, False, None), (0, False, None), (0, True, None),
+                                                   (1, False, (600_000, 3000)), (0, True, (1 << 20, 500))])
+def test_stream_results_equal_alone(pool, exact, no_copy, policy):
+    """Every streamed result equals the synchronous call on its event alone,
+    also when the batching policy holds requests back to form larger batches
+    while another batch runs."""
     with Tracker(XR, exact_fp32=exact) as alone:
         ref = [alone.track(e.clusters, e.row_counts, 1) for e in pool]
     with Tracker(XR, exact_fp32=exact) as tr:
         tr.stream_configure(arena_bytes=4 << 30, max_batch_events=5, max_inflight=2, no_copy=no_copy)
+        if policy:
+            tr.stream_set_batching(*policy)
         order = np.random.default_rng(1).permutation(np.repeat(np.arange(len(pool)), 2))
         tickets, which, res = [], {}, {}
         for i in order:
@@ -253,3 +259,31 @@ def test_cluster_limit_is_validated():
     with Tracker(XR) as tr:
         with pytest.raises(TrackerError):
             tr.stream_configure(max_batch_clusters=-1)
+
+
+def test_batching_policy_holds_small_requests_while_a_batch_runs(pool):
+    """With the batching policy, requests that arrive while a batch runs wait
+    and go together once it ends, instead of forming a second small batch at
+    once (two slots are free); results are unchanged."""
+    big = S.central_event(seed=71)
+    small = pool[:3]
+    with Tracker(XR) as alone:
+        ref_big = alone.track(big.clusters, big.row_counts, 1)
+        ref = [alone.track(e.clusters, e.row_counts, 1) for e in small]
+    pinned = [torch.from_numpy(e.clusters).pin_memory() for e in [big] + small]
+    with Tracker(XR) as tr:
+        tr.stream_configure(arena_bytes=8 << 30, max_batch_events=8, max_inflight=2, no_copy=True)
+        tr.stream_set_batching(min_batch_clusters=1 << 30, max_wait_us=2_000_000)
+        t_big = tr.submit(pinned[0], big.row_counts, 1)   # nothing runs: goes at once
+        tickets = [tr.submit(c, e.row_counts, 1) for c, e in zip(pinned[1:], small)]
+        got = _drain(tr, [t_big] + tickets)
+        st = tr.stream_stats()
+    _same(got[t_big], ref_big)
+    for t, r in zip(tickets, ref):
+        _same(got[t], r)
+    assert st["batches"] == 2 and st["max_batch_events"] == 3
+    with Tracker(XR) as tr:
+        with pytest.raises(TrackerError):
+            tr.stream_set_batching(min_batch_clusters=-1)
+        with pytest.raises(TrackerError):
+            tr.stream_set_batching(max_wait_us=-5)
