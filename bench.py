@@ -285,7 +285,8 @@ def run_ours(args):
     N = len(cl_np)
     tr = Tracker(synth.row_x(), bz=0.5, use_graph=1, exact_fp32=1 if args.exact else 0,
                  bin_target=args.bin_target, threads_per_row=args.threads_per_row,
-                 tracklets_per_warp=args.tracklets_per_warp, schedule=args.schedule)
+                 tracklets_per_warp=args.tracklets_per_warp, schedule=args.schedule,
+                 lanes_per_hit=args.lanes_per_hit)
     stream = torch.cuda.Stream()
     sp = C.c_void_p(stream.cuda_stream)
     dev_cl = torch.from_numpy(cl_np).to(f"cuda:{local}")
@@ -433,6 +434,7 @@ def run_ours(args):
                        "bin_target": float(tr.params.bin_target),
                        "threads_per_row": int(tr.params.threads_per_row),
                        "tracklets_per_warp": int(tr.params.tracklets_per_warp),
+                       "lanes_per_hit": int(tr.params.lanes_per_hit),
                        "schedule": int(tr.params.schedule),
                        "l2": f"inputs larger than L2 ({N * 16 / 1e6:.0f} MB of clusters per step)",
                        "parallelism": f"events sharded over {world} GPU(s), no collective"},
@@ -567,7 +569,8 @@ def run_time_frame(frame, tr0, args, device):
                        ("chain", dict(refit=1, merge=1, t0=1))):
         tr = Tracker(synth.row_x(), bz=0.5, use_graph=1, exact_fp32=p.exact_fp32,
                      bin_target=p.bin_target, threads_per_row=p.threads_per_row,
-                     tracklets_per_warp=p.tracklets_per_warp, schedule=p.schedule, **over)
+                     tracklets_per_warp=p.tracklets_per_warp, schedule=p.schedule,
+                     lanes_per_hit=p.lanes_per_hit, **over)
         try:
             for _ in range(3):
                 r = tr.track(dev, rc, 1)
@@ -680,7 +683,8 @@ def run_slices(slices, tr0, args, device):
     for name, over in (("tracking", dict(refit=0, merge=0, t0=0)), ("chain", dict(refit=1, merge=1, t0=1))):
         tr = Tracker(synth.row_x(), bz=0.5, use_graph=1, exact_fp32=p.exact_fp32,
                      bin_target=p.bin_target, threads_per_row=p.threads_per_row,
-                     tracklets_per_warp=p.tracklets_per_warp, schedule=p.schedule, **over)
+                     tracklets_per_warp=p.tracklets_per_warp, schedule=p.schedule,
+                     lanes_per_hit=p.lanes_per_hit, **over)
         try:
             for _ in range(3):
                 r = tr.track(dev, rc, E)
@@ -751,7 +755,7 @@ def run_stream(tr0, pool, args, rate, batch=None, workload=MINBIAS_STREAM):
     p = tr0.params
     tr = Tracker(synth.row_x(), bz=0.5, exact_fp32=p.exact_fp32, bin_target=p.bin_target,
                  threads_per_row=p.threads_per_row, tracklets_per_warp=p.tracklets_per_warp,
-                 schedule=p.schedule)
+                 schedule=p.schedule, lanes_per_hit=p.lanes_per_hit)
     try:
         import torch
         # events arrive in pinned host memory (as from a readout link) and are
@@ -898,7 +902,7 @@ def run_e2e_stream(tr0, cl_np, rc_np, B, N, world, args):
     p = tr0.params
     tr = Tracker(synth.row_x(), bz=0.5, exact_fp32=p.exact_fp32, bin_target=p.bin_target,
                  threads_per_row=p.threads_per_row, tracklets_per_warp=p.tracklets_per_warp,
-                 schedule=p.schedule)
+                 schedule=p.schedule, lanes_per_hit=p.lanes_per_hit)
     try:
         pin = torch.from_numpy(cl_np).pin_memory()
         tr.stream_configure(arena_bytes=args.stream_arena_gb << 30, max_batch_events=B, max_inflight=2,
@@ -1008,6 +1012,8 @@ def main():
     ap.add_argument("--bin-target", type=float, default=0.25)
     ap.add_argument("--threads-per-row", type=int, default=128)
     ap.add_argument("--tracklets-per-warp", type=int, default=32)
+    ap.add_argument("--lanes-per-hit", type=int, default=1,
+                    help="lanes sharing one hit in the neighbour finder (1, 2, 4, 8)")
     ap.add_argument("--schedule", type=int, default=2,
                     help="0 unit by unit, 1 by start row, 2 by start row inside blocks of ~2 M clusters")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",

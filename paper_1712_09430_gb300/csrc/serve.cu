@@ -168,6 +168,13 @@ static int serve_init(tpc_tracker* tr)
         return tr->fail(TPC_ERR_NOMEM, "cannot allocate the serving arena");
     }
     S->arena.init(S->arena_bytes);
+    // the tracker's pinned plan buffer, which every batch's shape is planned
+    // in, sized for a full batch now (growing it later synchronizes the device)
+    if (tpc_reserve_plan(tr, (int64_t)S->max_batch_events * tr->geom.n_sectors * tr->geom.n_rows) != TPC_OK) {
+        cudaFree(S->arena_base);
+        S->arena_base = nullptr;
+        return TPC_ERR_NOMEM;
+    }
     const size_t pin_bytes = std::max<size_t>(S->arena_bytes / 8, (size_t)64 << 20);
     if (cudaMallocHost(&S->pin, pin_bytes) != cudaSuccess) {
         cudaGetLastError();
@@ -328,6 +335,12 @@ static int launch_batch_impl(tpc_tracker* tr)
         // estimated output, fetched right after the last kernel (Sec. 3.1)
         b->est_tracks = std::min<int>(sh.t_cap, (int)(S->tracks_per_cluster * sh.N * 1.3) + 256);
         b->est_hits = std::min<int>(sh.N, (int)(S->hits_per_cluster * sh.N * 1.3) + 4096);
+        if (S->max_batch_clusters > 0) {
+            // buffers sized when serving started: an estimate beyond them is
+            // left to the fetch of the rest rather than a reallocation
+            b->est_tracks = std::min<int>(b->est_tracks, (int)(b->tracks_cap / sizeof(tpc_track)));
+            b->est_hits = std::min<int>(b->est_hits, (int)(b->hits_cap / sizeof(int)));
+        }
         if (grow_pinned(tr, reinterpret_cast<void**>(&b->tracks), &b->tracks_cap,
                         sizeof(tpc_track) * (size_t)b->est_tracks) != TPC_OK ||
             grow_pinned(tr, reinterpret_cast<void**>(&b->hits), &b->hits_cap,

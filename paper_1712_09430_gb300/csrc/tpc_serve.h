@@ -67,6 +67,7 @@ struct tpc_tracker {
 // tracker.cu
 size_t tpc_layout(const tpc_tracker* tr, const BatchShape& sh, tpc::DevPtrs* p, char* base);
 int tpc_shape(tpc_tracker* tr, const int32_t* row_counts, int n_events, BatchShape* sh);
+int tpc_reserve_plan(tpc_tracker* tr, int64_t R);
 int tpc_enqueue(tpc_tracker* tr, const tpc::DevPtrs& p, const BatchShape& sh, cudaStream_t s,
                 bool with_events);
 

@@ -351,6 +351,24 @@ size_t tpc_layout(const tpc_tracker* tr, const BatchShape& sh, DevPtrs* p, char*
     return off;
 }
 
+// The pinned plan buffer sized for a call of R rows.  Growing it means
+// cudaFreeHost / cudaMallocHost, which synchronize the device: the request
+// loop reserves a full batch's size when serving starts.
+int tpc_reserve_plan(tpc_tracker* tr, int64_t R)
+{
+    if ((size_t)(3 * R + 2) <= tr->plan_cap) return TPC_OK;
+    cudaFreeHost(tr->plan_host);
+    tr->plan_host = nullptr;
+    tr->plan_cap = 0;
+    const size_t want = (size_t)(3 * R + 2) + (size_t)(R / 4) + 64;
+    if (cudaMallocHost(&tr->plan_host, want * sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        return tr->fail(TPC_ERR_NOMEM, "cannot allocate pinned plan buffer");
+    }
+    tr->plan_cap = want;
+    return TPC_OK;
+}
+
 // Shape of a batch from its (host) row counts.
 int tpc_shape(tpc_tracker* tr, const int32_t* row_counts, int n_events, BatchShape* sh)
 {
@@ -359,17 +377,8 @@ int tpc_shape(tpc_tracker* tr, const int32_t* row_counts, int n_events, BatchSha
     if (R > (1 << 28)) return tr->fail(TPC_ERR_INVALID, "too many rows in one call");
     int64_t N = 0, bins = 0, max_unit = 0;
     int max_row = 0, max3 = 0, max_slots = 0, max_slots3 = 0;
-    if ((size_t)(3 * R + 2) > tr->plan_cap) {
-        cudaFreeHost(tr->plan_host);
-        tr->plan_host = nullptr;
-        tr->plan_cap = 0;
-        size_t want = (size_t)(3 * R + 2) + (size_t)(R / 4) + 64;
-        if (cudaMallocHost(&tr->plan_host, want * sizeof(int)) != cudaSuccess) {
-            cudaGetLastError();
-            return tr->fail(TPC_ERR_NOMEM, "cannot allocate pinned plan buffer");
-        }
-        tr->plan_cap = want;
-    }
+    const int rc_plan = tpc_reserve_plan(tr, R);
+    if (rc_plan != TPC_OK) return rc_plan;
     // the pinned plan: row counts [R], CSR offsets of rows [R + 1], bin-table
     // offsets [R + 1], laid out as on the device so that one copy uploads all
     int* plan_cnt = tr->plan_host;
