@@ -205,7 +205,10 @@ def run_reference(args):
     # step in turn: a bounded sample of that workload
     seeds = rank_seeds(0, args.batch)
     n_ev = max(1, min(len(seeds), args.steps))
-    evs = [synth.central_event(seed=s) for s in seeds[:n_ev]]
+    # the whole step's events name the workload (the same config as the GPU
+    # arm's); the first n_ev of them are timed
+    all_evs = [synth.central_event(seed=s) for s in seeds]
+    evs = all_evs[:n_ev]
     cores = os.cpu_count() or 1
     for i in range(max(0, args.warmup)):
         ev = evs[i % n_ev]
@@ -223,8 +226,7 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "events_per_step": 1,
-                       "clusters_per_step": int(round(n_cl / max(1, args.steps)))},
+            "config": step_config(len(seeds), sum(ev.n for ev in all_evs), args.gpus),
             "cpu_baseline": {"value": value, "unit": "clusters/s", "cores": cores, "kind": "oracle",
                              "sample": f"one of the GPU step's {len(seeds)} central events per step "
                                        f"(seeds {seeds[0]}-{seeds[-1]} in turn), {args.steps} steps, "
@@ -232,6 +234,16 @@ def run_reference(args):
             "e2e": {"value": value, "unit": "clusters/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def step_config(batch, n_clusters, world):
+    """The workload of one step, as both arms name it: `batch` central
+    events per GPU, `n_clusters` of them on rank 0 (every rank's events are
+    drawn from the same distribution)."""
+    return {"workload": WORKLOAD, "events_per_step": batch * world, "events_per_rank": batch,
+            "clusters_per_step": int(n_clusters) * world,
+            "l2": f"inputs larger than L2 ({n_clusters * 16 / 1e6:.0f} MB of clusters per step)",
+            "parallelism": f"events sharded over {world} GPU(s), no collective"}
 
 
 def rank_seeds(rank, batch, base=3):
@@ -426,18 +438,16 @@ def run_ours(args):
     line = {"metric": METRIC, "value": value, "unit": "clusters/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "events_per_step": B, "events_per_rank": B,
-                       "clusters_per_step": int(N) * world, "tracks_per_step": int(M),
-                       "tracklets_per_step": int(T), "mode": "exact" if args.exact else "production",
-                       "launch": "batched, CUDA graph replay",
-                       "autotuned": tuned is not None,
-                       "bin_target": float(tr.params.bin_target),
-                       "threads_per_row": int(tr.params.threads_per_row),
-                       "tracklets_per_warp": int(tr.params.tracklets_per_warp),
-                       "lanes_per_hit": int(tr.params.lanes_per_hit),
-                       "schedule": int(tr.params.schedule),
-                       "l2": f"inputs larger than L2 ({N * 16 / 1e6:.0f} MB of clusters per step)",
-                       "parallelism": f"events sharded over {world} GPU(s), no collective"},
+            "config": step_config(B, int(N), world),
+            "execution": {"tracks_per_step": int(M), "tracklets_per_step": int(T),
+                          "mode": "exact" if args.exact else "production",
+                          "launch": "batched, CUDA graph replay",
+                          "autotuned": tuned is not None,
+                          "bin_target": float(tr.params.bin_target),
+                          "threads_per_row": int(tr.params.threads_per_row),
+                          "tracklets_per_warp": int(tr.params.tracklets_per_warp),
+                          "lanes_per_hit": int(tr.params.lanes_per_hit),
+                          "schedule": int(tr.params.schedule)},
             "events_per_s": B * world / (ms * 1e-3),
             "stage_ms": stage_ms, "wall_s": wall,
             "gpu_launches": LAUNCHES_PER_STEP * args.steps,

@@ -41,7 +41,7 @@ def test_ranks_track_disjoint_events():
 
 def test_reference_arm_line(capsys, monkeypatch):
     """--impl reference: the oracle on the GPU step's own events, one JSON
-    line with the GPU arm's metric and workload, its own cpu_baseline and an
+    line with the GPU arm's metric and config, its own cpu_baseline and an
     e2e without host-device bytes; ranks other than 0 print nothing."""
     import argparse
     import json
@@ -54,6 +54,10 @@ def test_reference_arm_line(capsys, monkeypatch):
     line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["metric"] == bench.METRIC
     assert line["config"]["workload"] == bench.WORKLOAD
+    # the GPU arm's config for the same batch, key for key
+    from paper_1712_09430_gb300 import synth
+    n = sum(synth.central_event(seed=s).n for s in bench.rank_seeds(0, args.batch))
+    assert line["config"] == bench.step_config(args.batch, n, args.gpus)
     assert line["unit"] == "clusters/s" and line["higher_is_better"] is True and line["value"] > 0
     cb = line["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["value"] == line["value"] and cb["cores"] >= 1
