@@ -452,6 +452,10 @@ __device__ __forceinline__ bool outside(const State& st, float X, const KConst& 
     return fabsf(st.y) > X * k.tan_h + k.y_margin || fabsf(st.z) > k.z_max;
 }
 
+// Candidates per lane tested as straight-line code in a row step (the
+// window of a central event holds 2.2 on average; 2 or 6 slots were slower).
+constexpr int kSearchSlots = 4;
+
 // Closest cluster of row rr to the predicted state inside the window
 // |dy| <= wy, |dz| <= wz with w = clamp(n_sigma sqrt(S), w_min, w_max);
 // distance d2 = dy^2 / S_y + dz^2 / S_z, ties by smaller id.  The G lanes of
@@ -486,10 +490,9 @@ __device__ __forceinline__ int search_row(const State& st, const RowGrid& g, flo
         work.x += 1;
         work.y += bz1 - bz0 + 1;
     }
-    // One flat loop over the candidates of the first two z rows of the window
-    // (their bin-table reads go out together), so that lanes with different
-    // numbers of z rows and candidates diverge as little as possible; a
-    // window over more z rows (rare) continues in the general loop below.
+    // The candidates of the first two z rows of the window are taken as one
+    // list (their bin-table reads go out together); a window over more z rows
+    // (rare) continues in the general loop below.
     const int* rb = p.bin_off + g.bin_base + by0;
     const int ja0 = __ldg(rb + bz0 * ny), ja1 = __ldg(rb + bz0 * ny + (by1 - by0) + 1);
     int jb0 = 0, jb1 = 0;
@@ -499,8 +502,10 @@ __device__ __forceinline__ int search_row(const State& st, const RowGrid& g, flo
     }
     const int na = ja1 - ja0, ntot = na + (jb1 - jb0);
     if (CW) work.z += ntot;
-    // one candidate: the window test and the distance, then a branch taken
-    // only for an improvement or a tie inside the window
+    // one candidate: the window test and the distance; an improvement is
+    // taken with selects (no branch), an exact tie (rare) in a branch that
+    // compares cluster ids.  The result is the minimum of (d2, id) over the
+    // candidates inside the window, whatever the order they are tested in.
     auto consider = [&](int j, const float2 c) {
         const float dy = c.x - st.y;
         const float dz = c.y - st.z;
@@ -509,36 +514,49 @@ __device__ __forceinline__ int search_row(const State& st, const RowGrid& g, flo
 #else
         const float d2 = dy * dy / Sy + dz * dz / Sz;
 #endif
-        if (fabsf(dy) <= wy && fabsf(dz) <= wz && d2 <= bd2) {
-            if (d2 < bd2) {
+        const bool in = fabsf(dy) <= wy && fabsf(dz) <= wz;
+        if (in && d2 == bd2) {  // exact tie: smaller cluster id
+            const unsigned id = __float_as_uint(__ldg(&p.hits[j].z));
+            if (!have_bid) {
+                bid = __float_as_uint(__ldg(&p.hits[best].z));
+                have_bid = true;
+            }
+            if (id < bid) {
                 best = j;
-                bd2 = d2;
-                have_bid = false;
+                bid = id;
                 found = c;
-            } else {  // exact tie: smaller cluster id
-                const unsigned id = __float_as_uint(__ldg(&p.hits[j].z));
-                if (!have_bid) {
-                    bid = __float_as_uint(__ldg(&p.hits[best].z));
-                    have_bid = true;
-                }
-                if (id < bid) {
-                    best = j;
-                    bid = id;
-                    found = c;
-                }
             }
         }
+        const bool lt = in && d2 < bd2;
+        best = lt ? j : best;
+        have_bid = lt ? false : have_bid;
+        found.x = lt ? c.x : found.x;
+        found.y = lt ? c.y : found.y;
+        bd2 = lt ? d2 : bd2;
     };
-    // candidates in pairs: both loads go out before either is tested
-    for (int i0 = gl; i0 < ntot; i0 += 2 * G) {
-        const int i1 = i0 + G;
-        const int j0 = i0 < na ? ja0 + i0 : jb0 + (i0 - na);
-        const int j1 = i1 < na ? ja0 + i1 : jb0 + (i1 - na);
-        const float2 c0 = __ldg(p.hyz + j0);
-        float2 c1 = c0;
-        if (i1 < ntot) c1 = __ldg(p.hyz + j1);
-        consider(j0, c0);
-        if (i1 < ntot) consider(j1, c1);
+    // The lane's first kSearchSlots candidates of the two z rows: every load
+    // goes out first, then the tests run as straight-line code for all lanes
+    // (a slot past the lane's count holds y = +inf, outside any window).  A
+    // warp then steps its lanes' candidates together instead of looping to
+    // the count of its most crowded lane; further candidates (a crowded
+    // window) follow one at a time.  Candidate i of the two rows sits at
+    // ja0 + i, or at jb0 + (i - na) past the first row.
+    {
+        const int dj = jb0 - ja0 - na;
+        int jq[kSearchSlots];
+        float2 cq[kSearchSlots];
+#pragma unroll
+        for (int q = 0; q < kSearchSlots; q++) {
+            const int i = gl + q * G;
+            jq[q] = ja0 + i + (i >= na ? dj : 0);
+            cq[q] = i < ntot ? __ldg(p.hyz + jq[q]) : make_float2(__int_as_float(0x7f800000), 0.0f);
+        }
+#pragma unroll
+        for (int q = 0; q < kSearchSlots; q++) consider(jq[q], cq[q]);
+        for (int i = gl + kSearchSlots * G; i < ntot; i += G) {
+            const int j = ja0 + i + (i >= na ? dj : 0);
+            consider(j, __ldg(p.hyz + j));
+        }
     }
     for (int bz = bz0 + 2; bz <= bz1; bz++) {
         const int j0 = __ldg(rb + bz * ny), j1 = __ldg(rb + bz * ny + (by1 - by0) + 1);
