@@ -74,8 +74,9 @@ __global__ void k_neighbours(KConst k, const float* __restrict__ row_x, DevPtrs 
         }
         return;
     }
-    const int bo_d = p.bin_cap_off[rr - 1];
-    const int n_bins3 = p.bin_cap_off[rr + 2] - bo_d;
+    // the bin tables of rows r - 1 and r + 1 (row r's own table is not searched)
+    const int bo_d = p.bin_cap_off[rr - 1], nb_d = p.bin_cap_off[rr] - bo_d;
+    const int bo_u = p.bin_cap_off[rr + 1], nb_u = p.bin_cap_off[rr + 2] - bo_u;
 
     // the pair copy starts at an even cluster (16-byte aligned) and covers an
     // even count; it may read the pad entry after the last cluster
@@ -88,13 +89,14 @@ __global__ void k_neighbours(KConst k, const float* __restrict__ row_x, DevPtrs 
     if (tid == 0) {
         mbar_init(bar, 1);
         fence_async_smem();
-        mbar_expect_tx(bar, (unsigned)n2 * 8u + (unsigned)n_bins3 * 4u);
+        mbar_expect_tx(bar, (unsigned)n2 * 8u + (unsigned)(nb_d + nb_u) * 4u);
         bulk_g2s(pairs, p.hyz + a0, (unsigned)n2 * 8u, bar);
-        bulk_g2s(bins, p.bin_off + bo_d, (unsigned)n_bins3 * 4u, bar);
+        bulk_g2s(bins, p.bin_off + bo_d, (unsigned)nb_d * 4u, bar);
+        bulk_g2s(bins + nb_d, p.bin_off + bo_u, (unsigned)nb_u * 4u, bar);
     }
     __syncthreads();
     const RowGrid gu = p.grid[rr + 1], gd = p.grid[rr - 1];
-    const int tu = gu.bin_base - bo_d, td = gd.bin_base - bo_d;  // tables in smem
+    const int td = gd.bin_base - bo_d, tu = nb_d + (gu.bin_base - bo_u);  // tables in smem
     const int nyu = grid_ny(gu), nzu = grid_nz(gu), nyd = grid_ny(gd), nzd = grid_nz(gd);
     const float Xr = row_x[r], Xu = row_x[r + 1], Xd = row_x[r - 1];
     const float yu0 = -(Xu * k.tan_h + k.y_margin), yd0 = -(Xd * k.tan_h + k.y_margin);
@@ -120,7 +122,7 @@ __global__ void k_neighbours(KConst k, const float* __restrict__ row_x, DevPtrs 
     const unsigned gmask = G == 1 ? 0u : (((1u << G) - 1u) << ((tid & 31) - gl));
     // the groups' lists follow the bin tables (16-byte aligned; one pad
     // entry per list so that the groups of a warp use different banks)
-    float4* list = reinterpret_cast<float4*>(smem + ((16u + (unsigned)n2 * 8u + (unsigned)n_bins3 * 4u + 15u) & ~15u)) +
+    float4* list = reinterpret_cast<float4*>(smem + ((16u + (unsigned)n2 * 8u + (unsigned)(nb_d + nb_u) * 4u + 15u) & ~15u)) +
                    (tid / G) * (kNbList + 1);
     for (int i = tid / G; i < cnt_m; i += nt / G) {
         const float2 ci = recm[i];
@@ -996,12 +998,12 @@ static cudaError_t launch_nb(const KConst& k, const float* row_x_dev, const DevP
 }
 
 cudaError_t launch_neighbours(const KConst& k, const float* row_x_dev, const DevPtrs& p, int max3,
-                              int max_slots3, int threads, int lanes_per_hit, int unit0, int n_units,
+                              int max_slots_nb, int threads, int lanes_per_hit, int unit0, int n_units,
                               cudaStream_t s)
 {
     // barrier, the (y, z) pairs of three rows (an even count, one more at
-    // most at each end) and their three bin tables
-    const size_t sm = 16 + (size_t)(max3 + 2) * 8 + (size_t)max_slots3 * 4;
+    // most at each end) and the bin tables of the outer two
+    const size_t sm = 16 + (size_t)(max3 + 2) * 8 + (size_t)max_slots_nb * 4;
     const int blocks = n_units * (k.n_rows - 2);
     if (blocks == 0) return cudaSuccess;
     switch (lanes_per_hit) {

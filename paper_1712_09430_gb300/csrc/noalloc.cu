@@ -92,7 +92,7 @@ extern "C" int tpc_links_noalloc(const tpc_geometry* g, const tpc_params* params
     int* plan_off = g_plan;
     int* plan_bins = g_plan + R + 1;
     int64_t N = 0, bins = 0;
-    int max_row = 1, max3 = 1, max_slots = 4, max_slots3 = 12;
+    int max_row = 1, max3 = 1, max_slots = 4, max_slots_nb = 12;
     for (int r = 0; r < R; r++) {
         const int c = row_counts[r];
         if (c < 0 || c > TPC_MAX_ROW_CLUSTERS) return TPC_ERR_INVALID;
@@ -107,9 +107,9 @@ extern "C" int tpc_links_noalloc(const tpc_geometry* g, const tpc_params* params
         if (rr >= 1 && rr + 1 < NR) {
             const int c3 = row_counts[r - 1] + c + row_counts[r + 1];
             if (c3 > max3) max3 = c3;
-            const int s3 = row_bin_slots(row_counts[r - 1], P.bin_target) + slots +
+            const int s2 = row_bin_slots(row_counts[r - 1], P.bin_target) +
                            row_bin_slots(row_counts[r + 1], P.bin_target);
-            if (s3 > max_slots3) max_slots3 = s3;
+            if (s2 > max_slots_nb) max_slots_nb = s2;
         }
     }
     if (N > kNoallocMaxClusters) return TPC_ERR_INVALID;  // beyond the fixed scratch
@@ -205,8 +205,8 @@ extern "C" int tpc_links_noalloc(const tpc_geometry* g, const tpc_params* params
     if (e == cudaSuccess) e = tpc_int::launch_plan(k, xd, p, nsm, s);
     if (e == cudaSuccess) e = tpc_int::launch_grid(k, xd, p, max_row, max_slots, P.threads_per_row, 0, S, s);
     if (e == cudaSuccess)
-        e = P.exact_fp32 ? tpc_exact::launch_neighbours(k, xd, p, max3, max_slots3, P.threads_per_row, 1, 0, S, s)
-                         : tpc_fast::launch_neighbours(k, xd, p, max3, max_slots3, P.threads_per_row, 1, 0, S, s);
+        e = P.exact_fp32 ? tpc_exact::launch_neighbours(k, xd, p, max3, max_slots_nb, P.threads_per_row, 1, 0, S, s)
+                         : tpc_fast::launch_neighbours(k, xd, p, max3, max_slots_nb, P.threads_per_row, 1, 0, S, s);
     if (e == cudaSuccess) e = tpc_int::launch_clean(k, p, P.threads_per_row, 0, S, true, s);
     if (e == cudaSuccess) e = tpc_int::launch_dump_links(p, 1, d_links, s);
     if (e == cudaSuccess)

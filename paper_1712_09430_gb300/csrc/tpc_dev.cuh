@@ -317,7 +317,7 @@ cudaError_t preload_link_kernels();
 
 #define TPC_FP_DECLS                                                                              \
     cudaError_t launch_neighbours(const tpc::KConst& k, const float* row_x_dev,                   \
-                                  const tpc::DevPtrs& p, int max3, int max_slots3, int threads,   \
+                                  const tpc::DevPtrs& p, int max3, int max_slots_nb, int threads, \
                                   int lanes_per_hit, int unit0, int n_units, cudaStream_t s);     \
     cudaError_t launch_tracklets(const tpc::KConst& k, const float* row_x_dev,                    \
                                  const tpc::DevPtrs& p, int n_sm, int lanes_per_tracklet,         \

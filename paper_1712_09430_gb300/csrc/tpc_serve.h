@@ -14,9 +14,9 @@ struct BatchShape {
     int64_t bin_slots = 0;
     int max_row = 1, max3 = 1;
     int max_unit = 0;  // clusters of the largest (event, sector) unit
-    // bin-table slots of the largest row and of the largest three adjacent
-    // rows (shared memory of the grid and neighbour kernels)
-    int max_slots = 4, max_slots3 = 12;
+    // bin-table slots of the largest row, and of the largest pair of rows
+    // r - 1 and r + 1 (shared memory of the grid and neighbour kernels)
+    int max_slots = 4, max_slots_nb = 12;
 };
 
 struct ServeState;  // defined in serve.cu

@@ -376,7 +376,7 @@ int tpc_shape(tpc_tracker* tr, const int32_t* row_counts, int n_events, BatchSha
     const int64_t R = (int64_t)n_events * S * NR;
     if (R > (1 << 28)) return tr->fail(TPC_ERR_INVALID, "too many rows in one call");
     int64_t N = 0, bins = 0, max_unit = 0;
-    int max_row = 0, max3 = 0, max_slots = 0, max_slots3 = 0;
+    int max_row = 0, max3 = 0, max_slots = 0, max_slots_nb = 0;
     const int rc_plan = tpc_reserve_plan(tr, R);
     if (rc_plan != TPC_OK) return rc_plan;
     // the pinned plan: row counts [R], CSR offsets of rows [R + 1], bin-table
@@ -420,7 +420,7 @@ int tpc_shape(tpc_tracker* tr, const int32_t* row_counts, int n_events, BatchSha
         max_unit = std::max<int64_t>(max_unit, N - n_before);
         for (int r = 1; r + 1 < NR; r++) {
             max3 = std::max(max3, cnt[r - 1] + cnt[r] + cnt[r + 1]);
-            max_slots3 = std::max(max_slots3, lut[cnt[r - 1]] + lut[cnt[r]] + lut[cnt[r + 1]]);
+            max_slots_nb = std::max(max_slots_nb, lut[cnt[r - 1]] + lut[cnt[r + 1]]);
         }
     }
     if (N >= (int64_t)1 << 30) return tr->fail(TPC_ERR_INVALID, "more than 2^30 clusters in one call");
@@ -438,7 +438,7 @@ int tpc_shape(tpc_tracker* tr, const int32_t* row_counts, int n_events, BatchSha
     sh->max3 = std::max(max3, 1);
     sh->max_unit = (int)max_unit;
     sh->max_slots = std::max(max_slots, 4);
-    sh->max_slots3 = std::max(max_slots3, 12);
+    sh->max_slots_nb = std::max(max_slots_nb, 12);
     return TPC_OK;
 }
 
@@ -486,11 +486,11 @@ int tpc_enqueue(tpc_tracker* tr, const DevPtrs& p, const BatchShape& sh, cudaStr
     const tpc_params& P = tr->params;
     const float* xd = tr->row_x_dev;
     const bool exact = P.exact_fp32 != 0;
-    auto nb = [&](const tpc::KConst& kk, const float* x, const DevPtrs& pp, int max3, int slots3, int th,
+    auto nb = [&](const tpc::KConst& kk, const float* x, const DevPtrs& pp, int max3, int slots_nb, int th,
                   int u0, int nu, cudaStream_t ss) {
         const int lh = P.lanes_per_hit;
-        return exact ? tpc_exact::launch_neighbours(kk, x, pp, max3, slots3, th, lh, u0, nu, ss)
-                     : tpc_fast::launch_neighbours(kk, x, pp, max3, slots3, th, lh, u0, nu, ss);
+        return exact ? tpc_exact::launch_neighbours(kk, x, pp, max3, slots_nb, th, lh, u0, nu, ss)
+                     : tpc_fast::launch_neighbours(kk, x, pp, max3, slots_nb, th, lh, u0, nu, ss);
     };
     auto seeds = [&](int u0, int u1, cudaStream_t ss) {
         return exact ? tpc_exact::launch_seeds(k, xd, p, tr->n_sm, u0, u1, ss)
@@ -508,7 +508,7 @@ int tpc_enqueue(tpc_tracker* tr, const DevPtrs& p, const BatchShape& sh, cudaStr
     if (!P.plain_per_sector) {
         TPC_CUDA(tpc_int::launch_grid(k, xd, p, sh.max_row, sh.max_slots, th, 0, sh.n_units, s));
         if (with_events) TPC_CUDA(cudaEventRecord(tr->ev[1], s));
-        TPC_CUDA(nb(k, xd, p, sh.max3, sh.max_slots3, th, 0, sh.n_units, s));
+        TPC_CUDA(nb(k, xd, p, sh.max3, sh.max_slots_nb, th, 0, sh.n_units, s));
         if (with_events) TPC_CUDA(cudaEventRecord(tr->ev[2], s));
         // the per-unit ownership kernel writes every owner key itself
         TPC_CUDA(tpc_int::launch_clean(k, p, th, 0, sh.n_units, false, s));
@@ -552,7 +552,7 @@ int tpc_enqueue(tpc_tracker* tr, const DevPtrs& p, const BatchShape& sh, cudaStr
         for (int u = 0; u < sh.n_units; u++) {
             cudaStream_t q = tr->queues[(size_t)(u % nq)];
             TPC_CUDA(tpc_int::launch_grid(k, xd, p, sh.max_row, sh.max_slots, th, u, 1, q));
-            TPC_CUDA(nb(k, xd, p, sh.max3, sh.max_slots3, th, u, 1, q));
+            TPC_CUDA(nb(k, xd, p, sh.max3, sh.max_slots_nb, th, u, 1, q));
             TPC_CUDA(tpc_int::launch_clean(k, p, th, u, 1, true, q));
         }
         rc = join();
@@ -580,7 +580,7 @@ int tpc_enqueue(tpc_tracker* tr, const DevPtrs& p, const BatchShape& sh, cudaStr
         for (int u = 0; u < sh.n_units; u++)
             TPC_CUDA(tpc_int::launch_grid(k, xd, p, sh.max_row, sh.max_slots, th, u, 1, s));
         if (with_events) TPC_CUDA(cudaEventRecord(tr->ev[1], s));
-        for (int u = 0; u < sh.n_units; u++) TPC_CUDA(nb(k, xd, p, sh.max3, sh.max_slots3, th, u, 1, s));
+        for (int u = 0; u < sh.n_units; u++) TPC_CUDA(nb(k, xd, p, sh.max3, sh.max_slots_nb, th, u, 1, s));
         if (with_events) TPC_CUDA(cudaEventRecord(tr->ev[2], s));
         for (int u = 0; u < sh.n_units; u++) TPC_CUDA(tpc_int::launch_clean(k, p, th, u, 1, true, s));
         TPC_CUDA(tpc_int::launch_start_scan(k, p, s));
@@ -615,7 +615,7 @@ static std::string graph_key_of(const tpc_tracker* tr, const BatchShape& sh, con
     // kernel variant) is derived from
     char b[320];
     std::snprintf(b, sizeof b, "%d/%d/%d/%d/%d/%d/%d/%d/%p/%p/%d/%d/%d/%d/%d/%g/%d/%d", sh.N, sh.R,
-                  sh.n_units, sh.max_row, sh.max3, sh.max_unit, sh.max_slots, sh.max_slots3,
+                  sh.n_units, sh.max_row, sh.max3, sh.max_unit, sh.max_slots, sh.max_slots_nb,
                   (const void*)p.clusters, (const void*)p.counters,
                   tr->params.exact_fp32, tr->params.threads_per_row, tr->params.tracklets_per_warp,
                   tr->params.plain_per_sector, tr->params.schedule, (double)tr->params.bin_target,
