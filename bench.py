@@ -1056,8 +1056,9 @@ def main():
                          "holds all its requests until its last kernel)")
     ap.add_argument("--stream-arena-gb", type=int, default=16)
     ap.add_argument("--stream-inflight", type=int, default=2, help="serving batches in flight")
-    ap.add_argument("--stream-batch-clusters", type=int, default=1 << 22,
-                    help="most clusters in one serving batch (the library's default: 2^22)")
+    ap.add_argument("--stream-batch-clusters", type=int, default=1 << 23,
+                    help="most clusters in one serving batch (2^23: four central events; the "
+                         "library's default is 2^22)")
     ap.add_argument("--stream-min-batch-clusters", type=int, default=1 << 20,
                     help="serving: while a batch runs, form the next once this many clusters are "
                          "pending (0: whenever a slot is free)")
