@@ -941,7 +941,9 @@ def run_e2e_stream(tr0, cl_np, rc_np, B, N, world, args):
                 take(q.popleft())
         run(3)
         torch.cuda.synchronize()
-        k2 = max(3, args.steps // 2)
+        # the pipeline fills and drains once per timed run: enough steps that
+        # this costs little
+        k2 = max(20, args.steps)
         t1 = time.perf_counter()
         run(k2)
         e2e_s = (time.perf_counter() - t1) / k2
@@ -1056,9 +1058,8 @@ def main():
                          "holds all its requests until its last kernel)")
     ap.add_argument("--stream-arena-gb", type=int, default=16)
     ap.add_argument("--stream-inflight", type=int, default=2, help="serving batches in flight")
-    ap.add_argument("--stream-batch-clusters", type=int, default=1 << 23,
-                    help="most clusters in one serving batch (2^23: four central events; the "
-                         "library's default is 2^22)")
+    ap.add_argument("--stream-batch-clusters", type=int, default=1 << 22,
+                    help="most clusters in one serving batch (the library's default: 2^22)")
     ap.add_argument("--stream-min-batch-clusters", type=int, default=1 << 20,
                     help="serving: while a batch runs, form the next once this many clusters are "
                          "pending (0: whenever a slot is free)")
