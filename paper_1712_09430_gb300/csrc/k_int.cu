@@ -454,7 +454,7 @@ __global__ void k_owner(KConst k, DevPtrs p, int u0, int u1)
 // tracklets without clusters in the chunk are skipped; the cluster lists of
 // the remaining ones are read kOwnerTracklets at a time, with all their loads
 // in flight together.
-constexpr int kOwnerChunk = 56 * 1024;  // 224 KB of keys
+constexpr int kOwnerChunk = 56 * 1024;  // keys of one chunk at most (224 KB)
 constexpr int kListLoads = 5;           // loads per lane per pass: 160 list entries
 constexpr int kOwnerTracklets = 4;      // tracklets whose lists are read together
 constexpr int kEmitTracklets = 4;       // accepted tracklets written together
@@ -870,13 +870,20 @@ cudaError_t launch_select(const KConst& k, const DevPtrs& p, int n_sm, int u0, i
 }
 
 // Ownership with owned counts (the per-unit kernel counts them as well).
-cudaError_t launch_owner_units(const KConst& k, const DevPtrs& p, int n_units, int max_unit,
+cudaError_t launch_owner_units(const KConst& k, const DevPtrs& p, int n_units, int max_unit, int n_sm,
                                cudaStream_t s, bool* counted)
 {
     *counted = true;
     if (n_units == 0 || max_unit == 0) return cudaSuccess;
-    const int chunks = (max_unit + kOwnerChunk - 1) / kOwnerChunk;
-    const int cap_keys = std::min(max_unit, kOwnerChunk);
+    // a unit larger than kOwnerChunk keys is split into chunks; large units
+    // in a batch of fewer units than half the SMs (one central event) are
+    // split into three at least, so that more SMs take part.  The shared
+    // memory holds the largest chunk only: what it leaves of the SM's 256 KB
+    // serves as L1 for the list reads (224 KB of keys for chunks of 33 K
+    // cost 10 %).
+    int chunks = (max_unit + kOwnerChunk - 1) / kOwnerChunk;
+    if (2 * n_units < n_sm && max_unit > kOwnerChunk / 2) chunks = std::max(chunks, 3);
+    const int cap_keys = (max_unit + chunks - 1) / chunks;
     const size_t sm = (size_t)cap_keys * 4;
     cudaError_t e = cudaFuncSetAttribute(k_owner_units, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;

@@ -301,7 +301,7 @@ cudaError_t launch_start_write(const tpc::KConst& k, const tpc::DevPtrs& p, int 
 cudaError_t launch_select(const tpc::KConst& k, const tpc::DevPtrs& p, int n_sm, int u0, int u1, bool owner,
                           cudaStream_t s, bool counted = false);
 cudaError_t launch_owner_units(const tpc::KConst& k, const tpc::DevPtrs& p, int n_units, int max_unit,
-                               cudaStream_t s, bool* counted);
+                               int n_sm, cudaStream_t s, bool* counted);
 cudaError_t launch_rebase(const tpc::KConst& k, const tpc::DevPtrs& p, int n_sm, cudaStream_t s);
 cudaError_t launch_emit(const tpc::KConst& k, const tpc::DevPtrs& p, int n_sm, cudaStream_t s);
 cudaError_t launch_dump_links(const tpc::DevPtrs& p, int cleaned, int* dst, cudaStream_t s);

@@ -519,7 +519,7 @@ int tpc_enqueue(tpc_tracker* tr, const DevPtrs& p, const BatchShape& sh, cudaStr
         TPC_CUDA(tl(-1, -1));
         if (with_events) TPC_CUDA(cudaEventRecord(tr->ev[4], s));
         bool counted = false;
-        TPC_CUDA(tpc_int::launch_owner_units(k, p, sh.n_units, sh.max_unit, s, &counted));
+        TPC_CUDA(tpc_int::launch_owner_units(k, p, sh.n_units, sh.max_unit, tr->n_sm, s, &counted));
         TPC_CUDA(tpc_int::launch_select(k, p, tr->n_sm, 0, sh.n_units, false, s, counted));
     } else if (P.plain_per_sector == 2) {
         // Multi-queue scheme (Sec. 3.1, Fig. 3): each unit's stages in order
