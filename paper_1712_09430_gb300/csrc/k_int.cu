@@ -220,6 +220,8 @@ __global__ void k_grid(KConst k, const float* __restrict__ row_x, DevPtrs p, int
         bulk_commit();
     }
     for (int i = tid; i < cnt; i += nt) p.hyz[off + i] = make_float2(out[i].x, out[i].y);
+    if (p.hpos)  // the link-only path has no emit pass
+        for (int i = tid; i < cnt; i += nt) p.hpos[off + i] = __float_as_int(out[i].w);
     if (tid == 0) bulk_wait_all();
 }
 
@@ -695,7 +697,7 @@ __global__ void k_emit(KConst k, DevPtrs p)
                 for (int v = 0; v < kEmitTracklets; v++)
 #pragma unroll
                     for (int i = 0; i < kListLoads; i++)
-                        id[v][i] = own[v][i] ? __float_as_int(p.hits[b[v][i]].w) : 0;
+                        id[v][i] = own[v][i] ? p.hpos[b[v][i]] : 0;
 #pragma unroll
                 for (int v = 0; v < kEmitTracklets; v++)
 #pragma unroll

@@ -83,6 +83,7 @@ struct DevPtrs {
     RowGrid* grid;             // [R]
     float4* hits;              // [N] binned: (y, z, id bits, input position bits)
     float2* hyz;               // [N + 2] binned (y, z): what the window scans read (+ pad)
+    int* hpos;                 // [N] binned: input position, gathered by the emit pass (nullptr: no emit)
     int* bin_off;              // bin tables: absolute binned offsets
     int* up;                   // [N] binned space, before cleaning
     int* dn;

@@ -285,6 +285,7 @@ size_t tpc_layout(const tpc_tracker* tr, const BatchShape& sh, DevPtrs* p, char*
     q.grid = reinterpret_cast<RowGrid*>(take(R * sizeof(RowGrid)));
     q.hits = reinterpret_cast<float4*>(take(N * 16));
     q.hyz = reinterpret_cast<float2*>(take((N + 2) * 8));  // + a pad entry read by whole-pair copies
+    q.hpos = reinterpret_cast<int*>(take(N * 4));
     q.bin_off = reinterpret_cast<int*>(take((size_t)sh.bin_slots * 4));
     q.up = reinterpret_cast<int*>(take(N * 4));
     q.dn = reinterpret_cast<int*>(take(N * 4));
