@@ -877,14 +877,16 @@ cudaError_t launch_owner_units(const KConst& k, const DevPtrs& p, int n_units, i
 {
     *counted = true;
     if (n_units == 0 || max_unit == 0) return cudaSuccess;
-    // a unit larger than kOwnerChunk keys is split into chunks; large units
-    // in a batch of fewer units than half the SMs (one central event) are
-    // split into three at least, so that more SMs take part.  The shared
-    // memory holds the largest chunk only: what it leaves of the SM's 256 KB
-    // serves as L1 for the list reads (224 KB of keys for chunks of 33 K
-    // cost 10 %).
+    // a unit larger than kOwnerChunk keys is split into chunks; when the
+    // chunks of large units would leave more than half the SMs idle (one
+    // central event: 36 units), they are split further, so that more SMs
+    // take part (more chunks than that cost list re-reads).  The shared
+    // memory holds the largest chunk only: what it leaves of the SM's
+    // 256 KB serves as L1 for the list reads (224 KB of keys for chunks of
+    // 33 K cost 10 %).
     int chunks = (max_unit + kOwnerChunk - 1) / kOwnerChunk;
-    if (2 * n_units < n_sm && max_unit > kOwnerChunk / 2) chunks = std::max(chunks, 3);
+    if (max_unit > kOwnerChunk / 2 && 2 * n_units * chunks < n_sm)
+        chunks = (n_sm + 2 * n_units - 1) / (2 * n_units);
     const int cap_keys = (max_unit + chunks - 1) / chunks;
     const size_t sm = (size_t)cap_keys * 4;
     cudaError_t e = cudaFuncSetAttribute(k_owner_units, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
