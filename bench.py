@@ -415,15 +415,15 @@ def run_ours(args):
         # the headline: the hot path's per-cluster byte model of the stage
         # (every stage reads its inputs and writes its outputs once: 55 B per
         # input cluster for tracklet construction) x the clusters of a launch
-        survey = TRACKLET_SURVEY_BYTES_PER_CLUSTER * N
-        achieved = survey / t_s / 1e9
+        model_bytes = TRACKLET_MODEL_BYTES_PER_CLUSTER * N
+        achieved = model_bytes / t_s / 1e9
         traffic = None
         if B == 8 and not args.exact:
             traffic = measured_traffic(TRACKLET_SOURCES, TRACKLET_TRAFFIC_SUMMARY)
         rl = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
               "frac": achieved / hbm, "traffic": traffic, "kernel": TRACKLET_KERNEL,
-              "algorithmic_bytes_per_launch": survey,
-              "model": f"{TRACKLET_SURVEY_BYTES_PER_CLUSTER} B per input cluster x {N} clusters",
+              "algorithmic_bytes_per_launch": model_bytes,
+              "model": f"{TRACKLET_MODEL_BYTES_PER_CLUSTER} B per input cluster x {N} clusters",
               # the kernel's own count of what it reads and writes (row steps,
               # bin-table rows, candidates), from one untimed counting call
               "frac_counted": algo["bytes"] / t_s / 1e9 / hbm,
@@ -431,7 +431,7 @@ def run_ours(args):
               # DRAM bytes of one launch (ncu) over the same time
               "frac_dram": (traffic / t_s / 1e9 / hbm) if traffic else None,
               # the whole step against the model's 220 B per cluster
-              "frac_step": STEP_SURVEY_BYTES_PER_CLUSTER * N / (ms * 1e-3) / 1e9 / hbm,
+              "frac_step": STEP_MODEL_BYTES_PER_CLUSTER * N / (ms * 1e-3) / 1e9 / hbm,
               "counts": {k: v for k, v in algo.items() if k not in ("bytes", "model")},
               "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy) of measured" if peaks else "fallback"}
     cpu = None if args.no_cpu_baseline else cpu_baseline(args.cpu_seconds)
@@ -987,8 +987,8 @@ def measured_traffic(kernel_sources, summary):
 # outputs once: tracklet construction about 55 B per input cluster (about 2
 # row steps per cluster x (8 B bin entry + 16 B candidate + 4 B hit id)); the
 # whole step about 220 B per cluster.
-TRACKLET_SURVEY_BYTES_PER_CLUSTER = 55
-STEP_SURVEY_BYTES_PER_CLUSTER = 220
+TRACKLET_MODEL_BYTES_PER_CLUSTER = 55
+STEP_MODEL_BYTES_PER_CLUSTER = 220
 TRACKLET_KERNEL = "k_tracklets_sched"
 TRACKLET_SOURCES = [os.path.join(ROOT, "paper_1712_09430_gb300", "csrc", f) for f in ("k_fp.cu", "tpc_dev.cuh")]
 TRACKLET_TRAFFIC_SUMMARY = os.path.join(ROOT, "profiles", "k_tracklets_sched_traffic_central8.md")
