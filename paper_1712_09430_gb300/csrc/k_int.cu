@@ -886,7 +886,7 @@ cudaError_t launch_owner_units(const KConst& k, const DevPtrs& p, int n_units, i
     // 33 K cost 10 %).
     int chunks = (max_unit + kOwnerChunk - 1) / kOwnerChunk;
     if (max_unit > kOwnerChunk / 2 && 2 * n_units * chunks < n_sm)
-        chunks = (n_sm + 2 * n_units - 1) / (2 * n_units);
+        chunks = std::max(chunks, std::min(4, (n_sm + 2 * n_units - 1) / (2 * n_units)));
     const int cap_keys = (max_unit + chunks - 1) / chunks;
     const size_t sm = (size_t)cap_keys * 4;
     cudaError_t e = cudaFuncSetAttribute(k_owner_units, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
