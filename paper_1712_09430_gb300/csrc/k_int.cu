@@ -449,8 +449,9 @@ __global__ void k_owner(KConst k, DevPtrs p, int u0, int u1)
 // applies atomicMax in shared memory to the clusters of its chunk, then
 // writes the chunk's keys out coalesced.  Ownership never crosses units, so
 // the keys need no global atomics (the owned counts use one global add per
-// owned cluster).  The chunks of a unit hold equal shares of
-// its clusters (one chunk whenever the unit fits).  A warp takes 32
+// owned cluster).  The chunks of a unit hold equal shares of its clusters
+// (one chunk whenever the unit fits, unless the batch has too few units to
+// occupy the SMs: see launch_owner_units).  A warp takes 32
 // tracklets at a time: their lengths (and, with several chunks, their
 // outermost and innermost clusters) are read one per lane, so that
 // tracklets without clusters in the chunk are skipped; the cluster lists of
