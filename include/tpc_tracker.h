@@ -430,6 +430,12 @@ typedef struct {
     double host_launch_ms;   /* host time spent forming and enqueueing batches  */
     double host_finish_ms;   /* host time spent slicing finished batches        */
     double host_copy_ms;     /* host time spent copying results in polls        */
+    double max_launch_ms;    /* longest host time forming and enqueueing one
+                                batch                                           */
+    double max_submit_ms;    /* longest single tpc_stream_submit call, without
+                                the first call's set-up of the arena and staging
+                                (a submit never waits for the device, so a long
+                                one points at the host: this library or the OS) */
 } tpc_stream_stats;
 
 /* Fill *stats (caller-owned); zeros before tpc_stream_configure. */

@@ -98,7 +98,8 @@ class tpc_stream_stats(C.Structure):
     _fields_ = [("batches", C.c_int64), ("events", C.c_int64), ("clusters", C.c_int64),
                 ("refetches", C.c_int64), ("max_batch_events", C.c_int64), ("gpu_ms", C.c_double),
                 ("host_launch_ms", C.c_double), ("host_finish_ms", C.c_double),
-                ("host_copy_ms", C.c_double)]
+                ("host_copy_ms", C.c_double), ("max_launch_ms", C.c_double),
+                ("max_submit_ms", C.c_double)]
 
 
 class tpc_stream_view(C.Structure):

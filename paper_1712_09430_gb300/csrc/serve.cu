@@ -243,7 +243,9 @@ static int launch_batch(tpc_tracker* tr)
 {
     const auto t0 = std::chrono::steady_clock::now();
     const int rc = launch_batch_impl(tr);
-    tr->serve->stats.host_launch_ms += ms_since(t0);
+    const double ms = ms_since(t0);
+    tr->serve->stats.host_launch_ms += ms;
+    tr->serve->stats.max_launch_ms = std::max(tr->serve->stats.max_launch_ms, ms);
     return rc;
 }
 
@@ -599,6 +601,17 @@ extern "C" int tpc_stream_set_batching(tpc_tracker* tr, int64_t min_batch_cluste
     return TPC_OK;
 }
 
+// The longest tpc_stream_submit call after serving was set up, kept in the
+// stats on every return.
+struct SubmitTimer {
+    tpc_tracker* tr;
+    std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+    ~SubmitTimer()
+    {
+        if (tr && tr->serve) tr->serve->stats.max_submit_ms = std::max(tr->serve->stats.max_submit_ms, ms_since(t0));
+    }
+};
+
 extern "C" int tpc_stream_submit(tpc_tracker* tr, const tpc_cluster* clusters, const int32_t* row_counts,
                                  int n_events, uint64_t tag, uint64_t* ticket)
 {
@@ -606,8 +619,9 @@ extern "C" int tpc_stream_submit(tpc_tracker* tr, const tpc_cluster* clusters, c
     if (!row_counts || !ticket || n_events < 1) return tr->fail(TPC_ERR_INVALID, "NULL argument or n_events < 1");
     if (cudaSetDevice(tr->dev) != cudaSuccess) return tr->fail(TPC_ERR_DEVICE, "cudaSetDevice");
     if (!tr->serve) tr->serve = new ServeState();
-    int rc = serve_init(tr);
+    int rc = serve_init(tr);  // the first submit allocates the arena and staging
     if (rc != TPC_OK) return rc;
+    const SubmitTimer timer{tr};  // from here: the submit itself
     ServeState* S = tr->serve;
     rc = progress(tr);
     if (rc != TPC_OK) return rc;

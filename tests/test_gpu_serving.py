@@ -253,6 +253,9 @@ def test_batches_respect_the_cluster_limit(cap):
         assert st["batches"] == 4 and st["max_batch_events"] == 1
     else:  # the three queued behind the first run together (unless it ended first)
         assert st["batches"] < 4 and st["max_batch_events"] >= 2
+    # the longest single launch and submit are kept beside the sums
+    assert 0 < st["max_launch_ms"] <= st["host_launch_ms"]
+    assert st["max_submit_ms"] > 0
 
 
 def test_cluster_limit_is_validated():
