@@ -35,3 +35,28 @@ def test_mirrored_event_gives_mirrored_tracks(make, mode):
     want = o["tl_f"].copy()
     want[:, ODD] = -want[:, ODD]
     np.testing.assert_array_equal(o2["tl_f"], want)
+
+
+@pytest.mark.parametrize("mode", ["f64", "f32"])
+def test_refit_of_the_mirrored_event_is_mirrored(mode):
+    """The final refit (full 5x5 covariance, a field polynomial in z and
+    rho^2, both even in y) of the mirrored event's tracks: x, z, tan(lambda),
+    chi2, ndf and status unchanged, y, sin(phi) and q/pT negated, and each
+    covariance entry negated exactly when it pairs one of those three with z
+    or tan(lambda), bit for bit."""
+    ev = S.central_event(seed=5, scale=0.2)
+    field = (1e-5, -2e-8, 3e-7, 1e-9, -1e-11)
+    o = oracle.run(ev.clusters, ev.row_counts, 1, ev.bz, XR, mode=mode)
+    cl = ev.clusters.copy()
+    cl[:, 1] = -cl[:, 1]
+    o2 = oracle.run(cl, ev.row_counts, 1, ev.bz, XR, mode=mode)
+    f1 = oracle.refit_tracks(o, ev.clusters, ev.bz, field=field, mode=mode)
+    f2 = oracle.refit_tracks(o2, cl, ev.bz, field=field, mode=mode)
+    assert len(f1) > 1000 and np.all(f1[:, 23] == f2[:, 23])
+    odd = np.array([True, False, True, False, True])  # y z sin(phi) tan(lambda) q/pT
+    sign = np.ones(oracle.N_FIT)
+    sign[1:6] = np.where(odd, -1.0, 1.0)
+    for i in range(5):
+        for j in range(i + 1):
+            sign[6 + i * (i + 1) // 2 + j] = -1.0 if odd[i] != odd[j] else 1.0
+    np.testing.assert_array_equal(f2, f1 * sign)
