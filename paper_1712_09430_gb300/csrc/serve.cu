@@ -601,6 +601,7 @@ extern "C" int tpc_stream_set_batching(tpc_tracker* tr, int64_t min_batch_cluste
     return TPC_OK;
 }
 
+namespace {
 // The longest tpc_stream_submit call after serving was set up, kept in the
 // stats on every return.
 struct SubmitTimer {
@@ -611,6 +612,7 @@ struct SubmitTimer {
         if (tr && tr->serve) tr->serve->stats.max_submit_ms = std::max(tr->serve->stats.max_submit_ms, ms_since(t0));
     }
 };
+}  // namespace
 
 extern "C" int tpc_stream_submit(tpc_tracker* tr, const tpc_cluster* clusters, const int32_t* row_counts,
                                  int n_events, uint64_t tag, uint64_t* ticket)
